@@ -1,0 +1,388 @@
+"""Benchmark: matrix-free K_theta . V forward + backward throughput (GPair/s) on the
+N = 65,536, d = 8, ARD, m = 16 workload, plus the leapfrog step rate.
+
+One step = kmv_forward (Y = A V) + kmv_backward (dL/dtheta, dL/dV) over the
+whole workload: 2 N^2 kernel entries ("pairs").  Inputs are resident in HBM
+before the timed region; L2 (129 MB on GB300) is flushed between steps by a
+256 MiB write because the inputs (10 MB) would otherwise stay cached.
+Timing is device-side (CUDA events on the launching stream), W warm-up steps
+first, K timed steps, max over ranks.  N > 1 runs independent replicas of the
+workload (weak scaling; no data-path collective).
+
+--impl reference times the FP64 oracle on the host cores instead (a bounded
+row sample per step, scaled to pairs) and prints the same line with
+"impl": "reference".
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "GPair/s for K_θ·V fwd+bwd (% roofline); HMC leapfrog steps/s vs plain FP32 at stated err"
+WORKLOAD = "kmv fwd+bwd, N=65536 points x~N(0,I) in d=8, ARD SE (10 hyperparameters), m=16 vectors V,G~N(0,I)"
+# Per-pair work of each kernel form, used for the issue-rate roofline:
+#   bf16_hilo : one MUFU ex2 per pair and pass -> roof = MUFU rate
+#   fp32      : FMA-pipe ops per pair (fwd 2d + m, bwd 4d + 2m + 2) -> roof = FMA rate / ops
+SM_COUNT = 152
+FMA_LANES = 128        # FP32 FMA lanes per SM per clock
+MUFU_EX2_LANES = 32    # ex2 per SM per clock on GB300 (measured by the microbenchmark in the design doc)
+DRAM_TRAFFIC = {}      # kernel form -> dram bytes per launch from ncu (see profiles/); empty = null
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+class Clocks:
+    """Samples the SM clock and clock-event reasons every few ms during the timed
+    region, through NVML (read-only queries) or, if NVML is unavailable, nvidia-smi."""
+
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
+               0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown"}
+
+    def __init__(self, torch_device_index):
+        self.idx = torch_device_index
+        self.samples, self.reasons, self.max_mhz, self.source = [], set(), None, None
+
+    def _nvml(self):
+        import ctypes
+        nv = ctypes.CDLL("libnvidia-ml.so.1")
+        if nv.nvmlInit_v2() != 0:
+            raise RuntimeError("nvmlInit failed")
+        dev = ctypes.c_void_p()
+        ok = False
+        try:
+            import torch
+            p = torch.cuda.get_device_properties(self.idx)
+            bus = "%08X:%02X:%02X.0" % (p.pci_domain_id, p.pci_bus_id, p.pci_device_id)
+            ok = nv.nvmlDeviceGetHandleByPciBusId_v2(bus.encode(), ctypes.byref(dev)) == 0
+        except Exception:
+            ok = False
+        if not ok and nv.nvmlDeviceGetHandleByIndex_v2(self.idx, ctypes.byref(dev)) != 0:
+            raise RuntimeError("no NVML handle")
+        return nv, dev
+
+    def __enter__(self):
+        import threading
+        self.stop = threading.Event()
+        try:
+            import ctypes
+            nv, dev = self._nvml()
+            mx = ctypes.c_uint()
+            if nv.nvmlDeviceGetMaxClockInfo(dev, 1, ctypes.byref(mx)) == 0:
+                self.max_mhz = float(mx.value)
+            get_reasons = getattr(nv, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+                nv.nvmlDeviceGetCurrentClocksThrottleReasons
+
+            def loop():
+                c = ctypes.c_uint()
+                r = ctypes.c_ulonglong()
+                while not self.stop.is_set():
+                    if nv.nvmlDeviceGetClockInfo(dev, 1, ctypes.byref(c)) == 0:
+                        self.samples.append(float(c.value))
+                    if get_reasons(dev, ctypes.byref(r)) == 0:
+                        for bit, name in self.REASONS.items():
+                            if r.value & bit:
+                                self.reasons.add(name)
+                    time.sleep(0.004)
+            self.source = "nvml"
+        except Exception:
+            def loop():
+                while not self.stop.is_set():
+                    try:
+                        out = subprocess.run(["nvidia-smi", "-i", str(self.idx), "--query-gpu=clocks.sm,clocks.max.sm,"
+                                              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                                              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+                                              "--format=csv,noheader,nounits"], capture_output=True, text=True,
+                                             timeout=5).stdout
+                        f = [x.strip() for x in out.split(",")]
+                        self.samples.append(float(f[0]))
+                        self.max_mhz = float(f[1])
+                        for n, v in zip(["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown",
+                                         "sw_power_cap"], f[2:6]):
+                            if v.lower().startswith("active"):
+                                self.reasons.add(n)
+                    except Exception:
+                        return
+            self.source = "nvidia-smi"
+        self.thread = threading.Thread(target=loop, daemon=True)
+        self.thread.start()
+        time.sleep(0.01)
+        return self
+
+    def __exit__(self, *a):
+        self.stop.set()
+        self.thread.join(timeout=10)
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": self.max_mhz, "reasons": ["unsampled"], "samples": 0,
+                    "source": self.source}
+        return {"sm_mhz": float(np.median(self.samples)), "sm_max_mhz": self.max_mhz,
+                "reasons": sorted(self.reasons), "samples": len(self.samples), "source": self.source}
+
+
+def cpu_oracle_rate(rows_per_step: int, steps: int, seed: int = 0):
+    """FP64 oracle fwd + bwd on a row sample of the same workload; returns (GPair/s, seconds, cores)."""
+    import workloads as wl
+    from oracle import se_kernel as sk
+    w = wl.c2(seed=seed)
+    rng = np.random.default_rng(1)
+    t_total, pairs = 0.0, 0
+    for _ in range(steps):
+        rows = np.sort(rng.choice(w.n_total, rows_per_step, replace=False))
+        G = np.zeros_like(w.G[0])
+        G[rows] = w.G[0][rows]
+        t0 = time.perf_counter()
+        sk.kmv(w.X, w.theta[0], w.V[0], True, rows=rows)
+        sk.kmv_adjoint(w.X, w.theta[0], w.V[0], G, True, rows=rows)
+        t_total += time.perf_counter() - t0
+        pairs += 2 * rows_per_step * w.n_total
+    return pairs / t_total / 1e9, t_total, len(os.sched_getaffinity(0))
+
+
+def roof_pairs_per_s(prec, d, m, clock_mhz, which):
+    f = clock_mhz * 1e6
+    if prec == "bf16_hilo":
+        return SM_COUNT * MUFU_EX2_LANES * f, "MUFU ex2 issue, 1 exp per pair"
+    ops = 2 * d + m if which == "fwd" else 4 * d + 2 * m + 2
+    return SM_COUNT * FMA_LANES * f / ops, f"FP32 FMA-pipe issue, {ops} ops per pair"
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    rows = 64
+    for _ in range(args.warmup):
+        cpu_oracle_rate(rows, 1)
+    rate, secs, cores = cpu_oracle_rate(rows, args.steps)
+    line = {"impl": "reference", "metric": METRIC, "value": rate, "unit": "GPair/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "N": 65536, "d": 8, "m": 16, "ard": True},
+            "cpu_baseline": {"value": rate, "unit": "GPair/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{rows} random rows x 65536 columns, fwd + bwd (sampled-row adjoint) per step"},
+            "e2e": {"value": rate, "unit": "GPair/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--prec", default="auto", choices=["auto", "fp32", "bf16_hilo"])
+    ap.add_argument("--cpu-rows", type=int, default=512, help="rows of the oracle sample for cpu_baseline")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-leapfrog", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+    import workloads as wl
+    from paper_2412_20884_gb300 import Kmv, Points, KmvError
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    h = Kmv(local)
+
+    w = wl.c2(seed=rank)
+    pts = Points(torch.tensor(w.X, dtype=torch.float32, device=dev), w.offsets, ard=True)
+    theta = torch.tensor(w.theta, dtype=torch.float64, device=dev)
+    V = torch.tensor(w.V, dtype=torch.float32, device=dev)
+    G = torch.tensor(w.G, dtype=torch.float32, device=dev)
+    Y = torch.empty_like(V)
+    gth = torch.empty_like(theta)
+    gV = torch.empty_like(V)
+
+    prec = args.prec
+    if prec == "auto":
+        prec = "bf16_hilo"
+        try:
+            h.kmv_forward(pts, theta, V, Y=Y, prec=prec)
+        except KmvError:
+            prec = "fp32"
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    n = w.n_total
+    pairs = 2 * n * n
+
+    def step():
+        h.kmv_forward(pts, theta, V, Y=Y, prec=prec)
+        h.kmv_backward(pts, theta, V, G, grad_theta=gth, grad_V=gV, prec=prec)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with Clocks(local) as clk:
+        t_wall0 = time.perf_counter()
+        for k in range(args.steps):
+            flush.zero_()
+            ev[k][0].record(stream)
+            h.kmv_forward(pts, theta, V, Y=Y, prec=prec)
+            ev[k][1].record(stream)
+            h.kmv_backward(pts, theta, V, G, grad_theta=gth, grad_V=gV, prec=prec)
+            ev[k][2].record(stream)
+        torch.cuda.synchronize()
+        t_wall = time.perf_counter() - t_wall0
+    if world > 1:
+        dist.barrier()
+    t_f = [ev[k][0].elapsed_time(ev[k][1]) for k in range(args.steps)]
+    t_b = [ev[k][1].elapsed_time(ev[k][2]) for k in range(args.steps)]
+    ms = (sum(t_f) + sum(t_b)) / args.steps
+    ms_t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+    ms_max = float(ms_t.item())
+    value = world * pairs / (ms_max * 1e-3) / 1e9
+    launches_per_step = 3   # forward, backward, gradient finalisation
+
+    # end to end through the public API: host inputs (pinned) -> device -> host results
+    hX = torch.tensor(w.X, dtype=torch.float32).pin_memory()
+    hth = torch.tensor(w.theta, dtype=torch.float64).pin_memory()
+    hV = torch.tensor(w.V, dtype=torch.float32).pin_memory()
+    hG = torch.tensor(w.G, dtype=torch.float32).pin_memory()
+    oY = torch.empty(V.shape, dtype=torch.float32).pin_memory()
+    og = torch.empty(theta.shape, dtype=torch.float64).pin_memory()
+    ogV = torch.empty(V.shape, dtype=torch.float32).pin_memory()
+    dX = torch.empty_like(pts.x)
+    pts_e = Points(dX, w.offsets, ard=True)
+    dth, dV, dG = torch.empty_like(theta), torch.empty_like(V), torch.empty_like(G)
+    h2d = sum(t.numel() * t.element_size() for t in (hX, hth, hV, hG))
+    d2h = sum(t.numel() * t.element_size() for t in (oY, og, ogV))
+    e2e_ms = []
+    for k in range(args.steps + 2):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        dX.copy_(hX, non_blocking=True)
+        dth.copy_(hth, non_blocking=True)
+        dV.copy_(hV, non_blocking=True)
+        dG.copy_(hG, non_blocking=True)
+        h.kmv_forward(pts_e, dth, dV, Y=Y, prec=prec)
+        h.kmv_backward(pts_e, dth, dV, dG, grad_theta=gth, grad_V=gV, prec=prec)
+        oY.copy_(Y, non_blocking=True)
+        og.copy_(gth, non_blocking=True)
+        ogV.copy_(gV, non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if k >= 2:
+            e2e_ms.append(e0.elapsed_time(e1))
+    e2e_t = torch.tensor([float(np.mean(e2e_ms))], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
+    e2e_value = world * pairs / (float(e2e_t.item()) * 1e-3) / 1e9
+
+    out = None
+    if rank == 0:
+        pk = peaks()
+        clock = pk.get("sm_max_mhz", 2070.0)
+        mf, mb = float(np.mean(t_f)), float(np.mean(t_b))
+        which = "bwd" if mb >= mf else "fwd"
+        dur = max(mf, mb) * 1e-3
+        achieved = n * n / dur / 1e9
+        peak, basis = roof_pairs_per_s(prec, w.d, w.m, clock, which)
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak / 1e9, "unit": "GPair/s",
+                "frac": achieved * 1e9 / peak, "traffic": DRAM_TRAFFIC.get((prec, which)),
+                "kernel": f"kmv_{which} ({prec})", "basis": f"{basis} at {clock:.0f} MHz x {SM_COUNT} SMs"}
+        rf, _ = roof_pairs_per_s(prec, w.d, w.m, clock, "fwd")
+        rb, _ = roof_pairs_per_s(prec, w.d, w.m, clock, "bwd")
+        both_roof_ms = 1e3 * (n * n / rf + n * n / rb)
+        out = {"metric": METRIC, "value": value, "unit": "GPair/s", "n_gpus": world, "steps": args.steps,
+               "warmup": max(3, args.warmup), "ms_per_step": ms_max, "higher_is_better": True,
+               "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec == "fp32" else "bf16",
+               "data": "synthetic",
+               "config": {"workload": WORKLOAD, "N": n, "d": w.d, "m": w.m, "ard": True, "chains": 1,
+                          "precision": prec, "l2": "flushed between steps (256 MiB write)",
+                          "parallelism": f"replicas x{world}"},
+               "fwd_ms": mf, "bwd_ms": mb, "roof_frac_fwd_bwd": both_roof_ms / ms_max,
+               "roofline": roof,
+               "e2e": {"value": e2e_value, "unit": "GPair/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+               "gpu_launches": launches_per_step * args.steps,
+               "clocks": clk.summary(), "wall_s_timed": t_wall}
+
+    # leapfrog steps/s (fp32 vs bf16_hilo) on the N = 2048, d = 1 workload
+    if not args.no_leapfrog:
+        lf = leapfrog_rates(h, dev, rank, world)
+        if out is not None:
+            out["leapfrog"] = lf
+
+    if rank == 0 and not args.no_cpu and world == 1:
+        rate, secs, cores = cpu_oracle_rate(args.cpu_rows, 1)
+        out["cpu_baseline"] = {"value": rate, "unit": "GPair/s", "cores": cores, "kind": "oracle",
+                               "sample": f"{args.cpu_rows} random rows x 65536 columns, fwd + bwd, {secs:.1f} s"}
+    if out is not None:
+        print(json.dumps(out))
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    h.close()
+    return 0
+
+
+def leapfrog_rates(h, dev, rank, world):
+    """Leapfrog steps per second for the N = 2048, d = 1 isotropic workload (theta at
+    alpha = 1, l = 0.2, sigma^2 = 0.01, step 0.05), each form timed on 10 steps;
+    the force and the final energy are compared with the FP32 form."""
+    import torch
+    import workloads as wl
+    from paper_2412_20884_gb300 import Points, KmvError
+    w = wl.c1(seed=rank)
+    pts = Points(torch.tensor(w.X, dtype=torch.float32, device=dev), w.offsets, ard=False)
+    y = torch.tensor(w.y, dtype=torch.float32, device=dev)
+    phi = torch.tensor(np.random.default_rng(5).standard_normal((1, w.n_total)), dtype=torch.float32, device=dev)
+    res = {"workload": "N=2048 d=1 iso SE, alpha=1 l=0.2 sigma2=0.01, dt=0.05, cg_tol=1e-6, 10 steps"}
+    finals = {}
+    for prec in ("fp32", "bf16_hilo"):
+        th = torch.tensor(w.theta, dtype=torch.float64, device=dev)
+        pi = torch.tensor([[0.2, -0.1, 0.1]], dtype=torch.float64, device=dev)
+        try:
+            h.leapfrog_step(pts, y, phi, th.clone(), pi.clone(), 0.05, prec=prec)
+        except KmvError as e:
+            res[prec] = {"unavailable": str(e)}
+            continue
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        its = []
+        for _ in range(10):
+            st, it, _ = h.leapfrog_step(pts, y, phi, th, pi, 0.05, prec=prec)
+            its.append(int(it[0]))
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        finals[prec] = (th.cpu().numpy(), pi.cpu().numpy())
+        res[prec] = {"steps_per_s": 10 / dt, "mean_cg_iters": float(np.mean(its))}
+    if "fp32" in finals and "bf16_hilo" in finals:
+        res["bf16_vs_fp32_theta_maxdiff"] = float(np.abs(finals["fp32"][0] - finals["bf16_hilo"][0]).max())
+    return res
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,197 @@
+/*
+ * kmv.h - matrix-free squared-exponential kernel products for determinant-free
+ * fully Bayesian Gaussian-process regression, on one GB300 (sm_103a).
+ *
+ * The operator is A(theta) = K(theta) + sigma^2 I (Eq. kerdef) with the
+ * squared-exponential kernel of Sec. 1,
+ *     K_ij = alpha * exp(-1/2 * sum_k (x_ik - x_jk)^2 / l_k^2),
+ * isotropic (one l) or ARD (one l_k per input dimension).  K is never stored:
+ * every call recomputes its entries tile by tile, so device memory stays
+ * linear in N.
+ *
+ * Hyperparameters are FP64 log parameters, one row per (instance, chain):
+ *     theta[s, :] = [log alpha, log l_1 .. log l_k, log sigma^2],
+ *     n_theta = 2 + (ard ? d : 1),   s = b * chains + c.
+ *
+ * Common conventions
+ *   - Every pointer documented DEVICE is caller-owned device memory on the
+ *     handle's device; HOST pointers are read during the call only.  The
+ *     library never frees caller memory.  It owns only its handle workspace,
+ *     which grows on demand (cudaMalloc) and is released by kmv_destroy.
+ *   - Point sets: instances are concatenated along rows; kmv_points.offsets
+ *     (HOST, n_inst + 1 entries, offsets[0] = 0, non-decreasing) delimits
+ *     instance b as rows [offsets[b], offsets[b+1]).  Empty instances are
+ *     allowed.  N_total = offsets[n_inst].
+ *   - Vectors: per-chain arrays are (chains, N_total, m) row-major FP32; the
+ *     rows of chain c of instance b are the rows of that instance.
+ *   - Calls are asynchronous and stream-ordered on `stream` (a cudaStream_t,
+ *     NULL = legacy default stream) unless stated otherwise.
+ *   - Errors: argument errors return KMV_EINVAL synchronously before any
+ *     launch; CUDA errors return KMV_ECUDA; kmv_last_error() gives a message.
+ *     Per-system numerical failures (a solve that did not converge, a
+ *     non-finite energy) are reported in the caller's chain_status array.
+ *     No call traps or aborts.
+ *   - A handle is not thread-safe; use one handle per host thread.
+ */
+#ifndef KMV_H
+#define KMV_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  KMV_OK = 0,
+  KMV_EINVAL = 1,       /* bad argument (null pointer, size, layout) */
+  KMV_ENOMEM = 2,       /* workspace allocation failed */
+  KMV_ECUDA = 3,        /* a CUDA runtime call or launch failed */
+  KMV_ENOTCONV = 4,     /* per-system status: solve hit cg_maxiter */
+  KMV_ETIMEOUT = 5,     /* a bounded device-side wait gave up */
+  KMV_ENONFINITE = 6,   /* per-system status: non-finite value met */
+  KMV_EUNSUPPORTED = 7  /* shape or precision not built in this library */
+} kmv_status;
+
+typedef enum {
+  /* Plain FP32 on the FMA/MUFU pipes: direct differences, FP32 exp2, FP32
+   * products folded into FP64 accumulators every 512 columns.  Relative
+   * error against FP64 <= 1e-5 on outputs, <= 1e-4 on gradients. */
+  KMV_FP32 = 0,
+  /* Tensor-core form (tcgen05): cross term X_I X_J^T in BF16 with a hi/lo
+   * split (hi.hi + hi.lo + lo.hi) and the row biases folded into the same
+   * contraction, exp2 in FP32 registers, P.V in FP16 with FP32 accumulation
+   * folded into FP64.  Relative error against FP64 <= 2e-3. */
+  KMV_BF16_HILO = 1
+} kmv_precision;
+
+typedef struct kmv_handle_s* kmv_handle;
+
+typedef struct {
+  int32_t n_inst;          /* number of independent GP instances, >= 1 */
+  const int64_t* offsets;  /* HOST, n_inst + 1 row offsets (see above) */
+  int32_t d;               /* input dimension, 1 <= d <= 64 */
+  int32_t ard;             /* 0: isotropic kernel, 1: one lengthscale per dimension */
+  const float* x;          /* DEVICE, (N_total, d) row-major input points */
+} kmv_points;
+
+/* Create a handle bound to CUDA device `device` (made current by every call). */
+kmv_status kmv_create(kmv_handle* out, int device);
+/* Free the handle and its workspace; synchronises the device first. */
+kmv_status kmv_destroy(kmv_handle h);
+const char* kmv_status_string(kmv_status s);
+/* Last error message recorded on this handle ("" if none). */
+const char* kmv_last_error(kmv_handle h);
+/* Workspace bytes currently held by the handle. */
+int64_t kmv_workspace_bytes(kmv_handle h);
+
+/*
+ * kmv_forward - Y = A(theta) V (+ col_shift o V), the matrix-free product of
+ * Eq. kerdef; col_shift gives the shifted operators A + lambda_p I of Eq. pex.
+ *
+ *   chains     >= 1 independent hyperparameter sets per instance.
+ *   theta      DEVICE FP64 (n_inst * chains, n_theta).
+ *   V          DEVICE FP32 (chains, N_total, m), m >= 1.
+ *   col_shift  DEVICE FP32 (m) or NULL: column c uses A + col_shift[c] I.
+ *   Y          DEVICE FP32 (chains, N_total, m), written (must not alias V).
+ *   Y64        DEVICE FP64 (chains, N_total, m) or NULL: the same result before
+ *              rounding to FP32 (used for FP64 energy accumulation).
+ * Work: sum_b N_b^2 * chains kernel entries ("pairs").
+ */
+kmv_status kmv_forward(kmv_handle h, const kmv_points* pts, int32_t chains,
+                       const double* theta, const float* V, int32_t m,
+                       const float* col_shift, float* Y, double* Y64,
+                       kmv_precision prec, void* stream);
+
+/*
+ * kmv_backward - adjoint of L_s = sum_{i in b, k} G[c,i,k] (A(theta_s) V)[c,i,k]
+ * for each system s = (b, c); the quadratic-form gradient of primitive (3),
+ * Sec. 3.2.1, generalised to many vectors.
+ *
+ *   grad_theta DEVICE FP64 (n_inst * chains, n_theta), overwritten with dL_s/dtheta_s:
+ *                d/dlog alpha   = sum_ij (G V^T)_ij K_ij
+ *                d/dlog l_k     = sum_ij (G V^T)_ij K_ij (x_ik - x_jk)^2 / l_k^2
+ *                                 (isotropic: summed over k)
+ *                d/dlog sigma^2 = sigma^2 sum_i G_i . V_i
+ *   grad_V     DEVICE FP32 (chains, N_total, m) or NULL: dL/dV = A G.
+ * K entries are recomputed, never stored.  The FP64 reduction over tiles is
+ * in a fixed order, so results are bitwise reproducible.
+ */
+kmv_status kmv_backward(kmv_handle h, const kmv_points* pts, int32_t chains,
+                        const double* theta, const float* V, const float* G,
+                        int32_t m, double* grad_theta, float* grad_V,
+                        kmv_precision prec, void* stream);
+
+/*
+ * kmv_cg_solve - solve A(theta_s) x = rhs for every system s by conjugate
+ * gradients (primitive (1) of Sec. 3.2.1; Eq. xtheta), stopping a system when
+ * ||r|| <= tol ||rhs|| (Sec. 4 uses tol = 1e-6).
+ *
+ *   rhs          DEVICE FP32 (N_total) shared by all chains if rhs_per_chain == 0,
+ *                else (chains, N_total).
+ *   x            DEVICE FP32 (chains, N_total): initial guess if warm_start != 0,
+ *                otherwise ignored; overwritten with the solution.
+ *   chain_status DEVICE int32 (n_inst * chains): KMV_OK or KMV_ENOTCONV.
+ *   iters        DEVICE int32 (n_inst * chains) or NULL: iterations used.
+ * Synchronises `stream` once every few iterations to test convergence on the
+ * host, so this call (and the calls built on it) cannot be stream-captured.
+ */
+kmv_status kmv_cg_solve(kmv_handle h, const kmv_points* pts, int32_t chains,
+                        const double* theta, const float* rhs, int32_t rhs_per_chain,
+                        float* x, double tol, int32_t maxiter, int32_t warm_start,
+                        int32_t* chain_status, int32_t* iters,
+                        kmv_precision prec, void* stream);
+
+/*
+ * leapfrog_step - one drift-kick-drift step of Sec. 3.2.2 for every chain:
+ *     theta_h = theta + dt/2 pi
+ *     x       = A(theta_h)^{-1} y                         (kmv_cg_solve, cold start)
+ *     F       = grad S(theta_h) + d/dtheta [ -x^T A x / 2 + phi^T A phi / 2 ]
+ *               (the frozen-x force of Eq. u, via kmv_backward with
+ *                V = [x, phi], G = [-x/2, phi/2])
+ *     pi     <- pi - dt F
+ *     theta  <- theta_h + dt/2 pi
+ * Components with free_mask[p] == 0 receive neither drift nor kick.
+ *
+ *   y            DEVICE FP32 (N_total) observations.
+ *   phi          DEVICE FP32 (chains, N_total) auxiliary Gaussian variables.
+ *   theta, pi    DEVICE FP64 (n_inst * chains, n_theta), updated in place.
+ *   prior_mu, prior_prec DEVICE FP64 (n_theta) or both NULL (flat prior,
+ *                S = 0); otherwise S = sum prec (theta - mu)^2 / 2.
+ *   free_mask    DEVICE uint8 (n_theta) or NULL (all free).
+ *   x_work       DEVICE FP32 (chains, N_total): receives x.
+ *   chain_status DEVICE int32 (n_inst * chains): KMV_OK, or KMV_ENOTCONV when
+ *                the solve failed (theta/pi then hold theta_h / the un-kicked pi;
+ *                the caller must reject the trajectory).
+ *   cg_iters     DEVICE int32 (n_inst * chains) or NULL.
+ */
+kmv_status leapfrog_step(kmv_handle h, const kmv_points* pts, int32_t chains,
+                         const float* y, const float* phi, double* theta, double* pi,
+                         double dt, const double* prior_mu, const double* prior_prec,
+                         const uint8_t* free_mask, double cg_tol, int32_t cg_maxiter,
+                         float* x_work, int32_t* chain_status, int32_t* cg_iters,
+                         kmv_precision prec, void* stream);
+
+/*
+ * kmv_energy - the Hamiltonian of Sec. 3.2 per chain, accumulated in FP64:
+ *     U = S(theta) + y^T x / 2 + phi^T A phi / 2,  x = A(theta)^{-1} y   (Eq. U)
+ *     H = U + pi^T pi / 2                                            (M = I)
+ *   pi       DEVICE FP64 (n_inst * chains, n_theta) or NULL (H = U).
+ *   H        DEVICE FP64 (n_inst * chains), written.
+ *   terms    DEVICE FP64 (n_inst * chains, 3) or NULL: [S, y^T x / 2, phi^T A phi / 2].
+ *   Other arguments as in leapfrog_step.  prec selects the operator used by
+ *   the solve and the product; KMV_FP32 is the accurate form meant for the
+ *   Metropolis test.
+ */
+kmv_status kmv_energy(kmv_handle h, const kmv_points* pts, int32_t chains,
+                      const float* y, const float* phi, const double* theta,
+                      const double* pi, const double* prior_mu, const double* prior_prec,
+                      double cg_tol, int32_t cg_maxiter, float* x_work,
+                      double* H, double* terms, int32_t* chain_status, int32_t* cg_iters,
+                      kmv_precision prec, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KMV_H */

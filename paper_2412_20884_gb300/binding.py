@@ -1,0 +1,281 @@
+"""ctypes binding of libkmv (include/kmv.h).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library.  There is no CPU fallback; if ``_build/libkmv.so`` is missing the
+binding raises at load time.  Tensors are torch CUDA tensors (torch supplies
+device memory and streams); all calls are enqueued on the current torch
+stream unless a stream is given.
+
+Python names match the C entry points: ``kmv_forward``, ``kmv_backward``,
+``kmv_cg_solve``, ``leapfrog_step``, ``kmv_energy``.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+import torch
+
+from . import build as _build
+
+KMV_OK, KMV_EINVAL, KMV_ENOMEM, KMV_ECUDA, KMV_ENOTCONV, KMV_ETIMEOUT, KMV_ENONFINITE, KMV_EUNSUPPORTED = range(8)
+PRECISIONS = {"fp32": 0, "bf16_hilo": 1}
+
+_LIB = None
+
+
+class KmvError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__(f"{message} (status {status})")
+        self.status = status
+
+
+class _Points(C.Structure):
+    _fields_ = [("n_inst", C.c_int32), ("offsets", C.POINTER(C.c_int64)), ("d", C.c_int32),
+                ("ard", C.c_int32), ("x", C.c_void_p)]
+
+
+_P = C.c_void_p
+_SIGS = {
+    "kmv_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int]),
+    "kmv_destroy": (C.c_int, [_P]),
+    "kmv_status_string": (C.c_char_p, [C.c_int]),
+    "kmv_last_error": (C.c_char_p, [_P]),
+    "kmv_workspace_bytes": (C.c_int64, [_P]),
+    "kmv_forward": (C.c_int, [_P, C.POINTER(_Points), C.c_int32, _P, _P, C.c_int32, _P, _P, _P, C.c_int, _P]),
+    "kmv_backward": (C.c_int, [_P, C.POINTER(_Points), C.c_int32, _P, _P, _P, C.c_int32, _P, _P, C.c_int, _P]),
+    "kmv_cg_solve": (C.c_int, [_P, C.POINTER(_Points), C.c_int32, _P, _P, C.c_int32, _P, C.c_double,
+                               C.c_int32, C.c_int32, _P, _P, C.c_int, _P]),
+    "leapfrog_step": (C.c_int, [_P, C.POINTER(_Points), C.c_int32, _P, _P, _P, _P, C.c_double, _P, _P, _P,
+                                C.c_double, C.c_int32, _P, _P, _P, C.c_int, _P]),
+    "kmv_energy": (C.c_int, [_P, C.POINTER(_Points), C.c_int32, _P, _P, _P, _P, _P, _P, C.c_double,
+                             C.c_int32, _P, _P, _P, _P, _P, C.c_int, _P]),
+}
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """Load libkmv.so (built by ``__graft_entry__.build()``); raises if it is missing."""
+    global _LIB
+    if _LIB is None:
+        path = lib_path()
+        if not os.path.exists(path):
+            raise RuntimeError(f"libkmv.so not found at {path}: run __graft_entry__.build() first")
+        L = C.CDLL(path)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _LIB = L
+    return _LIB
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    s = torch.cuda.current_stream() if stream is None else stream
+    return C.c_void_p(s.cuda_stream)
+
+
+def _need(t, dtype, name, shape=None):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} must have shape {tuple(shape)}, got {tuple(t.shape)}")
+    return t
+
+
+class Points:
+    """A point set: instances concatenated along rows of x (N_total, d)."""
+
+    def __init__(self, x: torch.Tensor, offsets=None, ard: bool = True):
+        _need(x, torch.float32, "x")
+        if x.dim() != 2:
+            raise ValueError("x must be (N_total, d)")
+        self.x = x
+        n = x.shape[0]
+        off = np.array([0, n] if offsets is None else offsets, dtype=np.int64)
+        if off[0] != 0 or off[-1] != n or np.any(np.diff(off) < 0):
+            raise ValueError("offsets must start at 0, end at N_total and be non-decreasing")
+        self.offsets = np.ascontiguousarray(off)
+        self.ard = bool(ard)
+        self.d = x.shape[1]
+        self.n_inst = len(off) - 1
+        self.n_total = n
+        self.n_theta = 2 + (self.d if self.ard else 1)
+        self._c = _Points(self.n_inst, self.offsets.ctypes.data_as(C.POINTER(C.c_int64)), self.d,
+                          int(self.ard), C.c_void_p(x.data_ptr()))
+
+    @property
+    def c(self):
+        return C.byref(self._c)
+
+    def pairs(self, chains: int = 1) -> int:
+        nb = np.diff(self.offsets).astype(np.float64)
+        return int(np.sum(nb * nb)) * chains
+
+
+class Kmv:
+    """A libkmv handle bound to one CUDA device."""
+
+    def __init__(self, device: int = 0):
+        self.L = lib()
+        self.device = device
+        h = C.c_void_p()
+        st = self.L.kmv_create(C.byref(h), device)
+        if st != KMV_OK:
+            raise KmvError(st, "kmv_create failed")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.kmv_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st):
+        if st != KMV_OK:
+            msg = self.L.kmv_last_error(self.h).decode() or self.L.kmv_status_string(st).decode()
+            raise KmvError(st, msg)
+
+    def workspace_bytes(self) -> int:
+        return int(self.L.kmv_workspace_bytes(self.h))
+
+    @staticmethod
+    def _prec(prec):
+        return PRECISIONS[prec] if isinstance(prec, str) else int(prec)
+
+    def _chains(self, pts, theta):
+        n_sys = theta.shape[0]
+        if n_sys % pts.n_inst:
+            raise ValueError("theta rows must be n_inst * chains")
+        return n_sys // pts.n_inst
+
+    # ------------------------------------------------------------------ products
+    def kmv_forward(self, pts: Points, theta, V, col_shift=None, Y=None, Y64=False,
+                    prec="fp32", stream=None):
+        chains = self._chains(pts, theta)
+        _need(theta, torch.float64, "theta", (pts.n_inst * chains, pts.n_theta))
+        m = V.shape[-1]
+        _need(V, torch.float32, "V", (chains, pts.n_total, m))
+        if col_shift is not None:
+            _need(col_shift, torch.float32, "col_shift", (m,))
+        if Y is None:
+            Y = torch.empty_like(V)
+        _need(Y, torch.float32, "Y", V.shape)
+        y64 = None
+        if Y64 is True:
+            y64 = torch.empty(V.shape, dtype=torch.float64, device=V.device)
+        elif isinstance(Y64, torch.Tensor):
+            y64 = _need(Y64, torch.float64, "Y64", V.shape)
+        self._check(self.L.kmv_forward(self.h, pts.c, chains, _ptr(theta), _ptr(V), m, _ptr(col_shift),
+                                       _ptr(Y), _ptr(y64), self._prec(prec), _stream(stream)))
+        return (Y, y64) if y64 is not None else Y
+
+    def kmv_backward(self, pts: Points, theta, V, G, want_grad_V=True, grad_theta=None, grad_V=None,
+                     prec="fp32", stream=None):
+        chains = self._chains(pts, theta)
+        _need(theta, torch.float64, "theta", (pts.n_inst * chains, pts.n_theta))
+        m = V.shape[-1]
+        _need(V, torch.float32, "V", (chains, pts.n_total, m))
+        _need(G, torch.float32, "G", V.shape)
+        if grad_theta is None:
+            grad_theta = torch.empty_like(theta)
+        _need(grad_theta, torch.float64, "grad_theta", theta.shape)
+        if want_grad_V and grad_V is None:
+            grad_V = torch.empty_like(V)
+        if grad_V is not None:
+            _need(grad_V, torch.float32, "grad_V", V.shape)
+        self._check(self.L.kmv_backward(self.h, pts.c, chains, _ptr(theta), _ptr(V), _ptr(G), m,
+                                        _ptr(grad_theta), _ptr(grad_V), self._prec(prec), _stream(stream)))
+        return grad_theta, grad_V
+
+    # ------------------------------------------------------------------ solves / HMC
+    def kmv_cg_solve(self, pts: Points, theta, rhs, x=None, tol=1e-6, maxiter=1000, warm_start=False,
+                     prec="fp32", stream=None):
+        chains = self._chains(pts, theta)
+        _need(theta, torch.float64, "theta", (pts.n_inst * chains, pts.n_theta))
+        per_chain = rhs.dim() == 2
+        _need(rhs, torch.float32, "rhs", (chains, pts.n_total) if per_chain else (pts.n_total,))
+        if x is None:
+            x = torch.zeros((chains, pts.n_total), dtype=torch.float32, device=rhs.device)
+        _need(x, torch.float32, "x", (chains, pts.n_total))
+        status = torch.empty(pts.n_inst * chains, dtype=torch.int32, device=rhs.device)
+        iters = torch.empty_like(status)
+        self._check(self.L.kmv_cg_solve(self.h, pts.c, chains, _ptr(theta), _ptr(rhs), int(per_chain),
+                                        _ptr(x), float(tol), int(maxiter), int(bool(warm_start)),
+                                        _ptr(status), _ptr(iters), self._prec(prec), _stream(stream)))
+        return x, status, iters
+
+    def leapfrog_step(self, pts: Points, y, phi, theta, pi, dt, prior=None, free_mask=None,
+                      cg_tol=1e-6, cg_maxiter=1000, x_work=None, prec="fp32", stream=None):
+        chains = self._chains(pts, theta)
+        n_sys = pts.n_inst * chains
+        _need(y, torch.float32, "y", (pts.n_total,))
+        _need(phi, torch.float32, "phi", (chains, pts.n_total))
+        _need(theta, torch.float64, "theta", (n_sys, pts.n_theta))
+        _need(pi, torch.float64, "pi", (n_sys, pts.n_theta))
+        mu = prec_ = None
+        if prior is not None:
+            mu = _need(prior[0], torch.float64, "prior_mu", (pts.n_theta,))
+            prec_ = _need(prior[1], torch.float64, "prior_prec", (pts.n_theta,))
+        if free_mask is not None:
+            _need(free_mask, torch.uint8, "free_mask", (pts.n_theta,))
+        if x_work is None:
+            x_work = torch.empty((chains, pts.n_total), dtype=torch.float32, device=y.device)
+        status = torch.empty(n_sys, dtype=torch.int32, device=y.device)
+        iters = torch.empty_like(status)
+        self._check(self.L.leapfrog_step(self.h, pts.c, chains, _ptr(y), _ptr(phi), _ptr(theta), _ptr(pi),
+                                         float(dt), _ptr(mu), _ptr(prec_), _ptr(free_mask), float(cg_tol),
+                                         int(cg_maxiter), _ptr(x_work), _ptr(status), _ptr(iters),
+                                         self._prec(prec), _stream(stream)))
+        return status, iters, x_work
+
+    def kmv_energy(self, pts: Points, y, phi, theta, pi=None, prior=None, cg_tol=1e-6, cg_maxiter=1000,
+                   x_work=None, prec="fp32", stream=None):
+        chains = self._chains(pts, theta)
+        n_sys = pts.n_inst * chains
+        _need(y, torch.float32, "y", (pts.n_total,))
+        _need(phi, torch.float32, "phi", (chains, pts.n_total))
+        _need(theta, torch.float64, "theta", (n_sys, pts.n_theta))
+        if pi is not None:
+            _need(pi, torch.float64, "pi", (n_sys, pts.n_theta))
+        mu = prec_ = None
+        if prior is not None:
+            mu = _need(prior[0], torch.float64, "prior_mu", (pts.n_theta,))
+            prec_ = _need(prior[1], torch.float64, "prior_prec", (pts.n_theta,))
+        if x_work is None:
+            x_work = torch.empty((chains, pts.n_total), dtype=torch.float32, device=y.device)
+        H = torch.empty(n_sys, dtype=torch.float64, device=y.device)
+        terms = torch.empty((n_sys, 3), dtype=torch.float64, device=y.device)
+        status = torch.empty(n_sys, dtype=torch.int32, device=y.device)
+        iters = torch.empty_like(status)
+        self._check(self.L.kmv_energy(self.h, pts.c, chains, _ptr(y), _ptr(phi), _ptr(theta), _ptr(pi),
+                                      _ptr(mu), _ptr(prec_), float(cg_tol), int(cg_maxiter), _ptr(x_work),
+                                      _ptr(H), _ptr(terms), _ptr(status), _ptr(iters), self._prec(prec),
+                                      _stream(stream)))
+        return H, terms, status, iters
+
+
+_DEFAULT = {}
+
+
+def default_handle(device: int = 0) -> Kmv:
+    if device not in _DEFAULT:
+        _DEFAULT[device] = Kmv(device)
+    return _DEFAULT[device]

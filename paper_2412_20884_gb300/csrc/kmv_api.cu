@@ -1,0 +1,499 @@
+// C ABI of libkmv: argument checks, work-item tables, workspace and dispatch.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "kmv_internal.cuh"
+#include "kmv_tc.cuh"
+
+using namespace kmv;
+
+namespace {
+
+kmv_status fail(kmv_handle h, kmv_status s, const std::string& msg) {
+  if (h) h->last_error = msg;
+  return s;
+}
+
+#define KMV_CUDA(h, expr)                                                              \
+  do {                                                                                 \
+    cudaError_t e_ = (expr);                                                           \
+    if (e_ != cudaSuccess)                                                             \
+      return fail(h, KMV_ECUDA, std::string(#expr) + ": " + cudaGetErrorString(e_));   \
+  } while (0)
+
+#define KMV_TRY(expr)                 \
+  do {                                \
+    kmv_status s_ = (expr);           \
+    if (s_ != KMV_OK) return s_;      \
+  } while (0)
+
+// Bump allocator over the handle workspace; 256-byte aligned regions.
+struct Arena {
+  size_t used = 0;
+  size_t take(size_t bytes) {
+    const size_t off = used;
+    used += (bytes + 255) & ~size_t(255);
+    return off;
+  }
+};
+
+kmv_status reserve(kmv_handle h, size_t bytes) {
+  if (bytes <= h->ws_bytes) return KMV_OK;
+  if (h->ws) {
+    KMV_CUDA(h, cudaDeviceSynchronize());
+    KMV_CUDA(h, cudaFree(h->ws));
+    h->ws = nullptr;
+    h->ws_bytes = 0;
+  }
+  const size_t want = bytes + bytes / 4 + (1 << 20);
+  if (cudaMalloc(&h->ws, want) != cudaSuccess) {
+    cudaGetLastError();
+    h->ws = nullptr;
+    return fail(h, KMV_ENOMEM, "workspace allocation of " + std::to_string(want) + " bytes failed");
+  }
+  h->ws_bytes = want;
+  return KMV_OK;
+}
+
+template <class T>
+T* at(kmv_handle h, size_t off) {
+  return reinterpret_cast<T*>(static_cast<char*>(h->ws) + off);
+}
+
+kmv_status check_points(kmv_handle h, const kmv_points* pts, int32_t chains) {
+  if (!h) return KMV_EINVAL;
+  if (!pts) return fail(h, KMV_EINVAL, "points is NULL");
+  if (pts->n_inst < 1) return fail(h, KMV_EINVAL, "n_inst must be >= 1");
+  if (!pts->offsets) return fail(h, KMV_EINVAL, "offsets is NULL");
+  if (pts->d < 1 || pts->d > kMaxD) return fail(h, KMV_EINVAL, "d must be in [1, 64]");
+  if (pts->ard != 0 && pts->ard != 1) return fail(h, KMV_EINVAL, "ard must be 0 or 1");
+  if (chains < 1) return fail(h, KMV_EINVAL, "chains must be >= 1");
+  if (pts->offsets[0] != 0) return fail(h, KMV_EINVAL, "offsets[0] must be 0");
+  for (int b = 0; b < pts->n_inst; ++b)
+    if (pts->offsets[b + 1] < pts->offsets[b]) return fail(h, KMV_EINVAL, "offsets must be non-decreasing");
+  const int64_t n = pts->offsets[pts->n_inst];
+  if (n > (int64_t(1) << 40)) return fail(h, KMV_EINVAL, "too many rows");
+  if (n > 0 && !pts->x) return fail(h, KMV_EINVAL, "x is NULL");
+  if ((int64_t)pts->n_inst * chains > (int64_t(1) << 30)) return fail(h, KMV_EINVAL, "too many systems");
+  return KMV_OK;
+}
+
+// Builds (or reuses) the row-tile work items of this point set on the device.
+kmv_status prepare_layout(kmv_handle h, const kmv_points* pts, int32_t chains, cudaStream_t st) {
+  KMV_CUDA(h, cudaSetDevice(h->device));
+  Layout& L = h->layout;
+  const int n_inst = pts->n_inst;
+  const bool same = h->cached_d == pts->d && (int)h->cached_offsets.size() == n_inst + 1 &&
+                    std::equal(h->cached_offsets.begin(), h->cached_offsets.end(), pts->offsets);
+  L.chains = chains;
+  L.d = pts->d;
+  L.ard = pts->ard;
+  L.n_theta = 2 + (pts->ard ? pts->d : 1);
+  if (same) return KMV_OK;
+
+  L.n_inst = n_inst;
+  L.offsets.assign(pts->offsets, pts->offsets + n_inst + 1);
+  L.n_total = L.offsets[n_inst];
+  L.item_inst.clear();
+  L.item_row0.clear();
+  L.inst_item0.assign(n_inst + 1, 0);
+  L.max_items_per_inst = 0;
+  for (int b = 0; b < n_inst; ++b) {
+    L.inst_item0[b] = (int32_t)L.item_inst.size();
+    const int64_t nb = L.offsets[b + 1] - L.offsets[b];
+    const int64_t tiles = (nb + kTile - 1) / kTile;
+    for (int64_t t = 0; t < tiles; ++t) {
+      L.item_inst.push_back(b);
+      L.item_row0.push_back(L.offsets[b] + t * kTile);
+    }
+    L.max_items_per_inst = std::max<int>(L.max_items_per_inst, (int)tiles);
+  }
+  L.inst_item0[n_inst] = (int32_t)L.item_inst.size();
+  L.n_items = (int)L.item_inst.size();
+  if ((int64_t)L.item_inst.size() > (int64_t(1) << 30)) return fail(h, KMV_EINVAL, "too many tiles");
+
+  const size_t b_off = sizeof(int64_t) * (n_inst + 1);
+  const size_t b_inst = sizeof(int32_t) * std::max(1, L.n_items);
+  const size_t b_row0 = sizeof(int64_t) * std::max(1, L.n_items);
+  const size_t b_ii = sizeof(int32_t) * (n_inst + 1);
+  const size_t o_off = 0, o_row0 = (b_off + 255) & ~size_t(255);
+  const size_t o_inst = o_row0 + ((b_row0 + 255) & ~size_t(255));
+  const size_t o_ii = o_inst + ((b_inst + 255) & ~size_t(255));
+  const size_t total = o_ii + b_ii;
+  if (total > h->tables_bytes) {
+    if (h->tables) {
+      KMV_CUDA(h, cudaDeviceSynchronize());
+      KMV_CUDA(h, cudaFree(h->tables));
+      h->tables = nullptr;
+      h->tables_bytes = 0;
+    }
+    if (cudaMalloc(&h->tables, total) != cudaSuccess) {
+      cudaGetLastError();
+      h->tables = nullptr;
+      return fail(h, KMV_ENOMEM, "table allocation failed");
+    }
+    h->tables_bytes = total;
+  }
+  // The tables are staged through host memory that outlives the copy: wait for it.
+  char* base = static_cast<char*>(h->tables);
+  KMV_CUDA(h, cudaMemcpyAsync(base + o_off, L.offsets.data(), b_off, cudaMemcpyHostToDevice, st));
+  if (L.n_items) {
+    KMV_CUDA(h, cudaMemcpyAsync(base + o_row0, L.item_row0.data(), sizeof(int64_t) * L.n_items,
+                                cudaMemcpyHostToDevice, st));
+    KMV_CUDA(h, cudaMemcpyAsync(base + o_inst, L.item_inst.data(), sizeof(int32_t) * L.n_items,
+                                cudaMemcpyHostToDevice, st));
+  }
+  KMV_CUDA(h, cudaMemcpyAsync(base + o_ii, L.inst_item0.data(), b_ii, cudaMemcpyHostToDevice, st));
+  KMV_CUDA(h, cudaStreamSynchronize(st));
+  h->dev.offsets = reinterpret_cast<const int64_t*>(base + o_off);
+  h->dev.item_row0 = reinterpret_cast<const int64_t*>(base + o_row0);
+  h->dev.item_inst = reinterpret_cast<const int32_t*>(base + o_inst);
+  h->dev.inst_item0 = reinterpret_cast<const int32_t*>(base + o_ii);
+  h->cached_offsets = L.offsets;
+  h->cached_d = pts->d;
+  return KMV_OK;
+}
+
+KmvArgs base_args(kmv_handle h, const kmv_points* pts, const double* theta) {
+  KmvArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.L = h->dev;
+  a.chains = h->layout.chains;
+  a.d = pts->d;
+  a.ard = pts->ard;
+  a.n_theta = h->layout.n_theta;
+  a.n_total = h->layout.n_total;
+  a.x = pts->x;
+  a.theta = theta;
+  a.n_z = 1;
+  return a;
+}
+
+// --- building blocks used by several entry points -------------------------------------
+
+kmv_status run_forward(kmv_handle h, const KmvArgs& a, kmv_precision prec, cudaStream_t st) {
+  if (h->layout.n_items == 0) return KMV_OK;
+  if (prec == KMV_BF16_HILO) {
+    kmv_status s = tc_forward(h, a, st);
+    return s;
+  }
+  KMV_CUDA(h, launch_forward_simt(a, h->layout.n_items, st));
+  return KMV_OK;
+}
+
+size_t backward_ws_bytes(const Layout& L, int m) {
+  const int mp = backward_mp(m);
+  const int nz = (m + mp - 1) / mp;
+  return sizeof(double) * (size_t)std::max(1, L.n_items) * L.chains * nz * L.n_theta;
+}
+
+kmv_status run_backward(kmv_handle h, KmvArgs a, double* grad, double* partial,
+                        kmv_precision prec, cudaStream_t st) {
+  const Layout& L = h->layout;
+  if (prec == KMV_BF16_HILO) return tc_backward(h, a, grad, st);
+  const int mp = backward_mp(a.m);
+  a.n_z = (a.m + mp - 1) / mp;
+  a.grad_partial = partial;
+  if (L.n_items > 0) KMV_CUDA(h, launch_backward_simt(a, L.n_items, st));
+  KMV_CUDA(h, launch_grad_finalize(h->dev, L.n_inst, L.chains, L.n_theta, L.ard, L.d, a.n_z,
+                                   a.theta, partial, grad, st));
+  return KMV_OK;
+}
+
+struct CgBufs {
+  float *r, *p, *q;
+  double *partial, *partial2;
+  CgSys* sys;
+  int32_t *active, *n_active;
+};
+
+size_t cg_layout(const Layout& L, Arena& ar, size_t off[8]) {
+  const size_t vec = sizeof(float) * (size_t)L.chains * std::max<int64_t>(1, L.n_total);
+  const size_t items = (size_t)std::max(1, L.n_items) * L.chains;
+  const size_t n_sys = (size_t)L.n_inst * L.chains;
+  off[0] = ar.take(vec);
+  off[1] = ar.take(vec);
+  off[2] = ar.take(vec);
+  off[3] = ar.take(sizeof(double) * items);
+  off[4] = ar.take(sizeof(double) * items * 2);
+  off[5] = ar.take(sizeof(CgSys) * n_sys);
+  off[6] = ar.take(sizeof(int32_t) * n_sys);
+  off[7] = ar.take(sizeof(int32_t) * 4);
+  return ar.used;
+}
+
+CgBufs cg_bufs(kmv_handle h, const size_t off[8]) {
+  CgBufs b;
+  b.r = at<float>(h, off[0]);
+  b.p = at<float>(h, off[1]);
+  b.q = at<float>(h, off[2]);
+  b.partial = at<double>(h, off[3]);
+  b.partial2 = at<double>(h, off[4]);
+  b.sys = at<CgSys>(h, off[5]);
+  b.active = at<int32_t>(h, off[6]);
+  b.n_active = at<int32_t>(h, off[7]);
+  return b;
+}
+
+// Batched CG on A(theta_s) x = rhs (Sec. 3.2.1 primitive (1)); see kmv_cg_solve.
+kmv_status run_cg(kmv_handle h, const kmv_points* pts, const double* theta, const float* rhs,
+                  int64_t rhs_stride, float* x, double tol, int maxiter, int warm,
+                  int32_t* status, int32_t* iters, const CgBufs& B, kmv_precision prec,
+                  cudaStream_t st) {
+  const Layout& L = h->layout;
+  const int n_sys = L.n_inst * L.chains;
+  KmvArgs a = base_args(h, pts, theta);
+  a.m = 1;
+  if (warm) {
+    a.V = x;
+    a.Y = B.q;
+    KMV_TRY(run_forward(h, a, prec, st));
+  }
+  if (L.n_items > 0)
+    KMV_CUDA(h, launch_cg_init(h->dev, L.n_items, L.chains, L.n_total, rhs, rhs_stride, B.q, x, B.r,
+                               B.p, warm, B.partial2, st));
+  KMV_CUDA(h, launch_cg_reduce_init(h->dev, L.n_inst, L.chains, B.partial2, tol, B.sys, B.active,
+                                    B.n_active, st));
+  const int check_every = 4;
+  a.V = B.p;
+  a.Y = B.q;
+  a.sys_active = B.active;
+  a.dot_partial = B.partial;
+  for (int it = 0; it < maxiter; ++it) {
+    if (it % check_every == 0) {
+      KMV_CUDA(h, cudaMemcpyAsync(h->host_flag, B.n_active, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+      KMV_CUDA(h, cudaStreamSynchronize(st));
+      if (*h->host_flag == 0) break;
+    }
+    KMV_TRY(run_forward(h, a, prec, st));
+    KMV_CUDA(h, launch_cg_reduce_pq(h->dev, L.n_inst, L.chains, B.partial, B.sys, B.active, st));
+    KMV_CUDA(h, launch_cg_update_xr(h->dev, L.n_items, L.chains, L.n_total, B.sys, B.active, x, B.r,
+                                    B.p, B.q, B.partial, st));
+    KMV_CUDA(h, launch_cg_reduce_rr(h->dev, L.n_inst, L.chains, B.partial, tol, maxiter, B.sys,
+                                    B.active, B.n_active, st));
+    KMV_CUDA(h, launch_cg_update_p(h->dev, L.n_items, L.chains, L.n_total, B.sys, B.active, B.r,
+                                   B.p, st));
+  }
+  KMV_CUDA(h, launch_cg_finish(n_sys, B.sys, status, iters, st));
+  return KMV_OK;
+}
+
+kmv_status check_prec(kmv_handle h, kmv_precision prec) {
+  if (prec != KMV_FP32 && prec != KMV_BF16_HILO) return fail(h, KMV_EINVAL, "unknown precision");
+  return KMV_OK;
+}
+
+}  // namespace
+
+// =====================================================================================
+extern "C" {
+
+kmv_status kmv_create(kmv_handle* out, int device) {
+  if (!out) return KMV_EINVAL;
+  *out = nullptr;
+  int n = 0;
+  if (cudaGetDeviceCount(&n) != cudaSuccess) {
+    cudaGetLastError();
+    return KMV_ECUDA;
+  }
+  if (device < 0 || device >= n) return KMV_EINVAL;
+  kmv_handle h = new (std::nothrow) kmv_handle_s();
+  if (!h) return KMV_ENOMEM;
+  h->device = device;
+  if (cudaSetDevice(device) != cudaSuccess ||
+      cudaMallocHost(reinterpret_cast<void**>(&h->host_flag), 64) != cudaSuccess) {
+    cudaGetLastError();
+    delete h;
+    return KMV_ECUDA;
+  }
+  *out = h;
+  return KMV_OK;
+}
+
+kmv_status kmv_destroy(kmv_handle h) {
+  if (!h) return KMV_EINVAL;
+  cudaSetDevice(h->device);
+  cudaDeviceSynchronize();
+  tc_release(h);
+  if (h->ws) cudaFree(h->ws);
+  if (h->tables) cudaFree(h->tables);
+  if (h->host_flag) cudaFreeHost(h->host_flag);
+  delete h;
+  return KMV_OK;
+}
+
+const char* kmv_status_string(kmv_status s) {
+  switch (s) {
+    case KMV_OK: return "ok";
+    case KMV_EINVAL: return "invalid argument";
+    case KMV_ENOMEM: return "out of device memory";
+    case KMV_ECUDA: return "CUDA error";
+    case KMV_ENOTCONV: return "solver did not converge";
+    case KMV_ETIMEOUT: return "device-side wait timed out";
+    case KMV_ENONFINITE: return "non-finite value";
+    case KMV_EUNSUPPORTED: return "unsupported shape or precision";
+  }
+  return "unknown status";
+}
+
+const char* kmv_last_error(kmv_handle h) { return h ? h->last_error.c_str() : ""; }
+
+int64_t kmv_workspace_bytes(kmv_handle h) {
+  return h ? (int64_t)(h->ws_bytes + h->tables_bytes + tc_workspace_bytes(h)) : 0;
+}
+
+kmv_status kmv_forward(kmv_handle h, const kmv_points* pts, int32_t chains, const double* theta,
+                       const float* V, int32_t m, const float* col_shift, float* Y, double* Y64,
+                       kmv_precision prec, void* stream) {
+  KMV_TRY(check_points(h, pts, chains));
+  KMV_TRY(check_prec(h, prec));
+  if (m < 1) return fail(h, KMV_EINVAL, "m must be >= 1");
+  if (!theta || !V || !Y) return fail(h, KMV_EINVAL, "theta, V and Y must be non-NULL");
+  if ((const void*)V == (const void*)Y) return fail(h, KMV_EINVAL, "Y must not alias V");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  KMV_TRY(prepare_layout(h, pts, chains, st));
+  KmvArgs a = base_args(h, pts, theta);
+  a.V = V;
+  a.m = m;
+  a.col_shift = col_shift;
+  a.Y = Y;
+  a.Y64 = Y64;
+  return run_forward(h, a, prec, st);
+}
+
+kmv_status kmv_backward(kmv_handle h, const kmv_points* pts, int32_t chains, const double* theta,
+                        const float* V, const float* G, int32_t m, double* grad_theta,
+                        float* grad_V, kmv_precision prec, void* stream) {
+  KMV_TRY(check_points(h, pts, chains));
+  KMV_TRY(check_prec(h, prec));
+  if (m < 1) return fail(h, KMV_EINVAL, "m must be >= 1");
+  if (!theta || !V || !G || !grad_theta) return fail(h, KMV_EINVAL, "theta, V, G, grad_theta must be non-NULL");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  KMV_TRY(prepare_layout(h, pts, chains, st));
+  Arena ar;
+  const size_t o_part = ar.take(backward_ws_bytes(h->layout, m));
+  KMV_TRY(reserve(h, ar.used));
+  KmvArgs a = base_args(h, pts, theta);
+  a.V = V;
+  a.G = G;
+  a.m = m;
+  a.Y = grad_V;
+  return run_backward(h, a, grad_theta, at<double>(h, o_part), prec, st);
+}
+
+kmv_status kmv_cg_solve(kmv_handle h, const kmv_points* pts, int32_t chains, const double* theta,
+                        const float* rhs, int32_t rhs_per_chain, float* x, double tol,
+                        int32_t maxiter, int32_t warm_start, int32_t* chain_status, int32_t* iters,
+                        kmv_precision prec, void* stream) {
+  KMV_TRY(check_points(h, pts, chains));
+  KMV_TRY(check_prec(h, prec));
+  if (!theta || !rhs || !x || !chain_status) return fail(h, KMV_EINVAL, "NULL argument");
+  if (!(tol > 0.0) || maxiter < 1) return fail(h, KMV_EINVAL, "tol must be > 0 and maxiter >= 1");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  KMV_TRY(prepare_layout(h, pts, chains, st));
+  Arena ar;
+  size_t off[8];
+  cg_layout(h->layout, ar, off);
+  KMV_TRY(reserve(h, ar.used));
+  const int64_t stride = rhs_per_chain ? h->layout.n_total : 0;
+  return run_cg(h, pts, theta, rhs, stride, x, tol, maxiter, warm_start, chain_status, iters,
+                cg_bufs(h, off), prec, st);
+}
+
+kmv_status leapfrog_step(kmv_handle h, const kmv_points* pts, int32_t chains, const float* y,
+                         const float* phi, double* theta, double* pi, double dt,
+                         const double* prior_mu, const double* prior_prec, const uint8_t* free_mask,
+                         double cg_tol, int32_t cg_maxiter, float* x_work, int32_t* chain_status,
+                         int32_t* cg_iters, kmv_precision prec, void* stream) {
+  KMV_TRY(check_points(h, pts, chains));
+  KMV_TRY(check_prec(h, prec));
+  if (!y || !phi || !theta || !pi || !x_work || !chain_status) return fail(h, KMV_EINVAL, "NULL argument");
+  if ((prior_mu == nullptr) != (prior_prec == nullptr))
+    return fail(h, KMV_EINVAL, "prior_mu and prior_prec must both be set or both be NULL");
+  if (!std::isfinite(dt) || !(cg_tol > 0.0) || cg_maxiter < 1) return fail(h, KMV_EINVAL, "bad dt / cg_tol / cg_maxiter");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  KMV_TRY(prepare_layout(h, pts, chains, st));
+  const Layout& L = h->layout;
+  const int n_sys = L.n_inst * L.chains;
+  Arena ar;
+  size_t off[8];
+  cg_layout(L, ar, off);
+  const size_t o_th = ar.take(sizeof(double) * n_sys * L.n_theta);
+  const size_t o_gr = ar.take(sizeof(double) * n_sys * L.n_theta);
+  const size_t vec2 = sizeof(float) * 2 * (size_t)L.chains * std::max<int64_t>(1, L.n_total);
+  const size_t o_vf = ar.take(vec2);
+  const size_t o_gf = ar.take(vec2);
+  const size_t o_bp = ar.take(backward_ws_bytes(L, 2));
+  KMV_TRY(reserve(h, ar.used));
+  double* theta_h = at<double>(h, o_th);
+  double* grad = at<double>(h, o_gr);
+  float* Vf = at<float>(h, o_vf);
+  float* Gf = at<float>(h, o_gf);
+
+  // drift: theta_h = theta + dt/2 pi
+  KMV_CUDA(h, launch_lf_drift(n_sys, L.n_theta, theta, pi, free_mask, 0.5 * dt, theta_h, st));
+  // x = A(theta_h)^{-1} y, cold start (keeps the force a function of theta_h only)
+  KMV_TRY(run_cg(h, pts, theta_h, y, 0, x_work, cg_tol, cg_maxiter, 0, chain_status, cg_iters,
+                 cg_bufs(h, off), prec, st));
+  // force: d/dtheta [-x^T A x / 2 + phi^T A phi / 2] at frozen x (Eq. u)
+  KMV_CUDA(h, launch_pack_force(L.chains, L.n_total, x_work, phi, Vf, Gf, st));
+  KmvArgs a = base_args(h, pts, theta_h);
+  a.V = Vf;
+  a.G = Gf;
+  a.m = 2;
+  a.Y = nullptr;
+  KMV_TRY(run_backward(h, a, grad, at<double>(h, o_bp), prec, st));
+  // kick + drift
+  KMV_CUDA(h, launch_lf_kick_drift(n_sys, L.n_theta, theta_h, grad, prior_mu, prior_prec, free_mask,
+                                   chain_status, dt, theta, pi, st));
+  return KMV_OK;
+}
+
+kmv_status kmv_energy(kmv_handle h, const kmv_points* pts, int32_t chains, const float* y,
+                      const float* phi, const double* theta, const double* pi,
+                      const double* prior_mu, const double* prior_prec, double cg_tol,
+                      int32_t cg_maxiter, float* x_work, double* H, double* terms,
+                      int32_t* chain_status, int32_t* cg_iters, kmv_precision prec, void* stream) {
+  KMV_TRY(check_points(h, pts, chains));
+  KMV_TRY(check_prec(h, prec));
+  if (!y || !phi || !theta || !x_work || !H || !chain_status) return fail(h, KMV_EINVAL, "NULL argument");
+  if ((prior_mu == nullptr) != (prior_prec == nullptr))
+    return fail(h, KMV_EINVAL, "prior_mu and prior_prec must both be set or both be NULL");
+  if (!(cg_tol > 0.0) || cg_maxiter < 1) return fail(h, KMV_EINVAL, "bad cg_tol / cg_maxiter");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  KMV_TRY(prepare_layout(h, pts, chains, st));
+  const Layout& L = h->layout;
+  Arena ar;
+  size_t off[8];
+  cg_layout(L, ar, off);
+  const size_t vec = (size_t)L.chains * std::max<int64_t>(1, L.n_total);
+  const size_t o_y = ar.take(sizeof(float) * vec);
+  const size_t o_y64 = ar.take(sizeof(double) * vec);
+  const size_t items = (size_t)std::max(1, L.n_items) * L.chains;
+  const size_t o_p1 = ar.take(sizeof(double) * items);
+  const size_t o_p2 = ar.take(sizeof(double) * items);
+  KMV_TRY(reserve(h, ar.used));
+  KMV_TRY(run_cg(h, pts, theta, y, 0, x_work, cg_tol, cg_maxiter, 0, chain_status, cg_iters,
+                 cg_bufs(h, off), prec, st));
+  KmvArgs a = base_args(h, pts, theta);
+  a.V = phi;
+  a.m = 1;
+  a.Y = at<float>(h, o_y);
+  a.Y64 = at<double>(h, o_y64);
+  KMV_TRY(run_forward(h, a, prec, st));
+  if (L.n_items > 0) {
+    KMV_CUDA(h, launch_dot_partial(h->dev, L.n_items, L.chains, L.n_total, y, 0, x_work, nullptr,
+                                   at<double>(h, o_p1), st));
+    KMV_CUDA(h, launch_dot_partial(h->dev, L.n_items, L.chains, L.n_total, phi, L.n_total, nullptr,
+                                   at<double>(h, o_y64), at<double>(h, o_p2), st));
+  }
+  KMV_CUDA(h, launch_energy_finalize(h->dev, L.n_inst, L.chains, L.n_theta, theta, pi, prior_mu,
+                                     prior_prec, at<double>(h, o_p1), at<double>(h, o_p2),
+                                     chain_status, H, terms, st));
+  return KMV_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,139 @@
+// Internal declarations shared by the CUDA translation units of libkmv.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "kmv.h"
+
+namespace kmv {
+
+// Rows per work item of the SIMT kernels and of the reductions built on them.
+constexpr int kTile = 128;
+constexpr int kMaxD = 64;
+// Columns of V handled by one SIMT pass (forward / backward).
+constexpr int kMaxMPFwd = 64;
+constexpr int kMaxMPBwd = 32;
+// exp(-r^2/2) = 2^(-h r^2) with h = log2(e)/2; points are pre-scaled by sqrt(h)/l.
+constexpr double kHalfLog2e = 0.72134752044448170368;
+// The SIMT kernels fold FP32 partial sums into FP64 accumulators every
+// kFoldTiles * kTile columns.
+constexpr int kFoldTiles = 4;
+
+// Host description of one call's point set and its row-tile work items.
+struct Layout {
+  int n_inst = 0, chains = 0, d = 0, ard = 0, n_theta = 0;
+  int64_t n_total = 0;
+  int n_items = 0;
+  int max_items_per_inst = 0;
+  std::vector<int64_t> offsets;     // n_inst + 1
+  std::vector<int32_t> item_inst;   // n_items
+  std::vector<int64_t> item_row0;   // n_items
+  std::vector<int32_t> inst_item0;  // n_inst + 1 prefix over items
+};
+
+// Device copies of a Layout's tables (owned by the handle, cached).
+struct DevLayout {
+  const int64_t* offsets = nullptr;
+  const int32_t* item_inst = nullptr;
+  const int64_t* item_row0 = nullptr;
+  const int32_t* inst_item0 = nullptr;
+};
+
+// Per-system CG state, kept in the handle workspace.
+struct CgSys {
+  double rr, bb, pq, alpha, beta;
+  int32_t iters, status;
+};
+
+// ---------------------------------------------------------------------------
+// Kernel argument blocks
+// ---------------------------------------------------------------------------
+struct KmvArgs {
+  DevLayout L;
+  int chains, d, ard, n_theta;
+  int64_t n_total;
+  const float* x;
+  const double* theta;
+  const float* V;       // (chains, N, m)
+  const float* G;       // backward seed (chains, N, m)
+  int m;
+  const float* col_shift;
+  float* Y;             // forward output / backward dL/dV
+  double* Y64;
+  const int32_t* sys_active;   // optional mask: skip systems with 0
+  double* dot_partial;         // forward m == 1: per-item sum_i V_i Y_i
+  double* grad_partial;        // backward: per-(item, chain, z) partial sums
+  int n_z;                     // column chunks
+};
+
+// SIMT kernels (kmv_simt.cu)
+cudaError_t launch_forward_simt(const KmvArgs& a, int n_items, cudaStream_t st);
+cudaError_t launch_backward_simt(const KmvArgs& a, int n_items, cudaStream_t st);
+int backward_mp(int m);      // columns per backward pass
+int forward_mp(int m);
+
+// Gradient finalisation: sums partials per system in a fixed order and scales.
+cudaError_t launch_grad_finalize(const DevLayout& L, int n_inst, int chains, int n_theta,
+                                 int ard, int d, int n_z, const double* theta,
+                                 const double* partial, double* grad, cudaStream_t st);
+
+// CG / leapfrog / energy kernels (kmv_cg.cu)
+cudaError_t launch_cg_init(const DevLayout& L, int n_items, int chains, int64_t n_total,
+                           const float* rhs, int64_t rhs_stride, const float* q,
+                           float* x, float* r, float* p, int warm, double* partial2, cudaStream_t st);
+cudaError_t launch_cg_reduce_init(const DevLayout& L, int n_inst, int chains, const double* partial2,
+                                  double tol, CgSys* sys, int32_t* active, int32_t* n_active,
+                                  cudaStream_t st);
+cudaError_t launch_cg_reduce_pq(const DevLayout& L, int n_inst, int chains, const double* partial,
+                                CgSys* sys, int32_t* active, cudaStream_t st);
+cudaError_t launch_cg_update_xr(const DevLayout& L, int n_items, int chains, int64_t n_total,
+                                const CgSys* sys, const int32_t* active, float* x, float* r,
+                                const float* p, const float* q, double* partial, cudaStream_t st);
+cudaError_t launch_cg_reduce_rr(const DevLayout& L, int n_inst, int chains, const double* partial,
+                                double tol, int maxiter, CgSys* sys, int32_t* active,
+                                int32_t* n_active, cudaStream_t st);
+cudaError_t launch_cg_update_p(const DevLayout& L, int n_items, int chains, int64_t n_total,
+                               const CgSys* sys, const int32_t* active, const float* r, float* p,
+                               cudaStream_t st);
+cudaError_t launch_cg_finish(int n_sys, const CgSys* sys, int32_t* status, int32_t* iters,
+                             cudaStream_t st);
+
+cudaError_t launch_lf_drift(int n_sys, int n_theta, const double* theta, const double* pi,
+                            const uint8_t* mask, double half_dt, double* theta_h, cudaStream_t st);
+cudaError_t launch_pack_force(int chains, int64_t n_total, const float* xsol, const float* phi,
+                              float* Vf, float* Gf, cudaStream_t st);
+cudaError_t launch_lf_kick_drift(int n_sys, int n_theta, const double* theta_h, const double* grad,
+                                 const double* mu, const double* prec, const uint8_t* mask,
+                                 const int32_t* status, double dt, double* theta, double* pi,
+                                 cudaStream_t st);
+cudaError_t launch_dot_partial(const DevLayout& L, int n_items, int chains, int64_t n_total,
+                               const float* a, int64_t a_stride, const float* b32, const double* b64,
+                               double* partial, cudaStream_t st);
+cudaError_t launch_energy_finalize(const DevLayout& L, int n_inst, int chains, int n_theta,
+                                   const double* theta, const double* pi, const double* mu,
+                                   const double* prec, const double* partial_yx,
+                                   const double* partial_pap, int32_t* status, double* H,
+                                   double* terms, cudaStream_t st);
+
+}  // namespace kmv
+
+// Handle definition (C ABI opaque type).
+struct kmv_handle_s {
+  int device = 0;
+  std::string last_error;
+  // cached device tables for the last layout
+  std::vector<int64_t> cached_offsets;
+  int cached_d = -1;
+  void* tables = nullptr;
+  size_t tables_bytes = 0;
+  kmv::DevLayout dev;
+  kmv::Layout layout;
+  // grow-only workspace arena
+  void* ws = nullptr;
+  size_t ws_bytes = 0;
+  int32_t* host_flag = nullptr;   // pinned, for convergence checks
+};

@@ -1,0 +1,146 @@
+// Plain FP32 forward product Y = A(theta) V on the FMA/MUFU pipes.
+//
+// One CTA of kTile threads owns kTile rows i of one (instance, chain) system
+// and one chunk of at most MP columns of V.  It streams the instance's rows j
+// through shared memory kJT at a time and, per pair, evaluates
+//   K0_ij = 2^(-sum_k (xh_ik - xh_jk)^2),  xh = x sqrt(log2(e)/2) / l,
+// from direct differences (no |x|^2 expansion, so no cancellation), then
+// accumulates K0_ij V_j in FP32, folded into FP64 every 512 columns.
+// Epilogue (Eq. kerdef): Y_i = alpha * acc_i + (sigma^2 + shift) V_i.
+#include "simt_common.cuh"
+
+namespace kmv {
+
+template <int D, int MP>
+__global__ void __launch_bounds__(kTile) fwd_simt_kernel(KmvArgs a) {
+  constexpr int DA = D ? D : kMaxD;
+  constexpr int DP = DA + 1;  // padded row stride of the staged X tile
+  const int dd = D ? D : a.d;
+  const int item = blockIdx.x, c = blockIdx.y, z = blockIdx.z;
+  const int b = a.L.item_inst[item];
+  const int s = b * a.chains + c;
+  if (a.sys_active && !a.sys_active[s]) return;
+
+  __shared__ float sc[DA];
+  __shared__ float sx[kJT * DP];
+  __shared__ float sv[kJT * MP];
+  __shared__ double red[kTile / 32];
+
+  const int64_t j0 = a.L.offsets[b], j1 = a.L.offsets[b + 1];
+  const int64_t r0 = a.L.item_row0[item];
+  const int64_t i = r0 + threadIdx.x;
+  const bool valid = i < j1;
+  const double* th = a.theta + (int64_t)s * a.n_theta;
+  load_scale(th, dd, a.ard, sc);
+  const int c0 = z * MP;
+  const int mc = min(MP, a.m - c0);
+  const int64_t vbase = (int64_t)c * a.n_total;  // row offset of chain c
+  __syncthreads();
+
+  float xi[DA];
+#pragma unroll
+  for (int k = 0; k < DA; ++k) xi[k] = 0.f;
+  if (valid) {
+    for (int k = 0; k < dd; ++k) xi[k] = a.x[i * dd + k] * sc[k];
+  }
+  float acc[MP];
+  double acc64[MP];
+#pragma unroll
+  for (int q = 0; q < MP; ++q) { acc[q] = 0.f; acc64[q] = 0.0; }
+
+  int step = 0;
+  for (int64_t jt = j0; jt < j1; jt += kJT, ++step) {
+    const int nj = (int)min((int64_t)kJT, j1 - jt);
+    for (int e = threadIdx.x; e < kJT * dd; e += kTile) {
+      const int r = e / dd, k = e - r * dd;
+      sx[r * DP + k] = r < nj ? a.x[(jt + r) * dd + k] * sc[k] : 0.f;
+    }
+    for (int e = threadIdx.x; e < kJT * MP; e += kTile) {
+      const int r = e / MP, q = e - r * MP;
+      sv[e] = (r < nj && q < mc) ? a.V[(vbase + jt + r) * a.m + c0 + q] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int jj = 0; jj < kJT; ++jj) {
+      float r2 = 0.f;
+      if (D) {
+#pragma unroll
+        for (int k = 0; k < DA; ++k) {
+          const float df = xi[k] - sx[jj * DP + k];
+          r2 = fmaf(df, df, r2);
+        }
+      } else {
+        for (int k = 0; k < dd; ++k) {
+          const float df = xi[k] - sx[jj * DP + k];
+          r2 = fmaf(df, df, r2);
+        }
+      }
+      const float p = ex2_approx(-r2);
+#pragma unroll
+      for (int q = 0; q < MP; ++q) acc[q] = fmaf(p, sv[jj * MP + q], acc[q]);
+    }
+    __syncthreads();
+    if ((step + 1) % (kFoldTiles * kTile / kJT) == 0) {
+#pragma unroll
+      for (int q = 0; q < MP; ++q) { acc64[q] += (double)acc[q]; acc[q] = 0.f; }
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < MP; ++q) acc64[q] += (double)acc[q];
+
+  const double alpha = exp(th[0]);
+  const double s2 = exp(th[a.n_theta - 1]);
+  double dot = 0.0;
+  if (valid) {
+#pragma unroll
+    for (int q = 0; q < MP; ++q) {
+      if (q < mc) {
+        const int64_t idx = (vbase + i) * a.m + c0 + q;
+        const double shift = a.col_shift ? (double)a.col_shift[c0 + q] : 0.0;
+        const double vi = (double)a.V[idx];
+        const double y = alpha * acc64[q] + (s2 + shift) * vi;
+        a.Y[idx] = (float)y;
+        if (a.Y64) a.Y64[idx] = y;
+        dot += vi * y;
+      }
+    }
+  }
+  if (a.dot_partial) {
+    const double t = block_sum(dot, red);
+    if (threadIdx.x == 0) a.dot_partial[(int64_t)item * a.chains + c] = t;
+  }
+}
+
+int forward_mp(int m) { return m >= kMaxMPFwd ? kMaxMPFwd : pow2ceil(m); }
+
+template <int MP>
+static cudaError_t fwd_by_d(const KmvArgs& a, dim3 grid, cudaStream_t st) {
+  switch (a.d) {
+    case 1: fwd_simt_kernel<1, MP><<<grid, kTile, 0, st>>>(a); break;
+    case 2: fwd_simt_kernel<2, MP><<<grid, kTile, 0, st>>>(a); break;
+    case 3: fwd_simt_kernel<3, MP><<<grid, kTile, 0, st>>>(a); break;
+    case 4: fwd_simt_kernel<4, MP><<<grid, kTile, 0, st>>>(a); break;
+    case 8: fwd_simt_kernel<8, MP><<<grid, kTile, 0, st>>>(a); break;
+    case 16: fwd_simt_kernel<16, MP><<<grid, kTile, 0, st>>>(a); break;
+    case 32: fwd_simt_kernel<32, MP><<<grid, kTile, 0, st>>>(a); break;
+    default: fwd_simt_kernel<0, MP><<<grid, kTile, 0, st>>>(a); break;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_forward_simt(const KmvArgs& a, int n_items, cudaStream_t st) {
+  const int mp = forward_mp(a.m);
+  const int nz = (a.m + mp - 1) / mp;
+  dim3 grid(n_items, a.chains, nz);
+  switch (mp) {
+    case 1: return fwd_by_d<1>(a, grid, st);
+    case 2: return fwd_by_d<2>(a, grid, st);
+    case 4: return fwd_by_d<4>(a, grid, st);
+    case 8: return fwd_by_d<8>(a, grid, st);
+    case 16: return fwd_by_d<16>(a, grid, st);
+    case 32: return fwd_by_d<32>(a, grid, st);
+    default: return fwd_by_d<64>(a, grid, st);
+  }
+}
+
+}  // namespace kmv

@@ -14,10 +14,12 @@ def pytest_configure(config):
 
 
 @pytest.fixture(scope="session")
-def kmv_lib():
-    """The CUDA library binding; GPU tests only."""
+def kmv_handle():
+    """A libkmv handle on cuda:0 (GPU tests only; the library must be built)."""
     import torch
     if not torch.cuda.is_available():
-        pytest.skip("no CUDA device")
-    from paper_2412_20884_gb300 import binding
-    return binding.lib()
+        pytest.fail("GPU test collected without a CUDA device")
+    from paper_2412_20884_gb300 import Kmv
+    h = Kmv(0)
+    yield h
+    h.close()
