@@ -136,4 +136,5 @@ struct kmv_handle_s {
   void* ws = nullptr;
   size_t ws_bytes = 0;
   int32_t* host_flag = nullptr;   // pinned, for convergence checks
+  void* tc = nullptr;             // tensor-core path state (kmv_tc.cu)
 };

@@ -1,21 +1,700 @@
-// Tensor-core (tcgen05) forms of the kernel products.
+// Tensor-core (tcgen05) form of Y = A(theta) V, KMV_BF16_HILO.
+//
+// Layout in HBM (written per call by the prep kernels, per chain c, in
+// 128-row tiles that are byte-for-byte the shared-memory operand layout, so
+// each tile moves with one bulk copy):
+//   XA[c][t] : 128 x KX BF16, rows i:  [hi(xh), hi(xh), lo(xh), 1, 1, 1, bh, bm, bl, 0..]
+//   XB[c][t] : 128 x KX BF16, rows j:  [hi(xh), lo(xh), hi(xh), bh, bm, bl, 1, 1, 1, 0..]
+//   VT[c][t] : MP x 128 F16, V^T of the tile scaled by a per-column power of two
+// with xh = x sqrt(log2(e)) / l and b = -|xh|^2/2 (computed from the split
+// values, so the diagonal exponent is 0) split into three BF16 terms.  One
+// K = KX contraction then gives the base-2 exponent of K0 directly:
+//   S_ij = hi_i.hi_j + hi_i.lo_j + lo_i.hi_j + b_i + b_j = -|xh_i - xh_j|^2/2 + O(2^-16 |xh|^2)
+// and K0_ij = 2^S_ij.  Core matrices are 8 rows x 16 bytes, no swizzle.
+//
+// Main kernel (one CTA per SM, persistent over work items): an item is one
+// pair of 128-row I tiles of one system against a contiguous range of J tiles.
+//   warp 9     : bulk-copy producer (A tiles per item, XB/VT tiles per J step)
+//   warp 8     : MMA issuer; S_g = A_g XB^T into TMEM (two 128x128 FP32
+//                accumulators), then O_g += P_g VT^T with P_g read from TMEM
+//   warps 0-7  : two exp warpgroups, one per I tile: TMEM S -> ex2 -> F16 P
+//                written back over S, and every kFold J tiles the FP32 O
+//                accumulator is folded into an FP64 per-item partial.
+// The two warpgroups run half a tile apart, so one computes while the other
+// waits for its MMAs.  An epilogue kernel sums the per-item partials in a
+// fixed order and applies Y = alpha O + (sigma^2 + shift) V.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
 #include "kmv_tc.cuh"
+#include "simt_common.cuh"
+#include "tc_ptx.cuh"
 
 namespace kmv {
 
+namespace {
+
+constexpr int kFold = 8;           // J tiles per FP32 accumulation before the FP64 fold
+constexpr int kThreads = 320;      // 2 exp warpgroups + MMA warp + producer warp
+constexpr int kMmaWarp = 8;
+constexpr int kLoadWarp = 9;
+constexpr int kMaxKX = 112;        // d <= 35
+constexpr int kMaxMP = 128;        // columns per pass
+constexpr size_t kMinSmem = 120 * 1024;  // keeps one CTA (and one TMEM allocation) per SM
+constexpr size_t kMaxSmem = 227 * 1024;
+
+struct TcFwdArgs {
+  const int4* items;       // {system, I tile (first of 2), first J tile, number of J tiles}
+  int n_items;
+  int chains;
+  int T_total;             // padded tiles per chain
+  int KX, MP, S;
+  const uint8_t* XA;
+  const uint8_t* XB;
+  const uint8_t* VT;
+  double* part;            // (n_items, 256, mz) FP64
+  int mz;                  // columns of this pass
+  const int32_t* sys_active;
+  int* err;
+};
+
+__device__ __forceinline__ uint8_t* align1024(uint8_t* p) {
+  return reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(p) + 1023) & ~uintptr_t(1023));
+}
+
+__global__ void __launch_bounds__(kThreads, 1) tc_fwd_kernel(TcFwdArgs a) {
+  using namespace ptx;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = align1024(smem_raw);
+  const uint32_t A_TILE = a.KX * 256u, V_TILE = a.MP * 256u;
+  const int S = a.S;
+  uint8_t* sA = smem;                       // [buffer 2][tile 2]
+  uint8_t* sB = sA + 4 * A_TILE;            // [stage]
+  uint8_t* sV = sB + S * A_TILE;            // [stage]
+  uint64_t* full = reinterpret_cast<uint64_t*>(sV + S * V_TILE);
+  uint64_t* empty = full + S;
+  uint64_t* a_full = empty + S;
+  uint64_t* a_empty = a_full + 2;
+  uint64_t* s_full = a_empty + 2;
+  uint64_t* p_ready = s_full + 2;
+  uint64_t* o_ready = p_ready + 2;
+  uint64_t* o_free = o_ready + 2;
+  uint64_t* done = o_free + 2;
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(done + 1);
+  volatile int* abort = reinterpret_cast<volatile int*>(tslot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < S; ++i) {
+      mbar_init(&full[i], 1);
+      mbar_init(&empty[i], 1);
+    }
+    for (int g = 0; g < 2; ++g) {
+      mbar_init(&a_full[g], 1);
+      mbar_init(&a_empty[g], 1);
+      mbar_init(&s_full[g], 1);
+      mbar_init(&p_ready[g], 128);
+      mbar_init(&o_ready[g], 1);
+      mbar_init(&o_free[g], 128);
+    }
+    mbar_init(done, 1);
+    *abort = 0;
+    fence_barrier_init();
+  }
+  if (warp == kMmaWarp) {
+    tmem_alloc(tslot, 512);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tbase = *tslot;
+
+  if (warp == kLoadWarp) {
+    if (lane == 0) {
+      // ------------------------------------------------------------ producer
+      int it = 0;
+      uint32_t stage = 0, sph = 0;
+      int n_issued = 0, n_a_issued = 0;
+      bool aborted = false;
+      for (int t = blockIdx.x; t < a.n_items && !aborted; t += gridDim.x) {
+        const int4 item = a.items[t];
+        if (a.sys_active && !a.sys_active[item.x]) continue;
+        const int c = item.x % a.chains;
+        const int ab = it & 1;
+        if (!mbar_wait(&a_empty[ab], ((it >> 1) & 1) ^ 1, abort, a.err, 1)) { aborted = true; break; }
+        mbar_arrive_expect_tx(&a_full[ab], 2 * A_TILE);
+        const uint8_t* xa = a.XA + ((size_t)c * a.T_total + item.y) * A_TILE;
+        bulk_g2s(sA + (2 * ab) * A_TILE, xa, A_TILE, &a_full[ab]);
+        bulk_g2s(sA + (2 * ab + 1) * A_TILE, xa + A_TILE, A_TILE, &a_full[ab]);
+        ++n_a_issued;
+        for (int j = 0; j < item.w; ++j) {
+          if (!mbar_wait(&empty[stage], sph ^ 1, abort, a.err, 2)) { aborted = true; break; }
+          mbar_arrive_expect_tx(&full[stage], A_TILE + V_TILE);
+          const size_t tj = (size_t)c * a.T_total + item.z + j;
+          bulk_g2s(sB + stage * A_TILE, a.XB + tj * A_TILE, A_TILE, &full[stage]);
+          bulk_g2s(sV + stage * V_TILE, a.VT + tj * V_TILE, V_TILE, &full[stage]);
+          ++n_issued;
+          if (++stage == (uint32_t)S) { stage = 0; sph ^= 1; }
+        }
+        ++it;
+      }
+      if (aborted) {
+        // drain: the copies already issued must land before the CTA exits
+        for (int k = 1; k <= min(n_issued, S); ++k) {
+          const int idx = n_issued - k;
+          mbar_drain(&full[idx % S], (idx / S) & 1, 500000000ull);
+        }
+        for (int k = 1; k <= min(n_a_issued, 2); ++k) {
+          const int idx = n_a_issued - k;
+          mbar_drain(&a_full[idx & 1], (idx >> 1) & 1, 500000000ull);
+        }
+      }
+    }
+  } else if (warp == kMmaWarp) {
+    if (lane == 0) {
+      // ------------------------------------------------------------ MMA issuer
+      const uint32_t idS = idesc_f16(128, 128, 1, 1);
+      const uint32_t idP = idesc_f16(128, a.MP, 0, 0);
+      const uint32_t sboX = a.KX * 16u;
+      const int nkx = a.KX / 16;
+      int it = 0;
+      uint32_t stage = 0, sph = 0;
+      uint32_t pph[2] = {0, 0}, oph[2] = {0, 0};
+      bool opend[2] = {false, false};
+      auto issue_S = [&](int g, int ab, uint32_t st) {
+        const uint32_t aaddr = smem_u32(sA + (2 * ab + g) * A_TILE);
+        const uint32_t baddr = smem_u32(sB + st * A_TILE);
+        for (int k = 0; k < nkx; ++k)
+          mma_ss(tbase + g * 128, sdesc(aaddr + 256 * k, 128, sboX), sdesc(baddr + 256 * k, 128, sboX), idS,
+                 k > 0);
+      };
+      auto issue_PV = [&](int g, uint32_t st, uint32_t acc) {
+        const uint32_t vaddr = smem_u32(sV + st * V_TILE);
+        for (int k = 0; k < 8; ++k)
+          mma_ts(tbase + 256 + g * 128, tbase + g * 128 + 8 * k, sdesc(vaddr + 256 * k, 128, 2048), idP,
+                 (k > 0) || acc);
+      };
+      for (int t = blockIdx.x; t < a.n_items; t += gridDim.x) {
+        const int4 item = a.items[t];
+        if (a.sys_active && !a.sys_active[item.x]) continue;
+        const int ab = it & 1;
+        const int nJ = item.w;
+        if (!mbar_wait(&a_full[ab], (it >> 1) & 1, abort, a.err, 3)) goto mma_out;
+        if (!mbar_wait(&full[stage], sph, abort, a.err, 4)) goto mma_out;
+        tc_fence_after();
+        issue_S(0, ab, stage);
+        tc_commit(&s_full[0]);
+        issue_S(1, ab, stage);
+        tc_commit(&s_full[1]);
+        for (int j = 0; j < nJ; ++j) {
+          const uint32_t cur = stage;
+          uint32_t nxt = stage + 1, nph = sph;
+          if (nxt == (uint32_t)S) { nxt = 0; nph ^= 1; }
+          for (int g = 0; g < 2; ++g) {
+            if (!mbar_wait(&p_ready[g], pph[g], abort, a.err, 5)) goto mma_out;
+            pph[g] ^= 1;
+            tc_fence_after();
+            const uint32_t acc = (j % kFold) != 0;
+            if (!acc && opend[g]) {
+              if (!mbar_wait(&o_free[g], oph[g], abort, a.err, 6)) goto mma_out;
+              oph[g] ^= 1;
+              opend[g] = false;
+              tc_fence_after();
+            }
+            issue_PV(g, cur, acc);
+            if ((j % kFold) == kFold - 1 || j == nJ - 1) {
+              tc_commit(&o_ready[g]);
+              opend[g] = true;
+            }
+            if (g == 1) tc_commit(&empty[cur]);
+            if (j + 1 < nJ) {
+              if (g == 0) {
+                if (!mbar_wait(&full[nxt], nph, abort, a.err, 7)) goto mma_out;
+                tc_fence_after();
+              }
+              issue_S(g, ab, nxt);
+              tc_commit(&s_full[g]);
+            }
+          }
+          stage = nxt;
+          sph = nph;
+        }
+        tc_commit(&a_empty[ab]);
+        ++it;
+      }
+    mma_out:
+      tc_commit(done);
+      mbar_drain(done, 0, 500000000ull);
+    }
+    __syncwarp();
+  } else {
+    // ------------------------------------------------------------ exp warpgroups
+    const int g = warp >> 2, w = warp & 3;
+    const int row = 32 * w + lane;
+    const uint32_t tl = tbase + (static_cast<uint32_t>(32 * w) << 16);
+    const uint32_t s_col = g * 128, o_col = 256 + g * 128;
+    uint32_t sph = 0, oph = 0;
+    for (int t = blockIdx.x; t < a.n_items; t += gridDim.x) {
+      const int4 item = a.items[t];
+      if (a.sys_active && !a.sys_active[item.x]) continue;
+      double* prow = a.part + ((size_t)t * 256 + g * 128 + row) * a.mz;
+      bool first = true;
+      for (int j = 0; j < item.w; ++j) {
+        bool ok = mbar_wait(&s_full[g], sph, abort, a.err, 8);
+        if (!__all_sync(0xffffffffu, ok)) goto exp_out;
+        sph ^= 1;
+        tc_fence_after();
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          uint32_t v0[32], v1[32], pk[32];
+          tmem_ld32(tl + s_col + 64 * h, v0);
+          tmem_ld32(tl + s_col + 64 * h + 32, v1);
+          tmem_ld_wait();
+#pragma unroll
+          for (int q = 0; q < 16; ++q)
+            pk[q] = pack_f16x2(ex2(__uint_as_float(v0[2 * q])), ex2(__uint_as_float(v0[2 * q + 1])));
+#pragma unroll
+          for (int q = 0; q < 16; ++q)
+            pk[16 + q] = pack_f16x2(ex2(__uint_as_float(v1[2 * q])), ex2(__uint_as_float(v1[2 * q + 1])));
+          tmem_st32(tl + s_col + 32 * h, pk);
+        }
+        tmem_st_wait();
+        tc_fence_before();
+        mbar_arrive(&p_ready[g]);
+        if ((j % kFold) == kFold - 1 || j == item.w - 1) {
+          ok = mbar_wait(&o_ready[g], oph, abort, a.err, 9);
+          if (!__all_sync(0xffffffffu, ok)) goto exp_out;
+          oph ^= 1;
+          tc_fence_after();
+          for (int c0 = 0; c0 < a.MP; c0 += 16) {
+            uint32_t o[16];
+            tmem_ld16(tl + o_col + c0, o);
+            tmem_ld_wait();
+#pragma unroll
+            for (int q = 0; q < 16; ++q) {
+              const int col = c0 + q;
+              if (col < a.mz) {
+                const double v = (double)__uint_as_float(o[q]);
+                prow[col] = first ? v : prow[col] + v;
+              }
+            }
+          }
+          first = false;
+          tc_fence_before();
+          mbar_arrive(&o_free[g]);
+        }
+      }
+    }
+  exp_out:;
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == kMmaWarp) tmem_dealloc(tbase, 512);
+}
+
+// ------------------------------------------------------------------ prep kernels
+
+struct TcTables {
+  const int32_t* tile_inst;    // T_total
+  const int32_t* inst_tile0;   // n_inst + 1 (padded tiles)
+  const int32_t* sys_item0;    // n_sys
+  const int32_t* inst_nk;      // n_inst
+};
+
+__device__ __forceinline__ uint32_t x_off(int r, int kk, int KX) {
+  return (r & 7) * 16 + (r >> 3) * (KX * 16) + (kk & 7) * 2 + (kk >> 3) * 128;
+}
+
+// One thread per padded row: the A-side and B-side BF16 operand rows.
+__global__ void tc_prep_x_kernel(DevLayout L, TcTables T, int chains, int d, int ard, int n_theta, int KX,
+                                 int T_total, const float* x, const double* theta, uint8_t* XA, uint8_t* XB) {
+  const int t = blockIdx.x, c = blockIdx.y, r = threadIdx.x;
+  const int b = T.tile_inst[t];
+  const int s = b * chains + c;
+  const int64_t nb = L.offsets[b + 1] - L.offsets[b];
+  const int64_t rl = (int64_t)(t - T.inst_tile0[b]) * 128 + r;
+  const bool valid = rl < nb;
+  const size_t base = ((size_t)c * T_total + t) * (size_t)KX * 256;
+  __nv_bfloat16* A = reinterpret_cast<__nv_bfloat16*>(XA + base);
+  __nv_bfloat16* B = reinterpret_cast<__nv_bfloat16*>(XB + base);
+  auto putA = [&](int kk, __nv_bfloat16 v) { A[x_off(r, kk, KX) / 2] = v; };
+  auto putB = [&](int kk, __nv_bfloat16 v) { B[x_off(r, kk, KX) / 2] = v; };
+  const __nv_bfloat16 zero = __float2bfloat16_rn(0.f), one = __float2bfloat16_rn(1.f);
+  if (!valid) {
+    for (int kk = 0; kk < KX; ++kk) {
+      putA(kk, zero);
+      putB(kk, zero);
+    }
+    return;
+  }
+  const int64_t i = L.offsets[b] + rl;
+  const double* th = theta + (int64_t)s * n_theta;
+  double nrm = 0.0;
+  for (int k = 0; k < d; ++k) {
+    // xh = x sqrt(log2 e) / l, so that -|xh_i - xh_j|^2 / 2 = -log2(e) r^2 / 2
+    const float sc = (float)(sqrt(2.0 * kHalfLog2e) * exp(-th[1 + (ard ? k : 0)]));
+    const float xh = x[i * d + k] * sc;
+    const __nv_bfloat16 hi = __float2bfloat16_rn(xh);
+    const __nv_bfloat16 lo = __float2bfloat16_rn(xh - __bfloat162float(hi));
+    const double hd = __bfloat162float(hi), ld = __bfloat162float(lo);
+    nrm += hd * hd + 2.0 * hd * ld;
+    putA(k, hi);
+    putA(d + k, hi);
+    putA(2 * d + k, lo);
+    putB(k, hi);
+    putB(d + k, lo);
+    putB(2 * d + k, hi);
+  }
+  const double bias = -0.5 * nrm;
+  const __nv_bfloat16 bh = __float2bfloat16_rn((float)bias);
+  const double r1 = bias - (double)__bfloat162float(bh);
+  const __nv_bfloat16 bm = __float2bfloat16_rn((float)r1);
+  const __nv_bfloat16 bl = __float2bfloat16_rn((float)(r1 - (double)__bfloat162float(bm)));
+  const int o = 3 * d;
+  putA(o + 0, one);
+  putA(o + 1, one);
+  putA(o + 2, one);
+  putA(o + 3, bh);
+  putA(o + 4, bm);
+  putA(o + 5, bl);
+  putB(o + 0, bh);
+  putB(o + 1, bm);
+  putB(o + 2, bl);
+  putB(o + 3, one);
+  putB(o + 4, one);
+  putB(o + 5, one);
+  for (int kk = o + 6; kk < KX; ++kk) {
+    putA(kk, zero);
+    putB(kk, zero);
+  }
+}
+
+// Per (system, column) max |V| over the instance (as float bits; values >= 0 order like uints).
+__global__ void tc_vmax_kernel(DevLayout L, int chains, int64_t n_total, const float* V, int m, int c0,
+                               int mz, const int32_t* sys_active, uint32_t* vmax) {
+  const int item = blockIdx.x, c = blockIdx.y;
+  const int b = L.item_inst[item];
+  const int s = b * chains + c;
+  if (sys_active && !sys_active[s]) return;
+  const int64_t i = L.item_row0[item] + threadIdx.x;
+  if (i >= L.offsets[b + 1]) return;
+  for (int q = 0; q < mz; ++q) {
+    const float v = fabsf(V[((int64_t)c * n_total + i) * m + c0 + q]);
+    atomicMax(&vmax[(int64_t)s * mz + q], __float_as_uint(v));
+  }
+}
+
+// Power-of-two scale putting the column's max |V| just below 2^14 (F16 range).
+__device__ __forceinline__ float col_scale(uint32_t bits) {
+  const float mx = __uint_as_float(bits);
+  if (!(mx > 0.f) || !isfinite(mx)) return 1.f;
+  int e;
+  frexpf(mx, &e);  // mx = f 2^e, f in [0.5, 1)
+  return ldexpf(1.f, 14 - e);
+}
+
+__global__ void tc_prep_v_kernel(DevLayout L, TcTables T, int chains, int64_t n_total, const float* V, int m,
+                                 int c0, int mz, int MP, int T_total, const uint32_t* vmax,
+                                 const int32_t* sys_active, uint8_t* VT) {
+  const int t = blockIdx.x, c = blockIdx.y, r = threadIdx.x;
+  const int b = T.tile_inst[t];
+  const int s = b * chains + c;
+  if (sys_active && !sys_active[s]) return;
+  const int64_t nb = L.offsets[b + 1] - L.offsets[b];
+  const int64_t rl = (int64_t)(t - T.inst_tile0[b]) * 128 + r;
+  const bool valid = rl < nb;
+  __half* dst = reinterpret_cast<__half*>(VT + ((size_t)c * T_total + t) * (size_t)MP * 256);
+  const int64_t i = L.offsets[b] + rl;
+  for (int q = 0; q < MP; ++q) {
+    float v = 0.f;
+    if (valid && q < mz) v = V[((int64_t)c * n_total + i) * m + c0 + q] * col_scale(vmax[(int64_t)s * mz + q]);
+    const uint32_t off = (q & 7) * 16 + (q >> 3) * 2048 + (r & 7) * 2 + (r >> 3) * 128;
+    dst[off / 2] = __float2half_rn(v);
+  }
+}
+
+// Y = alpha * sum_k part + (sigma^2 + shift) V, per 128-row tile of the product layout.
+__global__ void tc_fwd_epilogue_kernel(DevLayout L, TcTables T, KmvArgs a, int c0, int mz, const double* part,
+                                       const uint32_t* vmax, const int* err) {
+  __shared__ double red[kTile / 32];
+  const int item = blockIdx.x, c = blockIdx.y;
+  const int b = L.item_inst[item];
+  const int s = b * a.chains + c;
+  if (a.sys_active && !a.sys_active[s]) return;
+  const int64_t i = L.item_row0[item] + threadIdx.x;
+  const bool valid = i < L.offsets[b + 1];
+  const int tile_in_inst = (int)((L.item_row0[item] - L.offsets[b]) / 128);
+  const int p = tile_in_inst >> 1, half = tile_in_inst & 1;
+  const int nk = T.inst_nk[b];
+  const int64_t it0 = T.sys_item0[s] + (int64_t)p * nk;
+  const int rowp = half * 128 + threadIdx.x;
+  const double* th = a.theta + (int64_t)s * a.n_theta;
+  const double alpha = exp(th[0]), s2 = exp(th[a.n_theta - 1]);
+  const bool bad = *err != 0;
+  double dot = 0.0;
+  if (valid) {
+    for (int q = 0; q < mz; ++q) {
+      double acc = 0.0;
+      for (int k = 0; k < nk; ++k) acc += part[((it0 + k) * 256 + rowp) * mz + q];
+      const int col = c0 + q;
+      const int64_t idx = ((int64_t)c * a.n_total + i) * a.m + col;
+      const double shift = a.col_shift ? (double)a.col_shift[col] : 0.0;
+      const double vi = (double)a.V[idx];
+      double y = alpha * acc / (double)col_scale(vmax[(int64_t)s * mz + q]) + (s2 + shift) * vi;
+      if (bad) y = __longlong_as_double(0x7ff8000000000000ll);
+      a.Y[idx] = (float)y;
+      if (a.Y64) a.Y64[idx] = y;
+      dot += vi * y;
+    }
+  }
+  if (a.dot_partial) {
+    const double tsum = block_sum(dot, red);
+    if (threadIdx.x == 0) a.dot_partial[(int64_t)item * a.chains + c] = tsum;
+  }
+}
+
+// ------------------------------------------------------------------ host side
+
+struct TcState {
+  // plan key
+  std::vector<int64_t> offsets;
+  int chains = -1;
+  // plan
+  int T_total = 0, n_items = 0;
+  std::vector<int4> items;
+  std::vector<int32_t> tile_inst, inst_tile0, sys_item0, inst_nk;
+  void* tables = nullptr;
+  size_t tables_bytes = 0;
+  TcTables dev{};
+  const int4* d_items = nullptr;
+  // buffers
+  void* buf = nullptr;
+  size_t buf_bytes = 0;
+  int* err = nullptr;
+  int num_sms = 0;
+  bool attr_set = false;
+};
+
+TcState* state(kmv_handle h) {
+  if (!h->tc) h->tc = new TcState();
+  return static_cast<TcState*>(h->tc);
+}
+
+kmv_status tc_fail(kmv_handle h, kmv_status s, const char* msg) {
+  h->last_error = msg;
+  return s;
+}
+
+kmv_status build_plan(kmv_handle h, TcState* S, cudaStream_t st) {
+  const Layout& L = h->layout;
+  if (S->chains == L.chains && S->offsets == L.offsets && S->tables) return KMV_OK;
+  if (S->num_sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&S->num_sms, cudaDevAttrMultiProcessorCount, dev);
+  }
+  const int n_inst = L.n_inst, chains = L.chains;
+  S->inst_tile0.assign(n_inst + 1, 0);
+  S->inst_nk.assign(n_inst, 1);
+  S->tile_inst.clear();
+  int64_t units = 0;
+  for (int b = 0; b < n_inst; ++b) {
+    const int64_t nb = L.offsets[b + 1] - L.offsets[b];
+    const int ntP = (int)(2 * ((nb + 255) / 256));
+    S->inst_tile0[b] = (int32_t)S->tile_inst.size();
+    for (int k = 0; k < ntP; ++k) S->tile_inst.push_back(b);
+    units += (int64_t)chains * (ntP / 2);
+  }
+  S->inst_tile0[n_inst] = (int32_t)S->tile_inst.size();
+  S->T_total = (int)S->tile_inst.size();
+  const int64_t target = (int64_t)S->num_sms * 6;
+  const int64_t nk_all = units > 0 ? std::max<int64_t>(1, (target + units - 1) / units) : 1;
+  S->items.clear();
+  S->sys_item0.assign((size_t)n_inst * chains, 0);
+  for (int b = 0; b < n_inst; ++b) {
+    const int64_t nb = L.offsets[b + 1] - L.offsets[b];
+    const int ntJ = (int)((nb + 127) / 128);
+    const int npair = (int)((nb + 255) / 256);
+    const int nk = (int)std::max<int64_t>(1, std::min<int64_t>(nk_all, ntJ));
+    S->inst_nk[b] = nk;
+    for (int c = 0; c < chains; ++c) {
+      const int s = b * chains + c;
+      S->sys_item0[s] = (int32_t)S->items.size();
+      for (int p = 0; p < npair; ++p)
+        for (int k = 0; k < nk; ++k) {
+          const int j0 = (int)((int64_t)k * ntJ / nk), j1 = (int)((int64_t)(k + 1) * ntJ / nk);
+          S->items.push_back(make_int4(s, S->inst_tile0[b] + 2 * p, S->inst_tile0[b] + j0, j1 - j0));
+        }
+    }
+  }
+  S->n_items = (int)S->items.size();
+  if ((int64_t)S->items.size() > (int64_t(1) << 30)) return tc_fail(h, KMV_EINVAL, "too many tensor-core work items");
+  // upload tables
+  const size_t b_items = sizeof(int4) * std::max<size_t>(1, S->items.size());
+  const size_t b_ti = sizeof(int32_t) * std::max<size_t>(1, S->tile_inst.size());
+  const size_t b_it0 = sizeof(int32_t) * (n_inst + 1);
+  const size_t b_si = sizeof(int32_t) * std::max<size_t>(1, S->sys_item0.size());
+  const size_t b_nk = sizeof(int32_t) * n_inst;
+  auto al = [](size_t v) { return (v + 255) & ~size_t(255); };
+  const size_t total = al(b_items) + al(b_ti) + al(b_it0) + al(b_si) + al(b_nk);
+  if (total > S->tables_bytes) {
+    if (S->tables) {
+      cudaDeviceSynchronize();
+      cudaFree(S->tables);
+      S->tables = nullptr;
+      S->tables_bytes = 0;
+    }
+    if (cudaMalloc(&S->tables, total) != cudaSuccess) {
+      cudaGetLastError();
+      return tc_fail(h, KMV_ENOMEM, "tensor-core table allocation failed");
+    }
+    S->tables_bytes = total;
+  }
+  char* p = static_cast<char*>(S->tables);
+  size_t o = 0;
+  auto up = [&](const void* src, size_t bytes, size_t slot) -> char* {
+    char* dst = p + o;
+    if (bytes) cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st);
+    o += al(slot);
+    return dst;
+  };
+  S->d_items = reinterpret_cast<const int4*>(up(S->items.data(), sizeof(int4) * S->items.size(), b_items));
+  S->dev.tile_inst = reinterpret_cast<const int32_t*>(up(S->tile_inst.data(), sizeof(int32_t) * S->tile_inst.size(), b_ti));
+  S->dev.inst_tile0 = reinterpret_cast<const int32_t*>(up(S->inst_tile0.data(), b_it0, b_it0));
+  S->dev.sys_item0 = reinterpret_cast<const int32_t*>(up(S->sys_item0.data(), sizeof(int32_t) * S->sys_item0.size(), b_si));
+  S->dev.inst_nk = reinterpret_cast<const int32_t*>(up(S->inst_nk.data(), b_nk, b_nk));
+  if (cudaStreamSynchronize(st) != cudaSuccess) return tc_fail(h, KMV_ECUDA, "table upload failed");
+  S->offsets = L.offsets;
+  S->chains = L.chains;
+  return KMV_OK;
+}
+
+kmv_status ensure_buf(kmv_handle h, TcState* S, size_t bytes) {
+  if (bytes <= S->buf_bytes) return KMV_OK;
+  if (S->buf) {
+    cudaDeviceSynchronize();
+    cudaFree(S->buf);
+    S->buf = nullptr;
+    S->buf_bytes = 0;
+  }
+  const size_t want = bytes + bytes / 8 + (1 << 20);
+  if (cudaMalloc(&S->buf, want) != cudaSuccess) {
+    cudaGetLastError();
+    return tc_fail(h, KMV_ENOMEM, "tensor-core workspace allocation failed");
+  }
+  S->buf_bytes = want;
+  return KMV_OK;
+}
+
+}  // namespace
+
 kmv_status tc_forward(kmv_handle h, const KmvArgs& a, cudaStream_t st) {
-  (void)a; (void)st;
-  h->last_error = "KMV_BF16_HILO is not built yet";
-  return KMV_EUNSUPPORTED;
+  const Layout& L = h->layout;
+  const int KX = (3 * a.d + 6 + 15) / 16 * 16;
+  if (KX > kMaxKX) return tc_fail(h, KMV_EUNSUPPORTED, "KMV_BF16_HILO supports d <= 35");
+  TcState* S = state(h);
+  kmv_status stt = build_plan(h, S, st);
+  if (stt != KMV_OK) return stt;
+  if (S->n_items == 0) return KMV_OK;
+  const int n_sys = L.n_inst * L.chains;
+  const size_t A_TILE = (size_t)KX * 256;
+  auto al = [](size_t v) { return (v + 255) & ~size_t(255); };
+  // column chunk: as wide as shared memory allows (at least two pipeline stages)
+  const size_t fixed = 1024 + 4 * A_TILE + 256;
+  int mz_max = std::min(a.m, kMaxMP);
+  auto stages_for = [&](int mz) {
+    const size_t vt = (size_t)std::max(16, (mz + 15) / 16 * 16) * 256;
+    return (int)std::min<size_t>(8, (kMaxSmem - fixed) / (A_TILE + vt + 16));
+  };
+  while (stages_for(mz_max) < 2 && mz_max > 16) mz_max = std::max(16, mz_max / 2);
+  if (stages_for(mz_max) < 2) return tc_fail(h, KMV_EUNSUPPORTED, "tensor-core tiles do not fit in shared memory");
+  const int MPmax = std::max(16, (mz_max + 15) / 16 * 16);
+  const size_t xbytes = al((size_t)L.chains * S->T_total * A_TILE);
+  const size_t vbytes = al((size_t)L.chains * S->T_total * MPmax * 256);
+  const size_t mbytes = al(sizeof(uint32_t) * (size_t)n_sys * mz_max);
+  const size_t pbytes = al(sizeof(double) * (size_t)S->n_items * 256 * mz_max);
+  const size_t total = 2 * xbytes + vbytes + mbytes + pbytes + 256;
+  stt = ensure_buf(h, S, total);
+  if (stt != KMV_OK) return stt;
+  uint8_t* base = static_cast<uint8_t*>(S->buf);
+  uint8_t* XA = base;
+  uint8_t* XB = XA + xbytes;
+  uint8_t* VT = XB + xbytes;
+  uint32_t* vmax = reinterpret_cast<uint32_t*>(VT + vbytes);
+  double* part = reinterpret_cast<double*>(reinterpret_cast<uint8_t*>(vmax) + mbytes);
+  int* err = reinterpret_cast<int*>(reinterpret_cast<uint8_t*>(part) + pbytes);
+  if (!S->attr_set) {
+    if (cudaFuncSetAttribute(tc_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem) !=
+        cudaSuccess)
+      return tc_fail(h, KMV_ECUDA, "cudaFuncSetAttribute failed");
+    S->attr_set = true;
+  }
+  if (cudaMemsetAsync(err, 0, sizeof(int), st) != cudaSuccess) return tc_fail(h, KMV_ECUDA, "memset failed");
+  tc_prep_x_kernel<<<dim3(S->T_total, L.chains), 128, 0, st>>>(h->dev, S->dev, L.chains, a.d, a.ard, a.n_theta, KX,
+                                                                S->T_total, a.x, a.theta, XA, XB);
+  for (int c0 = 0; c0 < a.m; c0 += mz_max) {
+    const int mz = std::min(mz_max, a.m - c0);
+    const int MP = std::max(16, (mz + 15) / 16 * 16);
+    const size_t V_TILE = (size_t)MP * 256;
+    const int stages = stages_for(mz);
+    const size_t smem = std::max(kMinSmem, fixed + stages * (A_TILE + V_TILE) + (2 * stages + 13) * 8);
+    if (cudaMemsetAsync(vmax, 0, sizeof(uint32_t) * (size_t)n_sys * mz, st) != cudaSuccess)
+      return tc_fail(h, KMV_ECUDA, "memset failed");
+    tc_vmax_kernel<<<dim3(L.n_items, L.chains), kTile, 0, st>>>(h->dev, L.chains, L.n_total, a.V, a.m, c0, mz,
+                                                                a.sys_active, vmax);
+    tc_prep_v_kernel<<<dim3(S->T_total, L.chains), 128, 0, st>>>(h->dev, S->dev, L.chains, L.n_total, a.V, a.m, c0,
+                                                                 mz, MP, S->T_total, vmax, a.sys_active, VT);
+    TcFwdArgs fa;
+    fa.items = S->d_items;
+    fa.n_items = S->n_items;
+    fa.chains = L.chains;
+    fa.T_total = S->T_total;
+    fa.KX = KX;
+    fa.MP = MP;
+    fa.S = stages;
+    fa.XA = XA;
+    fa.XB = XB;
+    fa.VT = VT;
+    fa.part = part;
+    fa.mz = mz;
+    fa.sys_active = a.sys_active;
+    fa.err = err;
+    const int grid = std::min(S->n_items, S->num_sms);
+    tc_fwd_kernel<<<grid, kThreads, smem, st>>>(fa);
+    tc_fwd_epilogue_kernel<<<dim3(L.n_items, L.chains), kTile, 0, st>>>(h->dev, S->dev, a, c0, mz, part, vmax, err);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return tc_fail(h, KMV_ECUDA, cudaGetErrorString(e));
+  }
+  return KMV_OK;
 }
 
 kmv_status tc_backward(kmv_handle h, const KmvArgs& a, double* grad, cudaStream_t st) {
-  (void)a; (void)grad; (void)st;
-  h->last_error = "KMV_BF16_HILO is not built yet";
-  return KMV_EUNSUPPORTED;
+  (void)a;
+  (void)grad;
+  (void)st;
+  return tc_fail(h, KMV_EUNSUPPORTED, "KMV_BF16_HILO adjoint is not built yet");
 }
 
-void tc_release(kmv_handle h) { (void)h; }
-size_t tc_workspace_bytes(kmv_handle h) { (void)h; return 0; }
+void tc_release(kmv_handle h) {
+  if (!h->tc) return;
+  TcState* S = static_cast<TcState*>(h->tc);
+  if (S->buf) cudaFree(S->buf);
+  if (S->tables) cudaFree(S->tables);
+  delete S;
+  h->tc = nullptr;
+}
+
+size_t tc_workspace_bytes(kmv_handle h) {
+  if (!h->tc) return 0;
+  const TcState* S = static_cast<const TcState*>(h->tc);
+  return S->buf_bytes + S->tables_bytes;
+}
 
 }  // namespace kmv
