@@ -193,7 +193,12 @@ size_t backward_ws_bytes(const Layout& L, int m) {
 kmv_status run_backward(kmv_handle h, KmvArgs a, double* grad, double* partial,
                         kmv_precision prec, cudaStream_t st) {
   const Layout& L = h->layout;
-  if (prec == KMV_BF16_HILO) return tc_backward(h, a, grad, st);
+  if (prec == KMV_BF16_HILO) {
+    // shapes outside the tensor-core adjoint's range (d > 15, or operand
+    // tiles that do not fit in shared memory) use the FP32 adjoint
+    const kmv_status s = tc_backward(h, a, grad, st);
+    if (s != KMV_EUNSUPPORTED) return s;
+  }
   const int mp = backward_mp(a.m);
   a.n_z = (a.m + mp - 1) / mp;
   a.grad_partial = partial;

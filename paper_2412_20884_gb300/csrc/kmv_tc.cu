@@ -32,20 +32,26 @@
 
 #include "kmv_tc.cuh"
 #include "simt_common.cuh"
+#include "tc_common.cuh"
 #include "tc_ptx.cuh"
 
 namespace kmv {
 
 namespace {
 
-constexpr int kFold = 8;           // J tiles per FP32 accumulation before the FP64 fold
-constexpr int kThreads = 320;      // 2 exp warpgroups + MMA warp + producer warp
-constexpr int kMmaWarp = 8;
-constexpr int kLoadWarp = 9;
-constexpr int kMaxKX = 112;        // d <= 35
-constexpr int kMaxMP = 128;        // columns per pass
-constexpr size_t kMinSmem = 120 * 1024;  // keeps one CTA (and one TMEM allocation) per SM
-constexpr size_t kMaxSmem = 227 * 1024;
+// J tiles accumulated in FP32 in TMEM before the FP64 fold (4096 columns):
+// the fold's FP64 adds are slow on this part, so they are kept rare.
+constexpr int kFold = 32;
+
+// Issues S = A B^T (K = 16 nk) and O (+)= P VT^T (K = 128 from TMEM).
+__device__ __forceinline__ void issue_s(uint32_t d_tmem, uint64_t da, uint64_t db, int nk, uint32_t idesc) {
+  for (int k = 0; k < nk; ++k) ptx::mma_ss(d_tmem, da + 16 * k, db + 16 * k, idesc, k > 0);
+}
+__device__ __forceinline__ void issue_pv(uint32_t d_tmem, uint32_t a_tmem, uint64_t db, uint32_t idesc,
+                                         uint32_t acc) {
+#pragma unroll
+  for (int k = 0; k < 8; ++k) ptx::mma_ts(d_tmem, a_tmem + 8 * k, db + 16 * k, idesc, (k > 0) || acc);
+}
 
 struct TcFwdArgs {
   const int4* items;       // {system, I tile (first of 2), first J tile, number of J tiles}
@@ -62,10 +68,9 @@ struct TcFwdArgs {
   int* err;
 };
 
-__device__ __forceinline__ uint8_t* align1024(uint8_t* p) {
-  return reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(p) + 1023) & ~uintptr_t(1023));
-}
-
+// RM > 0: the FP64 fold accumulators of up to RM columns live in registers;
+// RM == 0: they live in the per-item partial (global read-modify-write).
+template <int RM>
 __global__ void __launch_bounds__(kThreads, 1) tc_fwd_kernel(TcFwdArgs a) {
   using namespace ptx;
   extern __shared__ uint8_t smem_raw[];
@@ -162,64 +167,72 @@ __global__ void __launch_bounds__(kThreads, 1) tc_fwd_kernel(TcFwdArgs a) {
       const uint32_t idP = idesc_f16(128, a.MP, 0, 0);
       const uint32_t sboX = a.KX * 16u;
       const int nkx = a.KX / 16;
+      const uint64_t dA = sdesc(smem_u32(sA), 128, sboX);
+      const uint64_t dB = sdesc(smem_u32(sB), 128, sboX);
+      const uint64_t dV = sdesc(smem_u32(sV), 128, 2048);
       int it = 0;
       uint32_t stage = 0, sph = 0;
-      uint32_t pph[2] = {0, 0}, oph[2] = {0, 0};
-      bool opend[2] = {false, false};
-      auto issue_S = [&](int g, int ab, uint32_t st) {
-        const uint32_t aaddr = smem_u32(sA + (2 * ab + g) * A_TILE);
-        const uint32_t baddr = smem_u32(sB + st * A_TILE);
-        for (int k = 0; k < nkx; ++k)
-          mma_ss(tbase + g * 128, sdesc(aaddr + 256 * k, 128, sboX), sdesc(baddr + 256 * k, 128, sboX), idS,
-                 k > 0);
-      };
-      auto issue_PV = [&](int g, uint32_t st, uint32_t acc) {
-        const uint32_t vaddr = smem_u32(sV + st * V_TILE);
-        for (int k = 0; k < 8; ++k)
-          mma_ts(tbase + 256 + g * 128, tbase + g * 128 + 8 * k, sdesc(vaddr + 256 * k, 128, 2048), idP,
-                 (k > 0) || acc);
-      };
+      uint32_t pph0 = 0, pph1 = 0, oph0 = 0, oph1 = 0;
+      bool opend0 = false, opend1 = false;
       for (int t = blockIdx.x; t < a.n_items; t += gridDim.x) {
         const int4 item = a.items[t];
         if (a.sys_active && !a.sys_active[item.x]) continue;
         const int ab = it & 1;
         const int nJ = item.w;
+        const uint64_t dA0 = sdesc_add(dA, (2 * ab) * A_TILE), dA1 = sdesc_add(dA, (2 * ab + 1) * A_TILE);
         if (!mbar_wait(&a_full[ab], (it >> 1) & 1, abort, a.err, 3)) goto mma_out;
         if (!mbar_wait(&full[stage], sph, abort, a.err, 4)) goto mma_out;
         tc_fence_after();
-        issue_S(0, ab, stage);
+        issue_s(tbase, dA0, sdesc_add(dB, stage * A_TILE), nkx, idS);
         tc_commit(&s_full[0]);
-        issue_S(1, ab, stage);
+        issue_s(tbase + 128, dA1, sdesc_add(dB, stage * A_TILE), nkx, idS);
         tc_commit(&s_full[1]);
         for (int j = 0; j < nJ; ++j) {
           const uint32_t cur = stage;
           uint32_t nxt = stage + 1, nph = sph;
           if (nxt == (uint32_t)S) { nxt = 0; nph ^= 1; }
-          for (int g = 0; g < 2; ++g) {
-            if (!mbar_wait(&p_ready[g], pph[g], abort, a.err, 5)) goto mma_out;
-            pph[g] ^= 1;
+          const uint32_t acc = (j % kFold) != 0;
+          const bool fold = (j % kFold) == kFold - 1 || j == nJ - 1;
+          // ---- I tile 0
+          if (!mbar_wait(&p_ready[0], pph0, abort, a.err, 5)) goto mma_out;
+          pph0 ^= 1;
+          tc_fence_after();
+          if (!acc && opend0) {
+            if (!mbar_wait(&o_free[0], oph0, abort, a.err, 6)) goto mma_out;
+            oph0 ^= 1;
+            opend0 = false;
             tc_fence_after();
-            const uint32_t acc = (j % kFold) != 0;
-            if (!acc && opend[g]) {
-              if (!mbar_wait(&o_free[g], oph[g], abort, a.err, 6)) goto mma_out;
-              oph[g] ^= 1;
-              opend[g] = false;
-              tc_fence_after();
-            }
-            issue_PV(g, cur, acc);
-            if ((j % kFold) == kFold - 1 || j == nJ - 1) {
-              tc_commit(&o_ready[g]);
-              opend[g] = true;
-            }
-            if (g == 1) tc_commit(&empty[cur]);
-            if (j + 1 < nJ) {
-              if (g == 0) {
-                if (!mbar_wait(&full[nxt], nph, abort, a.err, 7)) goto mma_out;
-                tc_fence_after();
-              }
-              issue_S(g, ab, nxt);
-              tc_commit(&s_full[g]);
-            }
+          }
+          issue_pv(tbase + 256, tbase, sdesc_add(dV, cur * V_TILE), idP, acc);
+          if (fold) {
+            tc_commit(&o_ready[0]);
+            opend0 = true;
+          }
+          if (j + 1 < nJ) {
+            if (!mbar_wait(&full[nxt], nph, abort, a.err, 7)) goto mma_out;
+            tc_fence_after();
+            issue_s(tbase, dA0, sdesc_add(dB, nxt * A_TILE), nkx, idS);
+            tc_commit(&s_full[0]);
+          }
+          // ---- I tile 1
+          if (!mbar_wait(&p_ready[1], pph1, abort, a.err, 5)) goto mma_out;
+          pph1 ^= 1;
+          tc_fence_after();
+          if (!acc && opend1) {
+            if (!mbar_wait(&o_free[1], oph1, abort, a.err, 6)) goto mma_out;
+            oph1 ^= 1;
+            opend1 = false;
+            tc_fence_after();
+          }
+          issue_pv(tbase + 384, tbase + 128, sdesc_add(dV, cur * V_TILE), idP, acc);
+          if (fold) {
+            tc_commit(&o_ready[1]);
+            opend1 = true;
+          }
+          tc_commit(&empty[cur]);
+          if (j + 1 < nJ) {
+            issue_s(tbase + 128, dA1, sdesc_add(dB, nxt * A_TILE), nkx, idS);
+            tc_commit(&s_full[1]);
           }
           stage = nxt;
           sph = nph;
@@ -243,6 +256,9 @@ __global__ void __launch_bounds__(kThreads, 1) tc_fwd_kernel(TcFwdArgs a) {
       const int4 item = a.items[t];
       if (a.sys_active && !a.sys_active[item.x]) continue;
       double* prow = a.part + ((size_t)t * 256 + g * 128 + row) * a.mz;
+      double racc[RM > 0 ? RM : 1];
+#pragma unroll
+      for (int q = 0; q < (RM > 0 ? RM : 1); ++q) racc[q] = 0.0;
       bool first = true;
       for (int j = 0; j < item.w; ++j) {
         bool ok = mbar_wait(&s_full[g], sph, abort, a.err, 8);
@@ -271,16 +287,29 @@ __global__ void __launch_bounds__(kThreads, 1) tc_fwd_kernel(TcFwdArgs a) {
           if (!__all_sync(0xffffffffu, ok)) goto exp_out;
           oph ^= 1;
           tc_fence_after();
-          for (int c0 = 0; c0 < a.MP; c0 += 16) {
-            uint32_t o[16];
-            tmem_ld16(tl + o_col + c0, o);
-            tmem_ld_wait();
+          if (RM > 0) {
 #pragma unroll
-            for (int q = 0; q < 16; ++q) {
-              const int col = c0 + q;
-              if (col < a.mz) {
-                const double v = (double)__uint_as_float(o[q]);
-                prow[col] = first ? v : prow[col] + v;
+            for (int c0 = 0; c0 < (RM > 0 ? RM : 16); c0 += 16) {
+              if (c0 < a.MP) {
+                uint32_t o[16];
+                tmem_ld16(tl + o_col + c0, o);
+                tmem_ld_wait();
+#pragma unroll
+                for (int q = 0; q < 16; ++q) racc[c0 + q] += (double)__uint_as_float(o[q]);
+              }
+            }
+          } else {
+            for (int c0 = 0; c0 < a.MP; c0 += 16) {
+              uint32_t o[16];
+              tmem_ld16(tl + o_col + c0, o);
+              tmem_ld_wait();
+#pragma unroll
+              for (int q = 0; q < 16; ++q) {
+                const int col = c0 + q;
+                if (col < a.mz) {
+                  const double v = (double)__uint_as_float(o[q]);
+                  prow[col] = first ? v : prow[col] + v;
+                }
               }
             }
           }
@@ -288,6 +317,11 @@ __global__ void __launch_bounds__(kThreads, 1) tc_fwd_kernel(TcFwdArgs a) {
           tc_fence_before();
           mbar_arrive(&o_free[g]);
         }
+      }
+      if (RM > 0) {
+#pragma unroll
+        for (int q = 0; q < (RM > 0 ? RM : 1); ++q)
+          if (q < a.mz) prow[q] = racc[q];
       }
     }
   exp_out:;
@@ -300,17 +334,6 @@ __global__ void __launch_bounds__(kThreads, 1) tc_fwd_kernel(TcFwdArgs a) {
 }
 
 // ------------------------------------------------------------------ prep kernels
-
-struct TcTables {
-  const int32_t* tile_inst;    // T_total
-  const int32_t* inst_tile0;   // n_inst + 1 (padded tiles)
-  const int32_t* sys_item0;    // n_sys
-  const int32_t* inst_nk;      // n_inst
-};
-
-__device__ __forceinline__ uint32_t x_off(int r, int kk, int KX) {
-  return (r & 7) * 16 + (r >> 3) * (KX * 16) + (kk & 7) * 2 + (kk >> 3) * 128;
-}
 
 // One thread per padded row: the A-side and B-side BF16 operand rows.
 __global__ void tc_prep_x_kernel(DevLayout L, TcTables T, int chains, int d, int ard, int n_theta, int KX,
@@ -391,15 +414,6 @@ __global__ void tc_vmax_kernel(DevLayout L, int chains, int64_t n_total, const f
   }
 }
 
-// Power-of-two scale putting the column's max |V| just below 2^14 (F16 range).
-__device__ __forceinline__ float col_scale(uint32_t bits) {
-  const float mx = __uint_as_float(bits);
-  if (!(mx > 0.f) || !isfinite(mx)) return 1.f;
-  int e;
-  frexpf(mx, &e);  // mx = f 2^e, f in [0.5, 1)
-  return ldexpf(1.f, 14 - e);
-}
-
 __global__ void tc_prep_v_kernel(DevLayout L, TcTables T, int chains, int64_t n_total, const float* V, int m,
                                  int c0, int mz, int MP, int T_total, const uint32_t* vmax,
                                  const int32_t* sys_active, uint8_t* VT) {
@@ -415,8 +429,7 @@ __global__ void tc_prep_v_kernel(DevLayout L, TcTables T, int chains, int64_t n_
   for (int q = 0; q < MP; ++q) {
     float v = 0.f;
     if (valid && q < mz) v = V[((int64_t)c * n_total + i) * m + c0 + q] * col_scale(vmax[(int64_t)s * mz + q]);
-    const uint32_t off = (q & 7) * 16 + (q >> 3) * 2048 + (r & 7) * 2 + (r >> 3) * 128;
-    dst[off / 2] = __float2half_rn(v);
+    dst[t_off(q, r) / 2] = __float2half_rn(v);
   }
 }
 
@@ -462,27 +475,9 @@ __global__ void tc_fwd_epilogue_kernel(DevLayout L, TcTables T, KmvArgs a, int c
 
 // ------------------------------------------------------------------ host side
 
-struct TcState {
-  // plan key
-  std::vector<int64_t> offsets;
-  int chains = -1;
-  // plan
-  int T_total = 0, n_items = 0;
-  std::vector<int4> items;
-  std::vector<int32_t> tile_inst, inst_tile0, sys_item0, inst_nk;
-  void* tables = nullptr;
-  size_t tables_bytes = 0;
-  TcTables dev{};
-  const int4* d_items = nullptr;
-  // buffers
-  void* buf = nullptr;
-  size_t buf_bytes = 0;
-  int* err = nullptr;
-  int num_sms = 0;
-  bool attr_set = false;
-};
+}  // namespace
 
-TcState* state(kmv_handle h) {
+TcState* tc_state(kmv_handle h) {
   if (!h->tc) h->tc = new TcState();
   return static_cast<TcState*>(h->tc);
 }
@@ -492,7 +487,7 @@ kmv_status tc_fail(kmv_handle h, kmv_status s, const char* msg) {
   return s;
 }
 
-kmv_status build_plan(kmv_handle h, TcState* S, cudaStream_t st) {
+kmv_status tc_build_plan(kmv_handle h, TcState* S, cudaStream_t st) {
   const Layout& L = h->layout;
   if (S->chains == L.chains && S->offsets == L.offsets && S->tables) return KMV_OK;
   if (S->num_sms == 0) {
@@ -576,7 +571,7 @@ kmv_status build_plan(kmv_handle h, TcState* S, cudaStream_t st) {
   return KMV_OK;
 }
 
-kmv_status ensure_buf(kmv_handle h, TcState* S, size_t bytes) {
+kmv_status tc_ensure_buf(kmv_handle h, TcState* S, size_t bytes) {
   if (bytes <= S->buf_bytes) return KMV_OK;
   if (S->buf) {
     cudaDeviceSynchronize();
@@ -593,14 +588,24 @@ kmv_status ensure_buf(kmv_handle h, TcState* S, size_t bytes) {
   return KMV_OK;
 }
 
-}  // namespace
+void tc_launch_prep_x(kmv_handle h, TcState* S, const KmvArgs& a, int KX, uint8_t* XA, uint8_t* XB,
+                      cudaStream_t st) {
+  tc_prep_x_kernel<<<dim3(S->T_total, h->layout.chains), 128, 0, st>>>(
+      h->dev, S->dev, h->layout.chains, a.d, a.ard, a.n_theta, KX, S->T_total, a.x, a.theta, XA, XB);
+}
+
+void tc_launch_epilogue(kmv_handle h, TcState* S, const KmvArgs& a, int c0, int mz, const double* part,
+                        const uint32_t* colmax, const int* err, cudaStream_t st) {
+  tc_fwd_epilogue_kernel<<<dim3(h->layout.n_items, h->layout.chains), kTile, 0, st>>>(h->dev, S->dev, a, c0, mz,
+                                                                                      part, colmax, err);
+}
 
 kmv_status tc_forward(kmv_handle h, const KmvArgs& a, cudaStream_t st) {
   const Layout& L = h->layout;
-  const int KX = (3 * a.d + 6 + 15) / 16 * 16;
+  const int KX = x_width(a.d);
   if (KX > kMaxKX) return tc_fail(h, KMV_EUNSUPPORTED, "KMV_BF16_HILO supports d <= 35");
-  TcState* S = state(h);
-  kmv_status stt = build_plan(h, S, st);
+  TcState* S = tc_state(h);
+  kmv_status stt = tc_build_plan(h, S, st);
   if (stt != KMV_OK) return stt;
   if (S->n_items == 0) return KMV_OK;
   const int n_sys = L.n_inst * L.chains;
@@ -621,7 +626,7 @@ kmv_status tc_forward(kmv_handle h, const KmvArgs& a, cudaStream_t st) {
   const size_t mbytes = al(sizeof(uint32_t) * (size_t)n_sys * mz_max);
   const size_t pbytes = al(sizeof(double) * (size_t)S->n_items * 256 * mz_max);
   const size_t total = 2 * xbytes + vbytes + mbytes + pbytes + 256;
-  stt = ensure_buf(h, S, total);
+  stt = tc_ensure_buf(h, S, total);
   if (stt != KMV_OK) return stt;
   uint8_t* base = static_cast<uint8_t*>(S->buf);
   uint8_t* XA = base;
@@ -631,14 +636,15 @@ kmv_status tc_forward(kmv_handle h, const KmvArgs& a, cudaStream_t st) {
   double* part = reinterpret_cast<double*>(reinterpret_cast<uint8_t*>(vmax) + mbytes);
   int* err = reinterpret_cast<int*>(reinterpret_cast<uint8_t*>(part) + pbytes);
   if (!S->attr_set) {
-    if (cudaFuncSetAttribute(tc_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem) !=
-        cudaSuccess)
+    if (cudaFuncSetAttribute(tc_fwd_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem) !=
+            cudaSuccess ||
+        cudaFuncSetAttribute(tc_fwd_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem) !=
+            cudaSuccess)
       return tc_fail(h, KMV_ECUDA, "cudaFuncSetAttribute failed");
     S->attr_set = true;
   }
   if (cudaMemsetAsync(err, 0, sizeof(int), st) != cudaSuccess) return tc_fail(h, KMV_ECUDA, "memset failed");
-  tc_prep_x_kernel<<<dim3(S->T_total, L.chains), 128, 0, st>>>(h->dev, S->dev, L.chains, a.d, a.ard, a.n_theta, KX,
-                                                                S->T_total, a.x, a.theta, XA, XB);
+  tc_launch_prep_x(h, S, a, KX, XA, XB, st);
   for (int c0 = 0; c0 < a.m; c0 += mz_max) {
     const int mz = std::min(mz_max, a.m - c0);
     const int MP = std::max(16, (mz + 15) / 16 * 16);
@@ -667,19 +673,15 @@ kmv_status tc_forward(kmv_handle h, const KmvArgs& a, cudaStream_t st) {
     fa.sys_active = a.sys_active;
     fa.err = err;
     const int grid = std::min(S->n_items, S->num_sms);
-    tc_fwd_kernel<<<grid, kThreads, smem, st>>>(fa);
-    tc_fwd_epilogue_kernel<<<dim3(L.n_items, L.chains), kTile, 0, st>>>(h->dev, S->dev, a, c0, mz, part, vmax, err);
+    if (MP <= 16)
+      tc_fwd_kernel<16><<<grid, kThreads, smem, st>>>(fa);
+    else
+      tc_fwd_kernel<0><<<grid, kThreads, smem, st>>>(fa);
+    tc_launch_epilogue(h, S, a, c0, mz, part, vmax, err, st);
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return tc_fail(h, KMV_ECUDA, cudaGetErrorString(e));
   }
   return KMV_OK;
-}
-
-kmv_status tc_backward(kmv_handle h, const KmvArgs& a, double* grad, cudaStream_t st) {
-  (void)a;
-  (void)grad;
-  (void)st;
-  return tc_fail(h, KMV_EUNSUPPORTED, "KMV_BF16_HILO adjoint is not built yet");
 }
 
 void tc_release(kmv_handle h) {
