@@ -190,6 +190,35 @@ kmv_status kmv_energy(kmv_handle h, const kmv_points* pts, int32_t chains,
                       double* H, double* terms, int32_t* chain_status, int32_t* cg_iters,
                       kmv_precision prec, void* stream);
 
+/*
+ * kmv_backward_noalloc - kmv_backward with KMV_FP32 arithmetic that allocates
+ * no device memory and needs no handle.  The paper has no counterpart: this
+ * entry point exists for callers that cannot call cudaMalloc, such as code
+ * running while its stream is captured into a CUDA graph, code whose device
+ * memory all belongs to its own pool, or loops that cannot take the
+ * synchronisation an allocation may imply.
+ *
+ *   Arguments and results as in kmv_backward (grad_V may be NULL).
+ *   Scratch: a fixed 4 MiB device array inside the library, held by every
+ *     device that loads the library until the process exits.  It stores the
+ *     row-tile tables and the per-tile FP64 partial sums, so a call must fit
+ *       256-byte-aligned (8 (n_inst + 1) + 4 (n_inst + 1) + 12 n_tiles)
+ *       + 8 n_tiles * chains * ceil(m / 32) * n_theta  <=  4 MiB,
+ *     n_tiles = sum_b ceil(N_b / 128); a call that does not fit returns
+ *     KMV_EINVAL before doing any work.  Everything the call reads from the
+ *     array it has written first in the same call, so no clearing is needed.
+ *   Set-up: the first call on a device, with that device current, looks up
+ *     the array's device address (cudaGetSymbolAddress); make that first call
+ *     before any stream capture.
+ *   Concurrency: every call on a device shares the one array; calls whose
+ *     work overlaps on the GPU (other streams, other host threads) race and
+ *     must be ordered by the caller.
+ *   Errors: KMV_EINVAL (bad argument or scratch limit exceeded), KMV_ECUDA.
+ */
+kmv_status kmv_backward_noalloc(const kmv_points* pts, int32_t chains, const double* theta,
+                                const float* V, const float* G, int32_t m, double* grad_theta,
+                                float* grad_V, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

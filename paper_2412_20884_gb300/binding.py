@@ -51,6 +51,7 @@ _SIGS = {
                                 C.c_double, C.c_int32, _P, _P, _P, C.c_int, _P]),
     "kmv_energy": (C.c_int, [_P, C.POINTER(_Points), C.c_int32, _P, _P, _P, _P, _P, _P, C.c_double,
                              C.c_int32, _P, _P, _P, _P, _P, C.c_int, _P]),
+    "kmv_backward_noalloc": (C.c_int, [C.POINTER(_Points), C.c_int32, _P, _P, _P, C.c_int32, _P, _P, _P]),
 }
 
 
@@ -270,6 +271,39 @@ class Kmv:
                                       _ptr(H), _ptr(terms), _ptr(status), _ptr(iters), self._prec(prec),
                                       _stream(stream)))
         return H, terms, status, iters
+
+
+def kmv_backward_noalloc(pts: Points, theta, V, G, want_grad_V=True, grad_theta=None, grad_V=None,
+                         stream=None):
+    """The FP32 adjoint without device allocation or handle (include/kmv.h).
+
+    For callers that cannot allocate device memory (stream capture, their own
+    memory pool, allocation-free loops); its scratch is a fixed 4 MiB array in
+    the library, shared by all calls on a device.  Raises KmvError with status
+    KMV_EINVAL when the problem does not fit that array.
+    """
+    L = lib()
+    n_sys = theta.shape[0]
+    if n_sys % pts.n_inst:
+        raise ValueError("theta rows must be n_inst * chains")
+    chains = n_sys // pts.n_inst
+    _need(theta, torch.float64, "theta", (n_sys, pts.n_theta))
+    m = V.shape[-1]
+    _need(V, torch.float32, "V", (chains, pts.n_total, m))
+    _need(G, torch.float32, "G", V.shape)
+    if grad_theta is None:
+        grad_theta = torch.empty_like(theta)
+    _need(grad_theta, torch.float64, "grad_theta", theta.shape)
+    if want_grad_V and grad_V is None:
+        grad_V = torch.empty_like(V)
+    if grad_V is not None:
+        _need(grad_V, torch.float32, "grad_V", V.shape)
+    st = L.kmv_backward_noalloc(pts.c, chains, _ptr(theta), _ptr(V), _ptr(G), m, _ptr(grad_theta), _ptr(grad_V),
+                                _stream(stream))
+    if st != KMV_OK:
+        what = "bad argument or scratch limit exceeded" if st == KMV_EINVAL else L.kmv_status_string(st).decode()
+        raise KmvError(st, f"kmv_backward_noalloc: {what}")
+    return grad_theta, grad_V
 
 
 _DEFAULT = {}
