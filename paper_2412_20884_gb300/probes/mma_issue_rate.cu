@@ -1,0 +1,58 @@
+// tcgen05.mma issue rate (M=128, K=16, kind::f16) from 1, 2 or 4 issuing warps into separate accumulators.
+// Build and run (from this folder): nvcc -std=c++17 -O3 -gencode arch=compute_103a,code=sm_103a -o mma_issue_rate mma_issue_rate.cu && ./mma_issue_rate
+#include <cstdio>
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include "../csrc/tc_ptx.cuh"
+using namespace kmv::ptx;
+template <int N>
+__global__ void __launch_bounds__(128,1) probe(int nwarps, int reps, long long* out, int* err) {
+  extern __shared__ __align__(1024) uint8_t sm[];
+  uint64_t* bar = (uint64_t*)(sm + 65536);
+  uint32_t* slot = (uint32_t*)(bar + 4);
+  volatile int* abort = (volatile int*)(slot + 1);
+  for (int i = threadIdx.x; i < 65536 / 4; i += blockDim.x) ((uint32_t*)sm)[i] = 0;
+  if (threadIdx.x == 0) { for (int i = 0; i < 4; ++i) mbar_init(&bar[i], 1); *abort = 0; fence_barrier_init(); }
+  if (threadIdx.x < 32) { tmem_alloc(slot, 512); tmem_relinquish(); }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  tc_fence_before(); __syncthreads(); tc_fence_after();
+  uint32_t tb = *slot;
+  const int w = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0 && w < nwarps) {
+    const uint64_t da = sdesc(smem_u32(sm), 128, 512);
+    const uint64_t db = sdesc(smem_u32(sm + 32768), 128, 512);
+    const uint32_t idb = idesc_f16(128, N, 1, 1);
+    const uint32_t d = tb + 128 * w;
+    long long t0 = clock64();
+    for (int r = 0; r < reps; r += 8) {
+#pragma unroll
+      for (int u = 0; u < 8; ++u) mma_ss(d, da, db, idb, 1);
+    }
+    long long t1 = clock64();
+    tc_commit(&bar[w]);
+    bool ok = mbar_wait(&bar[w], 0, abort, err, 1);
+    long long t2 = clock64();
+    if (blockIdx.x == 0 && w == 0) { out[0] = t1 - t0; out[1] = t2 - t0; out[2] = ok; }
+  }
+  tc_fence_before(); __syncthreads(); tc_fence_after();
+  if (threadIdx.x < 32) tmem_dealloc(tb, 512);
+}
+int main() {
+  long long* out; int* err; cudaMalloc(&out, 64); cudaMalloc(&err, 4); cudaMemset(err, 0, 4);
+  cudaFuncSetAttribute(probe<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, 140 * 1024);
+  cudaFuncSetAttribute(probe<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, 140 * 1024);
+  const int reps = 512;
+  for (int nw : {1, 2, 4}) {
+    long long h[3];
+    probe<16><<<152, 128, 140 * 1024>>>(nw, reps, out, err);
+    cudaMemcpy(h, out, sizeof(h), cudaMemcpyDeviceToHost);
+    printf("N=16  warps=%d: issue %.1f clk/instr/warp, complete %.1f (ok=%lld)\n", nw, (double)h[0]/reps, (double)h[1]/reps, h[2]);
+    probe<128><<<152, 128, 140 * 1024>>>(nw, reps, out, err);
+    cudaMemcpy(h, out, sizeof(h), cudaMemcpyDeviceToHost);
+    printf("N=128 warps=%d: issue %.1f clk/instr/warp, complete %.1f (ok=%lld)\n", nw, (double)h[0]/reps, (double)h[1]/reps, h[2]);
+  }
+  int e; cudaMemcpy(&e, err, 4, cudaMemcpyDeviceToHost);
+  cudaError_t ce = cudaDeviceSynchronize();
+  printf("err=%d cuda=%s\n", e, cudaGetErrorString(ce));
+  return ce == cudaSuccess ? 0 : 1;
+}
