@@ -14,15 +14,18 @@
 //
 // Main kernel (one CTA per SM, persistent over work items): an item is one
 // pair of 128-row I tiles of one system against a contiguous range of J tiles.
-//   warp 9     : bulk-copy producer (A tiles per item, XB/VT tiles per J step)
-//   warp 8     : MMA issuer; S_g = A_g XB^T into TMEM (two 128x128 FP32
-//                accumulators), then O_g += P_g VT^T with P_g read from TMEM
-//   warps 0-7  : two exp warpgroups, one per I tile: TMEM S -> ex2 -> F16 P
-//                written back over S, and every kFold J tiles the FP32 O
-//                accumulator is folded into an FP64 per-item partial.
-// The two warpgroups run half a tile apart, so one computes while the other
-// waits for its MMAs.  An epilogue kernel sums the per-item partials in a
-// fixed order and applies Y = alpha O + (sigma^2 + shift) V.
+//   warp 9       : bulk-copy producer (A tiles per item, XB/VT tiles per J step)
+//   warps 8, 10  : one MMA issuer per I tile g: S_g = A_g XB^T into TMEM (a
+//                  128x128 FP32 accumulator), then O_g += P_g VT^T with P_g
+//                  read from TMEM.  Two issuers let the two tiles' thin P.V
+//                  MMAs overlap in the tensor pipe and keep the warpgroups
+//                  independent of each other.
+//   warps 0-7    : two exp warpgroups, one per I tile: TMEM S -> ex2 -> F16 P
+//                  written back over S (the second half tile's TMEM loads
+//                  overlap the first half's exps), and every kFold J tiles
+//                  the FP32 O accumulator is folded into FP64.
+// An epilogue kernel sums the per-item partials in a fixed order and applies
+// Y = alpha O + (sigma^2 + shift) V.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -42,6 +45,10 @@ namespace {
 // J tiles accumulated in FP32 in TMEM before the FP64 fold (4096 columns):
 // the fold's FP64 adds are slow on this part, so they are kept rare.
 constexpr int kFold = 32;
+// Forward warp roles: warps 0-7 two exp warpgroups, warp 8 MMA issuer for I
+// tile 0 (and TMEM owner), warp 9 producer, warp 10 MMA issuer for I tile 1.
+constexpr int kFwdThreads = 352;
+constexpr int kIssue1Warp = 10;
 
 // Issues S = A B^T (K = 16 nk) and O (+)= P VT^T (K = 128 from TMEM).
 __device__ __forceinline__ void issue_s(uint32_t d_tmem, uint64_t da, uint64_t db, int nk, uint32_t idesc) {
@@ -71,7 +78,7 @@ struct TcFwdArgs {
 // RM > 0: the FP64 fold accumulators of up to RM columns live in registers;
 // RM == 0: they live in the per-item partial (global read-modify-write).
 template <int RM>
-__global__ void __launch_bounds__(kThreads, 1) tc_fwd_kernel(TcFwdArgs a) {
+__global__ void __launch_bounds__(kFwdThreads, 1) tc_fwd_kernel(TcFwdArgs a) {
   using namespace ptx;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = align1024(smem_raw);
@@ -84,29 +91,33 @@ __global__ void __launch_bounds__(kThreads, 1) tc_fwd_kernel(TcFwdArgs a) {
   uint64_t* empty = full + S;
   uint64_t* a_full = empty + S;
   uint64_t* a_empty = a_full + 2;
-  uint64_t* s_full = a_empty + 2;
-  uint64_t* p_ready = s_full + 2;
-  uint64_t* o_ready = p_ready + 2;
+  uint64_t* s_full = a_empty + 2;    // [g] S_g written by the tensor core
+  uint64_t* s_free = s_full + 2;     // [g] S_g read into registers by warpgroup g
+  uint64_t* p_ready = s_free + 2;    // [g] P_g written by warpgroup g
+  uint64_t* p_free = p_ready + 2;    // [g] P_g consumed by the P.V MMAs
+  uint64_t* o_ready = p_free + 2;
   uint64_t* o_free = o_ready + 2;
-  uint64_t* done = o_free + 2;
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(done + 1);
+  uint64_t* done = o_free + 2;       // [g]
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(done + 2);
   volatile int* abort = reinterpret_cast<volatile int*>(tslot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
     for (int i = 0; i < S; ++i) {
       mbar_init(&full[i], 1);
-      mbar_init(&empty[i], 1);
+      mbar_init(&empty[i], 2);
     }
     for (int g = 0; g < 2; ++g) {
       mbar_init(&a_full[g], 1);
-      mbar_init(&a_empty[g], 1);
+      mbar_init(&a_empty[g], 2);
       mbar_init(&s_full[g], 1);
+      mbar_init(&s_free[g], 128);
       mbar_init(&p_ready[g], 128);
+      mbar_init(&p_free[g], 1);
       mbar_init(&o_ready[g], 1);
       mbar_init(&o_free[g], 128);
+      mbar_init(&done[g], 1);
     }
-    mbar_init(done, 1);
     *abort = 0;
     fence_barrier_init();
   }
@@ -118,6 +129,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_fwd_kernel(TcFwdArgs a) {
   __syncthreads();
   tc_fence_after();
   const uint32_t tbase = *tslot;
+  // TMEM columns: S_g [128 g, 128 g + 128), P_g [256 + 64 g, +64), O_g [384 + 64 g, +MP)
 
   if (warp == kLoadWarp) {
     if (lane == 0) {
@@ -133,9 +145,8 @@ __global__ void __launch_bounds__(kThreads, 1) tc_fwd_kernel(TcFwdArgs a) {
         const int ab = it & 1;
         if (!mbar_wait(&a_empty[ab], ((it >> 1) & 1) ^ 1, abort, a.err, 1)) { aborted = true; break; }
         mbar_arrive_expect_tx(&a_full[ab], 2 * A_TILE);
-        const uint8_t* xa = a.XA + ((size_t)c * a.T_total + item.y) * A_TILE;
-        bulk_g2s(sA + (2 * ab) * A_TILE, xa, A_TILE, &a_full[ab]);
-        bulk_g2s(sA + (2 * ab + 1) * A_TILE, xa + A_TILE, A_TILE, &a_full[ab]);
+        bulk_g2s(sA + (2 * ab) * A_TILE, a.XA + ((size_t)c * a.T_total + item.y) * A_TILE, 2 * A_TILE,
+                 &a_full[ab]);
         ++n_a_issued;
         for (int j = 0; j < item.w; ++j) {
           if (!mbar_wait(&empty[stage], sph ^ 1, abort, a.err, 2)) { aborted = true; break; }
@@ -160,89 +171,94 @@ __global__ void __launch_bounds__(kThreads, 1) tc_fwd_kernel(TcFwdArgs a) {
         }
       }
     }
-  } else if (warp == kMmaWarp) {
+  } else if (warp == kMmaWarp || warp == kIssue1Warp) {
     if (lane == 0) {
-      // ------------------------------------------------------------ MMA issuer
+      // ------------------------------------------------------------ MMA issuer of I tile g
+      // Tile stream k = 0, 1, ... over this CTA's items.  For tile k it issues
+      // S(k) once warpgroup g has read S(k-1), then P.V of tile k-1 once P(k-1)
+      // is written, so the tensor core computes the next S while the
+      // warpgroup computes exps, and P.V runs during the next tile's exps.
+      const int g = warp == kMmaWarp ? 0 : 1;
       const uint32_t idS = idesc_f16(128, 128, 1, 1);
       const uint32_t idP = idesc_f16(128, a.MP, 0, 0);
       const uint32_t sboX = a.KX * 16u;
       const int nkx = a.KX / 16;
-      const uint64_t dA = sdesc(smem_u32(sA), 128, sboX);
+      const uint64_t dA = sdesc(smem_u32(sA + g * A_TILE), 128, sboX);
       const uint64_t dB = sdesc(smem_u32(sB), 128, sboX);
       const uint64_t dV = sdesc(smem_u32(sV), 128, 2048);
+      const uint32_t s_tmem = tbase + g * 128, p_tmem = tbase + 256 + g * 64, o_tmem = tbase + 384 + g * 64;
       int it = 0;
       uint32_t stage = 0, sph = 0;
-      uint32_t pph0 = 0, pph1 = 0, oph0 = 0, oph1 = 0;
-      bool opend0 = false, opend1 = false;
+      uint32_t sf_ph = 0, pr_ph = 0, of_ph = 0;
+      bool opend = false;
+      long long k = 0;
+      // the previous tile, whose P.V is still to be issued
+      bool have_prev = false;
+      uint32_t prev_stage = 0;
+      int prev_j = 0, prev_nJ = 0, prev_ab = 0;
       for (int t = blockIdx.x; t < a.n_items; t += gridDim.x) {
         const int4 item = a.items[t];
         if (a.sys_active && !a.sys_active[item.x]) continue;
         const int ab = it & 1;
-        const int nJ = item.w;
-        const uint64_t dA0 = sdesc_add(dA, (2 * ab) * A_TILE), dA1 = sdesc_add(dA, (2 * ab + 1) * A_TILE);
-        if (!mbar_wait(&a_full[ab], (it >> 1) & 1, abort, a.err, 3)) goto mma_out;
-        if (!mbar_wait(&full[stage], sph, abort, a.err, 4)) goto mma_out;
-        tc_fence_after();
-        issue_s(tbase, dA0, sdesc_add(dB, stage * A_TILE), nkx, idS);
-        tc_commit(&s_full[0]);
-        issue_s(tbase + 128, dA1, sdesc_add(dB, stage * A_TILE), nkx, idS);
-        tc_commit(&s_full[1]);
-        for (int j = 0; j < nJ; ++j) {
-          const uint32_t cur = stage;
-          uint32_t nxt = stage + 1, nph = sph;
-          if (nxt == (uint32_t)S) { nxt = 0; nph ^= 1; }
-          const uint32_t acc = (j % kFold) != 0;
-          const bool fold = (j % kFold) == kFold - 1 || j == nJ - 1;
-          // ---- I tile 0
-          if (!mbar_wait(&p_ready[0], pph0, abort, a.err, 5)) goto mma_out;
-          pph0 ^= 1;
+        const uint64_t dAg = sdesc_add(dA, 2 * ab * A_TILE);
+        for (int j = 0; j < item.w; ++j, ++k) {
+          // ---- S(k)
+          if (k > 0) {
+            if (!mbar_wait(&s_free[g], sf_ph, abort, a.err, 3)) goto mma_out;
+            sf_ph ^= 1;
+          }
+          if (j == 0 && !mbar_wait(&a_full[ab], (it >> 1) & 1, abort, a.err, 4)) goto mma_out;
+          if (!mbar_wait(&full[stage], sph, abort, a.err, 5)) goto mma_out;
           tc_fence_after();
-          if (!acc && opend0) {
-            if (!mbar_wait(&o_free[0], oph0, abort, a.err, 6)) goto mma_out;
-            oph0 ^= 1;
-            opend0 = false;
+          issue_s(s_tmem, dAg, sdesc_add(dB, stage * A_TILE), nkx, idS);
+          tc_commit(&s_full[g]);
+          // ---- P.V of tile k-1
+          if (have_prev) {
+            if (!mbar_wait(&p_ready[g], pr_ph, abort, a.err, 6)) goto mma_out;
+            pr_ph ^= 1;
             tc_fence_after();
+            const uint32_t acc = (prev_j % kFold) != 0;
+            if (!acc && opend) {
+              if (!mbar_wait(&o_free[g], of_ph, abort, a.err, 7)) goto mma_out;
+              of_ph ^= 1;
+              opend = false;
+              tc_fence_after();
+            }
+            issue_pv(o_tmem, p_tmem, sdesc_add(dV, prev_stage * V_TILE), idP, acc);
+            tc_commit(&p_free[g]);
+            if ((prev_j % kFold) == kFold - 1 || prev_j == prev_nJ - 1) {
+              tc_commit(&o_ready[g]);
+              opend = true;
+            }
+            tc_commit(&empty[prev_stage]);
+            if (prev_j == prev_nJ - 1) tc_commit(&a_empty[prev_ab]);
           }
-          issue_pv(tbase + 256, tbase, sdesc_add(dV, cur * V_TILE), idP, acc);
-          if (fold) {
-            tc_commit(&o_ready[0]);
-            opend0 = true;
-          }
-          if (j + 1 < nJ) {
-            if (!mbar_wait(&full[nxt], nph, abort, a.err, 7)) goto mma_out;
-            tc_fence_after();
-            issue_s(tbase, dA0, sdesc_add(dB, nxt * A_TILE), nkx, idS);
-            tc_commit(&s_full[0]);
-          }
-          // ---- I tile 1
-          if (!mbar_wait(&p_ready[1], pph1, abort, a.err, 5)) goto mma_out;
-          pph1 ^= 1;
-          tc_fence_after();
-          if (!acc && opend1) {
-            if (!mbar_wait(&o_free[1], oph1, abort, a.err, 6)) goto mma_out;
-            oph1 ^= 1;
-            opend1 = false;
-            tc_fence_after();
-          }
-          issue_pv(tbase + 384, tbase + 128, sdesc_add(dV, cur * V_TILE), idP, acc);
-          if (fold) {
-            tc_commit(&o_ready[1]);
-            opend1 = true;
-          }
-          tc_commit(&empty[cur]);
-          if (j + 1 < nJ) {
-            issue_s(tbase + 128, dA1, sdesc_add(dB, nxt * A_TILE), nkx, idS);
-            tc_commit(&s_full[1]);
-          }
-          stage = nxt;
-          sph = nph;
+          have_prev = true;
+          prev_stage = stage;
+          prev_j = j;
+          prev_nJ = item.w;
+          prev_ab = ab;
+          if (++stage == (uint32_t)S) { stage = 0; sph ^= 1; }
         }
-        tc_commit(&a_empty[ab]);
         ++it;
       }
+      if (have_prev) {
+        if (!mbar_wait(&p_ready[g], pr_ph, abort, a.err, 6)) goto mma_out;
+        tc_fence_after();
+        const uint32_t acc = (prev_j % kFold) != 0;
+        if (!acc && opend) {
+          if (!mbar_wait(&o_free[g], of_ph, abort, a.err, 7)) goto mma_out;
+          tc_fence_after();
+        }
+        issue_pv(o_tmem, p_tmem, sdesc_add(dV, prev_stage * V_TILE), idP, acc);
+        tc_commit(&p_free[g]);
+        tc_commit(&o_ready[g]);
+        tc_commit(&empty[prev_stage]);
+        tc_commit(&a_empty[prev_ab]);
+      }
     mma_out:
-      tc_commit(done);
-      mbar_drain(done, 0, 500000000ull);
+      tc_commit(&done[g]);
+      mbar_drain(&done[g], 0, 500000000ull);
     }
     __syncwarp();
   } else {
@@ -250,8 +266,9 @@ __global__ void __launch_bounds__(kThreads, 1) tc_fwd_kernel(TcFwdArgs a) {
     const int g = warp >> 2, w = warp & 3;
     const int row = 32 * w + lane;
     const uint32_t tl = tbase + (static_cast<uint32_t>(32 * w) << 16);
-    const uint32_t s_col = g * 128, o_col = 256 + g * 128;
-    uint32_t sph = 0, oph = 0;
+    const uint32_t s_col = g * 128, p_col = 256 + g * 64, o_col = 384 + g * 64;
+    uint32_t sph = 0, pf_ph = 0, oph = 0;
+    long long k = 0;
     for (int t = blockIdx.x; t < a.n_items; t += gridDim.x) {
       const int4 item = a.items[t];
       if (a.sys_active && !a.sys_active[item.x]) continue;
@@ -260,24 +277,43 @@ __global__ void __launch_bounds__(kThreads, 1) tc_fwd_kernel(TcFwdArgs a) {
 #pragma unroll
       for (int q = 0; q < (RM > 0 ? RM : 1); ++q) racc[q] = 0.0;
       bool first = true;
-      for (int j = 0; j < item.w; ++j) {
+      for (int j = 0; j < item.w; ++j, ++k) {
         bool ok = mbar_wait(&s_full[g], sph, abort, a.err, 8);
         if (!__all_sync(0xffffffffu, ok)) goto exp_out;
         sph ^= 1;
         tc_fence_after();
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          uint32_t v0[32], v1[32], pk[32];
-          tmem_ld32(tl + s_col + 64 * h, v0);
-          tmem_ld32(tl + s_col + 64 * h + 32, v1);
+        {
+          uint32_t a0[32], a1[32], b0[32], b1[32], pk[32];
+          tmem_ld32(tl + s_col, a0);
+          tmem_ld32(tl + s_col + 32, a1);
           tmem_ld_wait();
+          tmem_ld32(tl + s_col + 64, b0);
+          tmem_ld32(tl + s_col + 96, b1);
 #pragma unroll
           for (int q = 0; q < 16; ++q)
-            pk[q] = pack_f16x2(ex2(__uint_as_float(v0[2 * q])), ex2(__uint_as_float(v0[2 * q + 1])));
+            pk[q] = pack_f16x2(ex2(__uint_as_float(a0[2 * q])), ex2(__uint_as_float(a0[2 * q + 1])));
 #pragma unroll
           for (int q = 0; q < 16; ++q)
-            pk[16 + q] = pack_f16x2(ex2(__uint_as_float(v1[2 * q])), ex2(__uint_as_float(v1[2 * q + 1])));
-          tmem_st32(tl + s_col + 32 * h, pk);
+            pk[16 + q] = pack_f16x2(ex2(__uint_as_float(a1[2 * q])), ex2(__uint_as_float(a1[2 * q + 1])));
+          tmem_ld_wait();
+          // S(k) is fully in registers: the tensor core may overwrite it
+          tc_fence_before();
+          mbar_arrive(&s_free[g]);
+          if (k > 0) {
+            // P(k-1) must have been consumed before P(k) overwrites it
+            ok = mbar_wait(&p_free[g], pf_ph, abort, a.err, 10);
+            if (!__all_sync(0xffffffffu, ok)) goto exp_out;
+            pf_ph ^= 1;
+            tc_fence_after();
+          }
+          tmem_st32(tl + p_col, pk);
+#pragma unroll
+          for (int q = 0; q < 16; ++q)
+            pk[q] = pack_f16x2(ex2(__uint_as_float(b0[2 * q])), ex2(__uint_as_float(b0[2 * q + 1])));
+#pragma unroll
+          for (int q = 0; q < 16; ++q)
+            pk[16 + q] = pack_f16x2(ex2(__uint_as_float(b1[2 * q])), ex2(__uint_as_float(b1[2 * q + 1])));
+          tmem_st32(tl + p_col + 32, pk);
         }
         tmem_st_wait();
         tc_fence_before();
@@ -650,7 +686,7 @@ kmv_status tc_forward(kmv_handle h, const KmvArgs& a, cudaStream_t st) {
     const int MP = std::max(16, (mz + 15) / 16 * 16);
     const size_t V_TILE = (size_t)MP * 256;
     const int stages = stages_for(mz);
-    const size_t smem = std::max(kMinSmem, fixed + stages * (A_TILE + V_TILE) + (2 * stages + 13) * 8);
+    const size_t smem = std::max(kMinSmem, fixed + stages * (A_TILE + V_TILE) + (2 * stages + 20) * 8);
     if (cudaMemsetAsync(vmax, 0, sizeof(uint32_t) * (size_t)n_sys * mz, st) != cudaSuccess)
       return tc_fail(h, KMV_ECUDA, "memset failed");
     tc_vmax_kernel<<<dim3(L.n_items, L.chains), kTile, 0, st>>>(h->dev, L.chains, L.n_total, a.V, a.m, c0, mz,
@@ -674,9 +710,9 @@ kmv_status tc_forward(kmv_handle h, const KmvArgs& a, cudaStream_t st) {
     fa.err = err;
     const int grid = std::min(S->n_items, S->num_sms);
     if (MP <= 16)
-      tc_fwd_kernel<16><<<grid, kThreads, smem, st>>>(fa);
+      tc_fwd_kernel<16><<<grid, kFwdThreads, smem, st>>>(fa);
     else
-      tc_fwd_kernel<0><<<grid, kThreads, smem, st>>>(fa);
+      tc_fwd_kernel<0><<<grid, kFwdThreads, smem, st>>>(fa);
     tc_launch_epilogue(h, S, a, c0, mz, part, vmax, err, st);
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return tc_fail(h, KMV_ECUDA, cudaGetErrorString(e));

@@ -14,7 +14,7 @@ constexpr int kThreads = 320;      // 2 exp warpgroups + MMA warp + producer war
 constexpr int kMmaWarp = 8;
 constexpr int kLoadWarp = 9;
 constexpr int kMaxKX = 112;        // d <= 35 (X operand width, BF16 elements)
-constexpr int kMaxMP = 128;        // forward columns per pass
+constexpr int kMaxMP = 64;         // forward columns per pass (O_g holds 64 TMEM columns)
 constexpr size_t kMinSmem = 120 * 1024;  // keeps one CTA (and one TMEM allocation) per SM
 constexpr size_t kMaxSmem = 227 * 1024;
 
