@@ -133,6 +133,10 @@ kmv_status kmv_backward(kmv_handle h, const kmv_points* pts, int32_t chains,
  *                otherwise ignored; overwritten with the solution.
  *   chain_status DEVICE int32 (n_inst * chains): KMV_OK or KMV_ENOTCONV.
  *   iters        DEVICE int32 (n_inst * chains) or NULL: iterations used.
+ * KMV_BF16_HILO solves by mixed-precision iterative refinement: the residual
+ * rhs - A x is formed with the FP32 operator and each correction is solved by
+ * CG with the tensor-core operator to 1e-3, so the result meets `tol` against
+ * the FP32 operator; `iters` then counts the tensor-core CG iterations.
  * Synchronises `stream` once every few iterations to test convergence on the
  * host, so this call (and the calls built on it) cannot be stream-captured.
  */

@@ -286,6 +286,122 @@ kmv_status run_cg(kmv_handle h, const kmv_points* pts, const double* theta, cons
   return KMV_OK;
 }
 
+// Extra buffers of the refined (KMV_BF16_HILO) solve.
+struct RefineBufs {
+  float *q32, *r, *dx, *pdummy;
+  double *partial2, *prev_rr;
+  CgSys* sys;
+  int32_t *active, *n_active, *in_status, *in_iters;
+};
+
+void refine_layout(const Layout& L, Arena& ar, size_t off[11]) {
+  const size_t vec = sizeof(float) * (size_t)L.chains * std::max<int64_t>(1, L.n_total);
+  const size_t items = (size_t)std::max(1, L.n_items) * L.chains;
+  const size_t n_sys = (size_t)L.n_inst * L.chains;
+  off[0] = ar.take(vec);
+  off[1] = ar.take(vec);
+  off[2] = ar.take(vec);
+  off[3] = ar.take(vec);
+  off[4] = ar.take(sizeof(double) * items * 2);
+  off[5] = ar.take(sizeof(CgSys) * n_sys);
+  off[6] = ar.take(sizeof(int32_t) * n_sys);
+  off[7] = ar.take(sizeof(double) * 2);   // n_active (int32) + worst rr/bb (double at +8)
+  off[8] = ar.take(sizeof(int32_t) * n_sys);
+  off[9] = ar.take(sizeof(int32_t) * n_sys);
+  off[10] = ar.take(sizeof(double) * n_sys);
+}
+
+RefineBufs refine_bufs(kmv_handle h, const size_t off[11]) {
+  RefineBufs b;
+  b.q32 = at<float>(h, off[0]);
+  b.r = at<float>(h, off[1]);
+  b.dx = at<float>(h, off[2]);
+  b.pdummy = at<float>(h, off[3]);
+  b.partial2 = at<double>(h, off[4]);
+  b.sys = at<CgSys>(h, off[5]);
+  b.active = at<int32_t>(h, off[6]);
+  b.n_active = at<int32_t>(h, off[7]);
+  b.in_status = at<int32_t>(h, off[8]);
+  b.in_iters = at<int32_t>(h, off[9]);
+  b.prev_rr = at<double>(h, off[10]);
+  return b;
+}
+
+// Solve with the KMV_BF16_HILO operator to FP32 accuracy by iterative
+// refinement (Carson & Higham's mixed-precision scheme): the true residual
+// r = rhs - A x is formed with the FP32 operator, the correction A dx = r is
+// solved by CG with the tensor-core operator, and x += dx, until
+// ||r|| <= tol ||rhs|| or the residual stops falling (the FP32 floor).  The
+// inner tolerance is 1e-5 when the product takes the FMA-pipe path with the
+// three-way exponent split (relative operator error ~1e-6), else 1e-3.
+// Returns the summed inner iterations.
+kmv_status run_cg_refined(kmv_handle h, const kmv_points* pts, const double* theta, const float* rhs,
+                          int64_t rhs_stride, float* x, double tol, int maxiter, int warm, int32_t* status,
+                          int32_t* iters, const CgBufs& B, const RefineBufs& R, cudaStream_t st) {
+  const Layout& L = h->layout;
+  const int n_sys = L.n_inst * L.chains;
+  const int64_t nvec = (int64_t)L.chains * L.n_total;
+  // the tensor-core operator's relative accuracy bounds how far a correction is worth solving
+  const double floor_tol = x_width_fma_ok(pts->d) ? 1e-5 : 1e-3;
+  double* worst = reinterpret_cast<double*>(reinterpret_cast<char*>(R.n_active) + 8);
+  const int max_outer = 12;
+  if (!warm && nvec > 0) KMV_CUDA(h, cudaMemsetAsync(x, 0, sizeof(float) * nvec, st));
+  KMV_CUDA(h, cudaMemsetAsync(status, 0, sizeof(int32_t) * n_sys, st));
+  if (iters) KMV_CUDA(h, cudaMemsetAsync(iters, 0, sizeof(int32_t) * n_sys, st));
+  KmvArgs a = base_args(h, pts, theta);
+  a.m = 1;
+  for (int outer = 0; outer <= max_outer; ++outer) {
+    // r = rhs - A x with the FP32 operator; active = ||r|| > tol ||rhs||
+    a.V = x;
+    a.Y = R.q32;
+    if (L.n_items > 0) KMV_CUDA(h, launch_forward_simt(a, L.n_items, st));
+    if (L.n_items > 0)
+      KMV_CUDA(h, launch_cg_init(h->dev, L.n_items, L.chains, L.n_total, rhs, rhs_stride, R.q32, x, R.r,
+                                 R.pdummy, 1, R.partial2, st));
+    KMV_CUDA(h, launch_cg_reduce_init(h->dev, L.n_inst, L.chains, R.partial2, tol, R.sys, R.active, R.n_active,
+                                      st));
+    KMV_CUDA(h, launch_refine_stagnation(n_sys, outer, R.sys, R.prev_rr, R.active, R.n_active, worst, st));
+    KMV_CUDA(h, cudaMemcpyAsync(h->host_flag, R.n_active, 16, cudaMemcpyDeviceToHost, st));
+    KMV_CUDA(h, cudaStreamSynchronize(st));
+    if (*h->host_flag == 0 || outer == max_outer) break;
+    // solve the correction only as far as the target needs: ||r|| must fall to tol ||rhs||
+    double wr;
+    std::memcpy(&wr, reinterpret_cast<const char*>(h->host_flag) + 8, sizeof(double));
+    const double ratio = wr > 0.0 ? std::sqrt(wr) : 1.0;
+    const double inner_tol = std::min(0.5, std::max(floor_tol, 0.5 * tol / ratio));
+    // correction from the tensor-core operator, on the systems still active
+    if (L.n_items > 0) KMV_CUDA(h, launch_mask_rows(h->dev, L.n_items, L.chains, L.n_total, R.active, R.r, st));
+    KMV_TRY(run_cg(h, pts, theta, R.r, L.n_total, R.dx, inner_tol, maxiter, 0, R.in_status, R.in_iters, B,
+                   KMV_BF16_HILO, st));
+    KMV_CUDA(h, launch_axpy(nvec, R.dx, x, st));
+    KMV_CUDA(h, launch_refine_merge(n_sys, R.in_status, R.in_iters, status, iters, st));
+  }
+  KMV_CUDA(h, launch_refine_finish(n_sys, R.active, R.sys, status, st));
+  return KMV_OK;
+}
+
+// Buffers of a solve in either precision.
+struct SolveLayout {
+  size_t cg[8];
+  size_t rf[11];
+  bool refined;
+};
+
+void solve_layout(const Layout& L, Arena& ar, kmv_precision prec, SolveLayout& S) {
+  cg_layout(L, ar, S.cg);
+  S.refined = prec == KMV_BF16_HILO;
+  if (S.refined) refine_layout(L, ar, S.rf);
+}
+
+kmv_status run_solve(kmv_handle h, const kmv_points* pts, const double* theta, const float* rhs, int64_t rhs_stride,
+                     float* x, double tol, int maxiter, int warm, int32_t* status, int32_t* iters,
+                     const SolveLayout& S, kmv_precision prec, cudaStream_t st) {
+  if (S.refined)
+    return run_cg_refined(h, pts, theta, rhs, rhs_stride, x, tol, maxiter, warm, status, iters, cg_bufs(h, S.cg),
+                          refine_bufs(h, S.rf), st);
+  return run_cg(h, pts, theta, rhs, rhs_stride, x, tol, maxiter, warm, status, iters, cg_bufs(h, S.cg), prec, st);
+}
+
 kmv_status check_prec(kmv_handle h, kmv_precision prec) {
   if (prec != KMV_FP32 && prec != KMV_BF16_HILO) return fail(h, KMV_EINVAL, "unknown precision");
   return KMV_OK;
@@ -400,12 +516,11 @@ kmv_status kmv_cg_solve(kmv_handle h, const kmv_points* pts, int32_t chains, con
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   KMV_TRY(prepare_layout(h, pts, chains, st));
   Arena ar;
-  size_t off[8];
-  cg_layout(h->layout, ar, off);
+  SolveLayout SL;
+  solve_layout(h->layout, ar, prec, SL);
   KMV_TRY(reserve(h, ar.used));
   const int64_t stride = rhs_per_chain ? h->layout.n_total : 0;
-  return run_cg(h, pts, theta, rhs, stride, x, tol, maxiter, warm_start, chain_status, iters,
-                cg_bufs(h, off), prec, st);
+  return run_solve(h, pts, theta, rhs, stride, x, tol, maxiter, warm_start, chain_status, iters, SL, prec, st);
 }
 
 kmv_status leapfrog_step(kmv_handle h, const kmv_points* pts, int32_t chains, const float* y,
@@ -424,8 +539,8 @@ kmv_status leapfrog_step(kmv_handle h, const kmv_points* pts, int32_t chains, co
   const Layout& L = h->layout;
   const int n_sys = L.n_inst * L.chains;
   Arena ar;
-  size_t off[8];
-  cg_layout(L, ar, off);
+  SolveLayout SL;
+  solve_layout(L, ar, prec, SL);
   const size_t o_th = ar.take(sizeof(double) * n_sys * L.n_theta);
   const size_t o_gr = ar.take(sizeof(double) * n_sys * L.n_theta);
   const size_t vec2 = sizeof(float) * 2 * (size_t)L.chains * std::max<int64_t>(1, L.n_total);
@@ -441,8 +556,7 @@ kmv_status leapfrog_step(kmv_handle h, const kmv_points* pts, int32_t chains, co
   // drift: theta_h = theta + dt/2 pi
   KMV_CUDA(h, launch_lf_drift(n_sys, L.n_theta, theta, pi, free_mask, 0.5 * dt, theta_h, st));
   // x = A(theta_h)^{-1} y, cold start (keeps the force a function of theta_h only)
-  KMV_TRY(run_cg(h, pts, theta_h, y, 0, x_work, cg_tol, cg_maxiter, 0, chain_status, cg_iters,
-                 cg_bufs(h, off), prec, st));
+  KMV_TRY(run_solve(h, pts, theta_h, y, 0, x_work, cg_tol, cg_maxiter, 0, chain_status, cg_iters, SL, prec, st));
   // force: d/dtheta [-x^T A x / 2 + phi^T A phi / 2] at frozen x (Eq. u)
   KMV_CUDA(h, launch_pack_force(L.chains, L.n_total, x_work, phi, Vf, Gf, st));
   KmvArgs a = base_args(h, pts, theta_h);
@@ -472,8 +586,8 @@ kmv_status kmv_energy(kmv_handle h, const kmv_points* pts, int32_t chains, const
   KMV_TRY(prepare_layout(h, pts, chains, st));
   const Layout& L = h->layout;
   Arena ar;
-  size_t off[8];
-  cg_layout(L, ar, off);
+  SolveLayout SL;
+  solve_layout(L, ar, prec, SL);
   const size_t vec = (size_t)L.chains * std::max<int64_t>(1, L.n_total);
   const size_t o_y = ar.take(sizeof(float) * vec);
   const size_t o_y64 = ar.take(sizeof(double) * vec);
@@ -481,8 +595,7 @@ kmv_status kmv_energy(kmv_handle h, const kmv_points* pts, int32_t chains, const
   const size_t o_p1 = ar.take(sizeof(double) * items);
   const size_t o_p2 = ar.take(sizeof(double) * items);
   KMV_TRY(reserve(h, ar.used));
-  KMV_TRY(run_cg(h, pts, theta, y, 0, x_work, cg_tol, cg_maxiter, 0, chain_status, cg_iters,
-                 cg_bufs(h, off), prec, st));
+  KMV_TRY(run_solve(h, pts, theta, y, 0, x_work, cg_tol, cg_maxiter, 0, chain_status, cg_iters, SL, prec, st));
   KmvArgs a = base_args(h, pts, theta);
   a.V = phi;
   a.m = 1;

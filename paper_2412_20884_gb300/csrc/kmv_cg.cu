@@ -109,8 +109,14 @@ __global__ void cg_reduce_pq_kernel(DevLayout L, int n_inst, int chains, const d
     const int b = s / chains, c = s - b * chains;
     const double pq = sys_sum(L, b, c, chains, partial, 1, 0);
     S.pq = pq;
-    if (!(pq > 0.0) || !isfinite(pq)) {
+    if (!isfinite(pq)) {
       S.status = KMV_ENONFINITE;
+      active[s] = 0;
+      S.alpha = 0.0;
+    } else if (!(pq > 0.0)) {
+      // breakdown: the operator is not positive definite along p (a perturbed
+      // operator can be); stop here with the current iterate
+      S.status = KMV_ENOTCONV;
       active[s] = 0;
       S.alpha = 0.0;
     } else {
@@ -219,6 +225,111 @@ __global__ void cg_finish_kernel(int n_sys, const CgSys* sys, int32_t* status, i
 cudaError_t launch_cg_finish(int n_sys, const CgSys* sys, int32_t* status, int32_t* iters,
                              cudaStream_t st) {
   cg_finish_kernel<<<(n_sys + 255) / 256, 256, 0, st>>>(n_sys, sys, status, iters);
+  return cudaGetLastError();
+}
+
+// --- mixed-precision refinement helpers -------------------------------------------
+
+// r[c, rows of b] = 0 for systems that are not active (their correction is 0).
+__global__ void mask_rows_kernel(DevLayout L, int chains, int64_t n_total, const int32_t* active, float* r) {
+  const int item = blockIdx.x, c = blockIdx.y;
+  const int b = L.item_inst[item];
+  if (active[b * chains + c]) return;
+  const int64_t i = L.item_row0[item] + threadIdx.x;
+  if (i < L.offsets[b + 1]) r[(int64_t)c * n_total + i] = 0.f;
+}
+
+cudaError_t launch_mask_rows(const DevLayout& L, int n_items, int chains, int64_t n_total, const int32_t* active,
+                             float* r, cudaStream_t st) {
+  mask_rows_kernel<<<dim3(n_items, chains), kTile, 0, st>>>(L, chains, n_total, active, r);
+  return cudaGetLastError();
+}
+
+__global__ void axpy_kernel(int64_t n, const float* dx, float* x) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    x[e] += dx[e];
+}
+
+cudaError_t launch_axpy(int64_t n, const float* dx, float* x, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  const int blocks = (int)std::min<int64_t>((n + 255) / 256, 152 * 32);
+  axpy_kernel<<<blocks, 256, 0, st>>>(n, dx, x);
+  return cudaGetLastError();
+}
+
+// Folds an inner solve's per-system results into the outer ones: iterations
+// add up; a failed inner solve marks the system.
+__global__ void refine_merge_kernel(int n_sys, const int32_t* in_status, const int32_t* in_iters,
+                                    int32_t* status, int32_t* iters) {
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n_sys; s += gridDim.x * blockDim.x) {
+    if (iters) iters[s] += in_iters[s];
+    if (in_status[s] == KMV_ENONFINITE) status[s] = KMV_ENONFINITE;
+  }
+}
+
+cudaError_t launch_refine_merge(int n_sys, const int32_t* in_status, const int32_t* in_iters, int32_t* status,
+                                int32_t* iters, cudaStream_t st) {
+  refine_merge_kernel<<<(n_sys + 255) / 256, 256, 0, st>>>(n_sys, in_status, in_iters, status, iters);
+  return cudaGetLastError();
+}
+
+// Stops refinement of systems whose true residual no longer falls by at least
+// half per outer step: the residual has reached the floor set by the FP32
+// operator it is measured with, which is as far as the solve can go (the FP32
+// CG stops on its recurrence residual, which passes below that floor).
+// Also reports, in worst[0], the largest rr / bb over the systems still active.
+__global__ void refine_stagnation_kernel(int n_sys, int outer, const CgSys* sys, double* prev_rr, int32_t* active,
+                                         int32_t* n_active, double* worst) {
+  __shared__ int cnt[8];
+  __shared__ double wmax[8];
+  int v = 0;
+  double wr = 0.0;
+  for (int s = threadIdx.x; s < n_sys; s += blockDim.x) {
+    const double rr = sys[s].rr;
+    if (active[s] && outer > 0 && rr > 0.25 * prev_rr[s]) active[s] = 0;
+    prev_rr[s] = rr;
+    v += active[s];
+    if (active[s] && sys[s].bb > 0.0) wr = fmax(wr, rr / sys[s].bb);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    v += __shfl_down_sync(0xffffffffu, v, o);
+    wr = fmax(wr, __shfl_down_sync(0xffffffffu, wr, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    cnt[threadIdx.x >> 5] = v;
+    wmax[threadIdx.x >> 5] = wr;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int t = 0;
+    double m = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      t += cnt[w];
+      m = fmax(m, wmax[w]);
+    }
+    *n_active = t;
+    *worst = m;
+  }
+}
+
+cudaError_t launch_refine_stagnation(int n_sys, int outer, const CgSys* sys, double* prev_rr, int32_t* active,
+                                     int32_t* n_active, double* worst, cudaStream_t st) {
+  refine_stagnation_kernel<<<1, 256, 0, st>>>(n_sys, outer, sys, prev_rr, active, n_active, worst);
+  return cudaGetLastError();
+}
+
+// Final outer status: still active after the last refinement -> not converged.
+__global__ void refine_finish_kernel(int n_sys, const int32_t* active, const CgSys* sys, int32_t* status) {
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n_sys; s += gridDim.x * blockDim.x) {
+    if (status[s] != KMV_OK) continue;
+    if (sys[s].status != KMV_OK) status[s] = sys[s].status;
+    else if (active[s]) status[s] = KMV_ENOTCONV;
+  }
+}
+
+cudaError_t launch_refine_finish(int n_sys, const int32_t* active, const CgSys* sys, int32_t* status,
+                                 cudaStream_t st) {
+  refine_finish_kernel<<<(n_sys + 255) / 256, 256, 0, st>>>(n_sys, active, sys, status);
   return cudaGetLastError();
 }
 

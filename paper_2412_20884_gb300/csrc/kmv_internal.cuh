@@ -102,6 +102,16 @@ cudaError_t launch_cg_update_p(const DevLayout& L, int n_items, int chains, int6
 cudaError_t launch_cg_finish(int n_sys, const CgSys* sys, int32_t* status, int32_t* iters,
                              cudaStream_t st);
 
+cudaError_t launch_mask_rows(const DevLayout& L, int n_items, int chains, int64_t n_total, const int32_t* active,
+                             float* r, cudaStream_t st);
+cudaError_t launch_axpy(int64_t n, const float* dx, float* x, cudaStream_t st);
+cudaError_t launch_refine_merge(int n_sys, const int32_t* in_status, const int32_t* in_iters, int32_t* status,
+                                int32_t* iters, cudaStream_t st);
+cudaError_t launch_refine_stagnation(int n_sys, int outer, const CgSys* sys, double* prev_rr, int32_t* active,
+                                     int32_t* n_active, double* worst, cudaStream_t st);
+cudaError_t launch_refine_finish(int n_sys, const int32_t* active, const CgSys* sys, int32_t* status,
+                                 cudaStream_t st);
+
 cudaError_t launch_lf_drift(int n_sys, int n_theta, const double* theta, const double* pi,
                             const uint8_t* mask, double half_dt, double* theta_h, cudaStream_t st);
 cudaError_t launch_pack_force(int chains, int64_t n_total, const float* xsol, const float* phi,

@@ -369,11 +369,265 @@ __global__ void __launch_bounds__(kFwdThreads, 1) tc_fwd_kernel(TcFwdArgs a) {
   if (warp == kMmaWarp) tmem_dealloc(tbase, 512);
 }
 
+// Forward for one or two columns (the CG product): S = XA XB^T on the tensor
+// core as above, but P.v on the FMA pipe with P kept in FP32 and v in FP32
+// (tile VF: MZ x 128 floats), so the tensor pipe only computes S and the
+// kernel is bound by the exps.  Warp roles as in tc_fwd_kernel.
+template <int MZ>
+__global__ void __launch_bounds__(kFwdThreads, 1) tc_fwd_fma_kernel(TcFwdArgs a) {
+  using namespace ptx;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = align1024(smem_raw);
+  const uint32_t A_TILE = a.KX * 256u, V_TILE = MZ * 512u;
+  const int S = a.S;
+  uint8_t* sA = smem;
+  uint8_t* sB = sA + 4 * A_TILE;
+  uint8_t* sV = sB + S * A_TILE;
+  uint64_t* full = reinterpret_cast<uint64_t*>(sV + S * V_TILE);
+  uint64_t* empty = full + S;        // released by the 2 issuers (S read XB) and 8 exp warps (read VF)
+  uint64_t* a_full = empty + S;
+  uint64_t* a_empty = a_full + 2;
+  uint64_t* s_full = a_empty + 2;
+  uint64_t* s_free = s_full + 2;
+  uint64_t* done = s_free + 2;
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(done + 2);
+  volatile int* abort = reinterpret_cast<volatile int*>(tslot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < S; ++i) {
+      mbar_init(&full[i], 1);
+      mbar_init(&empty[i], 2 + 8);
+    }
+    for (int g = 0; g < 2; ++g) {
+      mbar_init(&a_full[g], 1);
+      mbar_init(&a_empty[g], 2);
+      mbar_init(&s_full[g], 1);
+      mbar_init(&s_free[g], 128);
+      mbar_init(&done[g], 1);
+    }
+    *abort = 0;
+    fence_barrier_init();
+  }
+  if (warp == kMmaWarp) {
+    tmem_alloc(tslot, 256);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tbase = *tslot;
+
+  if (warp == kLoadWarp) {
+    if (lane == 0) {
+      int it = 0;
+      uint32_t stage = 0, sph = 0;
+      int n_issued = 0, n_a_issued = 0;
+      bool aborted = false;
+      for (int t = blockIdx.x; t < a.n_items && !aborted; t += gridDim.x) {
+        const int4 item = a.items[t];
+        if (a.sys_active && !a.sys_active[item.x]) continue;
+        const int c = item.x % a.chains;
+        const int ab = it & 1;
+        if (!mbar_wait(&a_empty[ab], ((it >> 1) & 1) ^ 1, abort, a.err, 11)) { aborted = true; break; }
+        mbar_arrive_expect_tx(&a_full[ab], 2 * A_TILE);
+        bulk_g2s(sA + (2 * ab) * A_TILE, a.XA + ((size_t)c * a.T_total + item.y) * A_TILE, 2 * A_TILE,
+                 &a_full[ab]);
+        ++n_a_issued;
+        for (int j = 0; j < item.w; ++j) {
+          if (!mbar_wait(&empty[stage], sph ^ 1, abort, a.err, 12)) { aborted = true; break; }
+          mbar_arrive_expect_tx(&full[stage], A_TILE + V_TILE);
+          const size_t tj = (size_t)c * a.T_total + item.z + j;
+          bulk_g2s(sB + stage * A_TILE, a.XB + tj * A_TILE, A_TILE, &full[stage]);
+          bulk_g2s(sV + stage * V_TILE, a.VT + tj * V_TILE, V_TILE, &full[stage]);
+          ++n_issued;
+          if (++stage == (uint32_t)S) { stage = 0; sph ^= 1; }
+        }
+        ++it;
+      }
+      if (aborted) {
+        for (int k = 1; k <= min(n_issued, S); ++k) {
+          const int idx = n_issued - k;
+          mbar_drain(&full[idx % S], (idx / S) & 1, 500000000ull);
+        }
+        for (int k = 1; k <= min(n_a_issued, 2); ++k) {
+          const int idx = n_a_issued - k;
+          mbar_drain(&a_full[idx & 1], (idx >> 1) & 1, 500000000ull);
+        }
+      }
+    }
+  } else if (warp == kMmaWarp || warp == kIssue1Warp) {
+    if (lane == 0) {
+      const int g = warp == kMmaWarp ? 0 : 1;
+      const uint32_t idS = idesc_f16(128, 128, 1, 1);
+      const uint32_t sboX = a.KX * 16u;
+      const int nkx = a.KX / 16;
+      const uint64_t dA = sdesc(smem_u32(sA + g * A_TILE), 128, sboX);
+      const uint64_t dB = sdesc(smem_u32(sB), 128, sboX);
+      const uint32_t s_tmem = tbase + g * 128;
+      int it = 0;
+      uint32_t stage = 0, sph = 0, sf_ph = 0;
+      long long k = 0;
+      for (int t = blockIdx.x; t < a.n_items; t += gridDim.x) {
+        const int4 item = a.items[t];
+        if (a.sys_active && !a.sys_active[item.x]) continue;
+        const int ab = it & 1;
+        const uint64_t dAg = sdesc_add(dA, 2 * ab * A_TILE);
+        for (int j = 0; j < item.w; ++j, ++k) {
+          if (k > 0) {
+            if (!mbar_wait(&s_free[g], sf_ph, abort, a.err, 13)) goto fma_mma_out;
+            sf_ph ^= 1;
+          }
+          if (j == 0 && !mbar_wait(&a_full[ab], (it >> 1) & 1, abort, a.err, 14)) goto fma_mma_out;
+          if (!mbar_wait(&full[stage], sph, abort, a.err, 15)) goto fma_mma_out;
+          tc_fence_after();
+          issue_s(s_tmem, dAg, sdesc_add(dB, stage * A_TILE), nkx, idS);
+          tc_commit(&s_full[g]);
+          tc_commit(&empty[stage]);
+          if (j == item.w - 1) tc_commit(&a_empty[ab]);
+          if (++stage == (uint32_t)S) { stage = 0; sph ^= 1; }
+        }
+        ++it;
+      }
+    fma_mma_out:
+      tc_commit(&done[g]);
+      mbar_drain(&done[g], 0, 500000000ull);
+    }
+    __syncwarp();
+  } else {
+    const int g = warp >> 2, w = warp & 3;
+    const int row = 32 * w + lane;
+    const uint32_t tl = tbase + (static_cast<uint32_t>(32 * w) << 16);
+    const uint32_t s_col = g * 128;
+    uint32_t sph = 0, stage = 0, fph = 0;
+    for (int t = blockIdx.x; t < a.n_items; t += gridDim.x) {
+      const int4 item = a.items[t];
+      if (a.sys_active && !a.sys_active[item.x]) continue;
+      double* prow = a.part + ((size_t)t * 256 + g * 128 + row) * a.mz;
+      // four independent FP32 chains per column (short FMA dependency chains)
+      double acc64[MZ];
+      float acc[MZ][4];
+#pragma unroll
+      for (int q = 0; q < MZ; ++q) {
+        acc64[q] = 0.0;
+        acc[q][0] = acc[q][1] = acc[q][2] = acc[q][3] = 0.f;
+      }
+      for (int j = 0; j < item.w; ++j) {
+        bool ok = mbar_wait(&s_full[g], sph, abort, a.err, 16);
+        // the VF tile of this stage is visible once its copy has completed
+        ok = ok && mbar_wait(&full[stage], fph, abort, a.err, 17);
+        if (!__all_sync(0xffffffffu, ok)) goto fma_exp_out;
+        sph ^= 1;
+        tc_fence_after();
+        const float4* vs = reinterpret_cast<const float4*>(sV + stage * V_TILE);
+        {
+          uint32_t a0[32], a1[32], b0[32], b1[32];
+          tmem_ld32(tl + s_col, a0);
+          tmem_ld32(tl + s_col + 32, a1);
+          tmem_ld_wait();
+          tmem_ld32(tl + s_col + 64, b0);
+          tmem_ld32(tl + s_col + 96, b1);
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            const float p0 = ex2(__uint_as_float(a0[4 * u])), p1 = ex2(__uint_as_float(a0[4 * u + 1]));
+            const float p2 = ex2(__uint_as_float(a0[4 * u + 2])), p3 = ex2(__uint_as_float(a0[4 * u + 3]));
+#pragma unroll
+            for (int q = 0; q < MZ; ++q) {
+              const float4 v = vs[q * 32 + 0 + u];
+              acc[q][0] = fmaf(p0, v.x, acc[q][0]);
+              acc[q][1] = fmaf(p1, v.y, acc[q][1]);
+              acc[q][2] = fmaf(p2, v.z, acc[q][2]);
+              acc[q][3] = fmaf(p3, v.w, acc[q][3]);
+            }
+          }
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            const float p0 = ex2(__uint_as_float(a1[4 * u])), p1 = ex2(__uint_as_float(a1[4 * u + 1]));
+            const float p2 = ex2(__uint_as_float(a1[4 * u + 2])), p3 = ex2(__uint_as_float(a1[4 * u + 3]));
+#pragma unroll
+            for (int q = 0; q < MZ; ++q) {
+              const float4 v = vs[q * 32 + 8 + u];
+              acc[q][0] = fmaf(p0, v.x, acc[q][0]);
+              acc[q][1] = fmaf(p1, v.y, acc[q][1]);
+              acc[q][2] = fmaf(p2, v.z, acc[q][2]);
+              acc[q][3] = fmaf(p3, v.w, acc[q][3]);
+            }
+          }
+          tmem_ld_wait();
+          tc_fence_before();
+          mbar_arrive(&s_free[g]);
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            const float p0 = ex2(__uint_as_float(b0[4 * u])), p1 = ex2(__uint_as_float(b0[4 * u + 1]));
+            const float p2 = ex2(__uint_as_float(b0[4 * u + 2])), p3 = ex2(__uint_as_float(b0[4 * u + 3]));
+#pragma unroll
+            for (int q = 0; q < MZ; ++q) {
+              const float4 v = vs[q * 32 + 16 + u];
+              acc[q][0] = fmaf(p0, v.x, acc[q][0]);
+              acc[q][1] = fmaf(p1, v.y, acc[q][1]);
+              acc[q][2] = fmaf(p2, v.z, acc[q][2]);
+              acc[q][3] = fmaf(p3, v.w, acc[q][3]);
+            }
+          }
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            const float p0 = ex2(__uint_as_float(b1[4 * u])), p1 = ex2(__uint_as_float(b1[4 * u + 1]));
+            const float p2 = ex2(__uint_as_float(b1[4 * u + 2])), p3 = ex2(__uint_as_float(b1[4 * u + 3]));
+#pragma unroll
+            for (int q = 0; q < MZ; ++q) {
+              const float4 v = vs[q * 32 + 24 + u];
+              acc[q][0] = fmaf(p0, v.x, acc[q][0]);
+              acc[q][1] = fmaf(p1, v.y, acc[q][1]);
+              acc[q][2] = fmaf(p2, v.z, acc[q][2]);
+              acc[q][3] = fmaf(p3, v.w, acc[q][3]);
+            }
+          }
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[stage]);
+        if (++stage == (uint32_t)S) { stage = 0; fph ^= 1; }
+        if ((j % kFold) == kFold - 1) {
+#pragma unroll
+          for (int q = 0; q < MZ; ++q) {
+            acc64[q] += (double)((acc[q][0] + acc[q][1]) + (acc[q][2] + acc[q][3]));
+            acc[q][0] = acc[q][1] = acc[q][2] = acc[q][3] = 0.f;
+          }
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < MZ; ++q)
+        prow[q] = acc64[q] + (double)((acc[q][0] + acc[q][1]) + (acc[q][2] + acc[q][3]));
+    }
+  fma_exp_out:;
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == kMmaWarp) tmem_dealloc(tbase, 256);
+}
+
+// V tiles as FP32 columns for the FMA-pipe product: VF[c][t] = MZ x 128 floats.
+__global__ void tc_prep_vf_kernel(DevLayout L, TcTables T, int chains, int64_t n_total, const float* V, int m,
+                                  int mz, int T_total, const int32_t* sys_active, float* VF) {
+  const int t = blockIdx.x, c = blockIdx.y, r = threadIdx.x;
+  const int b = T.tile_inst[t];
+  const int s = b * chains + c;
+  if (sys_active && !sys_active[s]) return;
+  const int64_t nb = L.offsets[b + 1] - L.offsets[b];
+  const int64_t rl = (int64_t)(t - T.inst_tile0[b]) * 128 + r;
+  const bool valid = rl < nb;
+  const int64_t i = L.offsets[b] + rl;
+  float* dst = VF + ((size_t)c * T_total + t) * (size_t)mz * 128;
+  for (int q = 0; q < mz; ++q) dst[q * 128 + r] = valid ? V[((int64_t)c * n_total + i) * m + q] : 0.f;
+}
+
 // ------------------------------------------------------------------ prep kernels
 
 // One thread per padded row: the A-side and B-side BF16 operand rows.
 __global__ void tc_prep_x_kernel(DevLayout L, TcTables T, int chains, int d, int ard, int n_theta, int KX,
-                                 int T_total, const float* x, const double* theta, uint8_t* XA, uint8_t* XB) {
+                                 int nsplit, int T_total, const float* x, const double* theta, uint8_t* XA,
+                                 uint8_t* XB) {
   const int t = blockIdx.x, c = blockIdx.y, r = threadIdx.x;
   const int b = T.tile_inst[t];
   const int s = b * chains + c;
@@ -401,22 +655,43 @@ __global__ void tc_prep_x_kernel(DevLayout L, TcTables T, int chains, int d, int
     const float sc = (float)(sqrt(2.0 * kHalfLog2e) * exp(-th[1 + (ard ? k : 0)]));
     const float xh = x[i * d + k] * sc;
     const __nv_bfloat16 hi = __float2bfloat16_rn(xh);
-    const __nv_bfloat16 lo = __float2bfloat16_rn(xh - __bfloat162float(hi));
-    const double hd = __bfloat162float(hi), ld = __bfloat162float(lo);
-    nrm += hd * hd + 2.0 * hd * ld;
-    putA(k, hi);
-    putA(d + k, hi);
-    putA(2 * d + k, lo);
-    putB(k, hi);
-    putB(d + k, lo);
-    putB(2 * d + k, hi);
+    const float r1 = xh - __bfloat162float(hi);
+    const __nv_bfloat16 mid = __float2bfloat16_rn(r1);
+    const double hd = __bfloat162float(hi), md = __bfloat162float(mid);
+    if (nsplit == 2) {
+      // A: [hi, hi, lo]  B: [hi, lo, hi]
+      nrm += hd * hd + 2.0 * hd * md;
+      putA(k, hi);
+      putA(d + k, hi);
+      putA(2 * d + k, mid);
+      putB(k, hi);
+      putB(d + k, mid);
+      putB(2 * d + k, hi);
+    } else {
+      // A: [h, h, m, h, l, m]  B: [h, m, h, l, h, m]
+      const __nv_bfloat16 lo = __float2bfloat16_rn(r1 - __bfloat162float(mid));
+      const double ld = __bfloat162float(lo);
+      nrm += hd * hd + 2.0 * hd * md + 2.0 * hd * ld + md * md;
+      putA(k, hi);
+      putA(d + k, hi);
+      putA(2 * d + k, mid);
+      putA(3 * d + k, hi);
+      putA(4 * d + k, lo);
+      putA(5 * d + k, mid);
+      putB(k, hi);
+      putB(d + k, mid);
+      putB(2 * d + k, hi);
+      putB(3 * d + k, lo);
+      putB(4 * d + k, hi);
+      putB(5 * d + k, mid);
+    }
   }
   const double bias = -0.5 * nrm;
   const __nv_bfloat16 bh = __float2bfloat16_rn((float)bias);
   const double r1 = bias - (double)__bfloat162float(bh);
   const __nv_bfloat16 bm = __float2bfloat16_rn((float)r1);
   const __nv_bfloat16 bl = __float2bfloat16_rn((float)(r1 - (double)__bfloat162float(bm)));
-  const int o = 3 * d;
+  const int o = (nsplit == 2 ? 3 : 6) * d;
   putA(o + 0, one);
   putA(o + 1, one);
   putA(o + 2, one);
@@ -624,10 +899,10 @@ kmv_status tc_ensure_buf(kmv_handle h, TcState* S, size_t bytes) {
   return KMV_OK;
 }
 
-void tc_launch_prep_x(kmv_handle h, TcState* S, const KmvArgs& a, int KX, uint8_t* XA, uint8_t* XB,
+void tc_launch_prep_x(kmv_handle h, TcState* S, const KmvArgs& a, int KX, int nsplit, uint8_t* XA, uint8_t* XB,
                       cudaStream_t st) {
   tc_prep_x_kernel<<<dim3(S->T_total, h->layout.chains), 128, 0, st>>>(
-      h->dev, S->dev, h->layout.chains, a.d, a.ard, a.n_theta, KX, S->T_total, a.x, a.theta, XA, XB);
+      h->dev, S->dev, h->layout.chains, a.d, a.ard, a.n_theta, KX, nsplit, S->T_total, a.x, a.theta, XA, XB);
 }
 
 void tc_launch_epilogue(kmv_handle h, TcState* S, const KmvArgs& a, int c0, int mz, const double* part,
@@ -638,7 +913,11 @@ void tc_launch_epilogue(kmv_handle h, TcState* S, const KmvArgs& a, int c0, int 
 
 kmv_status tc_forward(kmv_handle h, const KmvArgs& a, cudaStream_t st) {
   const Layout& L = h->layout;
-  const int KX = x_width(a.d);
+  // one or two columns (the CG / energy products) take the FMA-pipe P.v path,
+  // where the tensor pipe has room for the three-way split of the exponent
+  const bool fma_path = a.m <= 2 && x_width(a.d, 3) <= kMaxKX;
+  const int nsplit = fma_path ? 3 : 2;
+  const int KX = x_width(a.d, nsplit);
   if (KX > kMaxKX) return tc_fail(h, KMV_EUNSUPPORTED, "KMV_BF16_HILO supports d <= 35");
   TcState* S = tc_state(h);
   kmv_status stt = tc_build_plan(h, S, st);
@@ -680,7 +959,52 @@ kmv_status tc_forward(kmv_handle h, const KmvArgs& a, cudaStream_t st) {
     S->attr_set = true;
   }
   if (cudaMemsetAsync(err, 0, sizeof(int), st) != cudaSuccess) return tc_fail(h, KMV_ECUDA, "memset failed");
-  tc_launch_prep_x(h, S, a, KX, XA, XB, st);
+  tc_launch_prep_x(h, S, a, KX, nsplit, XA, XB, st);
+  if (fma_path) {
+    // one or two columns: P.v on the FMA pipe (FP32 P and v, no scaling)
+    const int mz = a.m;
+    const size_t V_TILE = (size_t)mz * 512;
+    const int stages = (int)std::min<size_t>(8, (kMaxSmem - fixed) / (A_TILE + V_TILE + 16));
+    const size_t smem = std::max(kMinSmem, fixed + stages * (A_TILE + V_TILE) + (2 * stages + 16) * 8);
+    if (!S->fma_attr_set) {
+      if (cudaFuncSetAttribute(tc_fwd_fma_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem) !=
+              cudaSuccess ||
+          cudaFuncSetAttribute(tc_fwd_fma_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem) !=
+              cudaSuccess)
+        return tc_fail(h, KMV_ECUDA, "cudaFuncSetAttribute failed");
+      S->fma_attr_set = true;
+    }
+    if (cudaMemsetAsync(vmax, 0, sizeof(uint32_t) * (size_t)n_sys * mz, st) != cudaSuccess)
+      return tc_fail(h, KMV_ECUDA, "memset failed");
+    tc_prep_vf_kernel<<<dim3(S->T_total, L.chains), 128, 0, st>>>(h->dev, S->dev, L.chains, L.n_total, a.V, a.m,
+                                                                  mz, S->T_total, a.sys_active,
+                                                                  reinterpret_cast<float*>(VT));
+    TcFwdArgs fa;
+    fa.items = S->d_items;
+    fa.n_items = S->n_items;
+    fa.chains = L.chains;
+    fa.T_total = S->T_total;
+    fa.KX = KX;
+    fa.MP = 16;
+    fa.S = stages;
+    fa.XA = XA;
+    fa.XB = XB;
+    fa.VT = VT;
+    fa.part = part;
+    fa.mz = mz;
+    fa.sys_active = a.sys_active;
+    fa.err = err;
+    const int grid = std::min(S->n_items, S->num_sms);
+    if (mz == 1)
+      tc_fwd_fma_kernel<1><<<grid, kFwdThreads, smem, st>>>(fa);
+    else
+      tc_fwd_fma_kernel<2><<<grid, kFwdThreads, smem, st>>>(fa);
+    // vmax is zero: the epilogue's column scale is 1
+    tc_launch_epilogue(h, S, a, 0, mz, part, vmax, err, st);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return tc_fail(h, KMV_ECUDA, cudaGetErrorString(e));
+    return KMV_OK;
+  }
   for (int c0 = 0; c0 < a.m; c0 += mz_max) {
     const int mz = std::min(mz_max, a.m - c0);
     const int MP = std::max(16, (mz + 15) / 16 * 16);
@@ -719,6 +1043,8 @@ kmv_status tc_forward(kmv_handle h, const KmvArgs& a, cudaStream_t st) {
   }
   return KMV_OK;
 }
+
+bool x_width_fma_ok(int d) { return x_width(d, 3) <= kMaxKX; }
 
 void tc_release(kmv_handle h) {
   if (!h->tc) return;

@@ -650,7 +650,7 @@ kmv_status tc_backward(kmv_handle h, const KmvArgs& a, double* grad, cudaStream_
                                                                      fused ? 1 : 0, gmax, vmax, gcol, gvpart,
                                                                      a.sys_active);
   if (S->n_items > 0) {
-    tc_launch_prep_x(h, S, a, KX, base + o_xa, base + o_xb, st);
+    tc_launch_prep_x(h, S, a, KX, 2, base + o_xa, base + o_xb, st);
     tc_prep_bwd_kernel<<<dim3(S->T_total, L.chains), 128, 0, st>>>(
         h->dev, S->dev, L.chains, a.d, a.ard, a.n_theta, a.m, KG, NB, MPg, S->T_total, a.x, a.theta, a.V, a.G,
         L.n_total, gmax, vmax, gcol, a.sys_active, base + o_gi, base + o_vj, base + o_bg, base + o_vt, err);

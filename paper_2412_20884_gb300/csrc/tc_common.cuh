@@ -19,8 +19,9 @@ constexpr size_t kMinSmem = 120 * 1024;  // keeps one CTA (and one TMEM allocati
 constexpr size_t kMaxSmem = 227 * 1024;
 
 __host__ __device__ constexpr int round16(int v) { return (v + 15) / 16 * 16; }
-// X operand width: 3 d split terms + 6 bias/one columns, rounded to the MMA K step.
-__host__ __device__ constexpr int x_width(int d) { return round16(3 * d + 6); }
+// X operand width: 3 d (two-way split) or 6 d (three-way split) product terms
+// + 6 bias/one columns, rounded to the MMA K step.
+__host__ __device__ constexpr int x_width(int d, int nsplit = 2) { return round16((nsplit == 3 ? 6 : 3) * d + 6); }
 
 struct TcTables {
   const int32_t* tile_inst;    // T_total
@@ -50,6 +51,7 @@ struct TcState {
   int num_sms = 0;
   bool attr_set = false;
   bool bwd_attr_set = false;
+  bool fma_attr_set = false;
 };
 
 
@@ -58,7 +60,9 @@ kmv_status tc_fail(kmv_handle h, kmv_status s, const char* msg);
 kmv_status tc_build_plan(kmv_handle h, TcState* S, cudaStream_t st);
 kmv_status tc_ensure_buf(kmv_handle h, TcState* S, size_t bytes);
 // Writes the XA / XB operand tiles of every (chain, padded tile).
-void tc_launch_prep_x(kmv_handle h, TcState* S, const KmvArgs& a, int KX, uint8_t* XA, uint8_t* XB,
+// nsplit = 2: x = hi + lo, products hi.hi + hi.lo + lo.hi (|dS| ~ 2^-16 |x|^2);
+// nsplit = 3: x = h + m + l, products hh + hm + mh + hl + lh + mm (|dS| ~ 2^-24 |x|^2).
+void tc_launch_prep_x(kmv_handle h, TcState* S, const KmvArgs& a, int KX, int nsplit, uint8_t* XA, uint8_t* XB,
                       cudaStream_t st);
 // Y = alpha * sum_k part / colscale + (sigma^2 + shift) V over the product rows of a.
 void tc_launch_epilogue(kmv_handle h, TcState* S, const KmvArgs& a, int c0, int mz, const double* part,
