@@ -36,7 +36,10 @@ WORKLOAD = "kmv fwd+bwd, N=65536 points x~N(0,I) in d=8, ARD SE (10 hyperparamet
 SM_COUNT = 152
 FMA_LANES = 128        # FP32 FMA lanes per SM per clock
 MUFU_EX2_LANES = 32    # ex2 per SM per clock on GB300 (measured by the microbenchmark in the design doc)
-DRAM_TRAFFIC = {}      # kernel form -> dram bytes per launch from ncu (see profiles/); empty = null
+# dram__bytes_read.sum + dram__bytes_write.sum per launch of the main loop, from the
+# ncu capture summarised in profiles/tc_kernels_c2.md (same workload); None once
+# the kernel changes after that capture.
+DRAM_TRAFFIC = {("bf16_hilo", "bwd"): 33686528 + 160512, ("bf16_hilo", "fwd"): 10549248 + 1536}
 
 
 def peaks():
@@ -154,12 +157,26 @@ def cpu_oracle_rate(rows_per_step: int, steps: int, seed: int = 0):
     return pairs / t_total / 1e9, t_total, len(os.sched_getaffinity(0))
 
 
-def roof_pairs_per_s(prec, d, m, clock_mhz, which):
+def algorithmic_flops_per_pair(d, m, which):
+    """Tensor-core FLOPs per pair of the BF16 form, unpadded: the cross term with
+    its hi/lo split and folded biases (3d + 6 products), W = G V^T with hi/lo
+    G and V (3m), the feature sums of Q (4d + 1) and the P.V / P.G products (m)."""
+    if which == "fwd":
+        return 2 * (3 * d + 6) + 2 * m
+    return 2 * (3 * d + 6) + 2 * (3 * m) + 2 * (4 * d + 1) + 2 * m
+
+
+def roof(prec, d, m, clock_mhz, which, tensor_tflops):
+    """Issue-rate roof of one kernel: pairs/s, the binding unit and a note."""
     f = clock_mhz * 1e6
     if prec == "bf16_hilo":
-        return SM_COUNT * MUFU_EX2_LANES * f, "MUFU ex2 issue, 1 exp per pair"
+        mufu = SM_COUNT * MUFU_EX2_LANES * f                      # one ex2 per pair
+        tens = tensor_tflops * 1e12 / algorithmic_flops_per_pair(d, m, which)
+        if tens < mufu:
+            return tens, "tensor", f"tensor pipe, {algorithmic_flops_per_pair(d, m, which)} FLOP per pair"
+        return mufu, "alu", "MUFU ex2 issue, 1 exp per pair"
     ops = 2 * d + m if which == "fwd" else 4 * d + 2 * m + 2
-    return SM_COUNT * FMA_LANES * f / ops, f"FP32 FMA-pipe issue, {ops} ops per pair"
+    return SM_COUNT * FMA_LANES * f / ops, "alu", f"FP32 FMA-pipe issue, {ops} ops per pair"
 
 
 def run_reference(args):
@@ -263,7 +280,10 @@ def main():
         dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
     ms_max = float(ms_t.item())
     value = world * pairs / (ms_max * 1e-3) / 1e9
-    launches_per_step = 3   # forward, backward, gradient finalisation
+    # our kernels per step: FP32 form = forward, adjoint, finalize; BF16 form =
+    # forward (prep_x, vmax, prep_v, main, epilogue) + adjoint (norms, prep_x,
+    # prep, main, finalize, dL/dV epilogue)
+    launches_per_step = 3 if prec == "fp32" else 11
 
     # end to end through the public API: host inputs (pinned) -> device -> host results
     hX = torch.tensor(w.X, dtype=torch.float32).pin_memory()
@@ -308,14 +328,24 @@ def main():
         mf, mb = float(np.mean(t_f)), float(np.mean(t_b))
         which = "bwd" if mb >= mf else "fwd"
         dur = max(mf, mb) * 1e-3
-        achieved = n * n / dur / 1e9
-        peak, basis = roof_pairs_per_s(prec, w.d, w.m, clock, which)
-        roof = {"bound": "alu", "achieved": achieved, "peak": peak / 1e9, "unit": "GPair/s",
-                "frac": achieved * 1e9 / peak, "traffic": DRAM_TRAFFIC.get((prec, which)),
-                "kernel": f"kmv_{which} ({prec})", "basis": f"{basis} at {clock:.0f} MHz x {SM_COUNT} SMs"}
-        rf, _ = roof_pairs_per_s(prec, w.d, w.m, clock, "fwd")
-        rb, _ = roof_pairs_per_s(prec, w.d, w.m, clock, "bwd")
+        tflops = pk.get("bf16_tflops", 1900.0)
+        peak_pairs, bound, basis = roof(prec, w.d, w.m, clock, which, tflops)
+        if bound == "tensor":
+            fpp = algorithmic_flops_per_pair(w.d, w.m, which)
+            ach = n * n * fpp / dur / 1e12
+            roof_obj = {"bound": "tensor", "achieved": ach, "peak": tflops, "unit": "TFLOP/s",
+                        "frac": ach / tflops, "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst), of measured"}
+        else:
+            ach = n * n / dur / 1e9
+            roof_obj = {"bound": "alu", "achieved": ach, "peak": peak_pairs / 1e9, "unit": "GPair/s",
+                        "frac": ach * 1e9 / peak_pairs,
+                        "peak_source": "derived: SM count x measured issue rate x max SM clock"}
+        roof_obj.update({"traffic": DRAM_TRAFFIC.get((prec, which)), "kernel": f"kmv_{which} ({prec})",
+                         "basis": f"{basis}; {clock:.0f} MHz x {SM_COUNT} SMs"})
+        rf, _, _ = roof(prec, w.d, w.m, clock, "fwd", tflops)
+        rb, _, _ = roof(prec, w.d, w.m, clock, "bwd", tflops)
         both_roof_ms = 1e3 * (n * n / rf + n * n / rb)
+        roof_out = roof_obj
         out = {"metric": METRIC, "value": value, "unit": "GPair/s", "n_gpus": world, "steps": args.steps,
                "warmup": max(3, args.warmup), "ms_per_step": ms_max, "higher_is_better": True,
                "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec == "fp32" else "bf16",
@@ -324,7 +354,7 @@ def main():
                           "precision": prec, "l2": "flushed between steps (256 MiB write)",
                           "parallelism": f"replicas x{world}"},
                "fwd_ms": mf, "bwd_ms": mb, "roof_frac_fwd_bwd": both_roof_ms / ms_max,
-               "roofline": roof,
+               "roofline": roof_out,
                "e2e": {"value": e2e_value, "unit": "GPair/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
                "gpu_launches": launches_per_step * args.steps,
                "clocks": clk.summary(), "wall_s_timed": t_wall}
@@ -349,38 +379,53 @@ def main():
 
 
 def leapfrog_rates(h, dev, rank, world):
-    """Leapfrog steps per second for the N = 2048, d = 1 isotropic workload (theta at
-    alpha = 1, l = 0.2, sigma^2 = 0.01, step 0.05), each form timed on 10 steps;
-    the force and the final energy are compared with the FP32 form."""
+    """Leapfrog steps per second of both forms on two workloads, with the FP32
+    energy before and after as the accuracy check (the BF16 form solves by
+    refinement against the FP32 operator; its force uses the BF16 adjoint)."""
     import torch
     import workloads as wl
     from paper_2412_20884_gb300 import Points, KmvError
-    w = wl.c1(seed=rank)
-    pts = Points(torch.tensor(w.X, dtype=torch.float32, device=dev), w.offsets, ard=False)
-    y = torch.tensor(w.y, dtype=torch.float32, device=dev)
-    phi = torch.tensor(np.random.default_rng(5).standard_normal((1, w.n_total)), dtype=torch.float32, device=dev)
-    res = {"workload": "N=2048 d=1 iso SE, alpha=1 l=0.2 sigma2=0.01, dt=0.05, cg_tol=1e-6, 10 steps"}
-    finals = {}
-    for prec in ("fp32", "bf16_hilo"):
-        th = torch.tensor(w.theta, dtype=torch.float64, device=dev)
-        pi = torch.tensor([[0.2, -0.1, 0.1]], dtype=torch.float64, device=dev)
-        try:
-            h.leapfrog_step(pts, y, phi, th.clone(), pi.clone(), 0.05, prec=prec)
-        except KmvError as e:
-            res[prec] = {"unavailable": str(e)}
-            continue
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        its = []
-        for _ in range(10):
-            st, it, _ = h.leapfrog_step(pts, y, phi, th, pi, 0.05, prec=prec)
-            its.append(int(it[0]))
-        torch.cuda.synchronize()
-        dt = time.perf_counter() - t0
-        finals[prec] = (th.cpu().numpy(), pi.cpu().numpy())
-        res[prec] = {"steps_per_s": 10 / dt, "mean_cg_iters": float(np.mean(its))}
-    if "fp32" in finals and "bf16_hilo" in finals:
-        res["bf16_vs_fp32_theta_maxdiff"] = float(np.abs(finals["fp32"][0] - finals["bf16_hilo"][0]).max())
+    cases = [("N=2048 d=1 iso SE (alpha=1, l=0.2, sigma2=0.01), 1 chain, dt=0.05, cg_tol=1e-6", wl.c1(seed=rank), 10),
+             ("N=16384 d=3 ARD SE (Sec. 4.2 narrowing rule, sigma2=0.1), 8 chains, dt=0.05, cg_tol=1e-6",
+              wl.c5(n=16384, chains=8, seed=rank), 2)]
+    res = {}
+    for label, w, steps in cases:
+        pts = Points(torch.tensor(w.X, dtype=torch.float32, device=dev), w.offsets, ard=w.ard)
+        y = torch.tensor(w.y, dtype=torch.float32, device=dev)
+        # phi ~ N(0, A^-1) has E[phi^T A phi] = N; xi / sqrt(alpha + sigma^2) matches that scale
+        # (A's mean eigenvalue is alpha + sigma^2), which keeps the force at its sampling size
+        diag = np.exp(w.theta[:, 0]) + np.exp(w.theta[:, -1])
+        phi = torch.tensor(np.random.default_rng(5).standard_normal((w.chains, w.n_total)) / np.sqrt(diag)[:, None],
+                           dtype=torch.float32, device=dev)
+        pi0 = 0.2 * np.random.default_rng(6).standard_normal(w.theta.shape)
+        r = {"workload": label, "steps_timed": steps}
+        th0 = torch.tensor(w.theta, dtype=torch.float64, device=dev)
+        p0 = torch.tensor(pi0, dtype=torch.float64, device=dev)
+        H0 = h.kmv_energy(pts, y, phi, th0, p0, cg_maxiter=5000)[0].cpu().numpy()
+        finals = {}
+        for prec in ("fp32", "bf16_hilo"):
+            th, pi = th0.clone(), p0.clone()
+            try:
+                h.leapfrog_step(pts, y, phi, th.clone(), pi.clone(), 0.05, cg_maxiter=5000, prec=prec)
+            except KmvError as e:
+                r[prec] = {"unavailable": str(e)}
+                continue
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            its = []
+            for _ in range(steps):
+                st, it, _ = h.leapfrog_step(pts, y, phi, th, pi, 0.05, cg_maxiter=5000, prec=prec)
+                its.append(it.cpu().numpy())
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            H1 = h.kmv_energy(pts, y, phi, th, pi, cg_maxiter=5000)[0].cpu().numpy()
+            finals[prec] = th.cpu().numpy()
+            r[prec] = {"steps_per_s": steps / dt, "mean_cg_iters": float(np.mean(its)),
+                       "dH_max_abs": float(np.max(np.abs(H1 - H0)))}
+        if "fp32" in finals and "bf16_hilo" in finals:
+            r["bf16_over_fp32_speed"] = r["bf16_hilo"]["steps_per_s"] / r["fp32"]["steps_per_s"]
+            r["theta_maxdiff_bf16_vs_fp32"] = float(np.abs(finals["fp32"] - finals["bf16_hilo"]).max())
+        res["c1" if w.n_total == 2048 else "c5_n16384"] = r
     return res
 
 
