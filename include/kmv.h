@@ -31,7 +31,9 @@
  *     Per-system numerical failures (a solve that did not converge, a
  *     non-finite energy) are reported in the caller's chain_status array.
  *     No call traps or aborts.
- *   - A handle is not thread-safe; use one handle per host thread.
+ *   - A handle is not thread-safe; use one handle per host thread.  Its
+ *     workspace is reused by successive calls, so calls on different streams
+ *     must be ordered by the caller.
  */
 #ifndef KMV_H
 #define KMV_H
@@ -137,8 +139,14 @@ kmv_status kmv_backward(kmv_handle h, const kmv_points* pts, int32_t chains,
  * rhs - A x is formed with the FP32 operator and each correction is solved by
  * CG with the tensor-core operator to 1e-3, so the result meets `tol` against
  * the FP32 operator; `iters` then counts the tensor-core CG iterations.
- * Synchronises `stream` once every few iterations to test convergence on the
- * host, so this call (and the calls built on it) cannot be stream-captured.
+ * Outside stream capture, the call synchronises `stream` every few iterations
+ * to test convergence on the host.  While `stream` is being captured into a
+ * CUDA graph it records exactly cg_maxiter iterations instead (KMV_BF16_HILO:
+ * three refinement steps of cg_maxiter each), with no host synchronisation;
+ * converged systems idle on device-side masks, so a replay gives the eager
+ * result whenever the eager solve converges within cg_maxiter.  Under capture
+ * nothing may be allocated: make the same call (same shapes, same stream
+ * device) once before capturing, and leapfrog_step / kmv_energy likewise.
  */
 kmv_status kmv_cg_solve(kmv_handle h, const kmv_points* pts, int32_t chains,
                         const double* theta, const float* rhs, int32_t rhs_per_chain,

@@ -42,6 +42,9 @@ struct Arena {
 
 kmv_status reserve(kmv_handle h, size_t bytes) {
   if (bytes <= h->ws_bytes) return KMV_OK;
+  if (h->capturing)
+    return fail(h, KMV_EINVAL,
+                "workspace would grow during stream capture: make the same call once before capturing");
   if (h->ws) {
     KMV_CUDA(h, cudaDeviceSynchronize());
     KMV_CUDA(h, cudaFree(h->ws));
@@ -84,6 +87,9 @@ kmv_status check_points(kmv_handle h, const kmv_points* pts, int32_t chains) {
 // Builds (or reuses) the row-tile work items of this point set on the device.
 kmv_status prepare_layout(kmv_handle h, const kmv_points* pts, int32_t chains, cudaStream_t st) {
   KMV_CUDA(h, cudaSetDevice(h->device));
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  KMV_CUDA(h, cudaStreamIsCapturing(st, &cs));
+  h->capturing = cs != cudaStreamCaptureStatusNone;
   Layout& L = h->layout;
   const int n_inst = pts->n_inst;
   const bool same = h->cached_d == pts->d && (int)h->cached_offsets.size() == n_inst + 1 &&
@@ -93,6 +99,8 @@ kmv_status prepare_layout(kmv_handle h, const kmv_points* pts, int32_t chains, c
   L.ard = pts->ard;
   L.n_theta = 2 + (pts->ard ? pts->d : 1);
   if (same) return KMV_OK;
+  if (h->capturing)
+    return fail(h, KMV_EINVAL, "new point layout during stream capture: make the same call once before capturing");
 
   L.n_inst = n_inst;
   L.offsets.assign(pts->offsets, pts->offsets + n_inst + 1);
@@ -267,8 +275,11 @@ kmv_status run_cg(kmv_handle h, const kmv_points* pts, const double* theta, cons
   a.Y = B.q;
   a.sys_active = B.active;
   a.dot_partial = B.partial;
+  // Under stream capture there is no host check: exactly maxiter masked
+  // iterations are recorded (converged systems idle on their device masks, so
+  // the result equals the eager solve that stops at convergence).
   for (int it = 0; it < maxiter; ++it) {
-    if (it % check_every == 0) {
+    if (!h->capturing && it % check_every == 0) {
       KMV_CUDA(h, cudaMemcpyAsync(h->host_flag, B.n_active, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
       KMV_CUDA(h, cudaStreamSynchronize(st));
       if (*h->host_flag == 0) break;
@@ -345,6 +356,7 @@ kmv_status run_cg_refined(kmv_handle h, const kmv_points* pts, const double* the
   const double floor_tol = x_width_fma_ok(pts->d) ? 1e-5 : 1e-3;
   double* worst = reinterpret_cast<double*>(reinterpret_cast<char*>(R.n_active) + 8);
   const int max_outer = 12;
+  const int kCaptureOuter = 3;
   if (!warm && nvec > 0) KMV_CUDA(h, cudaMemsetAsync(x, 0, sizeof(float) * nvec, st));
   KMV_CUDA(h, cudaMemsetAsync(status, 0, sizeof(int32_t) * n_sys, st));
   if (iters) KMV_CUDA(h, cudaMemsetAsync(iters, 0, sizeof(int32_t) * n_sys, st));
@@ -361,14 +373,20 @@ kmv_status run_cg_refined(kmv_handle h, const kmv_points* pts, const double* the
     KMV_CUDA(h, launch_cg_reduce_init(h->dev, L.n_inst, L.chains, R.partial2, tol, R.sys, R.active, R.n_active,
                                       st));
     KMV_CUDA(h, launch_refine_stagnation(n_sys, outer, R.sys, R.prev_rr, R.active, R.n_active, worst, st));
-    KMV_CUDA(h, cudaMemcpyAsync(h->host_flag, R.n_active, 16, cudaMemcpyDeviceToHost, st));
-    KMV_CUDA(h, cudaStreamSynchronize(st));
-    if (*h->host_flag == 0 || outer == max_outer) break;
-    // solve the correction only as far as the target needs: ||r|| must fall to tol ||rhs||
-    double wr;
-    std::memcpy(&wr, reinterpret_cast<const char*>(h->host_flag) + 8, sizeof(double));
-    const double ratio = wr > 0.0 ? std::sqrt(wr) : 1.0;
-    const double inner_tol = std::min(0.5, std::max(floor_tol, 0.5 * tol / ratio));
+    double inner_tol = floor_tol;
+    if (h->capturing) {
+      // no host check under capture: a fixed number of refinement steps
+      if (outer == kCaptureOuter) break;
+    } else {
+      KMV_CUDA(h, cudaMemcpyAsync(h->host_flag, R.n_active, 16, cudaMemcpyDeviceToHost, st));
+      KMV_CUDA(h, cudaStreamSynchronize(st));
+      if (*h->host_flag == 0 || outer == max_outer) break;
+      // solve the correction only as far as the target needs: ||r|| must fall to tol ||rhs||
+      double wr;
+      std::memcpy(&wr, reinterpret_cast<const char*>(h->host_flag) + 8, sizeof(double));
+      const double ratio = wr > 0.0 ? std::sqrt(wr) : 1.0;
+      inner_tol = std::min(0.5, std::max(floor_tol, 0.5 * tol / ratio));
+    }
     // correction from the tensor-core operator, on the systems still active
     if (L.n_items > 0) KMV_CUDA(h, launch_mask_rows(h->dev, L.n_items, L.chains, L.n_total, R.active, R.r, st));
     KMV_TRY(run_cg(h, pts, theta, R.r, L.n_total, R.dx, inner_tol, maxiter, 0, R.in_status, R.in_iters, B,

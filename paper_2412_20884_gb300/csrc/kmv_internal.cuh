@@ -147,4 +147,7 @@ struct kmv_handle_s {
   size_t ws_bytes = 0;
   int32_t* host_flag = nullptr;   // pinned, for convergence checks
   void* tc = nullptr;             // tensor-core path state (kmv_tc.cu)
+  // true while the current call's stream is being captured into a CUDA graph:
+  // no allocation, no table upload, no host synchronisation may happen then
+  bool capturing = false;
 };

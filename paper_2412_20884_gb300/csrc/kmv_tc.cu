@@ -801,6 +801,8 @@ kmv_status tc_fail(kmv_handle h, kmv_status s, const char* msg) {
 kmv_status tc_build_plan(kmv_handle h, TcState* S, cudaStream_t st) {
   const Layout& L = h->layout;
   if (S->chains == L.chains && S->offsets == L.offsets && S->tables) return KMV_OK;
+  if (h->capturing)
+    return tc_fail(h, KMV_EINVAL, "new work plan during stream capture: make the same call once before capturing");
   if (S->num_sms == 0) {
     int dev = 0;
     cudaGetDevice(&dev);
@@ -884,6 +886,9 @@ kmv_status tc_build_plan(kmv_handle h, TcState* S, cudaStream_t st) {
 
 kmv_status tc_ensure_buf(kmv_handle h, TcState* S, size_t bytes) {
   if (bytes <= S->buf_bytes) return KMV_OK;
+  if (h->capturing)
+    return tc_fail(h, KMV_EINVAL,
+                   "workspace would grow during stream capture: make the same call once before capturing");
   if (S->buf) {
     cudaDeviceSynchronize();
     cudaFree(S->buf);

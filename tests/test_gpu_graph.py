@@ -1,0 +1,75 @@
+"""Leapfrog trajectories captured in a CUDA graph reproduce eager execution
+(batching rows of the hot path: whole steps, solves included, recorded once and
+replayed without host synchronisation)."""
+import numpy as np
+import pytest
+import torch
+
+import workloads as wl
+from helpers import to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+def _inputs(seed):
+    w = wl.ragged([300, 200], d=2, chains=2, m=1, seed=seed, sigma2=0.1)
+    pts, theta0, _, _ = to_dev(w)
+    y = torch.tensor(w.y, dtype=torch.float32, device="cuda")
+    rng = np.random.default_rng(seed)
+    diag = np.exp(w.theta[:, 0]) + np.exp(w.theta[:, -1])
+    phi = torch.tensor(rng.standard_normal((2, w.n_total)) / np.sqrt(diag[:2])[:, None], dtype=torch.float32,
+                       device="cuda")
+    pi0 = torch.tensor(0.2 * rng.standard_normal(w.theta.shape), dtype=torch.float64, device="cuda")
+    return pts, theta0, y, phi, pi0
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16_hilo"])
+def test_graph_replay_equals_eager(kmv_handle, prec):
+    pts, theta0, y, phi, pi0 = _inputs(80)
+    steps, dt, maxit = 5, 0.02, 300
+    th_e, pi_e = theta0.clone(), pi0.clone()
+    xw_e = torch.empty_like(phi)
+    for _ in range(steps):
+        st, _, _ = kmv_handle.leapfrog_step(pts, y, phi, th_e, pi_e, dt, cg_maxiter=maxit, x_work=xw_e, prec=prec)
+        assert torch.all(st == 0)
+    th_g, pi_g = theta0.clone(), pi0.clone()
+    xw_g = torch.empty_like(phi)
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):          # eager warm-up sizes the workspace
+        kmv_handle.leapfrog_step(pts, y, phi, theta0.clone(), pi0.clone(), dt, cg_maxiter=maxit, x_work=xw_g,
+                                 prec=prec)
+    torch.cuda.current_stream().wait_stream(side)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        for _ in range(steps):
+            kmv_handle.leapfrog_step(pts, y, phi, th_g, pi_g, dt, cg_maxiter=maxit, x_work=xw_g, prec=prec)
+    th_g.copy_(theta0)
+    pi_g.copy_(pi0)
+    graph.replay()
+    torch.cuda.synchronize()
+    if prec == "fp32":
+        # same kernels in the same order; converged systems are masked on the device
+        assert torch.equal(th_g, th_e) and torch.equal(pi_g, pi_e)
+    else:
+        # The refined solve runs a fixed number of refinement steps under capture
+        # instead of the eager run's adaptive ones; both stop at the FP32 floor of
+        # the residual, and solutions meeting that floor differ by up to ~kappa x
+        # floor, i.e. ~1e-3 of the force.  Captured and eager BF16 trajectories
+        # must both stay within that band of the FP32 trajectory.
+        th_32, pi_32 = theta0.clone(), pi0.clone()
+        for _ in range(steps):
+            kmv_handle.leapfrog_step(pts, y, phi, th_32, pi_32, dt, cg_maxiter=maxit, prec="fp32")
+        band_pi = 1e-3 * float(pi_32.abs().max())
+        band_th = steps * dt * band_pi
+        for th, pi in ((th_g, pi_g), (th_e, pi_e)):
+            assert float((th - th_32).abs().max()) <= band_th
+            assert float((pi - pi_32).abs().max()) <= band_pi
+    # a second replay from the same start gives the same trajectory
+    th_first = th_g.clone()
+    th_g.copy_(theta0)
+    pi_g.copy_(pi0)
+    graph.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(th_g, th_first)
