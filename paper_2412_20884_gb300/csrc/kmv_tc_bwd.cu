@@ -1,17 +1,17 @@
 // Tensor-core (tcgen05) adjoint of L = sum G o (A V), KMV_BF16_HILO.
 //
 // For every pair the gradient needs W_ij = G_i . V_j, K0_ij and, per input
-// dimension, (xt_ik - xt_jk)^2.  Per 64-column half tile and I tile g the MMA
-// warp writes into TMEM
+// dimension, (xt_ik - xt_jk)^2.  Per 64-column half tile and I tile g an MMA
+// issuer writes into TMEM
 //   S_g = XA_g XB^T           the base-2 exponent (BF16 hi/lo, as in the forward)
 //   W_g = GI_g VJ^T           GI rows [gh, gh, gl], VJ rows [vh, vl, vh] (BF16 hi/lo)
-// the exp warpgroup forms P = 2^S and Q = W P and writes both back as F16, and
-// the MMA warp then accumulates, per row i,
+// the exp warpgroup forms Q = W 2^S and writes it to its own TMEM columns as
+// F16, and the issuer then accumulates, per row i,
 //   ACC_g += Q BG             BG columns for dimension k: 4k..4k+3 = [xh, xl, sh, sl]
 //                             (F16 hi/lo of xt_jk and of xt_jk^2), column 60 = 1;
 //                             giving R_ik = sum_j Q_ij xt_jk, T_ik = sum_j Q_ij xt_jk^2
 //                             and q_i = sum_j Q_ij
-//   O'_g  += P VTG            dL/dV = A G (F16 G^T, per-column power-of-two scale)
+// dL/dV = A G is the forward product with G in place of V (kmv_tc.cu).
 // Every kFoldH half tiles the warpgroup folds, per row,
 //   sum_j Q_ij (xt_ik - xt_jk)^2 = xt_ik^2 q_i - 2 xt_ik R_ik + T_ik
 // into FP64 accumulators.  Because q, R and T are formed from the same rounded
@@ -37,7 +37,6 @@ constexpr int kFoldH = 64;   // half tiles (64 columns) per FP32 accumulation (4
 constexpr int kMaxDB = 15;   // 4 d gradient features + the ones column fit a 64-column accumulator
 constexpr int kNB = 64;      // accumulator columns; the ones column is kQCol
 constexpr int kQCol = 60;
-constexpr int kMaxMB = 64;   // fused dL/dV columns
 constexpr int kGW = 16;      // doubles per (item, warp) gradient partial: [q, contrib_0..d-1]
 
 struct TcBwdArgs {
@@ -45,7 +44,7 @@ struct TcBwdArgs {
   int n_items;
   int chains;
   int T_total;
-  int KX, KG, NB, MPg, S, NA;
+  int KX, KG, NB, S, NA;
   int d, n_theta, ard;
   DevLayout L;
   TcTables T;
@@ -56,9 +55,7 @@ struct TcBwdArgs {
   const uint8_t* GI;
   const uint8_t* VJ;
   const uint8_t* BG;
-  const uint8_t* VTG;
   double* gpart;   // (n_items, 8 warps, kGW)
-  double* vpart;   // (n_items, 256, m), fused dL/dV, or null
   int m;
   const int32_t* sys_active;
   int* err;
@@ -90,16 +87,23 @@ __device__ __forceinline__ void issue_ts4(uint32_t d_tmem, uint32_t a_tmem, uint
   for (int k = 0; k < 4; ++k) ptx::mma_ts(d_tmem, a_tmem + 8 * k, db + 16 * k, idesc, (k > 0) || acc);
 }
 
-// RM > 0: FP64 accumulators of the fused dL/dV (up to RM columns) in registers;
-// RM == 0: in the per-item partial.
-template <int RM>
-__global__ void __launch_bounds__(kThreads, 1) tc_bwd_kernel(TcBwdArgs a) {
+// Warp roles: warps 0-7 two exp warpgroups (one per I tile), warp 8 MMA
+// issuer of I tile 0 (and TMEM owner), warp 9 producer, warp 10 MMA issuer of
+// I tile 1.  TMEM per I tile g (256 columns from 256 g): S [0,64), W [64,128),
+// Q [128,160), ACC [192,256).  A half tile's S and W are released as soon as
+// the warpgroup has loaded them, so the next half's S, W MMAs run during this
+// half's exps; Q has its own columns, so the feature-sum MMAs of this half run
+// during the next half's exps.
+constexpr int kBwdThreads = 352;
+constexpr int kBwdIssue1Warp = 10;
+
+__global__ void __launch_bounds__(kBwdThreads, 1) tc_bwd_kernel(TcBwdArgs a) {
   using namespace ptx;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = align1024(smem_raw);
-  const uint32_t XT = a.KX * 256u, GT = a.KG * 256u, BT = a.NB * 256u, OT = a.MPg * 256u;
+  const uint32_t XT = a.KX * 256u, GT = a.KG * 256u, BT = a.NB * 256u;
   const uint32_t ABUF = 2 * XT + 2 * GT;   // one A buffer: XA g0, XA g1, GI g0, GI g1
-  const uint32_t STG = XT + GT + BT + OT;  // one stage: XB, VJ, BG, VTG
+  const uint32_t STG = XT + GT + BT;       // one stage: XB, VJ, BG
   const int S = a.S, NA = a.NA;
   uint8_t* sA = smem;
   uint8_t* sS = sA + NA * ABUF;
@@ -107,29 +111,33 @@ __global__ void __launch_bounds__(kThreads, 1) tc_bwd_kernel(TcBwdArgs a) {
   uint64_t* empty = full + S;
   uint64_t* a_full = empty + S;
   uint64_t* a_empty = a_full + 2;
-  uint64_t* s_full = a_empty + 2;
-  uint64_t* p_ready = s_full + 2;
-  uint64_t* o_ready = p_ready + 2;
+  uint64_t* s_full = a_empty + 2;    // [g] S, W of a half tile written
+  uint64_t* s_free = s_full + 2;     // [g] S, W loaded into registers
+  uint64_t* q_ready = s_free + 2;    // [g] Q written
+  uint64_t* q_free = q_ready + 2;    // [g] Q consumed by the feature-sum MMAs
+  uint64_t* o_ready = q_free + 2;
   uint64_t* o_free = o_ready + 2;
-  uint64_t* done = o_free + 2;
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(done + 1);
+  uint64_t* done = o_free + 2;       // [g]
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(done + 2);
   volatile int* abort = reinterpret_cast<volatile int*>(tslot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
     for (int i = 0; i < S; ++i) {
       mbar_init(&full[i], 1);
-      mbar_init(&empty[i], 1);
+      mbar_init(&empty[i], 2);
     }
     for (int g = 0; g < 2; ++g) {
       mbar_init(&a_full[g], 1);
-      mbar_init(&a_empty[g], 1);
+      mbar_init(&a_empty[g], 2);
       mbar_init(&s_full[g], 1);
-      mbar_init(&p_ready[g], 128);
+      mbar_init(&s_free[g], 128);
+      mbar_init(&q_ready[g], 128);
+      mbar_init(&q_free[g], 1);
       mbar_init(&o_ready[g], 1);
       mbar_init(&o_free[g], 128);
+      mbar_init(&done[g], 1);
     }
-    mbar_init(done, 1);
     *abort = 0;
     fence_barrier_init();
   }
@@ -168,7 +176,6 @@ __global__ void __launch_bounds__(kThreads, 1) tc_bwd_kernel(TcBwdArgs a) {
           bulk_g2s(sd, a.XB + tj * XT, XT, &full[stage]);
           bulk_g2s(sd + XT, a.VJ + tj * GT, GT, &full[stage]);
           bulk_g2s(sd + XT + GT, a.BG + tj * BT, BT, &full[stage]);
-          if (OT) bulk_g2s(sd + XT + GT + BT, a.VTG + tj * OT, OT, &full[stage]);
           ++n_issued;
           if (++stage == (uint32_t)S) { stage = 0; sph ^= 1; }
         }
@@ -185,104 +192,106 @@ __global__ void __launch_bounds__(kThreads, 1) tc_bwd_kernel(TcBwdArgs a) {
         }
       }
     }
-  } else if (warp == kMmaWarp) {
+  } else if (warp == kMmaWarp || warp == kBwdIssue1Warp) {
     if (lane == 0) {
-      // ------------------------------------------------------------ MMA issuer
+      // ------------------------------------------------------------ MMA issuer of I tile g
+      // Half-tile stream k: S, W of half k once half k-1 is loaded by the
+      // warpgroup, then the feature sums of half k-1 once its Q is written.
+      const int g = warp == kMmaWarp ? 0 : 1;
       const uint32_t idSW = idesc_f16(128, 64, 1, 1);
-      const uint32_t idA = idesc_f16(128, kNB, 0, 0);
-      const uint32_t idO = a.MPg ? idesc_f16(128, a.MPg, 0, 0) : 0u;
+      const uint32_t idA = idesc_f16(128, a.NB, 0, 0);
       const uint32_t sboX = a.KX * 16u, sboG = a.KG * 16u;
       const int nkx = a.KX / 16, nkg = a.KG / 16;
-      const uint64_t dXA = sdesc(smem_u32(sA), 128, sboX);
-      const uint64_t dGI = sdesc(smem_u32(sA + 2 * XT), 128, sboG);
+      const uint64_t dXA = sdesc(smem_u32(sA + g * XT), 128, sboX);
+      const uint64_t dGI = sdesc(smem_u32(sA + 2 * XT + g * GT), 128, sboG);
       const uint64_t dXB = sdesc(smem_u32(sS), 128, sboX);
       const uint64_t dVJ = sdesc(smem_u32(sS + XT), 128, sboG);
       const uint64_t dBG = sdesc(smem_u32(sS + XT + GT), 128, 2048);
-      const uint64_t dVT = sdesc(smem_u32(sS + XT + GT + BT), 128, 2048);
+      const uint32_t tg = tbase + 256 * g;
       int it = 0;
-      uint32_t stage = 0, sph = 0;
-      uint32_t pph[2] = {0, 0}, oph[2] = {0, 0};
-      bool opend[2] = {false, false};
+      uint32_t stage = 0, sph = 0, sf_ph = 0, qr_ph = 0, of_ph = 0;
+      bool opend = false;
+      long long k = 0;
+      bool have_prev = false;
+      uint32_t prev_stage = 0;
+      int prev_h = 0, prev_nH = 0;
       for (int t = blockIdx.x; t < a.n_items; t += gridDim.x) {
         const int4 item = a.items[t];
         if (a.sys_active && !a.sys_active[item.x]) continue;
         const int ab = it % NA;
         const int nH = 2 * item.w;
-        if (!mbar_wait(&a_full[ab], (it / NA) & 1, abort, a.err, 23)) goto mma_out;
-        if (!mbar_wait(&full[stage], sph, abort, a.err, 24)) goto mma_out;
-        tc_fence_after();
-#pragma unroll
-        for (int g = 0; g < 2; ++g) {
-          issue_ss(tbase + g * 128, sdesc_add(dXA, ab * ABUF + g * XT), sdesc_add(dXB, stage * STG), nkx, idSW);
-          issue_ss(tbase + g * 128 + 64, sdesc_add(dGI, ab * ABUF + g * GT), sdesc_add(dVJ, stage * STG), nkg,
-                   idSW);
-          tc_commit(&s_full[g]);
-        }
-        for (int h = 0; h < nH; ++h) {
+        for (int h = 0; h < nH; ++h, ++k) {
           const int hh = h & 1;
-          const uint32_t cur = stage;
-          uint32_t nst = stage + 1, nph = sph;
-          if (nst == (uint32_t)S) { nst = 0; nph ^= 1; }
-          const uint32_t acc = (h % kFoldH) != 0;
-          const bool fold = (h % kFoldH) == kFoldH - 1 || h == nH - 1;
-#pragma unroll
-          for (int g = 0; g < 2; ++g) {
-            if (!mbar_wait(&p_ready[g], pph[g], abort, a.err, 25)) goto mma_out;
-            pph[g] ^= 1;
+          // ---- S, W of half k
+          if (k > 0) {
+            if (!mbar_wait(&s_free[g], sf_ph, abort, a.err, 23)) goto mma_out;
+            sf_ph ^= 1;
+          }
+          if (h == 0 && !mbar_wait(&a_full[ab], (it / NA) & 1, abort, a.err, 24)) goto mma_out;
+          if (hh == 0 && !mbar_wait(&full[stage], sph, abort, a.err, 25)) goto mma_out;
+          tc_fence_after();
+          issue_ss(tg, sdesc_add(dXA, ab * ABUF), sdesc_add(dXB, stage * STG + hh * a.KX * 128u), nkx, idSW);
+          issue_ss(tg + 64, sdesc_add(dGI, ab * ABUF), sdesc_add(dVJ, stage * STG + hh * a.KG * 128u), nkg, idSW);
+          tc_commit(&s_full[g]);
+          // the A buffer is read only by the S, W MMAs: release it after the
+          // item's last half, before the next item waits for its own A buffer
+          if (h == nH - 1) tc_commit(&a_empty[ab]);
+          // ---- feature sums of half k-1
+          if (have_prev) {
+            if (!mbar_wait(&q_ready[g], qr_ph, abort, a.err, 26)) goto mma_out;
+            qr_ph ^= 1;
             tc_fence_after();
-            if (!acc && opend[g]) {
-              if (!mbar_wait(&o_free[g], oph[g], abort, a.err, 26)) goto mma_out;
-              oph[g] ^= 1;
-              opend[g] = false;
+            const uint32_t acc = (prev_h % kFoldH) != 0;
+            if (!acc && opend) {
+              if (!mbar_wait(&o_free[g], of_ph, abort, a.err, 27)) goto mma_out;
+              of_ph ^= 1;
+              opend = false;
               tc_fence_after();
             }
-            issue_ts4(tbase + 256 + g * 128, tbase + g * 128 + 64, sdesc_add(dBG, cur * STG + hh * 1024), idA, acc);
-            if (a.MPg)
-              issue_ts4(tbase + 256 + g * 128 + 64, tbase + g * 128, sdesc_add(dVT, cur * STG + hh * 1024), idO, acc);
-            if (fold) {
+            issue_ts4(tg + 192, tg + 128, sdesc_add(dBG, prev_stage * STG + (prev_h & 1) * 1024u), idA, acc);
+            tc_commit(&q_free[g]);
+            if ((prev_h % kFoldH) == kFoldH - 1 || prev_h == prev_nH - 1) {
               tc_commit(&o_ready[g]);
-              opend[g] = true;
+              opend = true;
             }
-            if (g == 1 && hh == 1) tc_commit(&empty[cur]);
-            if (h + 1 < nH) {
-              uint32_t sst = cur;
-              int shh = 1;
-              if (hh == 1) {
-                if (g == 0) {
-                  if (!mbar_wait(&full[nst], nph, abort, a.err, 27)) goto mma_out;
-                  tc_fence_after();
-                }
-                sst = nst;
-                shh = 0;
-              }
-              issue_ss(tbase + g * 128, sdesc_add(dXA, ab * ABUF + g * XT),
-                       sdesc_add(dXB, sst * STG + shh * a.KX * 128u), nkx, idSW);
-              issue_ss(tbase + g * 128 + 64, sdesc_add(dGI, ab * ABUF + g * GT),
-                       sdesc_add(dVJ, sst * STG + shh * a.KG * 128u), nkg, idSW);
-              tc_commit(&s_full[g]);
-            }
+            if (prev_h & 1) tc_commit(&empty[prev_stage]);
           }
+          have_prev = true;
+          prev_stage = stage;
+          prev_h = h;
+          prev_nH = nH;
           if (hh == 1) {
-            stage = nst;
-            sph = nph;
+            if (++stage == (uint32_t)S) { stage = 0; sph ^= 1; }
           }
         }
-        tc_commit(&a_empty[ab]);
         ++it;
       }
+      if (have_prev) {
+        if (!mbar_wait(&q_ready[g], qr_ph, abort, a.err, 26)) goto mma_out;
+        tc_fence_after();
+        const uint32_t acc = (prev_h % kFoldH) != 0;
+        if (!acc && opend) {
+          if (!mbar_wait(&o_free[g], of_ph, abort, a.err, 27)) goto mma_out;
+          tc_fence_after();
+        }
+        issue_ts4(tg + 192, tg + 128, sdesc_add(dBG, prev_stage * STG + (prev_h & 1) * 1024u), idA, acc);
+        tc_commit(&q_free[g]);
+        tc_commit(&o_ready[g]);
+        tc_commit(&empty[prev_stage]);
+      }
     mma_out:
-      tc_commit(done);
-      mbar_drain(done, 0, 500000000ull);
+      tc_commit(&done[g]);
+      mbar_drain(&done[g], 0, 500000000ull);
     }
     __syncwarp();
   } else {
     // ------------------------------------------------------------ exp warpgroups
     const int g = warp >> 2, w = warp & 3;
     const int row = 32 * w + lane;
-    const uint32_t tl = tbase + (static_cast<uint32_t>(32 * w) << 16);
-    const uint32_t s_col = g * 128, w_col = g * 128 + 64, a_col = 256 + g * 128, o_col = 256 + g * 128 + 64;
+    const uint32_t tl = tbase + 256 * g + (static_cast<uint32_t>(32 * w) << 16);
     const int d = a.d;
-    uint32_t sph = 0, oph = 0;
+    uint32_t sph = 0, qf_ph = 0, oph = 0;
+    long long k = 0;
     for (int t = blockIdx.x; t < a.n_items; t += gridDim.x) {
       const int4 item = a.items[t];
       if (a.sys_active && !a.sys_active[item.x]) continue;
@@ -295,57 +304,64 @@ __global__ void __launch_bounds__(kThreads, 1) tc_bwd_kernel(TcBwdArgs a) {
       double dacc[kMaxDB];
       double dq = 0.0;
 #pragma unroll
-      for (int k = 0; k < kMaxDB; ++k) {
-        xt[k] = 0.f;
-        dacc[k] = 0.0;
+      for (int kk = 0; kk < kMaxDB; ++kk) {
+        xt[kk] = 0.f;
+        dacc[kk] = 0.0;
       }
       if (valid) {
         const int64_t i = a.L.offsets[b] + rl;
 #pragma unroll
-        for (int k = 0; k < kMaxDB; ++k) {
-          if (k < d) {
-            const float sc = (float)(sqrt(2.0 * kHalfLog2e) * exp(-th[1 + (a.ard ? k : 0)]));
-            xt[k] = xt_of(a.x[i * d + k], sc);
+        for (int kk = 0; kk < kMaxDB; ++kk) {
+          if (kk < d) {
+            const float sc = (float)(sqrt(2.0 * kHalfLog2e) * exp(-th[1 + (a.ard ? kk : 0)]));
+            xt[kk] = xt_of(a.x[i * d + kk], sc);
           }
         }
       }
-      double* vrow = a.vpart ? a.vpart + ((size_t)t * 256 + g * 128 + row) * a.m : nullptr;
-      double racc[RM > 0 ? RM : 1];
-#pragma unroll
-      for (int q = 0; q < (RM > 0 ? RM : 1); ++q) racc[q] = 0.0;
-      bool first = true;
       const int nH = 2 * item.w;
-      for (int h = 0; h < nH; ++h) {
+      for (int h = 0; h < nH; ++h, ++k) {
         bool ok = mbar_wait(&s_full[g], sph, abort, a.err, 28);
         if (!__all_sync(0xffffffffu, ok)) goto exp_out;
         sph ^= 1;
         tc_fence_after();
-#pragma unroll
-        for (int cc = 0; cc < 2; ++cc) {
-          uint32_t sv[32], wv[32], pp[16], qq[16];
-          tmem_ld32(tl + s_col + 32 * cc, sv);
-          tmem_ld32(tl + w_col + 32 * cc, wv);
+        {
+          uint32_t s0[32], w0[32], s1[32], w1[32], qq[32];
+          tmem_ld32(tl, s0);
+          tmem_ld32(tl + 64, w0);
           tmem_ld_wait();
+          tmem_ld32(tl + 32, s1);
+          tmem_ld32(tl + 96, w1);
 #pragma unroll
-          for (int q = 0; q < 16; ++q) {
-            const float p0 = ex2(__uint_as_float(sv[2 * q]));
-            const float p1 = ex2(__uint_as_float(sv[2 * q + 1]));
-            pp[q] = pack_f16x2(p0, p1);
-            qq[q] = pack_f16x2(p0 * __uint_as_float(wv[2 * q]), p1 * __uint_as_float(wv[2 * q + 1]));
+          for (int q = 0; q < 16; ++q)
+            qq[q] = pack_f16x2(ex2(__uint_as_float(s0[2 * q])) * __uint_as_float(w0[2 * q]),
+                               ex2(__uint_as_float(s0[2 * q + 1])) * __uint_as_float(w0[2 * q + 1]));
+          tmem_ld_wait();
+          // S, W of this half are in registers: the tensor core may overwrite them
+          tc_fence_before();
+          mbar_arrive(&s_free[g]);
+#pragma unroll
+          for (int q = 0; q < 16; ++q)
+            qq[16 + q] = pack_f16x2(ex2(__uint_as_float(s1[2 * q])) * __uint_as_float(w1[2 * q]),
+                                    ex2(__uint_as_float(s1[2 * q + 1])) * __uint_as_float(w1[2 * q + 1]));
+          if (k > 0) {
+            // Q of the previous half must have been consumed
+            ok = mbar_wait(&q_free[g], qf_ph, abort, a.err, 30);
+            if (!__all_sync(0xffffffffu, ok)) goto exp_out;
+            qf_ph ^= 1;
+            tc_fence_after();
           }
-          tmem_st16(tl + s_col + 16 * cc, pp);
-          tmem_st16(tl + w_col + 16 * cc, qq);
+          tmem_st32(tl + 128, qq);
         }
         tmem_st_wait();
         tc_fence_before();
-        mbar_arrive(&p_ready[g]);
+        mbar_arrive(&q_ready[g]);
         if ((h % kFoldH) == kFoldH - 1 || h == nH - 1) {
           ok = mbar_wait(&o_ready[g], oph, abort, a.err, 29);
           if (!__all_sync(0xffffffffu, ok)) goto exp_out;
           oph ^= 1;
           tc_fence_after();
           uint32_t o3[16];
-          tmem_ld16(tl + a_col + 48, o3);
+          tmem_ld16(tl + 192 + 48, o3);
           tmem_ld_wait();
           const float qs = __uint_as_float(o3[kQCol - 48]);
           dq += (double)qs;
@@ -357,58 +373,24 @@ __global__ void __launch_bounds__(kThreads, 1) tc_bwd_kernel(TcBwdArgs a) {
 #pragma unroll
                 for (int q = 0; q < 16; ++q) o[q] = o3[q];
               } else {
-                tmem_ld16(tl + a_col + 16 * c4, o);
+                tmem_ld16(tl + 192 + 16 * c4, o);
                 tmem_ld_wait();
               }
 #pragma unroll
               for (int u = 0; u < 4; ++u) {
-                const int k = 4 * c4 + u;
-                if (k < kMaxDB && k < d) {
+                const int kk = 4 * c4 + u;
+                if (kk < kMaxDB && kk < d) {
                   const float R = __uint_as_float(o[4 * u]) + __uint_as_float(o[4 * u + 1]);
                   const float T = __uint_as_float(o[4 * u + 2]) + __uint_as_float(o[4 * u + 3]);
-                  const float x = xt[k];
-                  dacc[k] += (double)fmaf(x, fmaf(x, qs, -2.f * R), T);
+                  const float x = xt[kk];
+                  dacc[kk] += (double)fmaf(x, fmaf(x, qs, -2.f * R), T);
                 }
               }
             }
           }
-          if (vrow) {
-            if (RM > 0) {
-#pragma unroll
-              for (int c0 = 0; c0 < (RM > 0 ? RM : 16); c0 += 16) {
-                if (c0 < a.MPg) {
-                  uint32_t o[16];
-                  tmem_ld16(tl + o_col + c0, o);
-                  tmem_ld_wait();
-#pragma unroll
-                  for (int q = 0; q < 16; ++q) racc[c0 + q] += (double)__uint_as_float(o[q]);
-                }
-              }
-            } else {
-              for (int c0 = 0; c0 < a.MPg; c0 += 16) {
-                uint32_t o[16];
-                tmem_ld16(tl + o_col + c0, o);
-                tmem_ld_wait();
-#pragma unroll
-                for (int q = 0; q < 16; ++q) {
-                  const int col = c0 + q;
-                  if (col < a.m) {
-                    const double v = (double)__uint_as_float(o[q]);
-                    vrow[col] = first ? v : vrow[col] + v;
-                  }
-                }
-              }
-            }
-          }
-          first = false;
           tc_fence_before();
           mbar_arrive(&o_free[g]);
         }
-      }
-      if (vrow && RM > 0) {
-#pragma unroll
-        for (int q = 0; q < (RM > 0 ? RM : 1); ++q)
-          if (q < a.m) vrow[q] = racc[q];
       }
       // per-warp partial of this item: [q, contrib_0 .. contrib_{d-1}]
       {
@@ -418,12 +400,12 @@ __global__ void __launch_bounds__(kThreads, 1) tc_bwd_kernel(TcBwdArgs a) {
         for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
         if (lane == 0) out[0] = v;
 #pragma unroll
-        for (int k = 0; k < kMaxDB; ++k) {
-          if (k < d) {
-            double u = dacc[k];
+        for (int kk = 0; kk < kMaxDB; ++kk) {
+          if (kk < d) {
+            double u = dacc[kk];
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) u += __shfl_down_sync(0xffffffffu, u, o);
-            if (lane == 0) out[1 + k] = u;
+            if (lane == 0) out[1 + kk] = u;
           }
         }
       }
@@ -437,10 +419,10 @@ __global__ void __launch_bounds__(kThreads, 1) tc_bwd_kernel(TcBwdArgs a) {
   if (warp == kMmaWarp) tmem_dealloc(tbase, 512);
 }
 
-// max |G_i| and max |V_j| per system (row norms), per-column max |G|, and sum_i G_i . V_i.
+// max |G_i| and max |V_j| per system (row norms) and sum_i G_i . V_i.
 __global__ void tc_bwd_norms_kernel(DevLayout L, int chains, int64_t n_total, const float* V, const float* G,
-                                    int m, int want_col, uint32_t* gmax, uint32_t* vmax, uint32_t* gcol,
-                                    double* gvpart, const int32_t* sys_active) {
+                                    int m, uint32_t* gmax, uint32_t* vmax, double* gvpart,
+                                    const int32_t* sys_active) {
   __shared__ double red[kTile / 32];
   const int item = blockIdx.x, c = blockIdx.y;
   const int b = L.item_inst[item];
@@ -456,7 +438,6 @@ __global__ void tc_bwd_norms_kernel(DevLayout L, int chains, int64_t n_total, co
       g2 = fmaf(gq, gq, g2);
       v2 = fmaf(vq, vq, v2);
       gv += (double)gq * (double)vq;
-      if (want_col) atomicMax(&gcol[(int64_t)s * m + q], __float_as_uint(fabsf(gq)));
     }
     atomicMax(&gmax[s], __float_as_uint(sqrtf(g2)));
     atomicMax(&vmax[s], __float_as_uint(sqrtf(v2)));
@@ -465,12 +446,12 @@ __global__ void tc_bwd_norms_kernel(DevLayout L, int chains, int64_t n_total, co
   if (threadIdx.x == 0) gvpart[(int64_t)item * chains + c] = t;
 }
 
-// GI, VJ, BG and VTG operand tiles of every (chain, padded tile).
+// GI, VJ and BG operand tiles of every (chain, padded tile).
 __global__ void tc_prep_bwd_kernel(DevLayout L, TcTables T, int chains, int d, int ard, int n_theta, int m,
-                                   int KG, int NB, int MPg, int T_total, const float* x, const double* theta,
+                                   int KG, int NB, int T_total, const float* x, const double* theta,
                                    const float* V, const float* G, int64_t n_total, const uint32_t* gmax,
-                                   const uint32_t* vmax, const uint32_t* gcol, const int32_t* sys_active,
-                                   uint8_t* GI, uint8_t* VJ, uint8_t* BG, uint8_t* VTG, int* err) {
+                                   const uint32_t* vmax, const int32_t* sys_active, uint8_t* GI, uint8_t* VJ,
+                                   uint8_t* BG, int* err) {
   const int t = blockIdx.x, c = blockIdx.y, r = threadIdx.x;
   const int b = T.tile_inst[t];
   const int s = b * chains + c;
@@ -519,14 +500,6 @@ __global__ void tc_prep_bwd_kernel(DevLayout L, TcTables T, int chains, int d, i
       bg[t_off(4 * k + 3, r) / 2] = sl;
     }
     bg[t_off(kQCol, r) / 2] = __float2half_rn(1.f);
-  }
-  if (MPg) {
-    __half* vt = reinterpret_cast<__half*>(VTG + tile * (size_t)MPg * 256);
-    for (int q = 0; q < MPg; ++q) {
-      float v = 0.f;
-      if (valid && q < m) v = G[((int64_t)c * n_total + i) * m + q] * col_scale(gcol[(int64_t)s * m + q]);
-      vt[t_off(q, r) / 2] = __float2half_rn(v);
-    }
   }
 }
 
@@ -599,10 +572,8 @@ kmv_status tc_backward(kmv_handle h, const KmvArgs& a, double* grad, cudaStream_
   if (stt != KMV_OK) return stt;
   const int n_sys = L.n_inst * L.chains;
   const int KX = x_width(a.d), KG = round16(3 * a.m), NB = kNB;
-  const bool fused = a.Y != nullptr && a.m <= kMaxMB;
-  const int MPg = fused ? round16(a.m) : 0;
-  const size_t XT = (size_t)KX * 256, GT = (size_t)KG * 256, BT = (size_t)NB * 256, OT = (size_t)MPg * 256;
-  const size_t ABUF = 2 * XT + 2 * GT, STG = XT + GT + BT + OT;
+  const size_t XT = (size_t)KX * 256, GT = (size_t)KG * 256, BT = (size_t)NB * 256;
+  const size_t ABUF = 2 * XT + 2 * GT, STG = XT + GT + BT;
   const size_t fixed = 1024 + 512;
   int NA = 2;
   int stages = (int)std::min<size_t>(6, (kMaxSmem - fixed - NA * ABUF) / STG);
@@ -616,29 +587,22 @@ kmv_status tc_backward(kmv_handle h, const KmvArgs& a, double* grad, cudaStream_
   auto al = [](size_t v) { return (v + 255) & ~size_t(255); };
   const size_t tiles = (size_t)L.chains * S->T_total;
   const size_t o_xa = 0, o_xb = o_xa + al(tiles * XT), o_gi = o_xb + al(tiles * XT);
-  const size_t o_vj = o_gi + al(tiles * GT), o_bg = o_vj + al(tiles * GT), o_vt = o_bg + al(tiles * BT);
-  const size_t o_mx = o_vt + al(tiles * OT);
-  const size_t o_gc = o_mx + al(sizeof(uint32_t) * 2 * n_sys);
-  const size_t o_gv = o_gc + al(sizeof(uint32_t) * (size_t)n_sys * a.m);
+  const size_t o_vj = o_gi + al(tiles * GT), o_bg = o_vj + al(tiles * GT), o_mx = o_bg + al(tiles * BT);
+  const size_t o_gv = o_mx + al(sizeof(uint32_t) * 2 * n_sys);
   const size_t o_gp = o_gv + al(sizeof(double) * (size_t)std::max(1, L.n_items) * L.chains);
-  const size_t o_vp = o_gp + al(sizeof(double) * (size_t)std::max(1, S->n_items) * 8 * kGW);
-  const size_t o_er = o_vp + (fused ? al(sizeof(double) * (size_t)S->n_items * 256 * a.m) : 0);
+  const size_t o_er = o_gp + al(sizeof(double) * (size_t)std::max(1, S->n_items) * 8 * kGW);
   stt = tc_ensure_buf(h, S, o_er + 256);
   if (stt != KMV_OK) return stt;
   uint8_t* base = static_cast<uint8_t*>(S->buf);
   uint32_t* gmax = reinterpret_cast<uint32_t*>(base + o_mx);
   uint32_t* vmax = gmax + n_sys;
-  uint32_t* gcol = reinterpret_cast<uint32_t*>(base + o_gc);
   double* gvpart = reinterpret_cast<double*>(base + o_gv);
   double* gpart = reinterpret_cast<double*>(base + o_gp);
-  double* vpart = fused ? reinterpret_cast<double*>(base + o_vp) : nullptr;
   int* err = reinterpret_cast<int*>(base + o_er);
 
   if (!S->bwd_attr_set) {
-    if (cudaFuncSetAttribute(tc_bwd_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem) !=
-            cudaSuccess ||
-        cudaFuncSetAttribute(tc_bwd_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem) !=
-            cudaSuccess)
+    if (cudaFuncSetAttribute(tc_bwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem) !=
+        cudaSuccess)
       return tc_fail(h, KMV_ECUDA, "cudaFuncSetAttribute failed");
     S->bwd_attr_set = true;
   }
@@ -647,13 +611,12 @@ kmv_status tc_backward(kmv_handle h, const KmvArgs& a, double* grad, cudaStream_
     return tc_fail(h, KMV_ECUDA, "memset failed");
   if (L.n_items > 0)
     tc_bwd_norms_kernel<<<dim3(L.n_items, L.chains), kTile, 0, st>>>(h->dev, L.chains, L.n_total, a.V, a.G, a.m,
-                                                                     fused ? 1 : 0, gmax, vmax, gcol, gvpart,
-                                                                     a.sys_active);
+                                                                     gmax, vmax, gvpart, a.sys_active);
   if (S->n_items > 0) {
     tc_launch_prep_x(h, S, a, KX, 2, base + o_xa, base + o_xb, st);
     tc_prep_bwd_kernel<<<dim3(S->T_total, L.chains), 128, 0, st>>>(
-        h->dev, S->dev, L.chains, a.d, a.ard, a.n_theta, a.m, KG, NB, MPg, S->T_total, a.x, a.theta, a.V, a.G,
-        L.n_total, gmax, vmax, gcol, a.sys_active, base + o_gi, base + o_vj, base + o_bg, base + o_vt, err);
+        h->dev, S->dev, L.chains, a.d, a.ard, a.n_theta, a.m, KG, NB, S->T_total, a.x, a.theta, a.V, a.G,
+        L.n_total, gmax, vmax, a.sys_active, base + o_gi, base + o_vj, base + o_bg, err);
     TcBwdArgs ba;
     ba.items = S->d_items;
     ba.n_items = S->n_items;
@@ -662,7 +625,6 @@ kmv_status tc_backward(kmv_handle h, const KmvArgs& a, double* grad, cudaStream_
     ba.KX = KX;
     ba.KG = KG;
     ba.NB = NB;
-    ba.MPg = MPg;
     ba.S = stages;
     ba.NA = NA;
     ba.d = a.d;
@@ -677,35 +639,26 @@ kmv_status tc_backward(kmv_handle h, const KmvArgs& a, double* grad, cudaStream_
     ba.GI = base + o_gi;
     ba.VJ = base + o_vj;
     ba.BG = base + o_bg;
-    ba.VTG = base + o_vt;
     ba.gpart = gpart;
-    ba.vpart = vpart;
     ba.m = a.m;
     ba.sys_active = a.sys_active;
     ba.err = err;
     const int grid = std::min(S->n_items, S->num_sms);
-    if (MPg <= 16)
-      tc_bwd_kernel<16><<<grid, kThreads, smem, st>>>(ba);
-    else
-      tc_bwd_kernel<0><<<grid, kThreads, smem, st>>>(ba);
+    tc_bwd_kernel<<<grid, kBwdThreads, smem, st>>>(ba);
   }
   tc_bwd_finalize_kernel<<<n_sys, kFinThreads, 0, st>>>(h->dev, S->dev, L.chains, a.n_theta, a.ard, a.d, a.theta, gpart,
                                                 gvpart, gmax, vmax, a.sys_active, err, grad);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return tc_fail(h, KMV_ECUDA, cudaGetErrorString(e));
   if (a.Y != nullptr) {
+    // dL/dV = A G: the forward product with G in place of V.  Stream order puts
+    // it after the finalize above, so it may reuse the workspace.
     KmvArgs fa = a;
     fa.V = a.G;
     fa.col_shift = nullptr;
     fa.Y64 = nullptr;
     fa.dot_partial = nullptr;
-    if (fused) {
-      if (L.n_items > 0) tc_launch_epilogue(h, S, fa, 0, a.m, vpart, gcol, err, st);
-      e = cudaGetLastError();
-      if (e != cudaSuccess) return tc_fail(h, KMV_ECUDA, cudaGetErrorString(e));
-    } else {
-      return tc_forward(h, fa, st);
-    }
+    return tc_forward(h, fa, st);
   }
   return KMV_OK;
 }
