@@ -30,16 +30,15 @@ sys.path.insert(0, ROOT)
 
 METRIC = "GPair/s for K_θ·V fwd+bwd (% roofline); HMC leapfrog steps/s vs plain FP32 at stated err"
 WORKLOAD = "kmv fwd+bwd, N=65536 points x~N(0,I) in d=8, ARD SE (10 hyperparameters), m=16 vectors V,G~N(0,I)"
-# Per-pair work of each kernel form, used for the issue-rate roofline (see DESIGN.md):
+# Per-pair work of each kernel form, used for the issue-rate roofline:
 #   bf16_hilo : one MUFU ex2 per pair and pass -> roof = MUFU rate
 #   fp32      : FMA-pipe ops per pair (fwd 2d + m, bwd 4d + 2m + 2) -> roof = FMA rate / ops
 SM_COUNT = 152
 FMA_LANES = 128        # FP32 FMA lanes per SM per clock
-MUFU_EX2_LANES = 32    # ex2 per SM per clock on GB300 (measured by the microbenchmark in the design doc)
-# dram__bytes_read.sum + dram__bytes_write.sum per launch of the main loop, from the
-# ncu capture summarised in profiles/tc_kernels_c2.md (same workload); None once
-# the kernel changes after that capture.
-DRAM_TRAFFIC = {("bf16_hilo", "bwd"): 33686528 + 160512, ("bf16_hilo", "fwd"): 10549248 + 1536}
+MUFU_EX2_LANES = 32    # ex2 per SM per clock on GB300 (measured by probes/ex2_ffma_rate.cu)
+# dram__bytes_read.sum + dram__bytes_write.sum per launch of the main loop, from an
+# ncu capture of the same workload; absent once the kernel changes after that capture.
+DRAM_TRAFFIC = {("bf16_hilo", "fwd"): 10549248 + 1536}
 
 
 def peaks():
@@ -282,8 +281,8 @@ def main():
     value = world * pairs / (ms_max * 1e-3) / 1e9
     # our kernels per step: FP32 form = forward, adjoint, finalize; BF16 form =
     # forward (prep_x, vmax, prep_v, main, epilogue) + adjoint (norms, prep_x,
-    # prep, main, finalize, dL/dV epilogue)
-    launches_per_step = 3 if prec == "fp32" else 11
+    # prep, main, finalize) + dL/dV = A G through the forward (5 more)
+    launches_per_step = 3 if prec == "fp32" else 15
 
     # end to end through the public API: host inputs (pinned) -> device -> host results
     hX = torch.tensor(w.X, dtype=torch.float32).pin_memory()
@@ -425,6 +424,42 @@ def leapfrog_rates(h, dev, rank, world):
         if "fp32" in finals and "bf16_hilo" in finals:
             r["bf16_over_fp32_speed"] = r["bf16_hilo"]["steps_per_s"] / r["fp32"]["steps_per_s"]
             r["theta_maxdiff_bf16_vs_fp32"] = float(np.abs(finals["fp32"] - finals["bf16_hilo"]).max())
+        if w.n_total == 2048:
+            # the same steps captured once in a CUDA graph and replayed (fixed 40 CG iterations per solve)
+            for prec in ("fp32", "bf16_hilo"):
+                try:
+                    th_g, pi_g = th0.clone(), p0.clone()
+                    xw = torch.empty_like(phi)
+                    side = torch.cuda.Stream()
+                    side.wait_stream(torch.cuda.current_stream())
+                    with torch.cuda.stream(side):
+                        h.leapfrog_step(pts, y, phi, th0.clone(), p0.clone(), 0.05, cg_maxiter=40, x_work=xw,
+                                        prec=prec)
+                    torch.cuda.current_stream().wait_stream(side)
+                    torch.cuda.synchronize()
+                    graph = torch.cuda.CUDAGraph()
+                    with torch.cuda.graph(graph):
+                        for _ in range(steps):
+                            h.leapfrog_step(pts, y, phi, th_g, pi_g, 0.05, cg_maxiter=40, x_work=xw, prec=prec)
+                    th_g.copy_(th0)
+                    pi_g.copy_(p0)
+                    graph.replay()
+                    torch.cuda.synchronize()
+                    reps = 5
+                    t0 = time.perf_counter()
+                    for _ in range(reps):
+                        graph.replay()
+                    torch.cuda.synchronize()
+                    dtg = time.perf_counter() - t0
+                    th_g.copy_(th0)
+                    pi_g.copy_(p0)
+                    graph.replay()
+                    torch.cuda.synchronize()
+                    r[prec]["graph_steps_per_s"] = reps * steps / dtg
+                    if prec in finals:
+                        r[prec]["graph_theta_maxdiff_vs_eager"] = float(np.abs(th_g.cpu().numpy() - finals[prec]).max())
+                except Exception as e:  # capture needs a CUDA-graph capable torch build
+                    r[prec]["graph_unavailable"] = str(e)[:200]
         res["c1" if w.n_total == 2048 else "c5_n16384"] = r
     return res
 

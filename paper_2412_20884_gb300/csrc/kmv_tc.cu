@@ -131,8 +131,13 @@ __global__ void __launch_bounds__(kFwdThreads, 1) tc_fwd_kernel(TcFwdArgs a) {
   const uint32_t tbase = *tslot;
   // TMEM columns: S_g [128 g, 128 g + 128), P_g [256 + 64 g, +64), O_g [384 + 64 g, +MP)
 
+  // The producer and issuer warps run their loops with all 32 lanes, so that
+  // addresses and descriptors stay warp-uniform, and one elected lane issues
+  // the copies, MMAs and commits: issuing from a lone lane was measured at
+  // 2-3x the cost per tcgen05.mma.
   if (warp == kLoadWarp) {
-    if (lane == 0) {
+    const bool leader = elect_one();
+    {
       // ------------------------------------------------------------ producer
       int it = 0;
       uint32_t stage = 0, sph = 0;
@@ -143,17 +148,23 @@ __global__ void __launch_bounds__(kFwdThreads, 1) tc_fwd_kernel(TcFwdArgs a) {
         if (a.sys_active && !a.sys_active[item.x]) continue;
         const int c = item.x % a.chains;
         const int ab = it & 1;
-        if (!mbar_wait(&a_empty[ab], ((it >> 1) & 1) ^ 1, abort, a.err, 1)) { aborted = true; break; }
-        mbar_arrive_expect_tx(&a_full[ab], 2 * A_TILE);
-        bulk_g2s(sA + (2 * ab) * A_TILE, a.XA + ((size_t)c * a.T_total + item.y) * A_TILE, 2 * A_TILE,
-                 &a_full[ab]);
+        if (!warp_wait(&a_empty[ab], ((it >> 1) & 1) ^ 1, abort, a.err, 1)) { aborted = true; break; }
+        if (leader) {
+          mbar_arrive_expect_tx(&a_full[ab], 2 * A_TILE);
+          bulk_g2s(sA + (2 * ab) * A_TILE, a.XA + ((size_t)c * a.T_total + item.y) * A_TILE, 2 * A_TILE,
+                   &a_full[ab]);
+        }
+        __syncwarp();
         ++n_a_issued;
         for (int j = 0; j < item.w; ++j) {
-          if (!mbar_wait(&empty[stage], sph ^ 1, abort, a.err, 2)) { aborted = true; break; }
-          mbar_arrive_expect_tx(&full[stage], A_TILE + V_TILE);
-          const size_t tj = (size_t)c * a.T_total + item.z + j;
-          bulk_g2s(sB + stage * A_TILE, a.XB + tj * A_TILE, A_TILE, &full[stage]);
-          bulk_g2s(sV + stage * V_TILE, a.VT + tj * V_TILE, V_TILE, &full[stage]);
+          if (!warp_wait(&empty[stage], sph ^ 1, abort, a.err, 2)) { aborted = true; break; }
+          if (leader) {
+            mbar_arrive_expect_tx(&full[stage], A_TILE + V_TILE);
+            const size_t tj = (size_t)c * a.T_total + item.z + j;
+            bulk_g2s(sB + stage * A_TILE, a.XB + tj * A_TILE, A_TILE, &full[stage]);
+            bulk_g2s(sV + stage * V_TILE, a.VT + tj * V_TILE, V_TILE, &full[stage]);
+          }
+          __syncwarp();
           ++n_issued;
           if (++stage == (uint32_t)S) { stage = 0; sph ^= 1; }
         }
@@ -172,7 +183,8 @@ __global__ void __launch_bounds__(kFwdThreads, 1) tc_fwd_kernel(TcFwdArgs a) {
       }
     }
   } else if (warp == kMmaWarp || warp == kIssue1Warp) {
-    if (lane == 0) {
+    const bool leader = elect_one();
+    {
       // ------------------------------------------------------------ MMA issuer of I tile g
       // Tile stream k = 0, 1, ... over this CTA's items.  For tile k it issues
       // S(k) once warpgroup g has read S(k-1), then P.V of tile k-1 once P(k-1)
@@ -204,34 +216,42 @@ __global__ void __launch_bounds__(kFwdThreads, 1) tc_fwd_kernel(TcFwdArgs a) {
         for (int j = 0; j < item.w; ++j, ++k) {
           // ---- S(k)
           if (k > 0) {
-            if (!mbar_wait(&s_free[g], sf_ph, abort, a.err, 3)) goto mma_out;
+            if (!warp_wait(&s_free[g], sf_ph, abort, a.err, 3)) goto mma_out;
             sf_ph ^= 1;
           }
-          if (j == 0 && !mbar_wait(&a_full[ab], (it >> 1) & 1, abort, a.err, 4)) goto mma_out;
-          if (!mbar_wait(&full[stage], sph, abort, a.err, 5)) goto mma_out;
+          if (j == 0 && !warp_wait(&a_full[ab], (it >> 1) & 1, abort, a.err, 4)) goto mma_out;
+          if (!warp_wait(&full[stage], sph, abort, a.err, 5)) goto mma_out;
           tc_fence_after();
-          issue_s(s_tmem, dAg, sdesc_add(dB, stage * A_TILE), nkx, idS);
-          tc_commit(&s_full[g]);
+          // operands computed by the whole warp (warp-uniform), issued by the leader
+          const uint64_t db = sdesc_add(dB, stage * A_TILE);
+          if (leader) {
+            issue_s(s_tmem, dAg, db, nkx, idS);
+            tc_commit(&s_full[g]);
+          }
+          __syncwarp();
           // ---- P.V of tile k-1
           if (have_prev) {
-            if (!mbar_wait(&p_ready[g], pr_ph, abort, a.err, 6)) goto mma_out;
+            if (!warp_wait(&p_ready[g], pr_ph, abort, a.err, 6)) goto mma_out;
             pr_ph ^= 1;
             tc_fence_after();
             const uint32_t acc = (prev_j % kFold) != 0;
             if (!acc && opend) {
-              if (!mbar_wait(&o_free[g], of_ph, abort, a.err, 7)) goto mma_out;
+              if (!warp_wait(&o_free[g], of_ph, abort, a.err, 7)) goto mma_out;
               of_ph ^= 1;
               opend = false;
               tc_fence_after();
             }
-            issue_pv(o_tmem, p_tmem, sdesc_add(dV, prev_stage * V_TILE), idP, acc);
-            tc_commit(&p_free[g]);
-            if ((prev_j % kFold) == kFold - 1 || prev_j == prev_nJ - 1) {
-              tc_commit(&o_ready[g]);
-              opend = true;
+            const bool fold_end = (prev_j % kFold) == kFold - 1 || prev_j == prev_nJ - 1;
+            const uint64_t dv = sdesc_add(dV, prev_stage * V_TILE);
+            if (leader) {
+              issue_pv(o_tmem, p_tmem, dv, idP, acc);
+              tc_commit(&p_free[g]);
+              if (fold_end) tc_commit(&o_ready[g]);
+              tc_commit(&empty[prev_stage]);
+              if (prev_j == prev_nJ - 1) tc_commit(&a_empty[prev_ab]);
             }
-            tc_commit(&empty[prev_stage]);
-            if (prev_j == prev_nJ - 1) tc_commit(&a_empty[prev_ab]);
+            __syncwarp();
+            if (fold_end) opend = true;
           }
           have_prev = true;
           prev_stage = stage;
@@ -243,21 +263,26 @@ __global__ void __launch_bounds__(kFwdThreads, 1) tc_fwd_kernel(TcFwdArgs a) {
         ++it;
       }
       if (have_prev) {
-        if (!mbar_wait(&p_ready[g], pr_ph, abort, a.err, 6)) goto mma_out;
+        if (!warp_wait(&p_ready[g], pr_ph, abort, a.err, 6)) goto mma_out;
         tc_fence_after();
         const uint32_t acc = (prev_j % kFold) != 0;
         if (!acc && opend) {
-          if (!mbar_wait(&o_free[g], of_ph, abort, a.err, 7)) goto mma_out;
+          if (!warp_wait(&o_free[g], of_ph, abort, a.err, 7)) goto mma_out;
           tc_fence_after();
         }
-        issue_pv(o_tmem, p_tmem, sdesc_add(dV, prev_stage * V_TILE), idP, acc);
-        tc_commit(&p_free[g]);
-        tc_commit(&o_ready[g]);
-        tc_commit(&empty[prev_stage]);
-        tc_commit(&a_empty[prev_ab]);
+        const uint64_t dv = sdesc_add(dV, prev_stage * V_TILE);
+        if (leader) {
+          issue_pv(o_tmem, p_tmem, dv, idP, acc);
+          tc_commit(&p_free[g]);
+          tc_commit(&o_ready[g]);
+          tc_commit(&empty[prev_stage]);
+          tc_commit(&a_empty[prev_ab]);
+        }
+        __syncwarp();
       }
     mma_out:
-      tc_commit(&done[g]);
+      if (leader) tc_commit(&done[g]);
+      __syncwarp();
       mbar_drain(&done[g], 0, 500000000ull);
     }
     __syncwarp();
@@ -286,7 +311,7 @@ __global__ void __launch_bounds__(kFwdThreads, 1) tc_fwd_kernel(TcFwdArgs a) {
           uint32_t a0[32], a1[32], b0[32], b1[32], pk[32];
           tmem_ld32(tl + s_col, a0);
           tmem_ld32(tl + s_col + 32, a1);
-          tmem_ld_wait();
+          tmem_ld_wait_regs(a0, a1);
           tmem_ld32(tl + s_col + 64, b0);
           tmem_ld32(tl + s_col + 96, b1);
 #pragma unroll
@@ -295,7 +320,7 @@ __global__ void __launch_bounds__(kFwdThreads, 1) tc_fwd_kernel(TcFwdArgs a) {
 #pragma unroll
           for (int q = 0; q < 16; ++q)
             pk[16 + q] = pack_f16x2(ex2(__uint_as_float(a1[2 * q])), ex2(__uint_as_float(a1[2 * q + 1])));
-          tmem_ld_wait();
+          tmem_ld_wait_regs(b0, b1);
           // S(k) is fully in registers: the tensor core may overwrite it
           tc_fence_before();
           mbar_arrive(&s_free[g]);
@@ -329,7 +354,7 @@ __global__ void __launch_bounds__(kFwdThreads, 1) tc_fwd_kernel(TcFwdArgs a) {
               if (c0 < a.MP) {
                 uint32_t o[16];
                 tmem_ld16(tl + o_col + c0, o);
-                tmem_ld_wait();
+                tmem_ld_wait_regs(o);
 #pragma unroll
                 for (int q = 0; q < 16; ++q) racc[c0 + q] += (double)__uint_as_float(o[q]);
               }
@@ -338,7 +363,7 @@ __global__ void __launch_bounds__(kFwdThreads, 1) tc_fwd_kernel(TcFwdArgs a) {
             for (int c0 = 0; c0 < a.MP; c0 += 16) {
               uint32_t o[16];
               tmem_ld16(tl + o_col + c0, o);
-              tmem_ld_wait();
+              tmem_ld_wait_regs(o);
 #pragma unroll
               for (int q = 0; q < 16; ++q) {
                 const int col = c0 + q;
@@ -419,7 +444,8 @@ __global__ void __launch_bounds__(kFwdThreads, 1) tc_fwd_fma_kernel(TcFwdArgs a)
   const uint32_t tbase = *tslot;
 
   if (warp == kLoadWarp) {
-    if (lane == 0) {
+    const bool leader = elect_one();
+    {
       int it = 0;
       uint32_t stage = 0, sph = 0;
       int n_issued = 0, n_a_issued = 0;
@@ -429,17 +455,23 @@ __global__ void __launch_bounds__(kFwdThreads, 1) tc_fwd_fma_kernel(TcFwdArgs a)
         if (a.sys_active && !a.sys_active[item.x]) continue;
         const int c = item.x % a.chains;
         const int ab = it & 1;
-        if (!mbar_wait(&a_empty[ab], ((it >> 1) & 1) ^ 1, abort, a.err, 11)) { aborted = true; break; }
-        mbar_arrive_expect_tx(&a_full[ab], 2 * A_TILE);
-        bulk_g2s(sA + (2 * ab) * A_TILE, a.XA + ((size_t)c * a.T_total + item.y) * A_TILE, 2 * A_TILE,
-                 &a_full[ab]);
+        if (!warp_wait(&a_empty[ab], ((it >> 1) & 1) ^ 1, abort, a.err, 11)) { aborted = true; break; }
+        if (leader) {
+          mbar_arrive_expect_tx(&a_full[ab], 2 * A_TILE);
+          bulk_g2s(sA + (2 * ab) * A_TILE, a.XA + ((size_t)c * a.T_total + item.y) * A_TILE, 2 * A_TILE,
+                   &a_full[ab]);
+        }
+        __syncwarp();
         ++n_a_issued;
         for (int j = 0; j < item.w; ++j) {
-          if (!mbar_wait(&empty[stage], sph ^ 1, abort, a.err, 12)) { aborted = true; break; }
-          mbar_arrive_expect_tx(&full[stage], A_TILE + V_TILE);
-          const size_t tj = (size_t)c * a.T_total + item.z + j;
-          bulk_g2s(sB + stage * A_TILE, a.XB + tj * A_TILE, A_TILE, &full[stage]);
-          bulk_g2s(sV + stage * V_TILE, a.VT + tj * V_TILE, V_TILE, &full[stage]);
+          if (!warp_wait(&empty[stage], sph ^ 1, abort, a.err, 12)) { aborted = true; break; }
+          if (leader) {
+            mbar_arrive_expect_tx(&full[stage], A_TILE + V_TILE);
+            const size_t tj = (size_t)c * a.T_total + item.z + j;
+            bulk_g2s(sB + stage * A_TILE, a.XB + tj * A_TILE, A_TILE, &full[stage]);
+            bulk_g2s(sV + stage * V_TILE, a.VT + tj * V_TILE, V_TILE, &full[stage]);
+          }
+          __syncwarp();
           ++n_issued;
           if (++stage == (uint32_t)S) { stage = 0; sph ^= 1; }
         }
@@ -457,7 +489,8 @@ __global__ void __launch_bounds__(kFwdThreads, 1) tc_fwd_fma_kernel(TcFwdArgs a)
       }
     }
   } else if (warp == kMmaWarp || warp == kIssue1Warp) {
-    if (lane == 0) {
+    const bool leader = elect_one();
+    {
       const int g = warp == kMmaWarp ? 0 : 1;
       const uint32_t idS = idesc_f16(128, 128, 1, 1);
       const uint32_t sboX = a.KX * 16u;
@@ -475,22 +508,27 @@ __global__ void __launch_bounds__(kFwdThreads, 1) tc_fwd_fma_kernel(TcFwdArgs a)
         const uint64_t dAg = sdesc_add(dA, 2 * ab * A_TILE);
         for (int j = 0; j < item.w; ++j, ++k) {
           if (k > 0) {
-            if (!mbar_wait(&s_free[g], sf_ph, abort, a.err, 13)) goto fma_mma_out;
+            if (!warp_wait(&s_free[g], sf_ph, abort, a.err, 13)) goto fma_mma_out;
             sf_ph ^= 1;
           }
-          if (j == 0 && !mbar_wait(&a_full[ab], (it >> 1) & 1, abort, a.err, 14)) goto fma_mma_out;
-          if (!mbar_wait(&full[stage], sph, abort, a.err, 15)) goto fma_mma_out;
+          if (j == 0 && !warp_wait(&a_full[ab], (it >> 1) & 1, abort, a.err, 14)) goto fma_mma_out;
+          if (!warp_wait(&full[stage], sph, abort, a.err, 15)) goto fma_mma_out;
           tc_fence_after();
-          issue_s(s_tmem, dAg, sdesc_add(dB, stage * A_TILE), nkx, idS);
-          tc_commit(&s_full[g]);
-          tc_commit(&empty[stage]);
-          if (j == item.w - 1) tc_commit(&a_empty[ab]);
+          const uint64_t db = sdesc_add(dB, stage * A_TILE);
+          if (leader) {
+            issue_s(s_tmem, dAg, db, nkx, idS);
+            tc_commit(&s_full[g]);
+            tc_commit(&empty[stage]);
+            if (j == item.w - 1) tc_commit(&a_empty[ab]);
+          }
+          __syncwarp();
           if (++stage == (uint32_t)S) { stage = 0; sph ^= 1; }
         }
         ++it;
       }
     fma_mma_out:
-      tc_commit(&done[g]);
+      if (leader) tc_commit(&done[g]);
+      __syncwarp();
       mbar_drain(&done[g], 0, 500000000ull);
     }
     __syncwarp();
@@ -524,7 +562,7 @@ __global__ void __launch_bounds__(kFwdThreads, 1) tc_fwd_fma_kernel(TcFwdArgs a)
           uint32_t a0[32], a1[32], b0[32], b1[32];
           tmem_ld32(tl + s_col, a0);
           tmem_ld32(tl + s_col + 32, a1);
-          tmem_ld_wait();
+          tmem_ld_wait_regs(a0, a1);
           tmem_ld32(tl + s_col + 64, b0);
           tmem_ld32(tl + s_col + 96, b1);
 #pragma unroll
@@ -553,7 +591,7 @@ __global__ void __launch_bounds__(kFwdThreads, 1) tc_fwd_fma_kernel(TcFwdArgs a)
               acc[q][3] = fmaf(p3, v.w, acc[q][3]);
             }
           }
-          tmem_ld_wait();
+          tmem_ld_wait_regs(b0, b1);
           tc_fence_before();
           mbar_arrive(&s_free[g]);
 #pragma unroll

@@ -45,6 +45,7 @@ struct TcBwdArgs {
   int chains;
   int T_total;
   int KX, KG, NB, S, NA;
+  int qcol;   // accumulator column of q_i (the ones column of BG)
   int d, n_theta, ard;
   DevLayout L;
   TcTables T;
@@ -90,10 +91,10 @@ __device__ __forceinline__ void issue_ts4(uint32_t d_tmem, uint32_t a_tmem, uint
 // Warp roles: warps 0-7 two exp warpgroups (one per I tile), warp 8 MMA
 // issuer of I tile 0 (and TMEM owner), warp 9 producer, warp 10 MMA issuer of
 // I tile 1.  TMEM per I tile g (256 columns from 256 g): S [0,64), W [64,128),
-// Q [128,160), ACC [192,256).  A half tile's S and W are released as soon as
-// the warpgroup has loaded them, so the next half's S, W MMAs run during this
-// half's exps; Q has its own columns, so the feature-sum MMAs of this half run
-// during the next half's exps.
+// Q double-buffered in [128,160) and [160,192), ACC [192,256).  A half tile's S
+// and W are released as soon as the warpgroup has loaded them, so the next
+// half's S, W MMAs run during this half's exps; Q has its own two buffers, so
+// the feature-sum MMAs of one half run during the next two halves' exps.
 constexpr int kBwdThreads = 352;
 constexpr int kBwdIssue1Warp = 10;
 
@@ -113,9 +114,9 @@ __global__ void __launch_bounds__(kBwdThreads, 1) tc_bwd_kernel(TcBwdArgs a) {
   uint64_t* a_empty = a_full + 2;
   uint64_t* s_full = a_empty + 2;    // [g] S, W of a half tile written
   uint64_t* s_free = s_full + 2;     // [g] S, W loaded into registers
-  uint64_t* q_ready = s_free + 2;    // [g] Q written
-  uint64_t* q_free = q_ready + 2;    // [g] Q consumed by the feature-sum MMAs
-  uint64_t* o_ready = q_free + 2;
+  uint64_t* q_ready = s_free + 2;    // [2 g + buffer] Q written
+  uint64_t* q_free = q_ready + 4;    // [2 g + buffer] Q consumed by the feature-sum MMAs
+  uint64_t* o_ready = q_free + 4;
   uint64_t* o_free = o_ready + 2;
   uint64_t* done = o_free + 2;       // [g]
   uint32_t* tslot = reinterpret_cast<uint32_t*>(done + 2);
@@ -132,8 +133,10 @@ __global__ void __launch_bounds__(kBwdThreads, 1) tc_bwd_kernel(TcBwdArgs a) {
       mbar_init(&a_empty[g], 2);
       mbar_init(&s_full[g], 1);
       mbar_init(&s_free[g], 128);
-      mbar_init(&q_ready[g], 128);
-      mbar_init(&q_free[g], 1);
+      mbar_init(&q_ready[2 * g], 128);
+      mbar_init(&q_ready[2 * g + 1], 128);
+      mbar_init(&q_free[2 * g], 1);
+      mbar_init(&q_free[2 * g + 1], 1);
       mbar_init(&o_ready[g], 1);
       mbar_init(&o_free[g], 128);
       mbar_init(&done[g], 1);
@@ -151,7 +154,8 @@ __global__ void __launch_bounds__(kBwdThreads, 1) tc_bwd_kernel(TcBwdArgs a) {
   const uint32_t tbase = *tslot;
 
   if (warp == kLoadWarp) {
-    if (lane == 0) {
+    const bool leader = elect_one();
+    {
       // ------------------------------------------------------------ producer
       int it = 0, n_issued = 0, n_a_issued = 0;
       uint32_t stage = 0, sph = 0;
@@ -161,21 +165,27 @@ __global__ void __launch_bounds__(kBwdThreads, 1) tc_bwd_kernel(TcBwdArgs a) {
         if (a.sys_active && !a.sys_active[item.x]) continue;
         const int c = item.x % a.chains;
         const int ab = it % NA;
-        if (!mbar_wait(&a_empty[ab], ((it / NA) & 1) ^ 1, abort, a.err, 21)) { aborted = true; break; }
-        mbar_arrive_expect_tx(&a_full[ab], ABUF);
-        const size_t ti = (size_t)c * a.T_total + item.y;
-        uint8_t* ad = sA + ab * ABUF;
-        bulk_g2s(ad, a.XA + ti * XT, 2 * XT, &a_full[ab]);
-        bulk_g2s(ad + 2 * XT, a.GI + ti * GT, 2 * GT, &a_full[ab]);
+        if (!warp_wait(&a_empty[ab], ((it / NA) & 1) ^ 1, abort, a.err, 21)) { aborted = true; break; }
+        if (leader) {
+          mbar_arrive_expect_tx(&a_full[ab], ABUF);
+          const size_t ti = (size_t)c * a.T_total + item.y;
+          uint8_t* ad = sA + ab * ABUF;
+          bulk_g2s(ad, a.XA + ti * XT, 2 * XT, &a_full[ab]);
+          bulk_g2s(ad + 2 * XT, a.GI + ti * GT, 2 * GT, &a_full[ab]);
+        }
+        __syncwarp();
         ++n_a_issued;
         for (int j = 0; j < item.w; ++j) {
-          if (!mbar_wait(&empty[stage], sph ^ 1, abort, a.err, 22)) { aborted = true; break; }
-          mbar_arrive_expect_tx(&full[stage], STG);
-          const size_t tj = (size_t)c * a.T_total + item.z + j;
-          uint8_t* sd = sS + stage * STG;
-          bulk_g2s(sd, a.XB + tj * XT, XT, &full[stage]);
-          bulk_g2s(sd + XT, a.VJ + tj * GT, GT, &full[stage]);
-          bulk_g2s(sd + XT + GT, a.BG + tj * BT, BT, &full[stage]);
+          if (!warp_wait(&empty[stage], sph ^ 1, abort, a.err, 22)) { aborted = true; break; }
+          if (leader) {
+            mbar_arrive_expect_tx(&full[stage], STG);
+            const size_t tj = (size_t)c * a.T_total + item.z + j;
+            uint8_t* sd = sS + stage * STG;
+            bulk_g2s(sd, a.XB + tj * XT, XT, &full[stage]);
+            bulk_g2s(sd + XT, a.VJ + tj * GT, GT, &full[stage]);
+            bulk_g2s(sd + XT + GT, a.BG + tj * BT, BT, &full[stage]);
+          }
+          __syncwarp();
           ++n_issued;
           if (++stage == (uint32_t)S) { stage = 0; sph ^= 1; }
         }
@@ -193,7 +203,8 @@ __global__ void __launch_bounds__(kBwdThreads, 1) tc_bwd_kernel(TcBwdArgs a) {
       }
     }
   } else if (warp == kMmaWarp || warp == kBwdIssue1Warp) {
-    if (lane == 0) {
+    const bool leader = elect_one();
+    {
       // ------------------------------------------------------------ MMA issuer of I tile g
       // Half-tile stream k: S, W of half k once half k-1 is loaded by the
       // warpgroup, then the feature sums of half k-1 once its Q is written.
@@ -209,7 +220,7 @@ __global__ void __launch_bounds__(kBwdThreads, 1) tc_bwd_kernel(TcBwdArgs a) {
       const uint64_t dBG = sdesc(smem_u32(sS + XT + GT), 128, 2048);
       const uint32_t tg = tbase + 256 * g;
       int it = 0;
-      uint32_t stage = 0, sph = 0, sf_ph = 0, qr_ph = 0, of_ph = 0;
+      uint32_t stage = 0, sph = 0, sf_ph = 0, of_ph = 0;
       bool opend = false;
       long long k = 0;
       bool have_prev = false;
@@ -224,37 +235,48 @@ __global__ void __launch_bounds__(kBwdThreads, 1) tc_bwd_kernel(TcBwdArgs a) {
           const int hh = h & 1;
           // ---- S, W of half k
           if (k > 0) {
-            if (!mbar_wait(&s_free[g], sf_ph, abort, a.err, 23)) goto mma_out;
+            if (!warp_wait(&s_free[g], sf_ph, abort, a.err, 23)) goto mma_out;
             sf_ph ^= 1;
           }
-          if (h == 0 && !mbar_wait(&a_full[ab], (it / NA) & 1, abort, a.err, 24)) goto mma_out;
-          if (hh == 0 && !mbar_wait(&full[stage], sph, abort, a.err, 25)) goto mma_out;
+          if (h == 0 && !warp_wait(&a_full[ab], (it / NA) & 1, abort, a.err, 24)) goto mma_out;
+          if (hh == 0 && !warp_wait(&full[stage], sph, abort, a.err, 25)) goto mma_out;
           tc_fence_after();
-          issue_ss(tg, sdesc_add(dXA, ab * ABUF), sdesc_add(dXB, stage * STG + hh * a.KX * 128u), nkx, idSW);
-          issue_ss(tg + 64, sdesc_add(dGI, ab * ABUF), sdesc_add(dVJ, stage * STG + hh * a.KG * 128u), nkg, idSW);
-          tc_commit(&s_full[g]);
-          // the A buffer is read only by the S, W MMAs: release it after the
-          // item's last half, before the next item waits for its own A buffer
-          if (h == nH - 1) tc_commit(&a_empty[ab]);
+          // operands computed by the whole warp (warp-uniform), issued by the leader
+          const uint64_t da = sdesc_add(dXA, ab * ABUF), db = sdesc_add(dXB, stage * STG + hh * a.KX * 128u);
+          const uint64_t dg = sdesc_add(dGI, ab * ABUF), dv = sdesc_add(dVJ, stage * STG + hh * a.KG * 128u);
+          if (leader) {
+            issue_ss(tg, da, db, nkx, idSW);
+            issue_ss(tg + 64, dg, dv, nkg, idSW);
+            tc_commit(&s_full[g]);
+            // the A buffer is read only by the S, W MMAs: release it after the
+            // item's last half, before the next item waits for its own A buffer
+            if (h == nH - 1) tc_commit(&a_empty[ab]);
+          }
+          __syncwarp();
           // ---- feature sums of half k-1
           if (have_prev) {
-            if (!mbar_wait(&q_ready[g], qr_ph, abort, a.err, 26)) goto mma_out;
-            qr_ph ^= 1;
+            // half k-1 used Q buffer (k-1) & 1 for the ((k-1) >> 1)-th time
+            const int qb = (int)((k - 1) & 1);
+            if (!warp_wait(&q_ready[2 * g + qb], (uint32_t)((k - 1) >> 1) & 1u, abort, a.err, 26)) goto mma_out;
             tc_fence_after();
             const uint32_t acc = (prev_h % kFoldH) != 0;
             if (!acc && opend) {
-              if (!mbar_wait(&o_free[g], of_ph, abort, a.err, 27)) goto mma_out;
+              if (!warp_wait(&o_free[g], of_ph, abort, a.err, 27)) goto mma_out;
               of_ph ^= 1;
               opend = false;
               tc_fence_after();
             }
-            issue_ts4(tg + 192, tg + 128, sdesc_add(dBG, prev_stage * STG + (prev_h & 1) * 1024u), idA, acc);
-            tc_commit(&q_free[g]);
-            if ((prev_h % kFoldH) == kFoldH - 1 || prev_h == prev_nH - 1) {
-              tc_commit(&o_ready[g]);
-              opend = true;
+            const bool fold_end = (prev_h % kFoldH) == kFoldH - 1 || prev_h == prev_nH - 1;
+            const uint64_t dbg = sdesc_add(dBG, prev_stage * STG + (prev_h & 1) * 1024u);
+            const uint32_t tq = tg + 128 + 32 * qb;
+            if (leader) {
+              issue_ts4(tg + 192, tq, dbg, idA, acc);
+              tc_commit(&q_free[2 * g + qb]);
+              if (fold_end) tc_commit(&o_ready[g]);
+              if (prev_h & 1) tc_commit(&empty[prev_stage]);
             }
-            if (prev_h & 1) tc_commit(&empty[prev_stage]);
+            __syncwarp();
+            if (fold_end) opend = true;
           }
           have_prev = true;
           prev_stage = stage;
@@ -267,20 +289,27 @@ __global__ void __launch_bounds__(kBwdThreads, 1) tc_bwd_kernel(TcBwdArgs a) {
         ++it;
       }
       if (have_prev) {
-        if (!mbar_wait(&q_ready[g], qr_ph, abort, a.err, 26)) goto mma_out;
+        const int qb = (int)((k - 1) & 1);
+        if (!warp_wait(&q_ready[2 * g + qb], (uint32_t)((k - 1) >> 1) & 1u, abort, a.err, 26)) goto mma_out;
         tc_fence_after();
         const uint32_t acc = (prev_h % kFoldH) != 0;
         if (!acc && opend) {
-          if (!mbar_wait(&o_free[g], of_ph, abort, a.err, 27)) goto mma_out;
+          if (!warp_wait(&o_free[g], of_ph, abort, a.err, 27)) goto mma_out;
           tc_fence_after();
         }
-        issue_ts4(tg + 192, tg + 128, sdesc_add(dBG, prev_stage * STG + (prev_h & 1) * 1024u), idA, acc);
-        tc_commit(&q_free[g]);
-        tc_commit(&o_ready[g]);
-        tc_commit(&empty[prev_stage]);
+        const uint64_t dbg = sdesc_add(dBG, prev_stage * STG + (prev_h & 1) * 1024u);
+        const uint32_t tq = tg + 128 + 32 * qb;
+        if (leader) {
+          issue_ts4(tg + 192, tq, dbg, idA, acc);
+          tc_commit(&q_free[2 * g + qb]);
+          tc_commit(&o_ready[g]);
+          tc_commit(&empty[prev_stage]);
+        }
+        __syncwarp();
       }
     mma_out:
-      tc_commit(&done[g]);
+      if (leader) tc_commit(&done[g]);
+      __syncwarp();
       mbar_drain(&done[g], 0, 500000000ull);
     }
     __syncwarp();
@@ -290,7 +319,7 @@ __global__ void __launch_bounds__(kBwdThreads, 1) tc_bwd_kernel(TcBwdArgs a) {
     const int row = 32 * w + lane;
     const uint32_t tl = tbase + 256 * g + (static_cast<uint32_t>(32 * w) << 16);
     const int d = a.d;
-    uint32_t sph = 0, qf_ph = 0, oph = 0;
+    uint32_t sph = 0, oph = 0;
     long long k = 0;
     for (int t = blockIdx.x; t < a.n_items; t += gridDim.x) {
       const int4 item = a.items[t];
@@ -328,14 +357,14 @@ __global__ void __launch_bounds__(kBwdThreads, 1) tc_bwd_kernel(TcBwdArgs a) {
           uint32_t s0[32], w0[32], s1[32], w1[32], qq[32];
           tmem_ld32(tl, s0);
           tmem_ld32(tl + 64, w0);
-          tmem_ld_wait();
+          tmem_ld_wait_regs(s0, w0);
           tmem_ld32(tl + 32, s1);
           tmem_ld32(tl + 96, w1);
 #pragma unroll
           for (int q = 0; q < 16; ++q)
             qq[q] = pack_f16x2(ex2(__uint_as_float(s0[2 * q])) * __uint_as_float(w0[2 * q]),
                                ex2(__uint_as_float(s0[2 * q + 1])) * __uint_as_float(w0[2 * q + 1]));
-          tmem_ld_wait();
+          tmem_ld_wait_regs(s1, w1);
           // S, W of this half are in registers: the tensor core may overwrite them
           tc_fence_before();
           mbar_arrive(&s_free[g]);
@@ -343,18 +372,18 @@ __global__ void __launch_bounds__(kBwdThreads, 1) tc_bwd_kernel(TcBwdArgs a) {
           for (int q = 0; q < 16; ++q)
             qq[16 + q] = pack_f16x2(ex2(__uint_as_float(s1[2 * q])) * __uint_as_float(w1[2 * q]),
                                     ex2(__uint_as_float(s1[2 * q + 1])) * __uint_as_float(w1[2 * q + 1]));
-          if (k > 0) {
-            // Q of the previous half must have been consumed
-            ok = mbar_wait(&q_free[g], qf_ph, abort, a.err, 30);
+          const int qb = (int)(k & 1);
+          if (k >= 2) {
+            // Q buffer qb must have been consumed by the feature sums of half k - 2
+            ok = mbar_wait(&q_free[2 * g + qb], (uint32_t)((k - 2) >> 1) & 1u, abort, a.err, 30);
             if (!__all_sync(0xffffffffu, ok)) goto exp_out;
-            qf_ph ^= 1;
             tc_fence_after();
           }
-          tmem_st32(tl + 128, qq);
+          tmem_st32(tl + 128 + 32 * qb, qq);
         }
         tmem_st_wait();
         tc_fence_before();
-        mbar_arrive(&q_ready[g]);
+        mbar_arrive(&q_ready[2 * g + (int)(k & 1)]);
         if ((h % kFoldH) == kFoldH - 1 || h == nH - 1) {
           ok = mbar_wait(&o_ready[g], oph, abort, a.err, 29);
           if (!__all_sync(0xffffffffu, ok)) goto exp_out;
@@ -362,7 +391,7 @@ __global__ void __launch_bounds__(kBwdThreads, 1) tc_bwd_kernel(TcBwdArgs a) {
           tc_fence_after();
           uint32_t o3[16];
           tmem_ld16(tl + 192 + 48, o3);
-          tmem_ld_wait();
+          tmem_ld_wait_regs(o3);
           const float qs = __uint_as_float(o3[kQCol - 48]);
           dq += (double)qs;
 #pragma unroll
@@ -374,7 +403,7 @@ __global__ void __launch_bounds__(kBwdThreads, 1) tc_bwd_kernel(TcBwdArgs a) {
                 for (int q = 0; q < 16; ++q) o[q] = o3[q];
               } else {
                 tmem_ld16(tl + 192 + 16 * c4, o);
-                tmem_ld_wait();
+                tmem_ld_wait_regs(o);
               }
 #pragma unroll
               for (int u = 0; u < 4; ++u) {
@@ -419,6 +448,363 @@ __global__ void __launch_bounds__(kBwdThreads, 1) tc_bwd_kernel(TcBwdArgs a) {
   if (warp == kMmaWarp) tmem_dealloc(tbase, 512);
 }
 
+// Variant with the I-side operands resident in TMEM, one I tile at a time.
+// S and W are A-from-TMEM MMAs that read only the 64-row J half from shared
+// memory (with A in shared memory a 128-row A tile is read for every K step,
+// which caps an N = 64 MMA at the shared-memory read rate).  The two exp
+// warpgroups share the I tile: warpgroup b takes J columns [64 b, 64 b + 64)
+// of every J tile, in its own S, W buffer, so the MMAs of one warpgroup's next
+// half run while the other warpgroup computes.  Warps: 0-7 the warpgroups,
+// 8 issues S, W for buffer 0 (and owns TMEM), 9 is the producer, 10 issues
+// S, W for buffer 1, 11 issues the feature sums.  TMEM (512 columns):
+//   S_b [128 b, 128 b + 64), W_b [128 b + 64, 128 b + 128), Q_b [256 + 32 b, +32),
+//   XA [320, 320 + KX/2), GI [320 + KX/2, + KG/2), ACC [512 - NB, 512);
+// the host selects this form while KX/2 + KG/2 + NB <= 192.  Warpgroup 0 also
+// folds the accumulator into the per-row FP64 sums.  A work item's two I tiles
+// are processed one after the other ("sub-items").
+constexpr int kTsThreads = 384;
+constexpr int kAccWarp = 11;
+constexpr int kTsCols = 192;   // columns for XA, GI and ACC
+constexpr int kMaxDT = 15;     // 4 d features + q in at most 64 accumulator columns
+constexpr int kTsBarBytes = 512;                           // mbarriers, TMEM slot, abort flag
+constexpr int kTsRowBytes = kMaxDT * 128 * (4 + 8);        // x~ and FP64 fold sums per row
+
+__global__ void __launch_bounds__(kTsThreads, 1) tc_bwd_ts_kernel(TcBwdArgs a) {
+  using namespace ptx;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = align1024(smem_raw);
+  const uint32_t XT = a.KX * 256u, GT = a.KG * 256u, BT = a.NB * 256u;
+  const uint32_t STG = XT + GT + BT;   // one stage: XB, VJ, BG of a J tile
+  const int S = a.S;
+  uint8_t* sS = smem;
+  uint64_t* full = reinterpret_cast<uint64_t*>(sS + S * STG);
+  uint64_t* empty = full + S;
+  uint64_t* a_ready = empty + S;     // XA, GI of the sub-item stored in TMEM (256 arrivals)
+  uint64_t* seg = a_ready + 1;       // both warpgroups finished the previous sub-item (256)
+  uint64_t* s_full = seg + 1;        // [b] S_b, W_b written
+  uint64_t* s_free = s_full + 2;     // [b] S_b, W_b loaded into registers
+  uint64_t* q_ready = s_free + 2;    // [b] Q_b written
+  uint64_t* q_free = q_ready + 2;    // [b] Q_b consumed by the feature sums
+  uint64_t* o_ready = q_free + 2;    // accumulator of a fold complete
+  uint64_t* o_free = o_ready + 1;    // accumulator read
+  uint64_t* done = o_free + 1;       // [issuer], 3
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(done + 3);
+  volatile int* abort = reinterpret_cast<volatile int*>(tslot + 1);
+  // per-row x~ and FP64 fold sums of warpgroup 0, [k][row]: kept out of registers,
+  // which the exp loop needs for a whole half tile of S and W
+  float* sxt = reinterpret_cast<float*>(reinterpret_cast<uint8_t*>(full) + kTsBarBytes);
+  double* sdacc = reinterpret_cast<double*>(sxt + kMaxDT * 128);
+  const uint32_t colA = 320, colG = 320 + a.KX / 2, colACC = 512 - a.NB;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < S; ++i) {
+      mbar_init(&full[i], 1);
+      mbar_init(&empty[i], 1);
+    }
+    mbar_init(a_ready, 256);
+    mbar_init(seg, 256);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&s_full[b], 1);
+      mbar_init(&s_free[b], 128);
+      mbar_init(&q_ready[b], 128);
+      mbar_init(&q_free[b], 1);
+    }
+    mbar_init(o_ready, 1);
+    mbar_init(o_free, 128);
+    for (int i = 0; i < 3; ++i) mbar_init(&done[i], 1);
+    *abort = 0;
+    fence_barrier_init();
+  }
+  if (warp == kMmaWarp) {
+    tmem_alloc(tslot, 512);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tbase = *tslot;
+
+  // The producer and issuer warps run their loops with all 32 lanes, so that
+  // addresses and descriptors stay warp-uniform, and one elected lane issues
+  // the copies, MMAs and commits: issuing from a lone lane was measured at
+  // 2-3x the cost per tcgen05.mma.
+  if (warp == kLoadWarp) {
+    const bool leader = elect_one();
+    // ------------------------------------------------------------ producer
+    int n_issued = 0;
+    uint32_t stage = 0, sph = 0;
+    bool aborted = false;
+    for (int t = blockIdx.x; t < a.n_items && !aborted; t += gridDim.x) {
+      const int4 item = a.items[t];
+      if (a.sys_active && !a.sys_active[item.x]) continue;
+      const int c = item.x % a.chains;
+      for (int g = 0; g < 2 && !aborted; ++g) {
+        for (int j = 0; j < item.w; ++j) {
+          if (!warp_wait(&empty[stage], sph ^ 1, abort, a.err, 22)) { aborted = true; break; }
+          if (leader) {
+            mbar_arrive_expect_tx(&full[stage], STG);
+            const size_t tj = (size_t)c * a.T_total + item.z + j;
+            uint8_t* sd = sS + stage * STG;
+            bulk_g2s(sd, a.XB + tj * XT, XT, &full[stage]);
+            bulk_g2s(sd + XT, a.VJ + tj * GT, GT, &full[stage]);
+            bulk_g2s(sd + XT + GT, a.BG + tj * BT, BT, &full[stage]);
+          }
+          __syncwarp();
+          ++n_issued;
+          if (++stage == (uint32_t)S) { stage = 0; sph ^= 1; }
+        }
+      }
+    }
+    if (aborted) {
+      for (int k = 1; k <= min(n_issued, S); ++k) {
+        const int idx = n_issued - k;
+        mbar_drain(&full[idx % S], (idx / S) & 1, 500000000ull);
+      }
+    }
+  } else if (warp == kMmaWarp || warp == kBwdIssue1Warp) {
+    // ------------------------------------------------------------ S, W issuer of buffer b
+    const bool leader = elect_one();
+    const int b = warp == kMmaWarp ? 0 : 1;
+    const uint32_t idSW = idesc_f16(128, 64, 1, 1);
+    const int nkx = a.KX / 16, nkg = a.KG / 16;
+    const uint64_t dXB = sdesc(smem_u32(sS + b * a.KX * 128u), 128, a.KX * 16u);
+    const uint64_t dVJ = sdesc(smem_u32(sS + XT + b * a.KG * 128u), 128, a.KG * 16u);
+    const uint32_t tS = tbase + 128 * b, tA = tbase + colA, tG = tbase + colG;
+    int u = 0, uses = 0;
+    uint32_t stage = 0, sph = 0;
+    for (int t = blockIdx.x; t < a.n_items; t += gridDim.x) {
+      const int4 item = a.items[t];
+      if (a.sys_active && !a.sys_active[item.x]) continue;
+      for (int g = 0; g < 2; ++g, ++u) {
+        if (!warp_wait(a_ready, (uint32_t)u & 1u, abort, a.err, 31)) goto sw_out;
+        for (int j = 0; j < item.w; ++j) {
+          if (uses > 0 && !warp_wait(&s_free[b], (uint32_t)(uses - 1) & 1u, abort, a.err, 23)) goto sw_out;
+          if (!warp_wait(&full[stage], sph, abort, a.err, 25)) goto sw_out;
+          tc_fence_after();
+          // operands computed by the whole warp (warp-uniform), issued by the leader
+          const uint64_t db = sdesc_add(dXB, stage * STG);
+          const uint64_t dv = sdesc_add(dVJ, stage * STG);
+          if (leader) {
+#pragma unroll
+            for (int q = 0; q < kMaxKX / 16; ++q)
+              if (q < nkx) mma_ts(tS, tA + 8 * q, db + 16 * q, idSW, q > 0);
+#pragma unroll
+            for (int q = 0; q < 2 * kTsCols / 16; ++q)
+              if (q < nkg) mma_ts(tS + 64, tG + 8 * q, dv + 16 * q, idSW, q > 0);
+            tc_commit(&s_full[b]);
+          }
+          __syncwarp();
+          ++uses;
+          if (++stage == (uint32_t)S) { stage = 0; sph ^= 1; }
+        }
+      }
+    }
+  sw_out:
+    if (leader) tc_commit(&done[b]);
+    __syncwarp();
+    mbar_drain(&done[b], 0, 500000000ull);
+  } else if (warp == kAccWarp) {
+    // ------------------------------------------------------------ feature-sum issuer
+    const bool leader = elect_one();
+    const uint32_t idA = idesc_f16(128, a.NB, 0, 0);
+    const uint64_t dBG = sdesc(smem_u32(sS + XT + GT), 128, 2048);
+    uint32_t stage = 0, of_ph = 0;
+    uint32_t qr0 = 0, qr1 = 0;
+    bool open = false;
+    for (int t = blockIdx.x; t < a.n_items; t += gridDim.x) {
+      const int4 item = a.items[t];
+      if (a.sys_active && !a.sys_active[item.x]) continue;
+      const int nH = 2 * item.w;
+      for (int g = 0; g < 2; ++g) {
+        for (int h = 0; h < nH; ++h) {
+          const int b = h & 1;
+          uint32_t& qr = b == 0 ? qr0 : qr1;
+          if (!warp_wait(&q_ready[b], qr & 1u, abort, a.err, 26)) goto acc_out;
+          ++qr;
+          tc_fence_after();
+          const uint32_t acc = (h % kFoldH) != 0;
+          const bool fold_end = (h % kFoldH) == kFoldH - 1 || h == nH - 1;
+          if (!acc && open) {
+            if (!warp_wait(o_free, of_ph, abort, a.err, 27)) goto acc_out;
+            of_ph ^= 1;
+            open = false;
+            tc_fence_after();
+          }
+          const uint64_t dbg = sdesc_add(dBG, stage * STG + b * 1024u);
+          const uint32_t tq = tbase + 256 + 32 * b, tacc = tbase + colACC;
+          if (leader) {
+            issue_ts4(tacc, tq, dbg, idA, acc);
+            tc_commit(&q_free[b]);
+            if (fold_end) tc_commit(o_ready);
+            // both halves of the stage read (their S, W MMAs completed before Q)
+            if (b == 1) tc_commit(&empty[stage]);
+          }
+          __syncwarp();
+          if (fold_end) open = true;
+          if (b == 1) {
+            if (++stage == (uint32_t)S) stage = 0;
+          }
+        }
+      }
+    }
+  acc_out:
+    if (leader) tc_commit(&done[2]);
+    __syncwarp();
+    mbar_drain(&done[2], 0, 500000000ull);
+  } else {
+    // ------------------------------------------------------------ exp warpgroups
+    const int b = warp >> 2, w = warp & 3;
+    const int row = 32 * w + lane;
+    const uint32_t lofs = static_cast<uint32_t>(32 * w) << 16;
+    const uint32_t tS = tbase + lofs + 128 * b, tQ = tbase + lofs + 256 + 32 * b;
+    const uint32_t tACC = tbase + lofs + colACC;
+    const int d = a.d;
+    const int qc = a.qcol;
+    uint32_t sph = 0, oph = 0;
+    long long uses = 0;
+    int u = 0;
+    for (int t = blockIdx.x; t < a.n_items; t += gridDim.x) {
+      const int4 item = a.items[t];
+      if (a.sys_active && !a.sys_active[item.x]) continue;
+      const int s = item.x, bi = s / a.chains, c = s % a.chains;
+      const int nH = 2 * item.w;
+      for (int g = 0; g < 2; ++g, ++u) {
+        if (u > 0) {
+          // both warpgroups have waited for their last S, W of the previous
+          // sub-item: no MMA reads XA or GI any more
+          mbar_arrive(seg);
+          const bool ok = mbar_wait(seg, (uint32_t)(u - 1) & 1u, abort, a.err, 32);
+          if (!__all_sync(0xffffffffu, ok)) goto exp_out;
+        }
+        {
+          // warpgroup 0 stores the sub-item's XA rows, warpgroup 1 its GI rows
+          const size_t ti = (size_t)c * a.T_total + item.y + g;
+          const int width = b == 0 ? a.KX : a.KG;
+          const uint8_t* src = (b == 0 ? a.XA + ti * XT : a.GI + ti * GT) + (row >> 3) * (width * 16) + (row & 7) * 16;
+          const uint32_t col = b == 0 ? colA : colG;
+          for (int q = 0; q < width / 16; ++q) {
+            const uint4 u0 = *reinterpret_cast<const uint4*>(src + 2 * q * 128);
+            const uint4 u1 = *reinterpret_cast<const uint4*>(src + (2 * q + 1) * 128);
+            const uint32_t v[8] = {u0.x, u0.y, u0.z, u0.w, u1.x, u1.y, u1.z, u1.w};
+            tmem_st8(tbase + lofs + col + 8 * q, v);
+          }
+          tmem_st_wait();
+          tc_fence_before();
+          mbar_arrive(a_ready);
+        }
+        const int64_t nb = a.L.offsets[bi + 1] - a.L.offsets[bi];
+        const int64_t rl = (int64_t)(item.y + g - a.T.inst_tile0[bi]) * 128 + row;
+        const bool valid = rl < nb;
+        double dq = 0.0;
+        if (b == 0) {
+          const double* th = a.theta + (int64_t)s * a.n_theta;
+          const int64_t i = a.L.offsets[bi] + rl;
+          for (int kk = 0; kk < d; ++kk) {
+            float v = 0.f;
+            if (valid) {
+              const float sc = (float)(sqrt(2.0 * kHalfLog2e) * exp(-th[1 + (a.ard ? kk : 0)]));
+              v = xt_of(a.x[i * d + kk], sc);
+            }
+            sxt[kk * 128 + row] = v;
+            sdacc[kk * 128 + row] = 0.0;
+          }
+        }
+        for (int h = b; h < nH; h += 2, ++uses) {
+          bool ok = mbar_wait(&s_full[b], sph, abort, a.err, 28);
+          if (!__all_sync(0xffffffffu, ok)) goto exp_out;
+          sph ^= 1;
+          tc_fence_after();
+          {
+            // the whole half of S and W in registers with one wait, so S_b, W_b
+            // are released at once and the next MMAs into them can start
+            uint32_t s0[32], s1[32], w0[32], w1[32], qq[32];
+            tmem_ld32(tS, s0);
+            tmem_ld32(tS + 32, s1);
+            tmem_ld32(tS + 64, w0);
+            tmem_ld32(tS + 96, w1);
+            tmem_ld_wait_regs(s0, s1, w0, w1);
+            tc_fence_before();
+            mbar_arrive(&s_free[b]);
+#pragma unroll
+            for (int q = 0; q < 16; ++q)
+              qq[q] = pack_f16x2(ex2(__uint_as_float(s0[2 * q])) * __uint_as_float(w0[2 * q]),
+                                 ex2(__uint_as_float(s0[2 * q + 1])) * __uint_as_float(w0[2 * q + 1]));
+#pragma unroll
+            for (int q = 0; q < 16; ++q)
+              qq[16 + q] = pack_f16x2(ex2(__uint_as_float(s1[2 * q])) * __uint_as_float(w1[2 * q]),
+                                      ex2(__uint_as_float(s1[2 * q + 1])) * __uint_as_float(w1[2 * q + 1]));
+            if (uses > 0) {
+              // Q_b of this warpgroup's previous half must have been consumed
+              ok = mbar_wait(&q_free[b], (uint32_t)((uses - 1) & 1), abort, a.err, 30);
+              if (!__all_sync(0xffffffffu, ok)) goto exp_out;
+              tc_fence_after();
+            }
+            tmem_st32(tQ, qq);
+          }
+          tmem_st_wait();
+          tc_fence_before();
+          mbar_arrive(&q_ready[b]);
+          // warpgroup 0 folds the accumulator after the fold's last (odd) half
+          if (b == 0 && (((h + 1) % kFoldH) == kFoldH - 1 || h + 1 == nH - 1)) {
+            ok = mbar_wait(o_ready, oph, abort, a.err, 29);
+            if (!__all_sync(0xffffffffu, ok)) goto exp_out;
+            oph ^= 1;
+            tc_fence_after();
+            uint32_t oq[16];
+            tmem_ld16(tACC + 16 * (qc >> 4), oq);
+            tmem_ld_wait_regs(oq);
+            const float qs = __uint_as_float(oq[qc & 15]);
+            dq += (double)qs;
+#pragma unroll
+            for (int c4 = 0; c4 < (kMaxDT + 3) / 4; ++c4) {
+              if (4 * c4 < d) {
+                uint32_t o[16];
+                tmem_ld16(tACC + 16 * c4, o);
+                tmem_ld_wait_regs(o);
+#pragma unroll
+                for (int uu = 0; uu < 4; ++uu) {
+                  const int kk = 4 * c4 + uu;
+                  if (kk < d) {
+                    const float R = __uint_as_float(o[4 * uu]) + __uint_as_float(o[4 * uu + 1]);
+                    const float T = __uint_as_float(o[4 * uu + 2]) + __uint_as_float(o[4 * uu + 3]);
+                    const float x = sxt[kk * 128 + row];
+                    sdacc[kk * 128 + row] += (double)fmaf(x, fmaf(x, qs, -2.f * R), T);
+                  }
+                }
+              }
+            }
+            tc_fence_before();
+            mbar_arrive(o_free);
+          }
+        }
+        if (b == 0) {
+          // per-warp partial of this sub-item: [q, contrib_0 .. contrib_{d-1}]
+          double* out = a.gpart + ((size_t)t * 8 + g * 4 + w) * kGW;
+          double v = dq;
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+          if (lane == 0) out[0] = v;
+          for (int kk = 0; kk < d; ++kk) {
+            {
+              double uu = sdacc[kk * 128 + row];
+#pragma unroll
+              for (int o = 16; o > 0; o >>= 1) uu += __shfl_down_sync(0xffffffffu, uu, o);
+              if (lane == 0) out[1 + kk] = uu;
+            }
+          }
+        }
+      }
+    }
+  exp_out:;
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == kMmaWarp) tmem_dealloc(tbase, 512);
+}
+
 // max |G_i| and max |V_j| per system (row norms) and sum_i G_i . V_i.
 __global__ void tc_bwd_norms_kernel(DevLayout L, int chains, int64_t n_total, const float* V, const float* G,
                                     int m, uint32_t* gmax, uint32_t* vmax, double* gvpart,
@@ -448,7 +834,7 @@ __global__ void tc_bwd_norms_kernel(DevLayout L, int chains, int64_t n_total, co
 
 // GI, VJ and BG operand tiles of every (chain, padded tile).
 __global__ void tc_prep_bwd_kernel(DevLayout L, TcTables T, int chains, int d, int ard, int n_theta, int m,
-                                   int KG, int NB, int T_total, const float* x, const double* theta,
+                                   int KG, int NB, int qcol, int T_total, const float* x, const double* theta,
                                    const float* V, const float* G, int64_t n_total, const uint32_t* gmax,
                                    const uint32_t* vmax, const int32_t* sys_active, uint8_t* GI, uint8_t* VJ,
                                    uint8_t* BG, int* err) {
@@ -499,7 +885,7 @@ __global__ void tc_prep_bwd_kernel(DevLayout L, TcTables T, int chains, int d, i
       bg[t_off(4 * k + 2, r) / 2] = sh;
       bg[t_off(4 * k + 3, r) / 2] = sl;
     }
-    bg[t_off(kQCol, r) / 2] = __float2half_rn(1.f);
+    bg[t_off(qcol, r) / 2] = __float2half_rn(1.f);
   }
 }
 
@@ -571,18 +957,28 @@ kmv_status tc_backward(kmv_handle h, const KmvArgs& a, double* grad, cudaStream_
   kmv_status stt = tc_build_plan(h, S, st);
   if (stt != KMV_OK) return stt;
   const int n_sys = L.n_inst * L.chains;
-  const int KX = x_width(a.d), KG = round16(3 * a.m), NB = kNB;
+  const int KX = x_width(a.d), KG = round16(3 * a.m);
+  // the TMEM-resident form while XA, GI and a round16(4 d + 1)-column accumulator fit
+  const int NBt = round16(4 * a.d + 1);
+  const bool ts = a.d <= kMaxDT && KX / 2 + KG / 2 + NBt <= kTsCols;
+  const int NB = ts ? NBt : kNB;
+  const int qcol = ts ? 4 * a.d : kQCol;
   const size_t XT = (size_t)KX * 256, GT = (size_t)KG * 256, BT = (size_t)NB * 256;
   const size_t ABUF = 2 * XT + 2 * GT, STG = XT + GT + BT;
   const size_t fixed = 1024 + 512;
-  int NA = 2;
-  int stages = (int)std::min<size_t>(6, (kMaxSmem - fixed - NA * ABUF) / STG);
-  if (kMaxSmem < fixed + NA * ABUF || stages < 2) {
-    NA = 1;
-    stages = kMaxSmem > fixed + ABUF ? (int)std::min<size_t>(6, (kMaxSmem - fixed - ABUF) / STG) : 0;
+  int NA = 2, stages = 0;
+  if (ts) {
+    NA = 0;
+    stages = (int)std::min<size_t>(6, (kMaxSmem - fixed - kTsRowBytes) / STG);
+  } else {
+    stages = kMaxSmem >= fixed + NA * ABUF ? (int)std::min<size_t>(6, (kMaxSmem - fixed - NA * ABUF) / STG) : 0;
+    if (stages < 2) {
+      NA = 1;
+      stages = kMaxSmem > fixed + ABUF ? (int)std::min<size_t>(6, (kMaxSmem - fixed - ABUF) / STG) : 0;
+    }
   }
   if (stages < 2) return tc_fail(h, KMV_EUNSUPPORTED, "tensor-core adjoint tiles do not fit in shared memory");
-  const size_t smem = std::max(kMinSmem, fixed + NA * ABUF + stages * STG);
+  const size_t smem = std::max(kMinSmem, fixed + NA * ABUF + stages * STG + (ts ? kTsRowBytes : 0));
 
   auto al = [](size_t v) { return (v + 255) & ~size_t(255); };
   const size_t tiles = (size_t)L.chains * S->T_total;
@@ -602,7 +998,9 @@ kmv_status tc_backward(kmv_handle h, const KmvArgs& a, double* grad, cudaStream_
 
   if (!S->bwd_attr_set) {
     if (cudaFuncSetAttribute(tc_bwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem) !=
-        cudaSuccess)
+            cudaSuccess ||
+        cudaFuncSetAttribute(tc_bwd_ts_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem) !=
+            cudaSuccess)
       return tc_fail(h, KMV_ECUDA, "cudaFuncSetAttribute failed");
     S->bwd_attr_set = true;
   }
@@ -615,7 +1013,7 @@ kmv_status tc_backward(kmv_handle h, const KmvArgs& a, double* grad, cudaStream_
   if (S->n_items > 0) {
     tc_launch_prep_x(h, S, a, KX, 2, base + o_xa, base + o_xb, st);
     tc_prep_bwd_kernel<<<dim3(S->T_total, L.chains), 128, 0, st>>>(
-        h->dev, S->dev, L.chains, a.d, a.ard, a.n_theta, a.m, KG, NB, S->T_total, a.x, a.theta, a.V, a.G,
+        h->dev, S->dev, L.chains, a.d, a.ard, a.n_theta, a.m, KG, NB, qcol, S->T_total, a.x, a.theta, a.V, a.G,
         L.n_total, gmax, vmax, a.sys_active, base + o_gi, base + o_vj, base + o_bg, err);
     TcBwdArgs ba;
     ba.items = S->d_items;
@@ -625,6 +1023,7 @@ kmv_status tc_backward(kmv_handle h, const KmvArgs& a, double* grad, cudaStream_
     ba.KX = KX;
     ba.KG = KG;
     ba.NB = NB;
+    ba.qcol = qcol;
     ba.S = stages;
     ba.NA = NA;
     ba.d = a.d;
@@ -644,7 +1043,10 @@ kmv_status tc_backward(kmv_handle h, const KmvArgs& a, double* grad, cudaStream_
     ba.sys_active = a.sys_active;
     ba.err = err;
     const int grid = std::min(S->n_items, S->num_sms);
-    tc_bwd_kernel<<<grid, kBwdThreads, smem, st>>>(ba);
+    if (ts)
+      tc_bwd_ts_kernel<<<grid, kTsThreads, smem, st>>>(ba);
+    else
+      tc_bwd_kernel<<<grid, kBwdThreads, smem, st>>>(ba);
   }
   tc_bwd_finalize_kernel<<<n_sys, kFinThreads, 0, st>>>(h->dev, S->dev, L.chains, a.n_theta, a.ard, a.d, a.theta, gpart,
                                                 gvpart, gmax, vmax, a.sys_active, err, grad);
