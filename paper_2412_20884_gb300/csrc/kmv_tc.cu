@@ -882,14 +882,56 @@ kmv_status tc_build_plan(kmv_handle h, TcState* S, cudaStream_t st) {
   }
   S->n_items = (int)S->items.size();
   if ((int64_t)S->items.size() > (int64_t(1) << 30)) return tc_fail(h, KMV_EINVAL, "too many tensor-core work items");
+  S->sys_pref.assign((size_t)n_inst * chains + 1, 0);
+  for (size_t q = 0; q < S->sys_item0.size(); ++q) S->sys_pref[q] = S->sys_item0[q];
+  S->sys_pref[S->sys_item0.size()] = S->n_items;
+  // Upper-triangle plan (J >= I) for the symmetric adjoint: row I of an instance
+  // with T tiles has T - I tile pairs, cut into near-equal chunks of at most C
+  // tiles; a system's items are ordered longest first, which the round-robin
+  // assignment of items to CTAs then balances.
+  {
+    int64_t pairs = 0;
+    for (int b = 0; b < n_inst; ++b) {
+      const int64_t T = (L.offsets[b + 1] - L.offsets[b] + 127) / 128;
+      pairs += (int64_t)chains * T * (T + 1) / 2;
+    }
+    const int64_t C = std::max<int64_t>(8, (pairs + target - 1) / std::max<int64_t>(1, target));
+    S->sym_items.clear();
+    S->sym_pref.assign((size_t)n_inst * chains + 1, 0);
+    std::vector<int4> row;
+    for (int b = 0; b < n_inst; ++b) {
+      const int T = (int)((L.offsets[b + 1] - L.offsets[b] + 127) / 128);
+      for (int c = 0; c < chains; ++c) {
+        const int s = b * chains + c;
+        S->sym_pref[s] = (int32_t)S->sym_items.size();
+        row.clear();
+        for (int I = 0; I < T; ++I) {
+          const int len = T - I;
+          const int nc = (int)((len + C - 1) / C);
+          for (int k = 0; k < nc; ++k) {
+            const int j0 = I + (int)((int64_t)k * len / nc), j1 = I + (int)((int64_t)(k + 1) * len / nc);
+            row.push_back(make_int4(s, S->inst_tile0[b] + I, S->inst_tile0[b] + j0, j1 - j0));
+          }
+        }
+        std::stable_sort(row.begin(), row.end(), [](const int4& x, const int4& y) { return x.w > y.w; });
+        S->sym_items.insert(S->sym_items.end(), row.begin(), row.end());
+      }
+    }
+    S->sym_pref[(size_t)n_inst * chains] = (int32_t)S->sym_items.size();
+    S->sym_n_items = (int)S->sym_items.size();
+    if ((int64_t)S->sym_items.size() > (int64_t(1) << 30))
+      return tc_fail(h, KMV_EINVAL, "too many tensor-core work items");
+  }
   // upload tables
   const size_t b_items = sizeof(int4) * std::max<size_t>(1, S->items.size());
   const size_t b_ti = sizeof(int32_t) * std::max<size_t>(1, S->tile_inst.size());
   const size_t b_it0 = sizeof(int32_t) * (n_inst + 1);
   const size_t b_si = sizeof(int32_t) * std::max<size_t>(1, S->sys_item0.size());
   const size_t b_nk = sizeof(int32_t) * n_inst;
+  const size_t b_pref = sizeof(int32_t) * ((size_t)n_inst * chains + 1);
+  const size_t b_sym = sizeof(int4) * std::max<size_t>(1, S->sym_items.size());
   auto al = [](size_t v) { return (v + 255) & ~size_t(255); };
-  const size_t total = al(b_items) + al(b_ti) + al(b_it0) + al(b_si) + al(b_nk);
+  const size_t total = al(b_items) + al(b_ti) + al(b_it0) + al(b_si) + al(b_nk) + 2 * al(b_pref) + al(b_sym);
   if (total > S->tables_bytes) {
     if (S->tables) {
       cudaDeviceSynchronize();
@@ -916,6 +958,9 @@ kmv_status tc_build_plan(kmv_handle h, TcState* S, cudaStream_t st) {
   S->dev.inst_tile0 = reinterpret_cast<const int32_t*>(up(S->inst_tile0.data(), b_it0, b_it0));
   S->dev.sys_item0 = reinterpret_cast<const int32_t*>(up(S->sys_item0.data(), sizeof(int32_t) * S->sys_item0.size(), b_si));
   S->dev.inst_nk = reinterpret_cast<const int32_t*>(up(S->inst_nk.data(), b_nk, b_nk));
+  S->dev.sys_pref = reinterpret_cast<const int32_t*>(up(S->sys_pref.data(), b_pref, b_pref));
+  S->dev.sym_pref = reinterpret_cast<const int32_t*>(up(S->sym_pref.data(), b_pref, b_pref));
+  S->d_sym_items = reinterpret_cast<const int4*>(up(S->sym_items.data(), sizeof(int4) * S->sym_items.size(), b_sym));
   if (cudaStreamSynchronize(st) != cudaSuccess) return tc_fail(h, KMV_ECUDA, "table upload failed");
   S->offsets = L.offsets;
   S->chains = L.chains;

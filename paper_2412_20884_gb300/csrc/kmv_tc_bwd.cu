@@ -46,6 +46,7 @@ struct TcBwdArgs {
   int T_total;
   int KX, KG, NB, S, NA;
   int qcol;   // accumulator column of q_i (the ones column of BG)
+  int sym;    // 1: upper-triangle items (one I tile each) with the symmetrised W; 0: I-pair items
   int d, n_theta, ard;
   DevLayout L;
   TcTables T;
@@ -495,6 +496,7 @@ __global__ void __launch_bounds__(kTsThreads, 1) tc_bwd_ts_kernel(TcBwdArgs a) {
   float* sxt = reinterpret_cast<float*>(reinterpret_cast<uint8_t*>(full) + kTsBarBytes);
   double* sdacc = reinterpret_cast<double*>(sxt + kMaxDT * 128);
   const uint32_t colA = 320, colG = 320 + a.KX / 2, colACC = 512 - a.NB;
+  const int nsub = a.sym ? 1 : 2;   // I tiles per work item
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
@@ -539,7 +541,7 @@ __global__ void __launch_bounds__(kTsThreads, 1) tc_bwd_ts_kernel(TcBwdArgs a) {
       const int4 item = a.items[t];
       if (a.sys_active && !a.sys_active[item.x]) continue;
       const int c = item.x % a.chains;
-      for (int g = 0; g < 2 && !aborted; ++g) {
+      for (int g = 0; g < nsub && !aborted; ++g) {
         for (int j = 0; j < item.w; ++j) {
           if (!warp_wait(&empty[stage], sph ^ 1, abort, a.err, 22)) { aborted = true; break; }
           if (leader) {
@@ -576,7 +578,7 @@ __global__ void __launch_bounds__(kTsThreads, 1) tc_bwd_ts_kernel(TcBwdArgs a) {
     for (int t = blockIdx.x; t < a.n_items; t += gridDim.x) {
       const int4 item = a.items[t];
       if (a.sys_active && !a.sys_active[item.x]) continue;
-      for (int g = 0; g < 2; ++g, ++u) {
+      for (int g = 0; g < nsub; ++g, ++u) {
         if (!warp_wait(a_ready, (uint32_t)u & 1u, abort, a.err, 31)) goto sw_out;
         for (int j = 0; j < item.w; ++j) {
           if (uses > 0 && !warp_wait(&s_free[b], (uint32_t)(uses - 1) & 1u, abort, a.err, 23)) goto sw_out;
@@ -616,7 +618,7 @@ __global__ void __launch_bounds__(kTsThreads, 1) tc_bwd_ts_kernel(TcBwdArgs a) {
       const int4 item = a.items[t];
       if (a.sys_active && !a.sys_active[item.x]) continue;
       const int nH = 2 * item.w;
-      for (int g = 0; g < 2; ++g) {
+      for (int g = 0; g < nsub; ++g) {
         for (int h = 0; h < nH; ++h) {
           const int b = h & 1;
           uint32_t& qr = b == 0 ? qr0 : qr1;
@@ -669,7 +671,7 @@ __global__ void __launch_bounds__(kTsThreads, 1) tc_bwd_ts_kernel(TcBwdArgs a) {
       if (a.sys_active && !a.sys_active[item.x]) continue;
       const int s = item.x, bi = s / a.chains, c = s % a.chains;
       const int nH = 2 * item.w;
-      for (int g = 0; g < 2; ++g, ++u) {
+      for (int g = 0; g < nsub; ++g, ++u) {
         if (u > 0) {
           // both warpgroups have waited for their last S, W of the previous
           // sub-item: no MMA reads XA or GI any more
@@ -726,6 +728,14 @@ __global__ void __launch_bounds__(kTsThreads, 1) tc_bwd_ts_kernel(TcBwdArgs a) {
             tmem_ld_wait_regs(s0, s1, w0, w1);
             tc_fence_before();
             mbar_arrive(&s_free[b]);
+            if (a.sym && item.z + (h >> 1) == item.y + g) {
+              // diagonal tile of the upper triangle: counted once, off-diagonal tiles twice
+#pragma unroll
+              for (int q = 0; q < 32; ++q) {
+                w0[q] = __float_as_uint(0.5f * __uint_as_float(w0[q]));
+                w1[q] = __float_as_uint(0.5f * __uint_as_float(w1[q]));
+              }
+            }
 #pragma unroll
             for (int q = 0; q < 16; ++q)
               qq[q] = pack_f16x2(ex2(__uint_as_float(s0[2 * q])) * __uint_as_float(w0[2 * q]),
@@ -780,7 +790,7 @@ __global__ void __launch_bounds__(kTsThreads, 1) tc_bwd_ts_kernel(TcBwdArgs a) {
         }
         if (b == 0) {
           // per-warp partial of this sub-item: [q, contrib_0 .. contrib_{d-1}]
-          double* out = a.gpart + ((size_t)t * 8 + g * 4 + w) * kGW;
+          double* out = a.gpart + ((size_t)t * (4 * nsub) + g * 4 + w) * kGW;
           double v = dq;
 #pragma unroll
           for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
@@ -834,7 +844,8 @@ __global__ void tc_bwd_norms_kernel(DevLayout L, int chains, int64_t n_total, co
 
 // GI, VJ and BG operand tiles of every (chain, padded tile).
 __global__ void tc_prep_bwd_kernel(DevLayout L, TcTables T, int chains, int d, int ard, int n_theta, int m,
-                                   int KG, int NB, int qcol, int T_total, const float* x, const double* theta,
+                                   int KG, int nparts, int NB, int qcol, int T_total, const float* x,
+                                   const double* theta,
                                    const float* V, const float* G, int64_t n_total, const uint32_t* gmax,
                                    const uint32_t* vmax, const int32_t* sys_active, uint8_t* GI, uint8_t* VJ,
                                    uint8_t* BG, int* err) {
@@ -854,15 +865,21 @@ __global__ void tc_prep_bwd_kernel(DevLayout L, TcTables T, int chains, int d, i
   const __nv_bfloat16 zb = __float2bfloat16_rn(0.f);
   for (int q = 0; q < KG; ++q) {
     __nv_bfloat16 gval = zb, vval = zb;
-    if (valid && q < 3 * m) {
+    if (valid && q < nparts * m) {
       const int col = q % m, part = q / m;
       const int64_t idx = ((int64_t)c * n_total + i) * m + col;
       const float gq = G[idx] * gs, vq = V[idx];
       const __nv_bfloat16 gh = __float2bfloat16_rn(gq), vh = __float2bfloat16_rn(vq);
       const __nv_bfloat16 gl = __float2bfloat16_rn(gq - __bfloat162float(gh));
       const __nv_bfloat16 vl = __float2bfloat16_rn(vq - __bfloat162float(vh));
-      gval = part < 2 ? gh : gl;        // [gh, gh, gl]
-      vval = part == 1 ? vl : vh;       // [vh, vl, vh]
+      if (part < 3) {
+        gval = part < 2 ? gh : gl;        // [gh, gh, gl]
+        vval = part == 1 ? vl : vh;       // [vh, vl, vh]
+      } else {
+        // symmetrised second half: I rows [vh, vh, vl], J rows [gh, gl, gh]
+        gval = part < 5 ? vh : vl;
+        vval = part == 4 ? gl : gh;
+      }
     }
     gi[x_off(r, q, KG) / 2] = gval;
     vj[x_off(r, q, KG) / 2] = vval;
@@ -895,17 +912,15 @@ __global__ void tc_prep_bwd_kernel(DevLayout L, TcTables T, int chains, int d, i
 constexpr int kFinThreads = 256;
 
 __global__ void __launch_bounds__(kFinThreads) tc_bwd_finalize_kernel(
-    DevLayout L, TcTables T, int chains, int n_theta, int ard, int d, const double* theta, const double* gpart,
-    const double* gvpart, const uint32_t* gmax, const uint32_t* vmax, const int32_t* sys_active, const int* err,
-    double* grad) {
+    DevLayout L, const int32_t* pref, int wpi, int chains, int n_theta, int ard, int d, const double* theta,
+    const double* gpart, const double* gvpart, const uint32_t* gmax, const uint32_t* vmax,
+    const int32_t* sys_active, const int* err, double* grad) {
   __shared__ double red[kFinThreads / 32][kGW + 1];
   const int s = blockIdx.x;
   if (sys_active && !sys_active[s]) return;
   const int b = s / chains, c = s - b * chains;
-  const int64_t nb = L.offsets[b + 1] - L.offsets[b];
-  const int npair = (int)((nb + 255) / 256);
-  const int64_t n_rows = (int64_t)npair * T.inst_nk[b] * 8;   // (item, warp) partial rows
-  const int64_t r0 = (int64_t)T.sys_item0[s] * 8;
+  const int64_t n_rows = (int64_t)(pref[s + 1] - pref[s]) * wpi;   // (item, warp) partial rows
+  const int64_t r0 = (int64_t)pref[s] * wpi;
   double acc[kGW + 1];
 #pragma unroll
   for (int v = 0; v <= kGW; ++v) acc[v] = 0.0;
@@ -957,10 +972,16 @@ kmv_status tc_backward(kmv_handle h, const KmvArgs& a, double* grad, cudaStream_
   kmv_status stt = tc_build_plan(h, S, st);
   if (stt != KMV_OK) return stt;
   const int n_sys = L.n_inst * L.chains;
-  const int KX = x_width(a.d), KG = round16(3 * a.m);
-  // the TMEM-resident form while XA, GI and a round16(4 d + 1)-column accumulator fit
+  const int KX = x_width(a.d);
+  // The TMEM-resident form while XA, GI and a round16(4 d + 1)-column accumulator
+  // fit; symmetrised (upper-triangle tiles, GI of depth 6 m) when that fits too.
   const int NBt = round16(4 * a.d + 1);
-  const bool ts = a.d <= kMaxDT && KX / 2 + KG / 2 + NBt <= kTsCols;
+  const int KGs = round16(6 * a.m), KGp = round16(3 * a.m);
+  const bool sym = a.d <= kMaxDT && KX / 2 + KGs / 2 + NBt <= kTsCols;
+  const bool ts = sym || (a.d <= kMaxDT && KX / 2 + KGp / 2 + NBt <= kTsCols);
+  const int KG = sym ? KGs : KGp;
+  const int n_items = sym ? S->sym_n_items : S->n_items;
+  const int wpi = sym ? 4 : 8;   // per-warp partial rows per item
   const int NB = ts ? NBt : kNB;
   const int qcol = ts ? 4 * a.d : kQCol;
   const size_t XT = (size_t)KX * 256, GT = (size_t)KG * 256, BT = (size_t)NB * 256;
@@ -986,7 +1007,7 @@ kmv_status tc_backward(kmv_handle h, const KmvArgs& a, double* grad, cudaStream_
   const size_t o_vj = o_gi + al(tiles * GT), o_bg = o_vj + al(tiles * GT), o_mx = o_bg + al(tiles * BT);
   const size_t o_gv = o_mx + al(sizeof(uint32_t) * 2 * n_sys);
   const size_t o_gp = o_gv + al(sizeof(double) * (size_t)std::max(1, L.n_items) * L.chains);
-  const size_t o_er = o_gp + al(sizeof(double) * (size_t)std::max(1, S->n_items) * 8 * kGW);
+  const size_t o_er = o_gp + al(sizeof(double) * (size_t)std::max(1, n_items) * wpi * kGW);
   stt = tc_ensure_buf(h, S, o_er + 256);
   if (stt != KMV_OK) return stt;
   uint8_t* base = static_cast<uint8_t*>(S->buf);
@@ -1010,14 +1031,15 @@ kmv_status tc_backward(kmv_handle h, const KmvArgs& a, double* grad, cudaStream_
   if (L.n_items > 0)
     tc_bwd_norms_kernel<<<dim3(L.n_items, L.chains), kTile, 0, st>>>(h->dev, L.chains, L.n_total, a.V, a.G, a.m,
                                                                      gmax, vmax, gvpart, a.sys_active);
-  if (S->n_items > 0) {
+  if (n_items > 0) {
     tc_launch_prep_x(h, S, a, KX, 2, base + o_xa, base + o_xb, st);
     tc_prep_bwd_kernel<<<dim3(S->T_total, L.chains), 128, 0, st>>>(
-        h->dev, S->dev, L.chains, a.d, a.ard, a.n_theta, a.m, KG, NB, qcol, S->T_total, a.x, a.theta, a.V, a.G,
-        L.n_total, gmax, vmax, a.sys_active, base + o_gi, base + o_vj, base + o_bg, err);
+        h->dev, S->dev, L.chains, a.d, a.ard, a.n_theta, a.m, KG, sym ? 6 : 3, NB, qcol, S->T_total, a.x, a.theta,
+        a.V, a.G, L.n_total, gmax, vmax, a.sys_active, base + o_gi, base + o_vj, base + o_bg, err);
     TcBwdArgs ba;
-    ba.items = S->d_items;
-    ba.n_items = S->n_items;
+    ba.items = sym ? S->d_sym_items : S->d_items;
+    ba.n_items = n_items;
+    ba.sym = sym ? 1 : 0;
     ba.chains = L.chains;
     ba.T_total = S->T_total;
     ba.KX = KX;
@@ -1042,14 +1064,15 @@ kmv_status tc_backward(kmv_handle h, const KmvArgs& a, double* grad, cudaStream_
     ba.m = a.m;
     ba.sys_active = a.sys_active;
     ba.err = err;
-    const int grid = std::min(S->n_items, S->num_sms);
+    const int grid = std::min(n_items, S->num_sms);
     if (ts)
       tc_bwd_ts_kernel<<<grid, kTsThreads, smem, st>>>(ba);
     else
       tc_bwd_kernel<<<grid, kBwdThreads, smem, st>>>(ba);
   }
-  tc_bwd_finalize_kernel<<<n_sys, kFinThreads, 0, st>>>(h->dev, S->dev, L.chains, a.n_theta, a.ard, a.d, a.theta, gpart,
-                                                gvpart, gmax, vmax, a.sys_active, err, grad);
+  tc_bwd_finalize_kernel<<<n_sys, kFinThreads, 0, st>>>(h->dev, sym ? S->dev.sym_pref : S->dev.sys_pref, wpi,
+                                                         L.chains, a.n_theta, a.ard, a.d, a.theta, gpart, gvpart,
+                                                         gmax, vmax, a.sys_active, err, grad);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return tc_fail(h, KMV_ECUDA, cudaGetErrorString(e));
   if (a.Y != nullptr) {

@@ -28,6 +28,8 @@ struct TcTables {
   const int32_t* inst_tile0;   // n_inst + 1 (padded tiles)
   const int32_t* sys_item0;    // n_sys
   const int32_t* inst_nk;      // n_inst
+  const int32_t* sys_pref;     // n_sys + 1: items of system s are [sys_pref[s], sys_pref[s + 1])
+  const int32_t* sym_pref;     // n_sys + 1, the same for the upper-triangle plan
 };
 
 
@@ -39,7 +41,12 @@ struct TcState {
   // plan
   int T_total = 0, n_items = 0;
   std::vector<int4> items;
-  std::vector<int32_t> tile_inst, inst_tile0, sys_item0, inst_nk;
+  std::vector<int32_t> tile_inst, inst_tile0, sys_item0, inst_nk, sys_pref;
+  // upper-triangle plan of the symmetric adjoint: {system, I tile, first J tile >= I, J tiles}
+  int sym_n_items = 0;
+  std::vector<int4> sym_items;
+  std::vector<int32_t> sym_pref;
+  const int4* d_sym_items = nullptr;
   void* tables = nullptr;
   size_t tables_bytes = 0;
   TcTables dev{};
