@@ -38,7 +38,7 @@ FMA_LANES = 128        # FP32 FMA lanes per SM per clock
 MUFU_EX2_LANES = 32    # ex2 per SM per clock on GB300 (measured by probes/ex2_ffma_rate.cu)
 # dram__bytes_read.sum + dram__bytes_write.sum per launch of the main loop, from an
 # ncu capture of the same workload; absent once the kernel changes after that capture.
-DRAM_TRAFFIC = {("bf16_hilo", "fwd"): 10549248 + 1536}
+DRAM_TRAFFIC = {}
 
 
 def peaks():
@@ -156,26 +156,51 @@ def cpu_oracle_rate(rows_per_step: int, steps: int, seed: int = 0):
     return pairs / t_total / 1e9, t_total, len(os.sched_getaffinity(0))
 
 
-def algorithmic_flops_per_pair(d, m, which):
-    """Tensor-core FLOPs per pair of the BF16 form, unpadded: the cross term with
-    its hi/lo split and folded biases (3d + 6 products), W = G V^T with hi/lo
-    G and V (3m), the feature sums of Q (4d + 1) and the P.V / P.G products (m)."""
-    if which == "fwd":
-        return 2 * (3 * d + 6) + 2 * m
-    return 2 * (3 * d + 6) + 2 * (3 * m) + 2 * (4 * d + 1) + 2 * m
+def kernel_work(prec, kind, d, m, n):
+    """Algorithmic work of one launch of a main kernel on one N x N system:
+    (ex2 count, tensor-core FLOPs, FMA-pipe ops).
 
-
-def roof(prec, d, m, clock_mhz, which, tensor_tflops):
-    """Issue-rate roof of one kernel: pairs/s, the binding unit and a note."""
-    f = clock_mhz * 1e6
+    Forward (one pass of Eq. kerdef over all N^2 pairs): one ex2 per pair; the
+    BF16 form contracts the cross term with its hi/lo split and folded biases
+    (3d + 6 products) and P.V (m).  Adjoint (the quadratic-form gradient of
+    Sec. 3.2.1): the BF16 form evaluates the upper triangle of tiles only
+    (T (T + 1) / 2 tiles of 128 x 128 pairs, half the logical pairs) with the
+    symmetrised G.V product of depth 6 m, the cross term and the 4 d + 1
+    feature sums.  The FP32 forms are FMA-pipe bound: 2 d + m operations per
+    pair forward, 4 d + 2 m + 2 adjoint."""
     if prec == "bf16_hilo":
-        mufu = SM_COUNT * MUFU_EX2_LANES * f                      # one ex2 per pair
-        tens = tensor_tflops * 1e12 / algorithmic_flops_per_pair(d, m, which)
-        if tens < mufu:
-            return tens, "tensor", f"tensor pipe, {algorithmic_flops_per_pair(d, m, which)} FLOP per pair"
-        return mufu, "alu", "MUFU ex2 issue, 1 exp per pair"
-    ops = 2 * d + m if which == "fwd" else 4 * d + 2 * m + 2
-    return SM_COUNT * FMA_LANES * f / ops, "alu", f"FP32 FMA-pipe issue, {ops} ops per pair"
+        if kind == "fwd":
+            pairs = n * n
+            return pairs, pairs * (2 * (3 * d + 6) + 2 * m), 0
+        t = -(-n // 128)
+        comp = t * (t + 1) // 2 * 128 * 128
+        return comp, comp * (2 * (3 * d + 6) + 2 * 6 * m + 2 * (4 * d + 1)), 0
+    ops = 2 * d + m if kind == "fwd" else 4 * d + 2 * m + 2
+    return 0, 0, n * n * ops
+
+
+def kernel_roof(prec, kind, d, m, n, clock_mhz, tensor_tflops, ms):
+    """Roofline of one kernel launch that took `ms`: the binding unit among
+    MUFU ex2 issue (MUFU_EX2_LANES per SM per clock), the tensor pipe (the
+    measured BF16 peak) and FMA issue (FMA_LANES per SM per clock)."""
+    f = clock_mhz * 1e6
+    e, fl, ops = kernel_work(prec, kind, d, m, n)
+    t = {"mufu": e / (SM_COUNT * MUFU_EX2_LANES * f), "tensor": fl / (tensor_tflops * 1e12),
+         "fma": ops / (SM_COUNT * FMA_LANES * f)}
+    unit = max(t, key=t.get)
+    sec = ms * 1e-3
+    if unit == "tensor":
+        r = {"bound": "tensor", "achieved": fl / sec / 1e12, "peak": tensor_tflops, "unit": "TFLOP/s",
+             "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst), of measured"}
+    elif unit == "mufu":
+        r = {"bound": "alu", "achieved": e / sec / 1e9, "peak": SM_COUNT * MUFU_EX2_LANES * f / 1e9,
+             "unit": "G ex2/s", "peak_source": f"derived: {SM_COUNT} SMs x {MUFU_EX2_LANES} ex2/clk x {clock_mhz:.0f} MHz"}
+    else:
+        r = {"bound": "alu", "achieved": ops / sec / 1e9, "peak": SM_COUNT * FMA_LANES * f / 1e9,
+             "unit": "G FMA-pipe op/s", "peak_source": f"derived: {SM_COUNT} SMs x {FMA_LANES} lanes x {clock_mhz:.0f} MHz"}
+    r["frac"] = r["achieved"] / r["peak"]
+    r["roof_ms"] = 1e3 * t[unit]
+    return r
 
 
 def run_reference(args):
@@ -216,6 +241,7 @@ def main():
     import torch.distributed as dist
     import workloads as wl
     from paper_2412_20884_gb300 import Kmv, Points, KmvError
+    from paper_2412_20884_gb300.binding import KMV_KERNEL_FORWARD, KMV_KERNEL_ADJOINT
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -258,6 +284,7 @@ def main():
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
+    h.profile_enable(True)
     with Clocks(local) as clk:
         t_wall0 = time.perf_counter()
         for k in range(args.steps):
@@ -269,6 +296,8 @@ def main():
             ev[k][2].record(stream)
         torch.cuda.synchronize()
         t_wall = time.perf_counter() - t_wall0
+    prof = {"fwd": h.profile_read(KMV_KERNEL_FORWARD), "adj": h.profile_read(KMV_KERNEL_ADJOINT)}
+    h.profile_enable(False)
     if world > 1:
         dist.barrier()
     t_f = [ev[k][0].elapsed_time(ev[k][1]) for k in range(args.steps)]
@@ -324,27 +353,23 @@ def main():
     if rank == 0:
         pk = peaks()
         clock = pk.get("sm_max_mhz", 2070.0)
-        mf, mb = float(np.mean(t_f)), float(np.mean(t_b))
-        which = "bwd" if mb >= mf else "fwd"
-        dur = max(mf, mb) * 1e-3
         tflops = pk.get("bf16_tflops", 1900.0)
-        peak_pairs, bound, basis = roof(prec, w.d, w.m, clock, which, tflops)
-        if bound == "tensor":
-            fpp = algorithmic_flops_per_pair(w.d, w.m, which)
-            ach = n * n * fpp / dur / 1e12
-            roof_obj = {"bound": "tensor", "achieved": ach, "peak": tflops, "unit": "TFLOP/s",
-                        "frac": ach / tflops, "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst), of measured"}
-        else:
-            ach = n * n / dur / 1e9
-            roof_obj = {"bound": "alu", "achieved": ach, "peak": peak_pairs / 1e9, "unit": "GPair/s",
-                        "frac": ach * 1e9 / peak_pairs,
-                        "peak_source": "derived: SM count x measured issue rate x max SM clock"}
-        roof_obj.update({"traffic": DRAM_TRAFFIC.get((prec, which)), "kernel": f"kmv_{which} ({prec})",
-                         "basis": f"{basis}; {clock:.0f} MHz x {SM_COUNT} SMs"})
-        rf, _, _ = roof(prec, w.d, w.m, clock, "fwd", tflops)
-        rb, _, _ = roof(prec, w.d, w.m, clock, "bwd", tflops)
-        both_roof_ms = 1e3 * (n * n / rf + n * n / rb)
-        roof_out = roof_obj
+        mf, mb = float(np.mean(t_f)), float(np.mean(t_b))
+        # per-kernel durations from events around each main-kernel launch (same stream)
+        kernels = {}
+        for kind, (tot_ms, nl) in prof.items():
+            if nl == 0:
+                continue
+            per = tot_ms / nl
+            kernels[kind] = {"launches_per_step": nl / args.steps, "ms_per_launch": per,
+                             "share_of_step": tot_ms / args.steps / ms_max,
+                             "roofline": kernel_roof(prec, kind, w.d, w.m, n, clock, tflops, per)}
+        dom = max(kernels, key=lambda k: kernels[k]["ms_per_launch"] * kernels[k]["launches_per_step"])
+        roof_out = dict(kernels[dom]["roofline"])
+        roof_out.update({"traffic": DRAM_TRAFFIC.get((prec, dom)),
+                         "kernel": {"fwd": "tc_fwd_kernel", "adj": "tc_bwd_ts_kernel"}[dom] if prec == "bf16_hilo"
+                         else {"fwd": "simt_fwd_kernel", "adj": "simt_bwd_kernel"}[dom],
+                         "ms_per_launch": kernels[dom]["ms_per_launch"]})
         out = {"metric": METRIC, "value": value, "unit": "GPair/s", "n_gpus": world, "steps": args.steps,
                "warmup": max(3, args.warmup), "ms_per_step": ms_max, "higher_is_better": True,
                "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec == "fp32" else "bf16",
@@ -352,7 +377,7 @@ def main():
                "config": {"workload": WORKLOAD, "N": n, "d": w.d, "m": w.m, "ard": True, "chains": 1,
                           "precision": prec, "l2": "flushed between steps (256 MiB write)",
                           "parallelism": f"replicas x{world}"},
-               "fwd_ms": mf, "bwd_ms": mb, "roof_frac_fwd_bwd": both_roof_ms / ms_max,
+               "fwd_ms": mf, "bwd_ms": mb, "kernels": kernels,
                "roofline": roof_out,
                "e2e": {"value": e2e_value, "unit": "GPair/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
                "gpu_launches": launches_per_step * args.steps,

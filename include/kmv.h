@@ -203,6 +203,26 @@ kmv_status kmv_energy(kmv_handle h, const kmv_points* pts, int32_t chains,
                       kmv_precision prec, void* stream);
 
 /*
+ * Kernel timing.  Instrumentation for measuring the library on a device; the
+ * paper has no counterpart.  While enabled, every launch of a main product
+ * kernel is bracketed by two CUDA events recorded on the call's stream:
+ *   KMV_KERNEL_FORWARD  the forward kernel (either precision, including the
+ *                       forward pass that kmv_backward runs for grad_V),
+ *   KMV_KERNEL_ADJOINT  the adjoint kernel of kmv_backward.
+ * The preparation and epilogue kernels around them are not included.  No
+ * events are recorded while the stream is being captured into a CUDA graph.
+ * kmv_profile_enable(h, on) switches timing on (on != 0) or off and drops
+ * the records so far.  kmv_profile_read(h, kind, &total_ms, &launches) waits
+ * for the recorded events, returns the summed device time in milliseconds and
+ * the number of launches of that kind since the last read or enable, and
+ * clears them.  Errors: KMV_EINVAL (null handle or output, unknown kind),
+ * KMV_ECUDA (an event could not be read; the others are still summed).
+ */
+typedef enum { KMV_KERNEL_FORWARD = 0, KMV_KERNEL_ADJOINT = 1 } kmv_kernel_kind;
+kmv_status kmv_profile_enable(kmv_handle h, int32_t on);
+kmv_status kmv_profile_read(kmv_handle h, int32_t kind, double* total_ms, int64_t* launches);
+
+/*
  * kmv_backward_noalloc - kmv_backward with KMV_FP32 arithmetic that allocates
  * no device memory and needs no handle.  The paper has no counterpart: this
  * entry point exists for callers that cannot call cudaMalloc, such as code

@@ -52,7 +52,11 @@ _SIGS = {
     "kmv_energy": (C.c_int, [_P, C.POINTER(_Points), C.c_int32, _P, _P, _P, _P, _P, _P, C.c_double,
                              C.c_int32, _P, _P, _P, _P, _P, C.c_int, _P]),
     "kmv_backward_noalloc": (C.c_int, [C.POINTER(_Points), C.c_int32, _P, _P, _P, C.c_int32, _P, _P, _P]),
+    "kmv_profile_enable": (C.c_int, [_P, C.c_int32]),
+    "kmv_profile_read": (C.c_int, [_P, C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
 }
+
+KMV_KERNEL_FORWARD, KMV_KERNEL_ADJOINT = 0, 1
 
 
 def lib_path() -> str:
@@ -156,6 +160,16 @@ class Kmv:
 
     def workspace_bytes(self) -> int:
         return int(self.L.kmv_workspace_bytes(self.h))
+
+    def profile_enable(self, on: bool = True):
+        """Time every main product-kernel launch with CUDA events (kmv_profile_enable)."""
+        self._check(self.L.kmv_profile_enable(self.h, 1 if on else 0))
+
+    def profile_read(self, kind: int):
+        """(total_ms, launches) of one kernel kind since the last read (kmv_profile_read)."""
+        ms, n = C.c_double(0.0), C.c_int64(0)
+        self._check(self.L.kmv_profile_read(self.h, kind, C.byref(ms), C.byref(n)))
+        return ms.value, n.value
 
     @staticmethod
     def _prec(prec):

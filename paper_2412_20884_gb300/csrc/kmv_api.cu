@@ -188,7 +188,10 @@ kmv_status run_forward(kmv_handle h, const KmvArgs& a, kmv_precision prec, cudaS
     kmv_status s = tc_forward(h, a, st);
     return s;
   }
-  KMV_CUDA(h, launch_forward_simt(a, h->layout.n_items, st));
+  {
+    ProfScope prof(h, KMV_KERNEL_FORWARD, st);
+    KMV_CUDA(h, launch_forward_simt(a, h->layout.n_items, st));
+  }
   return KMV_OK;
 }
 
@@ -210,7 +213,10 @@ kmv_status run_backward(kmv_handle h, KmvArgs a, double* grad, double* partial,
   const int mp = backward_mp(a.m);
   a.n_z = (a.m + mp - 1) / mp;
   a.grad_partial = partial;
-  if (L.n_items > 0) KMV_CUDA(h, launch_backward_simt(a, L.n_items, st));
+  if (L.n_items > 0) {
+    ProfScope prof(h, KMV_KERNEL_ADJOINT, st);
+    KMV_CUDA(h, launch_backward_simt(a, L.n_items, st));
+  }
   KMV_CUDA(h, launch_grad_finalize(h->dev, L.n_inst, L.chains, L.n_theta, L.ard, L.d, a.n_z,
                                    a.theta, partial, grad, st));
   return KMV_OK;
@@ -460,6 +466,8 @@ kmv_status kmv_destroy(kmv_handle h) {
   if (h->ws) cudaFree(h->ws);
   if (h->tables) cudaFree(h->tables);
   if (h->host_flag) cudaFreeHost(h->host_flag);
+  kmv_profile_enable(h, 0);
+  for (cudaEvent_t e : h->prof_pool) cudaEventDestroy(e);
   delete h;
   return KMV_OK;
 }

@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "kmv.h"
@@ -150,4 +151,21 @@ struct kmv_handle_s {
   // true while the current call's stream is being captured into a CUDA graph:
   // no allocation, no table upload, no host synchronisation may happen then
   bool capturing = false;
+  // kernel timing (kmv_profile_enable): event pairs around the main product kernels
+  bool prof = false;
+  std::vector<cudaEvent_t> prof_pool;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_rec[2];
 };
+
+namespace kmv {
+// Brackets one main-kernel launch with events on `st` while timing is enabled
+// and the stream is not being captured.
+struct ProfScope {
+  kmv_handle h;
+  int kind;
+  cudaStream_t st;
+  cudaEvent_t e1 = nullptr;
+  ProfScope(kmv_handle h_, int kind_, cudaStream_t st_);
+  ~ProfScope();
+};
+}  // namespace kmv

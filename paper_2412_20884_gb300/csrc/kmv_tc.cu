@@ -1083,10 +1083,13 @@ kmv_status tc_forward(kmv_handle h, const KmvArgs& a, cudaStream_t st) {
     fa.sys_active = a.sys_active;
     fa.err = err;
     const int grid = std::min(S->n_items, S->num_sms);
-    if (mz == 1)
-      tc_fwd_fma_kernel<1><<<grid, kFwdThreads, smem, st>>>(fa);
-    else
-      tc_fwd_fma_kernel<2><<<grid, kFwdThreads, smem, st>>>(fa);
+    {
+      ProfScope prof(h, KMV_KERNEL_FORWARD, st);
+      if (mz == 1)
+        tc_fwd_fma_kernel<1><<<grid, kFwdThreads, smem, st>>>(fa);
+      else
+        tc_fwd_fma_kernel<2><<<grid, kFwdThreads, smem, st>>>(fa);
+    }
     // vmax is zero: the epilogue's column scale is 1
     tc_launch_epilogue(h, S, a, 0, mz, part, vmax, err, st);
     const cudaError_t e = cudaGetLastError();
@@ -1121,10 +1124,13 @@ kmv_status tc_forward(kmv_handle h, const KmvArgs& a, cudaStream_t st) {
     fa.sys_active = a.sys_active;
     fa.err = err;
     const int grid = std::min(S->n_items, S->num_sms);
-    if (MP <= 16)
-      tc_fwd_kernel<16><<<grid, kFwdThreads, smem, st>>>(fa);
-    else
-      tc_fwd_kernel<0><<<grid, kFwdThreads, smem, st>>>(fa);
+    {
+      ProfScope prof(h, KMV_KERNEL_FORWARD, st);
+      if (MP <= 16)
+        tc_fwd_kernel<16><<<grid, kFwdThreads, smem, st>>>(fa);
+      else
+        tc_fwd_kernel<0><<<grid, kFwdThreads, smem, st>>>(fa);
+    }
     tc_launch_epilogue(h, S, a, c0, mz, part, vmax, err, st);
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return tc_fail(h, KMV_ECUDA, cudaGetErrorString(e));

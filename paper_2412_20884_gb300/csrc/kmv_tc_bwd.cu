@@ -1,24 +1,30 @@
 // Tensor-core (tcgen05) adjoint of L = sum G o (A V), KMV_BF16_HILO.
 //
 // For every pair the gradient needs W_ij = G_i . V_j, K0_ij and, per input
-// dimension, (xt_ik - xt_jk)^2.  Per 64-column half tile and I tile g an MMA
-// issuer writes into TMEM
-//   S_g = XA_g XB^T           the base-2 exponent (BF16 hi/lo, as in the forward)
-//   W_g = GI_g VJ^T           GI rows [gh, gh, gl], VJ rows [vh, vl, vh] (BF16 hi/lo)
-// the exp warpgroup forms Q = W 2^S and writes it to its own TMEM columns as
-// F16, and the issuer then accumulates, per row i,
-//   ACC_g += Q BG             BG columns for dimension k: 4k..4k+3 = [xh, xl, sh, sl]
-//                             (F16 hi/lo of xt_jk and of xt_jk^2), column 60 = 1;
+// dimension, (xt_ik - xt_jk)^2.  Because K0 and (xt_i - xt_j)^2 are symmetric
+// in (i, j), W may be replaced by W^s = (W + W^T) / 2, and then the sum over
+// tile (J, I) equals the sum over tile (I, J): only the upper triangle of
+// tiles (J >= I) is evaluated, off-diagonal tiles weighted twice.  For a J
+// half tile (64 columns) of an I tile the MMA issuers write into TMEM
+//   S = XA_I XB_J^T           the base-2 exponent (BF16 hi/lo, as in the forward)
+//   W = GI_I VJ_J^T           = G_i . V_j + V_i . G_j with GI rows
+//                             [gh gh gl vh vh vl] and VJ rows [vh vl vh gh gl gh]
+//                             (BF16 hi/lo, G scaled by a power of two)
+// an exp warpgroup forms Q = W 2^S (halved on the diagonal tile) as F16 in its
+// own TMEM columns, and the feature-sum issuer accumulates, per row i,
+//   ACC += Q BG               BG columns for dimension k: 4k..4k+3 = [xh, xl, sh, sl]
+//                             (F16 hi/lo of xt_jk and of xt_jk^2), column 4 d = 1;
 //                             giving R_ik = sum_j Q_ij xt_jk, T_ik = sum_j Q_ij xt_jk^2
 //                             and q_i = sum_j Q_ij
-// dL/dV = A G is the forward product with G in place of V (kmv_tc.cu).
-// Every kFoldH half tiles the warpgroup folds, per row,
+// Every kFoldH half tiles warpgroup 0 folds, per row,
 //   sum_j Q_ij (xt_ik - xt_jk)^2 = xt_ik^2 q_i - 2 xt_ik R_ik + T_ik
-// into FP64 accumulators.  Because q, R and T are formed from the same rounded
-// Q, the rounding of Q cancels in this combination exactly as in the exact
-// sum; the hi/lo splits keep xt and xt^2 to ~22 bits.  G is scaled by a power
-// of two so that |W| <= 2^14 (F16 range); the scale is removed at the end.
-// Per-warp FP64 partials are reduced per system in a fixed order.
+// into FP64 sums.  Because q, R and T are formed from the same rounded Q, the
+// rounding of Q cancels in this combination exactly as in the exact sum; the
+// hi/lo splits keep xt and xt^2 to ~22 bits.  The scale of G is removed at the
+// end; per-warp FP64 partials are reduced per system in a fixed order.  When
+// the depth-6m operands do not fit in TMEM (large m), the same kernel runs on
+// all tiles with the plain W (GI [gh gh gl], VJ [vh vl vh]) and I-pair items.
+// dL/dV = A G is the forward product with G in place of V (kmv_tc.cu).
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -34,9 +40,6 @@ namespace kmv {
 namespace {
 
 constexpr int kFoldH = 64;   // half tiles (64 columns) per FP32 accumulation (4096 columns)
-constexpr int kMaxDB = 15;   // 4 d gradient features + the ones column fit a 64-column accumulator
-constexpr int kNB = 64;      // accumulator columns; the ones column is kQCol
-constexpr int kQCol = 60;
 constexpr int kGW = 16;      // doubles per (item, warp) gradient partial: [q, contrib_0..d-1]
 
 struct TcBwdArgs {
@@ -44,7 +47,7 @@ struct TcBwdArgs {
   int n_items;
   int chains;
   int T_total;
-  int KX, KG, NB, S, NA;
+  int KX, KG, NB, S;
   int qcol;   // accumulator column of q_i (the ones column of BG)
   int sym;    // 1: upper-triangle items (one I tile each) with the symmetrised W; 0: I-pair items
   int d, n_theta, ard;
@@ -79,9 +82,6 @@ __device__ __forceinline__ float xt_of(float xv, float sc) {
   return __half2float(hi) + __half2float(lo);
 }
 
-__device__ __forceinline__ void issue_ss(uint32_t d_tmem, uint64_t da, uint64_t db, int nk, uint32_t idesc) {
-  for (int k = 0; k < nk; ++k) ptx::mma_ss(d_tmem, da + 16 * k, db + 16 * k, idesc, k > 0);
-}
 // K = 64 from TMEM (four K = 16 steps of 8 columns each).
 __device__ __forceinline__ void issue_ts4(uint32_t d_tmem, uint32_t a_tmem, uint64_t db, uint32_t idesc,
                                           uint32_t acc) {
@@ -89,368 +89,10 @@ __device__ __forceinline__ void issue_ts4(uint32_t d_tmem, uint32_t a_tmem, uint
   for (int k = 0; k < 4; ++k) ptx::mma_ts(d_tmem, a_tmem + 8 * k, db + 16 * k, idesc, (k > 0) || acc);
 }
 
-// Warp roles: warps 0-7 two exp warpgroups (one per I tile), warp 8 MMA
-// issuer of I tile 0 (and TMEM owner), warp 9 producer, warp 10 MMA issuer of
-// I tile 1.  TMEM per I tile g (256 columns from 256 g): S [0,64), W [64,128),
-// Q double-buffered in [128,160) and [160,192), ACC [192,256).  A half tile's S
-// and W are released as soon as the warpgroup has loaded them, so the next
-// half's S, W MMAs run during this half's exps; Q has its own two buffers, so
-// the feature-sum MMAs of one half run during the next two halves' exps.
-constexpr int kBwdThreads = 352;
 constexpr int kBwdIssue1Warp = 10;
 
-__global__ void __launch_bounds__(kBwdThreads, 1) tc_bwd_kernel(TcBwdArgs a) {
-  using namespace ptx;
-  extern __shared__ uint8_t smem_raw[];
-  uint8_t* smem = align1024(smem_raw);
-  const uint32_t XT = a.KX * 256u, GT = a.KG * 256u, BT = a.NB * 256u;
-  const uint32_t ABUF = 2 * XT + 2 * GT;   // one A buffer: XA g0, XA g1, GI g0, GI g1
-  const uint32_t STG = XT + GT + BT;       // one stage: XB, VJ, BG
-  const int S = a.S, NA = a.NA;
-  uint8_t* sA = smem;
-  uint8_t* sS = sA + NA * ABUF;
-  uint64_t* full = reinterpret_cast<uint64_t*>(sS + S * STG);
-  uint64_t* empty = full + S;
-  uint64_t* a_full = empty + S;
-  uint64_t* a_empty = a_full + 2;
-  uint64_t* s_full = a_empty + 2;    // [g] S, W of a half tile written
-  uint64_t* s_free = s_full + 2;     // [g] S, W loaded into registers
-  uint64_t* q_ready = s_free + 2;    // [2 g + buffer] Q written
-  uint64_t* q_free = q_ready + 4;    // [2 g + buffer] Q consumed by the feature-sum MMAs
-  uint64_t* o_ready = q_free + 4;
-  uint64_t* o_free = o_ready + 2;
-  uint64_t* done = o_free + 2;       // [g]
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(done + 2);
-  volatile int* abort = reinterpret_cast<volatile int*>(tslot + 1);
-
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (threadIdx.x == 0) {
-    for (int i = 0; i < S; ++i) {
-      mbar_init(&full[i], 1);
-      mbar_init(&empty[i], 2);
-    }
-    for (int g = 0; g < 2; ++g) {
-      mbar_init(&a_full[g], 1);
-      mbar_init(&a_empty[g], 2);
-      mbar_init(&s_full[g], 1);
-      mbar_init(&s_free[g], 128);
-      mbar_init(&q_ready[2 * g], 128);
-      mbar_init(&q_ready[2 * g + 1], 128);
-      mbar_init(&q_free[2 * g], 1);
-      mbar_init(&q_free[2 * g + 1], 1);
-      mbar_init(&o_ready[g], 1);
-      mbar_init(&o_free[g], 128);
-      mbar_init(&done[g], 1);
-    }
-    *abort = 0;
-    fence_barrier_init();
-  }
-  if (warp == kMmaWarp) {
-    tmem_alloc(tslot, 512);
-    tmem_relinquish();
-  }
-  tc_fence_before();
-  __syncthreads();
-  tc_fence_after();
-  const uint32_t tbase = *tslot;
-
-  if (warp == kLoadWarp) {
-    const bool leader = elect_one();
-    {
-      // ------------------------------------------------------------ producer
-      int it = 0, n_issued = 0, n_a_issued = 0;
-      uint32_t stage = 0, sph = 0;
-      bool aborted = false;
-      for (int t = blockIdx.x; t < a.n_items && !aborted; t += gridDim.x) {
-        const int4 item = a.items[t];
-        if (a.sys_active && !a.sys_active[item.x]) continue;
-        const int c = item.x % a.chains;
-        const int ab = it % NA;
-        if (!warp_wait(&a_empty[ab], ((it / NA) & 1) ^ 1, abort, a.err, 21)) { aborted = true; break; }
-        if (leader) {
-          mbar_arrive_expect_tx(&a_full[ab], ABUF);
-          const size_t ti = (size_t)c * a.T_total + item.y;
-          uint8_t* ad = sA + ab * ABUF;
-          bulk_g2s(ad, a.XA + ti * XT, 2 * XT, &a_full[ab]);
-          bulk_g2s(ad + 2 * XT, a.GI + ti * GT, 2 * GT, &a_full[ab]);
-        }
-        __syncwarp();
-        ++n_a_issued;
-        for (int j = 0; j < item.w; ++j) {
-          if (!warp_wait(&empty[stage], sph ^ 1, abort, a.err, 22)) { aborted = true; break; }
-          if (leader) {
-            mbar_arrive_expect_tx(&full[stage], STG);
-            const size_t tj = (size_t)c * a.T_total + item.z + j;
-            uint8_t* sd = sS + stage * STG;
-            bulk_g2s(sd, a.XB + tj * XT, XT, &full[stage]);
-            bulk_g2s(sd + XT, a.VJ + tj * GT, GT, &full[stage]);
-            bulk_g2s(sd + XT + GT, a.BG + tj * BT, BT, &full[stage]);
-          }
-          __syncwarp();
-          ++n_issued;
-          if (++stage == (uint32_t)S) { stage = 0; sph ^= 1; }
-        }
-        ++it;
-      }
-      if (aborted) {
-        for (int k = 1; k <= min(n_issued, S); ++k) {
-          const int idx = n_issued - k;
-          mbar_drain(&full[idx % S], (idx / S) & 1, 500000000ull);
-        }
-        for (int k = 1; k <= min(n_a_issued, NA); ++k) {
-          const int idx = n_a_issued - k;
-          mbar_drain(&a_full[idx % NA], (idx / NA) & 1, 500000000ull);
-        }
-      }
-    }
-  } else if (warp == kMmaWarp || warp == kBwdIssue1Warp) {
-    const bool leader = elect_one();
-    {
-      // ------------------------------------------------------------ MMA issuer of I tile g
-      // Half-tile stream k: S, W of half k once half k-1 is loaded by the
-      // warpgroup, then the feature sums of half k-1 once its Q is written.
-      const int g = warp == kMmaWarp ? 0 : 1;
-      const uint32_t idSW = idesc_f16(128, 64, 1, 1);
-      const uint32_t idA = idesc_f16(128, a.NB, 0, 0);
-      const uint32_t sboX = a.KX * 16u, sboG = a.KG * 16u;
-      const int nkx = a.KX / 16, nkg = a.KG / 16;
-      const uint64_t dXA = sdesc(smem_u32(sA + g * XT), 128, sboX);
-      const uint64_t dGI = sdesc(smem_u32(sA + 2 * XT + g * GT), 128, sboG);
-      const uint64_t dXB = sdesc(smem_u32(sS), 128, sboX);
-      const uint64_t dVJ = sdesc(smem_u32(sS + XT), 128, sboG);
-      const uint64_t dBG = sdesc(smem_u32(sS + XT + GT), 128, 2048);
-      const uint32_t tg = tbase + 256 * g;
-      int it = 0;
-      uint32_t stage = 0, sph = 0, sf_ph = 0, of_ph = 0;
-      bool opend = false;
-      long long k = 0;
-      bool have_prev = false;
-      uint32_t prev_stage = 0;
-      int prev_h = 0, prev_nH = 0;
-      for (int t = blockIdx.x; t < a.n_items; t += gridDim.x) {
-        const int4 item = a.items[t];
-        if (a.sys_active && !a.sys_active[item.x]) continue;
-        const int ab = it % NA;
-        const int nH = 2 * item.w;
-        for (int h = 0; h < nH; ++h, ++k) {
-          const int hh = h & 1;
-          // ---- S, W of half k
-          if (k > 0) {
-            if (!warp_wait(&s_free[g], sf_ph, abort, a.err, 23)) goto mma_out;
-            sf_ph ^= 1;
-          }
-          if (h == 0 && !warp_wait(&a_full[ab], (it / NA) & 1, abort, a.err, 24)) goto mma_out;
-          if (hh == 0 && !warp_wait(&full[stage], sph, abort, a.err, 25)) goto mma_out;
-          tc_fence_after();
-          // operands computed by the whole warp (warp-uniform), issued by the leader
-          const uint64_t da = sdesc_add(dXA, ab * ABUF), db = sdesc_add(dXB, stage * STG + hh * a.KX * 128u);
-          const uint64_t dg = sdesc_add(dGI, ab * ABUF), dv = sdesc_add(dVJ, stage * STG + hh * a.KG * 128u);
-          if (leader) {
-            issue_ss(tg, da, db, nkx, idSW);
-            issue_ss(tg + 64, dg, dv, nkg, idSW);
-            tc_commit(&s_full[g]);
-            // the A buffer is read only by the S, W MMAs: release it after the
-            // item's last half, before the next item waits for its own A buffer
-            if (h == nH - 1) tc_commit(&a_empty[ab]);
-          }
-          __syncwarp();
-          // ---- feature sums of half k-1
-          if (have_prev) {
-            // half k-1 used Q buffer (k-1) & 1 for the ((k-1) >> 1)-th time
-            const int qb = (int)((k - 1) & 1);
-            if (!warp_wait(&q_ready[2 * g + qb], (uint32_t)((k - 1) >> 1) & 1u, abort, a.err, 26)) goto mma_out;
-            tc_fence_after();
-            const uint32_t acc = (prev_h % kFoldH) != 0;
-            if (!acc && opend) {
-              if (!warp_wait(&o_free[g], of_ph, abort, a.err, 27)) goto mma_out;
-              of_ph ^= 1;
-              opend = false;
-              tc_fence_after();
-            }
-            const bool fold_end = (prev_h % kFoldH) == kFoldH - 1 || prev_h == prev_nH - 1;
-            const uint64_t dbg = sdesc_add(dBG, prev_stage * STG + (prev_h & 1) * 1024u);
-            const uint32_t tq = tg + 128 + 32 * qb;
-            if (leader) {
-              issue_ts4(tg + 192, tq, dbg, idA, acc);
-              tc_commit(&q_free[2 * g + qb]);
-              if (fold_end) tc_commit(&o_ready[g]);
-              if (prev_h & 1) tc_commit(&empty[prev_stage]);
-            }
-            __syncwarp();
-            if (fold_end) opend = true;
-          }
-          have_prev = true;
-          prev_stage = stage;
-          prev_h = h;
-          prev_nH = nH;
-          if (hh == 1) {
-            if (++stage == (uint32_t)S) { stage = 0; sph ^= 1; }
-          }
-        }
-        ++it;
-      }
-      if (have_prev) {
-        const int qb = (int)((k - 1) & 1);
-        if (!warp_wait(&q_ready[2 * g + qb], (uint32_t)((k - 1) >> 1) & 1u, abort, a.err, 26)) goto mma_out;
-        tc_fence_after();
-        const uint32_t acc = (prev_h % kFoldH) != 0;
-        if (!acc && opend) {
-          if (!warp_wait(&o_free[g], of_ph, abort, a.err, 27)) goto mma_out;
-          tc_fence_after();
-        }
-        const uint64_t dbg = sdesc_add(dBG, prev_stage * STG + (prev_h & 1) * 1024u);
-        const uint32_t tq = tg + 128 + 32 * qb;
-        if (leader) {
-          issue_ts4(tg + 192, tq, dbg, idA, acc);
-          tc_commit(&q_free[2 * g + qb]);
-          tc_commit(&o_ready[g]);
-          tc_commit(&empty[prev_stage]);
-        }
-        __syncwarp();
-      }
-    mma_out:
-      if (leader) tc_commit(&done[g]);
-      __syncwarp();
-      mbar_drain(&done[g], 0, 500000000ull);
-    }
-    __syncwarp();
-  } else {
-    // ------------------------------------------------------------ exp warpgroups
-    const int g = warp >> 2, w = warp & 3;
-    const int row = 32 * w + lane;
-    const uint32_t tl = tbase + 256 * g + (static_cast<uint32_t>(32 * w) << 16);
-    const int d = a.d;
-    uint32_t sph = 0, oph = 0;
-    long long k = 0;
-    for (int t = blockIdx.x; t < a.n_items; t += gridDim.x) {
-      const int4 item = a.items[t];
-      if (a.sys_active && !a.sys_active[item.x]) continue;
-      const int s = item.x, b = s / a.chains;
-      const int64_t nb = a.L.offsets[b + 1] - a.L.offsets[b];
-      const int64_t rl = (int64_t)(item.y + g - a.T.inst_tile0[b]) * 128 + row;
-      const bool valid = rl < nb;
-      const double* th = a.theta + (int64_t)s * a.n_theta;
-      float xt[kMaxDB];
-      double dacc[kMaxDB];
-      double dq = 0.0;
-#pragma unroll
-      for (int kk = 0; kk < kMaxDB; ++kk) {
-        xt[kk] = 0.f;
-        dacc[kk] = 0.0;
-      }
-      if (valid) {
-        const int64_t i = a.L.offsets[b] + rl;
-#pragma unroll
-        for (int kk = 0; kk < kMaxDB; ++kk) {
-          if (kk < d) {
-            const float sc = (float)(sqrt(2.0 * kHalfLog2e) * exp(-th[1 + (a.ard ? kk : 0)]));
-            xt[kk] = xt_of(a.x[i * d + kk], sc);
-          }
-        }
-      }
-      const int nH = 2 * item.w;
-      for (int h = 0; h < nH; ++h, ++k) {
-        bool ok = mbar_wait(&s_full[g], sph, abort, a.err, 28);
-        if (!__all_sync(0xffffffffu, ok)) goto exp_out;
-        sph ^= 1;
-        tc_fence_after();
-        {
-          uint32_t s0[32], w0[32], s1[32], w1[32], qq[32];
-          tmem_ld32(tl, s0);
-          tmem_ld32(tl + 64, w0);
-          tmem_ld_wait_regs(s0, w0);
-          tmem_ld32(tl + 32, s1);
-          tmem_ld32(tl + 96, w1);
-#pragma unroll
-          for (int q = 0; q < 16; ++q)
-            qq[q] = pack_f16x2(ex2(__uint_as_float(s0[2 * q])) * __uint_as_float(w0[2 * q]),
-                               ex2(__uint_as_float(s0[2 * q + 1])) * __uint_as_float(w0[2 * q + 1]));
-          tmem_ld_wait_regs(s1, w1);
-          // S, W of this half are in registers: the tensor core may overwrite them
-          tc_fence_before();
-          mbar_arrive(&s_free[g]);
-#pragma unroll
-          for (int q = 0; q < 16; ++q)
-            qq[16 + q] = pack_f16x2(ex2(__uint_as_float(s1[2 * q])) * __uint_as_float(w1[2 * q]),
-                                    ex2(__uint_as_float(s1[2 * q + 1])) * __uint_as_float(w1[2 * q + 1]));
-          const int qb = (int)(k & 1);
-          if (k >= 2) {
-            // Q buffer qb must have been consumed by the feature sums of half k - 2
-            ok = mbar_wait(&q_free[2 * g + qb], (uint32_t)((k - 2) >> 1) & 1u, abort, a.err, 30);
-            if (!__all_sync(0xffffffffu, ok)) goto exp_out;
-            tc_fence_after();
-          }
-          tmem_st32(tl + 128 + 32 * qb, qq);
-        }
-        tmem_st_wait();
-        tc_fence_before();
-        mbar_arrive(&q_ready[2 * g + (int)(k & 1)]);
-        if ((h % kFoldH) == kFoldH - 1 || h == nH - 1) {
-          ok = mbar_wait(&o_ready[g], oph, abort, a.err, 29);
-          if (!__all_sync(0xffffffffu, ok)) goto exp_out;
-          oph ^= 1;
-          tc_fence_after();
-          uint32_t o3[16];
-          tmem_ld16(tl + 192 + 48, o3);
-          tmem_ld_wait_regs(o3);
-          const float qs = __uint_as_float(o3[kQCol - 48]);
-          dq += (double)qs;
-#pragma unroll
-          for (int c4 = 0; c4 < 4; ++c4) {
-            if (4 * c4 < d) {
-              uint32_t o[16];
-              if (c4 == 3) {
-#pragma unroll
-                for (int q = 0; q < 16; ++q) o[q] = o3[q];
-              } else {
-                tmem_ld16(tl + 192 + 16 * c4, o);
-                tmem_ld_wait_regs(o);
-              }
-#pragma unroll
-              for (int u = 0; u < 4; ++u) {
-                const int kk = 4 * c4 + u;
-                if (kk < kMaxDB && kk < d) {
-                  const float R = __uint_as_float(o[4 * u]) + __uint_as_float(o[4 * u + 1]);
-                  const float T = __uint_as_float(o[4 * u + 2]) + __uint_as_float(o[4 * u + 3]);
-                  const float x = xt[kk];
-                  dacc[kk] += (double)fmaf(x, fmaf(x, qs, -2.f * R), T);
-                }
-              }
-            }
-          }
-          tc_fence_before();
-          mbar_arrive(&o_free[g]);
-        }
-      }
-      // per-warp partial of this item: [q, contrib_0 .. contrib_{d-1}]
-      {
-        double* out = a.gpart + ((size_t)t * 8 + g * 4 + w) * kGW;
-        double v = dq;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-        if (lane == 0) out[0] = v;
-#pragma unroll
-        for (int kk = 0; kk < kMaxDB; ++kk) {
-          if (kk < d) {
-            double u = dacc[kk];
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) u += __shfl_down_sync(0xffffffffu, u, o);
-            if (lane == 0) out[1 + kk] = u;
-          }
-        }
-      }
-    }
-  exp_out:;
-  }
-
-  tc_fence_before();
-  __syncthreads();
-  tc_fence_after();
-  if (warp == kMmaWarp) tmem_dealloc(tbase, 512);
-}
-
-// Variant with the I-side operands resident in TMEM, one I tile at a time.
-// S and W are A-from-TMEM MMAs that read only the 64-row J half from shared
+// The I-side operands are resident in TMEM, one I tile at a time.  S and W
+// are A-from-TMEM MMAs that read only the 64-row J half from shared
 // memory (with A in shared memory a 128-row A tile is read for every K step,
 // which caps an N = 64 MMA at the shared-memory read rate).  The two exp
 // warpgroups share the I tile: warpgroup b takes J columns [64 b, 64 b + 64)
@@ -967,7 +609,7 @@ __global__ void __launch_bounds__(kFinThreads) tc_bwd_finalize_kernel(
 
 kmv_status tc_backward(kmv_handle h, const KmvArgs& a, double* grad, cudaStream_t st) {
   const Layout& L = h->layout;
-  if (a.d > kMaxDB) return tc_fail(h, KMV_EUNSUPPORTED, "tensor-core adjoint supports d <= 15");
+  if (a.d > kMaxDT) return tc_fail(h, KMV_EUNSUPPORTED, "tensor-core adjoint supports d <= 15");
   TcState* S = tc_state(h);
   kmv_status stt = tc_build_plan(h, S, st);
   if (stt != KMV_OK) return stt;
@@ -977,29 +619,19 @@ kmv_status tc_backward(kmv_handle h, const KmvArgs& a, double* grad, cudaStream_
   // fit; symmetrised (upper-triangle tiles, GI of depth 6 m) when that fits too.
   const int NBt = round16(4 * a.d + 1);
   const int KGs = round16(6 * a.m), KGp = round16(3 * a.m);
-  const bool sym = a.d <= kMaxDT && KX / 2 + KGs / 2 + NBt <= kTsCols;
-  const bool ts = sym || (a.d <= kMaxDT && KX / 2 + KGp / 2 + NBt <= kTsCols);
+  const bool sym = KX / 2 + KGs / 2 + NBt <= kTsCols;
+  if (!sym && KX / 2 + KGp / 2 + NBt > kTsCols)
+    return tc_fail(h, KMV_EUNSUPPORTED, "tensor-core adjoint operands do not fit in tensor memory");
   const int KG = sym ? KGs : KGp;
   const int n_items = sym ? S->sym_n_items : S->n_items;
   const int wpi = sym ? 4 : 8;   // per-warp partial rows per item
-  const int NB = ts ? NBt : kNB;
-  const int qcol = ts ? 4 * a.d : kQCol;
+  const int NB = NBt, qcol = 4 * a.d;
   const size_t XT = (size_t)KX * 256, GT = (size_t)KG * 256, BT = (size_t)NB * 256;
-  const size_t ABUF = 2 * XT + 2 * GT, STG = XT + GT + BT;
-  const size_t fixed = 1024 + 512;
-  int NA = 2, stages = 0;
-  if (ts) {
-    NA = 0;
-    stages = (int)std::min<size_t>(6, (kMaxSmem - fixed - kTsRowBytes) / STG);
-  } else {
-    stages = kMaxSmem >= fixed + NA * ABUF ? (int)std::min<size_t>(6, (kMaxSmem - fixed - NA * ABUF) / STG) : 0;
-    if (stages < 2) {
-      NA = 1;
-      stages = kMaxSmem > fixed + ABUF ? (int)std::min<size_t>(6, (kMaxSmem - fixed - ABUF) / STG) : 0;
-    }
-  }
+  const size_t STG = XT + GT + BT;
+  const size_t fixed = 1024 + kTsBarBytes;
+  const int stages = (int)std::min<size_t>(6, (kMaxSmem - fixed - kTsRowBytes) / STG);
   if (stages < 2) return tc_fail(h, KMV_EUNSUPPORTED, "tensor-core adjoint tiles do not fit in shared memory");
-  const size_t smem = std::max(kMinSmem, fixed + NA * ABUF + stages * STG + (ts ? kTsRowBytes : 0));
+  const size_t smem = std::max(kMinSmem, fixed + stages * STG + kTsRowBytes);
 
   auto al = [](size_t v) { return (v + 255) & ~size_t(255); };
   const size_t tiles = (size_t)L.chains * S->T_total;
@@ -1018,10 +650,8 @@ kmv_status tc_backward(kmv_handle h, const KmvArgs& a, double* grad, cudaStream_
   int* err = reinterpret_cast<int*>(base + o_er);
 
   if (!S->bwd_attr_set) {
-    if (cudaFuncSetAttribute(tc_bwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem) !=
-            cudaSuccess ||
-        cudaFuncSetAttribute(tc_bwd_ts_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem) !=
-            cudaSuccess)
+    if (cudaFuncSetAttribute(tc_bwd_ts_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem) !=
+        cudaSuccess)
       return tc_fail(h, KMV_ECUDA, "cudaFuncSetAttribute failed");
     S->bwd_attr_set = true;
   }
@@ -1047,7 +677,6 @@ kmv_status tc_backward(kmv_handle h, const KmvArgs& a, double* grad, cudaStream_
     ba.NB = NB;
     ba.qcol = qcol;
     ba.S = stages;
-    ba.NA = NA;
     ba.d = a.d;
     ba.n_theta = a.n_theta;
     ba.ard = a.ard;
@@ -1065,10 +694,8 @@ kmv_status tc_backward(kmv_handle h, const KmvArgs& a, double* grad, cudaStream_
     ba.sys_active = a.sys_active;
     ba.err = err;
     const int grid = std::min(n_items, S->num_sms);
-    if (ts)
-      tc_bwd_ts_kernel<<<grid, kTsThreads, smem, st>>>(ba);
-    else
-      tc_bwd_kernel<<<grid, kBwdThreads, smem, st>>>(ba);
+    ProfScope prof(h, KMV_KERNEL_ADJOINT, st);
+    tc_bwd_ts_kernel<<<grid, kTsThreads, smem, st>>>(ba);
   }
   tc_bwd_finalize_kernel<<<n_sys, kFinThreads, 0, st>>>(h->dev, sym ? S->dev.sym_pref : S->dev.sys_pref, wpi,
                                                          L.chains, a.n_theta, a.ard, a.d, a.theta, gpart, gvpart,

@@ -197,3 +197,27 @@ def test_invalid_arguments(kmv_handle):
     with pytest.raises(KmvError):
         kmv_handle.kmv_forward(big, torch.zeros((1, 3), dtype=torch.float64, device="cuda"),
                                torch.zeros((1, 3, 1), device="cuda"))
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_kernel_timing(kmv_handle, prec):
+    """kmv_profile_enable / kmv_profile_read count the main-kernel launches of
+    each kind and return positive device time; reading clears the records."""
+    from paper_2412_20884_gb300.binding import KMV_KERNEL_FORWARD, KMV_KERNEL_ADJOINT
+    h = kmv_handle
+    w = wl.ragged([300, 77], d=3, chains=2, m=2, ard=True, seed=5)
+    pts, theta, V, G = to_dev(w)
+    h.profile_enable(True)
+    try:
+        h.kmv_forward(pts, theta, V, prec=prec)
+        h.kmv_backward(pts, theta, V, G, prec=prec)
+        fms, fn = h.profile_read(KMV_KERNEL_FORWARD)
+        ams, an = h.profile_read(KMV_KERNEL_ADJOINT)
+        # the BF16 backward forms dL/dV with a second forward pass
+        assert fn == (2 if prec == "bf16_hilo" else 1) and an == 1
+        assert fms > 0.0 and ams > 0.0
+        assert h.profile_read(KMV_KERNEL_FORWARD) == (0.0, 0)
+    finally:
+        h.profile_enable(False)
+    h.kmv_forward(pts, theta, V, prec=prec)
+    assert h.profile_read(KMV_KERNEL_FORWARD) == (0.0, 0)
