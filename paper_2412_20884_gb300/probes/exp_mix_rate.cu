@@ -4,6 +4,7 @@
 //   ex2 f16        : ex2, pack pairs to f16x2 (the forward's P)
 //   mul f16        : multiply, pack pairs to f16x2 (no exp)
 //   ex2 mul bf16t  : ex2, multiply, pack pairs to bf16x2 by keeping the high halves (byte permute)
+// Times are the block span (between two block barriers) in SM clocks.
 // Build and run (from this folder): nvcc -std=c++17 -O3 -gencode arch=compute_103a,code=sm_103a -o exp_mix_rate exp_mix_rate.cu && ./exp_mix_rate
 #include <cstdio>
 #include <cuda_fp16.h>
@@ -33,11 +34,12 @@ __global__ void __launch_bounds__(512, 1) probe(int reps, uint32_t* sink, long l
     w[q] = 1.0f + 0.001f * q;
   }
   uint32_t acc = 0;
+  __syncthreads();
   const long long t0 = clock64();
   for (int r = 0; r < reps; ++r) {
 #pragma unroll
     for (int q = 0; q < 16; ++q) {
-      const float a = s[2 * q] + (float)r * 1e-9f, b = s[2 * q + 1];
+      const float a = s[2 * q] + (float)r * 1e-9f, b = s[2 * q + 1] - (float)r * 1e-9f;
       uint32_t v;
       if (MODE == 0) {
         v = __float_as_uint(ex2f(a)) ^ __float_as_uint(ex2f(b));
@@ -53,6 +55,7 @@ __global__ void __launch_bounds__(512, 1) probe(int reps, uint32_t* sink, long l
       acc += v;
     }
   }
+  __syncthreads();
   const long long t1 = clock64();
   if (acc == 0x12345678u) sink[threadIdx.x] = acc;
   if (blockIdx.x == 0 && threadIdx.x == 0) out[0] = t1 - t0;

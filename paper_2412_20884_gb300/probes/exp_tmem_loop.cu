@@ -58,6 +58,7 @@ __global__ void __launch_bounds__(NT, 1) probe(int reps, long long* out) {
     tmem_st32(tl + 96, v);
     tmem_st_wait();
   }
+  __syncthreads();
   const long long t0 = clock64();
   for (int r = 0; r < reps; ++r) {
     uint32_t s0[32], w0[32], s1[32], w1[32], qq[16];
@@ -81,6 +82,7 @@ __global__ void __launch_bounds__(NT, 1) probe(int reps, long long* out) {
     tmem_st16(tl + 16, qq);
     tmem_st_wait();
   }
+  __syncthreads();
   const long long t1 = clock64();
   if (blockIdx.x == 0 && threadIdx.x == 0) out[0] = t1 - t0;
   tc_fence_before(); __syncthreads(); tc_fence_after();

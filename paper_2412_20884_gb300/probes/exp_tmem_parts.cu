@@ -27,6 +27,7 @@ __global__ void __launch_bounds__(256, 1) probe(int reps, long long* out, uint32
   }
   uint32_t acc = 0;
   float facc = 0.f;
+  __syncthreads();
   const long long t0 = clock64();
   for (int r = 0; r < reps; ++r) {
     uint32_t s0[32], s1[32], qq[16];
@@ -68,6 +69,7 @@ __global__ void __launch_bounds__(256, 1) probe(int reps, long long* out, uint32
       }
     }
   }
+  __syncthreads();
   const long long t1 = clock64();
   if (acc == 0x1234567u || facc == 1.f) sink[threadIdx.x] = acc;
   if (blockIdx.x == 0 && threadIdx.x == 0) out[0] = t1 - t0;
