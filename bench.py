@@ -38,7 +38,7 @@ FMA_LANES = 128        # FP32 FMA lanes per SM per clock
 MUFU_EX2_LANES = 32    # ex2 per SM per clock on GB300 (measured by probes/ex2_ffma_rate.cu)
 # dram__bytes_read.sum + dram__bytes_write.sum per launch of the main loop, from an
 # ncu capture of the same workload; absent once the kernel changes after that capture.
-DRAM_TRAFFIC = {}
+DRAM_TRAFFIC = {("bf16_hilo", "fwd"): 10542080}
 
 
 def peaks():
