@@ -176,6 +176,11 @@ kmv_status kmv_cg_solve(kmv_handle h, const kmv_points* pts, int32_t chains,
  *                the solve failed (theta/pi then hold theta_h / the un-kicked pi;
  *                the caller must reject the trajectory).
  *   cg_iters     DEVICE int32 (n_inst * chains) or NULL.
+ * prec selects the operator of the solve (KMV_BF16_HILO: refined to the FP32
+ * residual, see kmv_cg_solve).  The force always uses the FP32 adjoint: its two
+ * quadratic forms are sums of N^2 terms that cancel to a small fraction of
+ * their size (x = A^-1 y oscillates), and the F16 rounding of the tensor-core
+ * adjoint leaves errors far above the force there.
  */
 kmv_status leapfrog_step(kmv_handle h, const kmv_points* pts, int32_t chains,
                          const float* y, const float* phi, double* theta, double* pi,
@@ -201,6 +206,34 @@ kmv_status kmv_energy(kmv_handle h, const kmv_points* pts, int32_t chains,
                       double cg_tol, int32_t cg_maxiter, float* x_work,
                       double* H, double* terms, int32_t* chain_status, int32_t* cg_iters,
                       kmv_precision prec, void* stream);
+
+/*
+ * kmv_phi_refresh - the Gibbs draw of the auxiliary variable of Sec. 3.1,
+ * phi = A(theta_s)^{-1/2} xi for every system s, by the pole expansion of
+ * App. A (Eq. pex):  phi = sum_p w_p (A + lambda_p I)^{-1} xi, p = 1..n_poles,
+ * with weights and shifts from Jacobi elliptic functions on the spectral
+ * interval [sigma_s^2, M_s], M_s = 1.01 max_i (A 1)_i (the largest row sum
+ * bounds lambda_max because K0 >= 0 entrywise; 1% covers rounding).  The
+ * n_poles shifted systems of every system are solved together by CG to cg_tol
+ * (as kmv_cg_solve, cold start; the BF16 form by iterative refinement).
+ *
+ *   xi          DEVICE FP32 (chains, N_total): the caller's N(0, I) draw.
+ *   phi         DEVICE FP32 (chains, N_total), written (must not alias xi).
+ *   n_poles     1..32 (Sec. 3.1 uses 15).
+ *   chain_status DEVICE int32 (n_inst * chains): KMV_OK, or the first failure
+ *               (KMV_ENOTCONV, KMV_ENONFINITE) among the system's shifted solves.
+ *   cg_iters    DEVICE int32 (n_inst * chains) or NULL: the largest iteration count.
+ *   poles_out   DEVICE FP64 (n_inst * chains, 2 + 2 n_poles) or NULL:
+ *               [sigma^2, M, w_1..w_Np, lambda_1..lambda_Np] per system.
+ * Work: one N^2 pass for A 1, then n_poles * chains systems per CG iteration
+ * (converged shifts drop out).  Allocates workspace; not for use while the
+ * stream is being captured (the work plan changes between the two phases).
+ */
+kmv_status kmv_phi_refresh(kmv_handle h, const kmv_points* pts, int32_t chains,
+                           const double* theta, const float* xi, float* phi,
+                           int32_t n_poles, double cg_tol, int32_t cg_maxiter,
+                           int32_t* chain_status, int32_t* cg_iters, double* poles_out,
+                           kmv_precision prec, void* stream);
 
 /*
  * Kernel timing.  Instrumentation for measuring the library on a device; the

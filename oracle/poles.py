@@ -18,13 +18,21 @@ Then A^{-1/2} xi ~ sum_j w_j (A + lambda_j I)^{-1} xi.
 m is a lower bound on the spectrum of A (the noise variance sigma^2; App. A
 prints min sigma, read as min sigma^2, since lambda_min(A) >= sigma^2).
 
-Parity status: pinned (scalar function against x^{-1/2}, and the matrix form
-against an exact eigendecomposition) - see tests/test_oracle_poles.py.
+Spectral interval (Sec. 3.1 / App. A): m = sigma^2; M = the largest row sum of
+A, max_i (A 1)_i = alpha max_i sum_j K0_ij + sigma^2.  Because K0 >= 0
+entrywise, the largest row sum (the infinity norm of A) bounds lambda_max from
+above, where the power iteration App. A mentions approaches it from below.
+
+Parity status: pinned (scalar function against x^{-1/2}, the matrix form
+against an exact eigendecomposition, the spectral interval against the
+eigenvalues) - see tests/test_oracle_poles_diag.py.
 """
 from __future__ import annotations
 
 import numpy as np
 from scipy.special import ellipj, ellipk
+
+from .se_kernel import A_matrix, unpack_theta
 
 
 def pole_weights_shifts(m_lo: float, M_hi: float, n_poles: int = 15):
@@ -50,3 +58,17 @@ def inv_sqrt_apply(A, xi, m_lo, M_hi, n_poles: int = 15):
     for wj, sj in zip(w, s):
         out += wj * np.linalg.solve(A + sj * np.eye(n), xi)
     return out
+
+
+def spectral_interval(X, theta, ard: bool):
+    """(m, M): sigma^2 and the largest row sum of A(theta)."""
+    A = A_matrix(X, theta, ard)
+    _, _, s2 = unpack_theta(theta, np.asarray(X).shape[1], ard)
+    return float(s2), float(np.max(A.sum(axis=1)))
+
+
+def phi_pole(X, theta, xi, ard: bool, n_poles: int = 15):
+    """The Gibbs draw of Sec. 3.1, phi = A^{-1/2} xi, by the pole expansion of
+    App. A on the interval of spectral_interval, with dense solves."""
+    m_lo, M_hi = spectral_interval(X, theta, ard)
+    return inv_sqrt_apply(A_matrix(X, theta, ard), xi, m_lo, M_hi, n_poles)

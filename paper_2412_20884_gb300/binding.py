@@ -52,6 +52,8 @@ _SIGS = {
     "kmv_energy": (C.c_int, [_P, C.POINTER(_Points), C.c_int32, _P, _P, _P, _P, _P, _P, C.c_double,
                              C.c_int32, _P, _P, _P, _P, _P, C.c_int, _P]),
     "kmv_backward_noalloc": (C.c_int, [C.POINTER(_Points), C.c_int32, _P, _P, _P, C.c_int32, _P, _P, _P]),
+    "kmv_phi_refresh": (C.c_int, [_P, C.POINTER(_Points), C.c_int32, _P, _P, _P, C.c_int32, C.c_double,
+                                  C.c_int32, _P, _P, _P, C.c_int, _P]),
     "kmv_profile_enable": (C.c_int, [_P, C.c_int32]),
     "kmv_profile_read": (C.c_int, [_P, C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
 }
@@ -236,6 +238,25 @@ class Kmv:
                                         _ptr(x), float(tol), int(maxiter), int(bool(warm_start)),
                                         _ptr(status), _ptr(iters), self._prec(prec), _stream(stream)))
         return x, status, iters
+
+    def phi_refresh(self, pts: Points, theta, xi, n_poles=15, cg_tol=1e-6, cg_maxiter=1000, phi=None,
+                    want_poles=False, prec="fp32", stream=None):
+        """phi = A^{-1/2} xi per system by the pole expansion (kmv_phi_refresh).
+        Returns (phi, status, iters[, poles (n_sys, 2 + 2 n_poles)])."""
+        chains = self._chains(pts, theta)
+        n_sys = pts.n_inst * chains
+        _need(theta, torch.float64, "theta", (n_sys, pts.n_theta))
+        _need(xi, torch.float32, "xi", (chains, pts.n_total))
+        if phi is None:
+            phi = torch.empty_like(xi)
+        _need(phi, torch.float32, "phi", (chains, pts.n_total))
+        status = torch.empty(n_sys, dtype=torch.int32, device=xi.device)
+        iters = torch.empty_like(status)
+        poles = torch.empty((n_sys, 2 + 2 * n_poles), dtype=torch.float64, device=xi.device) if want_poles else None
+        self._check(self.L.kmv_phi_refresh(self.h, pts.c, chains, _ptr(theta), _ptr(xi), _ptr(phi), int(n_poles),
+                                           float(cg_tol), int(cg_maxiter), _ptr(status), _ptr(iters), _ptr(poles),
+                                           self._prec(prec), _stream(stream)))
+        return (phi, status, iters, poles) if want_poles else (phi, status, iters)
 
     def leapfrog_step(self, pts: Points, y, phi, theta, pi, dt, prior=None, free_mask=None,
                       cg_tol=1e-6, cg_maxiter=1000, x_work=None, prec="fp32", stream=None):

@@ -31,6 +31,8 @@ kmv_status fail(kmv_handle h, kmv_status s, const std::string& msg) {
   } while (0)
 
 // Bump allocator over the handle workspace; 256-byte aligned regions.
+constexpr int kMaxPoles = 32;
+
 struct Arena {
   size_t used = 0;
   size_t take(size_t bytes) {
@@ -549,6 +551,69 @@ kmv_status kmv_cg_solve(kmv_handle h, const kmv_points* pts, int32_t chains, con
   return run_solve(h, pts, theta, rhs, stride, x, tol, maxiter, warm_start, chain_status, iters, SL, prec, st);
 }
 
+kmv_status kmv_phi_refresh(kmv_handle h, const kmv_points* pts, int32_t chains, const double* theta,
+                           const float* xi, float* phi, int32_t n_poles, double cg_tol, int32_t cg_maxiter,
+                           int32_t* chain_status, int32_t* cg_iters, double* poles_out, kmv_precision prec,
+                           void* stream) {
+  KMV_TRY(check_points(h, pts, chains));
+  KMV_TRY(check_prec(h, prec));
+  if (!theta || !xi || !phi || !chain_status) return fail(h, KMV_EINVAL, "NULL argument");
+  if (n_poles < 1 || n_poles > kMaxPoles) return fail(h, KMV_EINVAL, "n_poles must be in [1, 32]");
+  if ((int64_t)chains * n_poles > (int64_t)1 << 20) return fail(h, KMV_EINVAL, "chains * n_poles too large");
+  if (!(cg_tol > 0.0) || cg_maxiter < 1) return fail(h, KMV_EINVAL, "cg_tol must be > 0 and cg_maxiter >= 1");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int cp = chains * n_poles;
+  // size everything with the layout of the shifted systems (system s p = s N_p + p)
+  KMV_TRY(prepare_layout(h, pts, cp, st));
+  const int n_theta = h->layout.n_theta, n_items = h->layout.n_items;
+  const int64_t n_total = h->layout.n_total;
+  const int n_sys = h->layout.n_inst * chains, n_sysp = n_sys * n_poles;
+  Arena ar;
+  SolveLayout SL;
+  solve_layout(h->layout, ar, prec, SL);
+  const size_t vecp = sizeof(float) * (size_t)cp * std::max<int64_t>(1, n_total);
+  const size_t vec1 = sizeof(float) * (size_t)chains * std::max<int64_t>(1, n_total);
+  const size_t o_rhs = ar.take(vecp), o_x = ar.take(vecp);
+  const size_t o_thp = ar.take(sizeof(double) * (size_t)n_sysp * n_theta);
+  const size_t o_w = ar.take(sizeof(double) * (size_t)n_sysp);
+  const size_t o_bnd = ar.take(sizeof(double) * (size_t)n_sys);
+  const size_t o_stp = ar.take(sizeof(int32_t) * (size_t)n_sysp), o_itp = ar.take(sizeof(int32_t) * (size_t)n_sysp);
+  const size_t o_one = ar.take(vec1), o_y = ar.take(vec1);
+  KMV_TRY(reserve(h, ar.used));
+  char* base = static_cast<char*>(h->ws);
+  float* rhs_p = reinterpret_cast<float*>(base + o_rhs);
+  float* x_p = reinterpret_cast<float*>(base + o_x);
+  double* theta_p = reinterpret_cast<double*>(base + o_thp);
+  double* weights = reinterpret_cast<double*>(base + o_w);
+  double* bounds = reinterpret_cast<double*>(base + o_bnd);
+  int32_t* st_p = reinterpret_cast<int32_t*>(base + o_stp);
+  int32_t* it_p = reinterpret_cast<int32_t*>(base + o_itp);
+  float* ones = reinterpret_cast<float*>(base + o_one);
+  float* y1 = reinterpret_cast<float*>(base + o_y);
+
+  // spectral interval [sigma^2, max row sum of A] from A 1 (App. A, read with the
+  // exact row-sum bound); 1% slack covers the rounding of the product
+  KMV_TRY(prepare_layout(h, pts, chains, st));
+  KMV_CUDA(h, launch_phi_fill(ones, (int64_t)chains * n_total, 1.0f, st));
+  {
+    KmvArgs a = base_args(h, pts, theta);
+    a.m = 1;
+    a.V = ones;
+    a.Y = y1;
+    KMV_TRY(run_forward(h, a, prec, st));
+  }
+  KMV_CUDA(h, launch_phi_bounds(h->dev, n_sys, chains, n_total, y1, 1.01, bounds, st));
+  KMV_CUDA(h, launch_phi_poles(n_sys, n_theta, n_poles, theta, bounds, theta_p, weights, poles_out, st));
+  KMV_CUDA(h, launch_phi_rhs(h->dev, n_items, chains, n_poles, n_total, xi, rhs_p, st));
+  // the N_p shifted systems of every (instance, chain) in one batched solve
+  KMV_TRY(prepare_layout(h, pts, cp, st));
+  KMV_TRY(run_solve(h, pts, theta_p, rhs_p, n_total, x_p, cg_tol, cg_maxiter, 0, st_p, it_p, SL, prec, st));
+  KMV_TRY(prepare_layout(h, pts, chains, st));
+  KMV_CUDA(h, launch_phi_combine(h->dev, n_items, chains, n_poles, n_total, weights, x_p, phi, st));
+  KMV_CUDA(h, launch_phi_status(n_sys, n_poles, st_p, it_p, chain_status, cg_iters, st));
+  return KMV_OK;
+}
+
 kmv_status leapfrog_step(kmv_handle h, const kmv_points* pts, int32_t chains, const float* y,
                          const float* phi, double* theta, double* pi, double dt,
                          const double* prior_mu, const double* prior_prec, const uint8_t* free_mask,
@@ -590,7 +655,10 @@ kmv_status leapfrog_step(kmv_handle h, const kmv_points* pts, int32_t chains, co
   a.G = Gf;
   a.m = 2;
   a.Y = nullptr;
-  KMV_TRY(run_backward(h, a, grad, at<double>(h, o_bp), prec, st));
+  // The two quadratic forms cancel to a small fraction of their size, below
+  // the F16 rounding of the tensor-core adjoint: the force is always FP32 (one
+  // N^2 pass per step, small next to the solve).
+  KMV_TRY(run_backward(h, a, grad, at<double>(h, o_bp), KMV_FP32, st));
   // kick + drift
   KMV_CUDA(h, launch_lf_kick_drift(n_sys, L.n_theta, theta_h, grad, prior_mu, prior_prec, free_mask,
                                    chain_status, dt, theta, pi, st));

@@ -112,6 +112,20 @@ cudaError_t launch_refine_stagnation(int n_sys, int outer, const CgSys* sys, dou
                                      int32_t* n_active, double* worst, cudaStream_t st);
 cudaError_t launch_refine_finish(int n_sys, const int32_t* active, const CgSys* sys, int32_t* status,
                                  cudaStream_t st);
+// phi refresh (kmv_phi.cu): spectral interval, pole weights/shifts, replicated
+// right-hand sides, weighted sum of the shifted solutions, per-system status
+cudaError_t launch_phi_fill(float* v, int64_t n, float val, cudaStream_t st);
+cudaError_t launch_phi_bounds(DevLayout L, int n_sys, int chains, int64_t n_total, const float* Y, double slack,
+                              double* bounds, cudaStream_t st);
+cudaError_t launch_phi_poles(int n_sys, int n_theta, int n_poles, const double* theta, const double* bounds,
+                             double* theta_p, double* weights, double* poles_out, cudaStream_t st);
+cudaError_t launch_phi_rhs(DevLayout L, int n_items, int chains, int n_poles, int64_t n_total, const float* xi,
+                           float* rhs_p, cudaStream_t st);
+cudaError_t launch_phi_combine(DevLayout L, int n_items, int chains, int n_poles, int64_t n_total,
+                               const double* weights, const float* x_p, float* phi, cudaStream_t st);
+cudaError_t launch_phi_status(int n_sys, int n_poles, const int32_t* st_p, const int32_t* it_p, int32_t* status,
+                              int32_t* iters, cudaStream_t st);
+
 
 cudaError_t launch_lf_drift(int n_sys, int n_theta, const double* theta, const double* pi,
                             const uint8_t* mask, double half_dt, double* theta_h, cudaStream_t st);

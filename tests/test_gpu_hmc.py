@@ -161,3 +161,30 @@ def test_energy_error_is_second_order_in_dt(kmv_handle):
         assert abs((H1 - H0) - dH_ref) <= 1e-2 * abs(dH_ref) + 1e-3 * abs(H0_ref) * 1e-3
         errs.append(abs(H1 - H0))
     assert 3.2 < errs[0] / errs[1] < 5.0, errs
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16_hilo"])
+def test_leapfrog_force_with_cancelling_quadratic_forms(kmv_handle, prec):
+    """On c1 (N = 2048, sigma^2 = 0.01) x = A^-1 y oscillates and the two
+    quadratic forms of the force are sums of N^2 terms that cancel to ~1e-7 of
+    their size.  Both forms must still give the oracle's step: the force is the
+    FP32 adjoint in either precision (the solve is refined in the BF16 form)."""
+    w = wl.c1()
+    pts, theta, _, _ = to_dev(w)
+    X, yh = f32(w.X), f32(w.y)
+    xi = np.random.default_rng(5).standard_normal(w.n_total)
+    phi = f32(ohmc.phi_exact(X, w.theta[0], xi, w.ard))
+    pi0 = np.array([[0.1, -0.2, 0.05]])
+    dt = 0.01
+    th = theta.clone()
+    pi = torch.tensor(pi0, dtype=torch.float64, device="cuda")
+    y = torch.tensor(w.y, dtype=torch.float32, device="cuda")
+    st, _, _ = kmv_handle.leapfrog_step(pts, y, torch.tensor(phi[None].astype(np.float32), device="cuda"), th, pi, dt,
+                                        cg_tol=1e-7, cg_maxiter=5000, prec=prec)
+    assert torch.all(st == 0)
+    t_o, p_o = ohmc.leapfrog(X, yh, phi, w.theta[0], pi0[0], dt, w.ard)
+    F_scale = np.abs(ohmc.force(X, yh, phi, w.theta[0], w.ard)).max()
+    # FP32 rounding of sums that cancel this strongly leaves ~1e-3 of the force
+    tol_F = 2e-3 * max(F_scale, 1.0)
+    np.testing.assert_allclose(pi.cpu().numpy()[0], p_o, atol=dt * tol_F, rtol=0)
+    np.testing.assert_allclose(th.cpu().numpy()[0], t_o, atol=0.5 * dt ** 2 * tol_F + 1e-12, rtol=0)

@@ -85,3 +85,43 @@ def test_marginal_cdf_of_gaussian_grid():
     c1 = dg.marginal_cdf_grid(logp, g, 1)
     np.testing.assert_allclose(c0, norm.cdf(g, 0.5, 0.8), atol=2e-4)
     np.testing.assert_allclose(c1, norm.cdf(g, -1.0, 1.5), atol=2e-4)
+
+
+@pytest.mark.parametrize("ard", [False, True])
+def test_spectral_interval_contains_the_spectrum(ard):
+    # App. A needs [m, M] to contain every eigenvalue of A: m = sigma^2 <= lambda_min,
+    # M = max row sum >= lambda_max (K0 >= 0 entrywise), with M - lambda_max small
+    # for a smooth kernel on clustered points
+    w = wl.ragged([240], d=3, chains=1, m=1, ard=ard, seed=41)
+    A = sk.A_matrix(w.X, w.theta[0], ard)
+    lam = np.linalg.eigvalsh(A)
+    m_lo, M_hi = poles.spectral_interval(w.X, w.theta[0], ard)
+    assert m_lo == pytest.approx(math.exp(w.theta[0][-1]), rel=1e-15)
+    assert m_lo <= lam[0] * (1 + 1e-12)
+    assert lam[-1] <= M_hi * (1 + 1e-12)
+    # for the all-equal-points limit (rank-one K0) the row sum is the top eigenvalue exactly
+    X1 = np.zeros((16, 2))
+    th = np.array([math.log(2.0), math.log(0.5), math.log(0.1)])
+    m1, M1 = poles.spectral_interval(X1, th, False)
+    assert M1 == pytest.approx(2.0 * 16 + 0.1, rel=1e-14)
+    assert np.linalg.eigvalsh(sk.A_matrix(X1, th, False))[-1] == pytest.approx(M1, rel=1e-12)
+
+
+def test_phi_pole_matches_inverse_square_root():
+    # the pole-expansion draw equals A^{-1/2} xi within the scalar error of the
+    # expansion on [m, M] (App. A) times |xi|
+    w = wl.ragged([200], d=2, chains=1, m=1, ard=True, seed=43)
+    xi = np.random.default_rng(7).standard_normal(200)
+    m_lo, M_hi = poles.spectral_interval(w.X, w.theta[0], True)
+    for npl in (8, 15):
+        phi = poles.phi_pole(w.X, w.theta[0], xi, True, npl)
+        exact = sk_hmc_phi(w, xi)
+        wts, sh = poles.pole_weights_shifts(m_lo, M_hi, npl)
+        lam = np.geomspace(m_lo, M_hi, 4001)
+        scal = np.abs(poles.inv_sqrt_scalar(lam, wts, sh) - lam ** -0.5).max()
+        assert np.linalg.norm(phi - exact) <= 1.01 * scal * np.linalg.norm(xi) + 1e-10
+
+
+def sk_hmc_phi(w, xi):
+    from oracle import hmc
+    return hmc.phi_exact(w.X, w.theta[0], xi, True)
