@@ -1019,7 +1019,7 @@ kmv_status tc_forward(kmv_handle h, const KmvArgs& a, cudaStream_t st) {
   int mz_max = std::min(a.m, kMaxMP);
   auto stages_for = [&](int mz) {
     const size_t vt = (size_t)std::max(16, (mz + 15) / 16 * 16) * 256;
-    return (int)std::min<size_t>(8, (kMaxSmem - fixed) / (A_TILE + vt + 16));
+    return (int)std::min<size_t>(8, (kMaxSmem - fixed - 20 * 8) / (A_TILE + vt + 16));
   };
   while (stages_for(mz_max) < 2 && mz_max > 16) mz_max = std::max(16, mz_max / 2);
   if (stages_for(mz_max) < 2) return tc_fail(h, KMV_EUNSUPPORTED, "tensor-core tiles do not fit in shared memory");

@@ -221,3 +221,14 @@ def test_kernel_timing(kmv_handle, prec):
         h.profile_enable(False)
     h.kmv_forward(pts, theta, V, prec=prec)
     assert h.profile_read(KMV_KERNEL_FORWARD) == (0.0, 0)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("m", [1, 16])
+def test_many_tiles_per_cta(kmv_handle, prec, m):
+    """Enough tiles that every persistent CTA runs several work items of
+    several J tiles each (the small cases give one tile per CTA), so the
+    phase bookkeeping of the pipelines is exercised over many rounds."""
+    w = wl.ragged([6000, 2192], d=4, chains=1, m=m, ard=True, seed=61)
+    _check_forward(kmv_handle, w, prec)
+    _check_backward(kmv_handle, w, prec)
