@@ -233,9 +233,13 @@ def main():
     ap.add_argument("--cpu-rows", type=int, default=512, help="rows of the oracle sample for cpu_baseline")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-leapfrog", action="store_true")
+    ap.add_argument("--suite", default=None, choices=["c3c4"],
+                    help="instead of the headline line: time the C3 products and the C4 leapfrog batch")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.suite == "c3c4":
+        return run_suite_c3c4(args)
 
     import torch
     import torch.distributed as dist
@@ -503,6 +507,109 @@ def leapfrog_rates(h, dev, rank, world):
                     r[prec]["graph_unavailable"] = str(e)[:200]
         res["c1" if w.n_total == 2048 else "c5_n16384"] = r
     return res
+
+
+def run_suite_c3c4(args):
+    """Secondary configurations (one GPU, one JSON line):
+    C3  N = 262,144, d = 32, ARD, m = 64: forward and backward times of both forms
+        (the tensor-core adjoint covers d <= 15, so the BF16 backward here is the
+        FP32 adjoint; the BF16 forward is the tensor-core kernel);
+    C4  256 instances of 1e3..2e4 points, d = 4, 4 chains (1024 systems): leapfrog
+        steps/s over the whole batch for both forms, eager and as a CUDA graph of
+        the same steps (a fixed number of masked CG iterations per solve)."""
+    import torch
+    import workloads as wl
+    from paper_2412_20884_gb300 import Kmv, Points
+    dev = torch.device("cuda", 0)
+    h = Kmv(0)
+    out = {"suite": "c3c4", "data": "synthetic"}
+
+    def timed(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    w = wl.c3()
+    pts = Points(torch.tensor(w.X, dtype=torch.float32, device=dev), w.offsets, ard=True)
+    th = torch.tensor(w.theta, dtype=torch.float64, device=dev)
+    V = torch.tensor(w.V, dtype=torch.float32, device=dev)
+    G = torch.tensor(w.G, dtype=torch.float32, device=dev)
+    n = w.n_total
+    c3 = {"workload": "N=262144 d=32 x~U[-1,1], ARD l~logU[0.5,5], m=64"}
+    for prec in ("bf16_hilo", "fp32"):
+        fm = timed(lambda: h.kmv_forward(pts, th, V, prec=prec), 2)
+        bm = timed(lambda: h.kmv_backward(pts, th, V, G, prec=prec), 1)
+        c3[prec] = {"fwd_ms": fm, "bwd_ms": bm, "fwd_gpair_s": n * n / fm / 1e6, "bwd_gpair_s": n * n / bm / 1e6}
+    c3["fwd_bf16_over_fp32"] = c3["fp32"]["fwd_ms"] / c3["bf16_hilo"]["fwd_ms"]
+    out["c3"] = c3
+    del pts, V, G
+
+    w = wl.c4()
+    pts = Points(torch.tensor(w.X, dtype=torch.float32, device=dev), w.offsets, ard=True)
+    th0 = torch.tensor(w.theta, dtype=torch.float64, device=dev)
+    y = torch.tensor(w.y, dtype=torch.float32, device=dev)
+    xi = torch.tensor(np.random.default_rng(5).standard_normal((w.chains, w.n_total)), dtype=torch.float32,
+                      device=dev)
+    pairs = float(np.sum(np.diff(w.offsets).astype(np.float64) ** 2) * w.chains)
+    c4 = {"workload": f"{w.n_inst} instances N_b~logU[1e3,2e4] (total {w.n_total}), d=4, 4 chains, "
+                      f"dt=0.01, cg_tol=1e-6", "pairs_per_sweep": pairs}
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    phi, st, its = h.phi_refresh(pts, th0, xi, n_poles=15, cg_tol=1e-6, cg_maxiter=5000, prec="bf16_hilo")
+    torch.cuda.synchronize()
+    c4["phi_refresh"] = {"prec": "bf16_hilo", "s": time.perf_counter() - t0, "max_cg_iters": int(its.max()),
+                         "ok_fraction": float((st == 0).float().mean())}
+    pi0 = torch.tensor(0.1 * np.random.default_rng(6).standard_normal(w.theta.shape), dtype=torch.float64,
+                       device=dev)
+    steps, dt, graph_cg = 2, 0.01, 400
+    for prec in ("bf16_hilo", "fp32"):
+        th, pi = th0.clone(), pi0.clone()
+        xw = torch.empty_like(phi)
+        h.leapfrog_step(pts, y, phi, th.clone(), pi.clone(), dt, cg_maxiter=5000, x_work=xw, prec=prec)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        its = []
+        for _ in range(steps):
+            st, it, _ = h.leapfrog_step(pts, y, phi, th, pi, dt, cg_maxiter=5000, x_work=xw, prec=prec)
+            its.append(it.float().mean().item())
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        r = {"steps_per_s": steps / el, "mean_cg_iters": float(np.mean(its)), "ok": bool((st == 0).all())}
+        try:
+            th_g, pi_g = th0.clone(), pi0.clone()
+            side = torch.cuda.Stream()
+            side.wait_stream(torch.cuda.current_stream())
+            with torch.cuda.stream(side):
+                h.leapfrog_step(pts, y, phi, th0.clone(), pi0.clone(), dt, cg_maxiter=graph_cg, x_work=xw, prec=prec)
+            torch.cuda.current_stream().wait_stream(side)
+            torch.cuda.synchronize()
+            graph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(graph):
+                for _ in range(steps):
+                    h.leapfrog_step(pts, y, phi, th_g, pi_g, dt, cg_maxiter=graph_cg, x_work=xw, prec=prec)
+            th_g.copy_(th0)
+            pi_g.copy_(pi0)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            graph.replay()
+            torch.cuda.synchronize()
+            r["graph_steps_per_s"] = steps / (time.perf_counter() - t0)
+            r["graph_theta_maxdiff_vs_eager"] = float((th_g - th).abs().max())
+            r["graph_cg_iterations_per_solve"] = graph_cg
+        except Exception as e:  # capture needs a CUDA-graph capable torch build
+            r["graph_unavailable"] = str(e)[:200]
+        c4[prec] = r
+    c4["bf16_over_fp32_speed"] = c4["bf16_hilo"]["steps_per_s"] / c4["fp32"]["steps_per_s"]
+    out["c4"] = c4
+    print(json.dumps(out))
+    h.close()
+    return 0
 
 
 if __name__ == "__main__":
