@@ -29,6 +29,7 @@
 #include <cuda_fp16.h>
 
 #include <algorithm>
+#include <climits>
 #include <cmath>
 
 #include "kmv_tc.cuh"
@@ -40,7 +41,7 @@ namespace kmv {
 namespace {
 
 constexpr int kFoldH = 64;   // half tiles (64 columns) per FP32 accumulation (4096 columns)
-constexpr int kGW = 16;      // doubles per (item, warp) gradient partial: [q, contrib_0..d-1]
+constexpr int kGW = 34;      // doubles per (item, warp) gradient partial: [q, contrib_0..d-1]
 
 struct TcBwdArgs {
   const int4* items;
@@ -49,7 +50,7 @@ struct TcBwdArgs {
   int T_total;
   int KX, KG, NB, S;
   int qcol;   // accumulator column of q_i (the ones column of BG)
-  int sym;    // 1: upper-triangle items (one I tile each) with the symmetrised W; 0: I-pair items
+  int chunk;  // index of this launch's block of G, V columns (partials are per block)
   int d, n_theta, ard;
   DevLayout L;
   TcTables T;
@@ -60,7 +61,7 @@ struct TcBwdArgs {
   const uint8_t* GI;
   const uint8_t* VJ;
   const uint8_t* BG;
-  double* gpart;   // (n_items, 8 warps, kGW)
+  double* gpart;   // (column blocks, n_items, 4 warps, kGW)
   int m;
   const int32_t* sys_active;
   int* err;
@@ -91,27 +92,27 @@ __device__ __forceinline__ void issue_ts4(uint32_t d_tmem, uint32_t a_tmem, uint
 
 constexpr int kBwdIssue1Warp = 10;
 
-// The I-side operands are resident in TMEM, one I tile at a time.  S and W
-// are A-from-TMEM MMAs that read only the 64-row J half from shared
-// memory (with A in shared memory a 128-row A tile is read for every K step,
-// which caps an N = 64 MMA at the shared-memory read rate).  The two exp
-// warpgroups share the I tile: warpgroup b takes J columns [64 b, 64 b + 64)
-// of every J tile, in its own S, W buffer, so the MMAs of one warpgroup's next
-// half run while the other warpgroup computes.  Warps: 0-7 the warpgroups,
-// 8 issues S, W for buffer 0 (and owns TMEM), 9 is the producer, 10 issues
-// S, W for buffer 1, 11 issues the feature sums.  TMEM (512 columns):
+// One I tile at a time over the upper triangle of tiles.  S and W are MMAs on
+// 64-column J halves; warpgroup b takes J columns [64 b, 64 b + 64) of every J
+// tile, in its own S, W buffer, so the MMAs of one warpgroup's next half run
+// while the other warpgroup computes.  The I tile's GI rows are resident in
+// TMEM and its XA rows too when they fit (XS = false): A-from-TMEM MMAs read
+// only the 64-row J half from shared memory.  Otherwise (XS, large d) XA is a
+// shared-memory tile loaded once per item.  Warps: 0-7 the warpgroups, 8 issues
+// S, W for buffer 0 (and owns TMEM), 9 is the producer, 10 issues S, W for
+// buffer 1, 11 issues the feature sums.  TMEM (512 columns):
 //   S_b [128 b, 128 b + 64), W_b [128 b + 64, 128 b + 128), Q_b [256 + 32 b, +32),
-//   XA [320, 320 + KX/2), GI [320 + KX/2, + KG/2), ACC [512 - NB, 512);
-// the host selects this form while KX/2 + KG/2 + NB <= 192.  Warpgroup 0 also
-// folds the accumulator into the per-row FP64 sums.  A work item's two I tiles
-// are processed one after the other ("sub-items").
+//   XA [320, 320 + KX/2) unless XS, GI after it, ACC [512 - NB, 512);
+// the host picks XS and the number of columns of G, V per launch so that these
+// fit.  Warpgroup 0 folds the accumulator into FP64 per-warp sums.
 constexpr int kTsThreads = 384;
 constexpr int kAccWarp = 11;
 constexpr int kTsCols = 192;   // columns for XA, GI and ACC
-constexpr int kMaxDT = 15;     // 4 d features + q in at most 64 accumulator columns
-constexpr int kTsBarBytes = 512;                           // mbarriers, TMEM slot, abort flag
-constexpr int kTsRowBytes = kMaxDT * 128 * (4 + 8);        // x~ and FP64 fold sums per row
+constexpr int kMaxDT = 32;     // 4 d features + q in at most 144 accumulator columns
+constexpr int kTsBarBytes = 512;                       // mbarriers, TMEM slot, abort flag
+constexpr int kTsFoldBytes = 4 * kGW * 8;              // per-warp FP64 fold sums of warpgroup 0
 
+template <bool XS>
 __global__ void __launch_bounds__(kTsThreads, 1) tc_bwd_ts_kernel(TcBwdArgs a) {
   using namespace ptx;
   extern __shared__ uint8_t smem_raw[];
@@ -119,11 +120,12 @@ __global__ void __launch_bounds__(kTsThreads, 1) tc_bwd_ts_kernel(TcBwdArgs a) {
   const uint32_t XT = a.KX * 256u, GT = a.KG * 256u, BT = a.NB * 256u;
   const uint32_t STG = XT + GT + BT;   // one stage: XB, VJ, BG of a J tile
   const int S = a.S;
-  uint8_t* sS = smem;
+  uint8_t* sXA = smem;                 // XS: the item's XA tile
+  uint8_t* sS = smem + (XS ? ((XT + 1023u) & ~1023u) : 0u);
   uint64_t* full = reinterpret_cast<uint64_t*>(sS + S * STG);
   uint64_t* empty = full + S;
-  uint64_t* a_ready = empty + S;     // XA, GI of the sub-item stored in TMEM (256 arrivals)
-  uint64_t* seg = a_ready + 1;       // both warpgroups finished the previous sub-item (256)
+  uint64_t* a_ready = empty + S;     // GI (and XA) of the item stored in TMEM (256 arrivals)
+  uint64_t* seg = a_ready + 1;       // both warpgroups finished the previous item (256)
   uint64_t* s_full = seg + 1;        // [b] S_b, W_b written
   uint64_t* s_free = s_full + 2;     // [b] S_b, W_b loaded into registers
   uint64_t* q_ready = s_free + 2;    // [b] Q_b written
@@ -131,14 +133,13 @@ __global__ void __launch_bounds__(kTsThreads, 1) tc_bwd_ts_kernel(TcBwdArgs a) {
   uint64_t* o_ready = q_free + 2;    // accumulator of a fold complete
   uint64_t* o_free = o_ready + 1;    // accumulator read
   uint64_t* done = o_free + 1;       // [issuer], 3
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(done + 3);
+  uint64_t* xa_full = done + 3;      // XS: XA tile landed
+  uint64_t* xa_empty = xa_full + 1;  // XS: both S issuers done with it (2 arrivals)
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(xa_empty + 1);
   volatile int* abort = reinterpret_cast<volatile int*>(tslot + 1);
-  // per-row x~ and FP64 fold sums of warpgroup 0, [k][row]: kept out of registers,
-  // which the exp loop needs for a whole half tile of S and W
-  float* sxt = reinterpret_cast<float*>(reinterpret_cast<uint8_t*>(full) + kTsBarBytes);
-  double* sdacc = reinterpret_cast<double*>(sxt + kMaxDT * 128);
-  const uint32_t colA = 320, colG = 320 + a.KX / 2, colACC = 512 - a.NB;
-  const int nsub = a.sym ? 1 : 2;   // I tiles per work item
+  // FP64 fold sums of warpgroup 0, [warp][q, contrib_0 .. contrib_{d-1}]
+  double* wpart = reinterpret_cast<double*>(reinterpret_cast<uint8_t*>(full) + kTsBarBytes);
+  const uint32_t colA = 320, colG = XS ? 320 : 320 + a.KX / 2, colACC = 512 - a.NB;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
@@ -157,6 +158,8 @@ __global__ void __launch_bounds__(kTsThreads, 1) tc_bwd_ts_kernel(TcBwdArgs a) {
     mbar_init(o_ready, 1);
     mbar_init(o_free, 128);
     for (int i = 0; i < 3; ++i) mbar_init(&done[i], 1);
+    mbar_init(xa_full, 1);
+    mbar_init(xa_empty, 2);
     *abort = 0;
     fence_barrier_init();
   }
@@ -176,28 +179,35 @@ __global__ void __launch_bounds__(kTsThreads, 1) tc_bwd_ts_kernel(TcBwdArgs a) {
   if (warp == kLoadWarp) {
     const bool leader = elect_one();
     // ------------------------------------------------------------ producer
-    int n_issued = 0;
+    int n_issued = 0, n_xa = 0;
     uint32_t stage = 0, sph = 0;
     bool aborted = false;
     for (int t = blockIdx.x; t < a.n_items && !aborted; t += gridDim.x) {
       const int4 item = a.items[t];
       if (a.sys_active && !a.sys_active[item.x]) continue;
       const int c = item.x % a.chains;
-      for (int g = 0; g < nsub && !aborted; ++g) {
-        for (int j = 0; j < item.w; ++j) {
-          if (!warp_wait(&empty[stage], sph ^ 1, abort, a.err, 22)) { aborted = true; break; }
-          if (leader) {
-            mbar_arrive_expect_tx(&full[stage], STG);
-            const size_t tj = (size_t)c * a.T_total + item.z + j;
-            uint8_t* sd = sS + stage * STG;
-            bulk_g2s(sd, a.XB + tj * XT, XT, &full[stage]);
-            bulk_g2s(sd + XT, a.VJ + tj * GT, GT, &full[stage]);
-            bulk_g2s(sd + XT + GT, a.BG + tj * BT, BT, &full[stage]);
-          }
-          __syncwarp();
-          ++n_issued;
-          if (++stage == (uint32_t)S) { stage = 0; sph ^= 1; }
+      if (XS) {
+        if (!warp_wait(xa_empty, (uint32_t)(n_xa & 1) ^ 1u, abort, a.err, 33)) { aborted = true; break; }
+        if (leader) {
+          mbar_arrive_expect_tx(xa_full, XT);
+          bulk_g2s(sXA, a.XA + ((size_t)c * a.T_total + item.y) * XT, XT, xa_full);
         }
+        __syncwarp();
+        ++n_xa;
+      }
+      for (int j = 0; j < item.w; ++j) {
+        if (!warp_wait(&empty[stage], sph ^ 1, abort, a.err, 22)) { aborted = true; break; }
+        if (leader) {
+          mbar_arrive_expect_tx(&full[stage], STG);
+          const size_t tj = (size_t)c * a.T_total + item.z + j;
+          uint8_t* sd = sS + stage * STG;
+          bulk_g2s(sd, a.XB + tj * XT, XT, &full[stage]);
+          bulk_g2s(sd + XT, a.VJ + tj * GT, GT, &full[stage]);
+          bulk_g2s(sd + XT + GT, a.BG + tj * BT, BT, &full[stage]);
+        }
+        __syncwarp();
+        ++n_issued;
+        if (++stage == (uint32_t)S) { stage = 0; sph ^= 1; }
       }
     }
     if (aborted) {
@@ -205,6 +215,7 @@ __global__ void __launch_bounds__(kTsThreads, 1) tc_bwd_ts_kernel(TcBwdArgs a) {
         const int idx = n_issued - k;
         mbar_drain(&full[idx % S], (idx / S) & 1, 500000000ull);
       }
+      if (XS && n_xa > 0) mbar_drain(xa_full, (uint32_t)(n_xa - 1) & 1u, 500000000ull);
     }
   } else if (warp == kMmaWarp || warp == kBwdIssue1Warp) {
     // ------------------------------------------------------------ S, W issuer of buffer b
@@ -212,36 +223,47 @@ __global__ void __launch_bounds__(kTsThreads, 1) tc_bwd_ts_kernel(TcBwdArgs a) {
     const int b = warp == kMmaWarp ? 0 : 1;
     const uint32_t idSW = idesc_f16(128, 64, 1, 1);
     const int nkx = a.KX / 16, nkg = a.KG / 16;
+    const uint64_t dXA = sdesc(smem_u32(sXA), 128, a.KX * 16u);
     const uint64_t dXB = sdesc(smem_u32(sS + b * a.KX * 128u), 128, a.KX * 16u);
     const uint64_t dVJ = sdesc(smem_u32(sS + XT + b * a.KG * 128u), 128, a.KG * 16u);
     const uint32_t tS = tbase + 128 * b, tA = tbase + colA, tG = tbase + colG;
     int u = 0, uses = 0;
     uint32_t stage = 0, sph = 0;
-    for (int t = blockIdx.x; t < a.n_items; t += gridDim.x) {
+    for (int t = blockIdx.x; t < a.n_items; t += gridDim.x, ++u) {
       const int4 item = a.items[t];
-      if (a.sys_active && !a.sys_active[item.x]) continue;
-      for (int g = 0; g < nsub; ++g, ++u) {
-        if (!warp_wait(a_ready, (uint32_t)u & 1u, abort, a.err, 31)) goto sw_out;
-        for (int j = 0; j < item.w; ++j) {
-          if (uses > 0 && !warp_wait(&s_free[b], (uint32_t)(uses - 1) & 1u, abort, a.err, 23)) goto sw_out;
-          if (!warp_wait(&full[stage], sph, abort, a.err, 25)) goto sw_out;
-          tc_fence_after();
-          // operands computed by the whole warp (warp-uniform), issued by the leader
-          const uint64_t db = sdesc_add(dXB, stage * STG);
-          const uint64_t dv = sdesc_add(dVJ, stage * STG);
-          if (leader) {
+      if (a.sys_active && !a.sys_active[item.x]) {
+        --u;
+        continue;
+      }
+      if (!warp_wait(a_ready, (uint32_t)u & 1u, abort, a.err, 31)) goto sw_out;
+      if (XS && !warp_wait(xa_full, (uint32_t)u & 1u, abort, a.err, 34)) goto sw_out;
+      for (int j = 0; j < item.w; ++j) {
+        if (uses > 0 && !warp_wait(&s_free[b], (uint32_t)(uses - 1) & 1u, abort, a.err, 23)) goto sw_out;
+        if (!warp_wait(&full[stage], sph, abort, a.err, 25)) goto sw_out;
+        tc_fence_after();
+        // operands computed by the whole warp (warp-uniform), issued by the leader
+        const uint64_t db = sdesc_add(dXB, stage * STG);
+        const uint64_t dv = sdesc_add(dVJ, stage * STG);
+        if (leader) {
 #pragma unroll
-            for (int q = 0; q < kMaxKX / 16; ++q)
-              if (q < nkx) mma_ts(tS, tA + 8 * q, db + 16 * q, idSW, q > 0);
-#pragma unroll
-            for (int q = 0; q < 2 * kTsCols / 16; ++q)
-              if (q < nkg) mma_ts(tS + 64, tG + 8 * q, dv + 16 * q, idSW, q > 0);
-            tc_commit(&s_full[b]);
+          for (int q = 0; q < kMaxKX / 16; ++q) {
+            if (q < nkx) {
+              if (XS)
+                mma_ss(tS, dXA + 16 * q, db + 16 * q, idSW, q > 0);
+              else
+                mma_ts(tS, tA + 8 * q, db + 16 * q, idSW, q > 0);
+            }
           }
-          __syncwarp();
-          ++uses;
-          if (++stage == (uint32_t)S) { stage = 0; sph ^= 1; }
+#pragma unroll
+          for (int q = 0; q < 2 * kTsCols / 16; ++q)
+            if (q < nkg) mma_ts(tS + 64, tG + 8 * q, dv + 16 * q, idSW, q > 0);
+          tc_commit(&s_full[b]);
+          // the XA tile is read only by the S MMAs: released after the item's last one
+          if (XS && j == item.w - 1) tc_commit(xa_empty);
         }
+        __syncwarp();
+        ++uses;
+        if (++stage == (uint32_t)S) { stage = 0; sph ^= 1; }
       }
     }
   sw_out:
@@ -260,35 +282,33 @@ __global__ void __launch_bounds__(kTsThreads, 1) tc_bwd_ts_kernel(TcBwdArgs a) {
       const int4 item = a.items[t];
       if (a.sys_active && !a.sys_active[item.x]) continue;
       const int nH = 2 * item.w;
-      for (int g = 0; g < nsub; ++g) {
-        for (int h = 0; h < nH; ++h) {
-          const int b = h & 1;
-          uint32_t& qr = b == 0 ? qr0 : qr1;
-          if (!warp_wait(&q_ready[b], qr & 1u, abort, a.err, 26)) goto acc_out;
-          ++qr;
+      for (int h = 0; h < nH; ++h) {
+        const int b = h & 1;
+        uint32_t& qr = b == 0 ? qr0 : qr1;
+        if (!warp_wait(&q_ready[b], qr & 1u, abort, a.err, 26)) goto acc_out;
+        ++qr;
+        tc_fence_after();
+        const uint32_t acc = (h % kFoldH) != 0;
+        const bool fold_end = (h % kFoldH) == kFoldH - 1 || h == nH - 1;
+        if (!acc && open) {
+          if (!warp_wait(o_free, of_ph, abort, a.err, 27)) goto acc_out;
+          of_ph ^= 1;
+          open = false;
           tc_fence_after();
-          const uint32_t acc = (h % kFoldH) != 0;
-          const bool fold_end = (h % kFoldH) == kFoldH - 1 || h == nH - 1;
-          if (!acc && open) {
-            if (!warp_wait(o_free, of_ph, abort, a.err, 27)) goto acc_out;
-            of_ph ^= 1;
-            open = false;
-            tc_fence_after();
-          }
-          const uint64_t dbg = sdesc_add(dBG, stage * STG + b * 1024u);
-          const uint32_t tq = tbase + 256 + 32 * b, tacc = tbase + colACC;
-          if (leader) {
-            issue_ts4(tacc, tq, dbg, idA, acc);
-            tc_commit(&q_free[b]);
-            if (fold_end) tc_commit(o_ready);
-            // both halves of the stage read (their S, W MMAs completed before Q)
-            if (b == 1) tc_commit(&empty[stage]);
-          }
-          __syncwarp();
-          if (fold_end) open = true;
-          if (b == 1) {
-            if (++stage == (uint32_t)S) stage = 0;
-          }
+        }
+        const uint64_t dbg = sdesc_add(dBG, stage * STG + b * 1024u);
+        const uint32_t tq = tbase + 256 + 32 * b, tacc = tbase + colACC;
+        if (leader) {
+          issue_ts4(tacc, tq, dbg, idA, acc);
+          tc_commit(&q_free[b]);
+          if (fold_end) tc_commit(o_ready);
+          // both halves of the stage read (their S, W MMAs completed before Q)
+          if (b == 1) tc_commit(&empty[stage]);
+        }
+        __syncwarp();
+        if (fold_end) open = true;
+        if (b == 1) {
+          if (++stage == (uint32_t)S) stage = 0;
         }
       }
     }
@@ -305,6 +325,7 @@ __global__ void __launch_bounds__(kTsThreads, 1) tc_bwd_ts_kernel(TcBwdArgs a) {
     const uint32_t tACC = tbase + lofs + colACC;
     const int d = a.d;
     const int qc = a.qcol;
+    double* wp = wpart + w * kGW;
     uint32_t sph = 0, oph = 0;
     long long uses = 0;
     int u = 0;
@@ -313,139 +334,130 @@ __global__ void __launch_bounds__(kTsThreads, 1) tc_bwd_ts_kernel(TcBwdArgs a) {
       if (a.sys_active && !a.sys_active[item.x]) continue;
       const int s = item.x, bi = s / a.chains, c = s % a.chains;
       const int nH = 2 * item.w;
-      for (int g = 0; g < nsub; ++g, ++u) {
-        if (u > 0) {
-          // both warpgroups have waited for their last S, W of the previous
-          // sub-item: no MMA reads XA or GI any more
-          mbar_arrive(seg);
-          const bool ok = mbar_wait(seg, (uint32_t)(u - 1) & 1u, abort, a.err, 32);
-          if (!__all_sync(0xffffffffu, ok)) goto exp_out;
+      if (u > 0) {
+        // both warpgroups have waited for their last S, W of the previous
+        // item: no MMA reads XA or GI any more
+        mbar_arrive(seg);
+        const bool ok = mbar_wait(seg, (uint32_t)(u - 1) & 1u, abort, a.err, 32);
+        if (!__all_sync(0xffffffffu, ok)) goto exp_out;
+      }
+      ++u;
+      {
+        // warpgroup 0 stores the item's XA rows (unless XA stays in shared
+        // memory), warpgroup 1 its GI rows
+        const size_t ti = (size_t)c * a.T_total + item.y;
+        const int width = b == 0 ? (XS ? 0 : a.KX) : a.KG;
+        const uint8_t* src = (b == 0 ? a.XA + ti * XT : a.GI + ti * GT) + (row >> 3) * (width * 16) + (row & 7) * 16;
+        const uint32_t col = b == 0 ? colA : colG;
+        for (int q = 0; q < width / 16; ++q) {
+          const uint4 u0 = *reinterpret_cast<const uint4*>(src + 2 * q * 128);
+          const uint4 u1 = *reinterpret_cast<const uint4*>(src + (2 * q + 1) * 128);
+          const uint32_t v[8] = {u0.x, u0.y, u0.z, u0.w, u1.x, u1.y, u1.z, u1.w};
+          tmem_st8(tbase + lofs + col + 8 * q, v);
         }
+        tmem_st_wait();
+        tc_fence_before();
+        mbar_arrive(a_ready);
+      }
+      const int64_t nb = a.L.offsets[bi + 1] - a.L.offsets[bi];
+      const int64_t rl = (int64_t)(item.y - a.T.inst_tile0[bi]) * 128 + row;
+      const bool valid = rl < nb;
+      const int64_t i = a.L.offsets[bi] + rl;
+      const double* th = a.theta + (int64_t)s * a.n_theta;
+      // lane k holds the scale of dimension k (d <= 32): one exp per lane per item
+      const float sc_lane =
+          lane < d ? (float)(sqrt(2.0 * kHalfLog2e) * exp(-th[1 + (a.ard ? lane : 0)])) : 0.f;
+      if (b == 0 && lane == 0)
+        for (int v = 0; v <= d; ++v) wp[v] = 0.0;
+      for (int h = b; h < nH; h += 2, ++uses) {
+        bool ok = mbar_wait(&s_full[b], sph, abort, a.err, 28);
+        if (!__all_sync(0xffffffffu, ok)) goto exp_out;
+        sph ^= 1;
+        tc_fence_after();
         {
-          // warpgroup 0 stores the sub-item's XA rows, warpgroup 1 its GI rows
-          const size_t ti = (size_t)c * a.T_total + item.y + g;
-          const int width = b == 0 ? a.KX : a.KG;
-          const uint8_t* src = (b == 0 ? a.XA + ti * XT : a.GI + ti * GT) + (row >> 3) * (width * 16) + (row & 7) * 16;
-          const uint32_t col = b == 0 ? colA : colG;
-          for (int q = 0; q < width / 16; ++q) {
-            const uint4 u0 = *reinterpret_cast<const uint4*>(src + 2 * q * 128);
-            const uint4 u1 = *reinterpret_cast<const uint4*>(src + (2 * q + 1) * 128);
-            const uint32_t v[8] = {u0.x, u0.y, u0.z, u0.w, u1.x, u1.y, u1.z, u1.w};
-            tmem_st8(tbase + lofs + col + 8 * q, v);
-          }
-          tmem_st_wait();
+          // the whole half of S and W in registers with one wait, so S_b, W_b
+          // are released at once and the next MMAs into them can start
+          uint32_t s0[32], s1[32], w0[32], w1[32], qq[32];
+          tmem_ld32(tS, s0);
+          tmem_ld32(tS + 32, s1);
+          tmem_ld32(tS + 64, w0);
+          tmem_ld32(tS + 96, w1);
+          tmem_ld_wait_regs(s0, s1, w0, w1);
           tc_fence_before();
-          mbar_arrive(a_ready);
-        }
-        const int64_t nb = a.L.offsets[bi + 1] - a.L.offsets[bi];
-        const int64_t rl = (int64_t)(item.y + g - a.T.inst_tile0[bi]) * 128 + row;
-        const bool valid = rl < nb;
-        double dq = 0.0;
-        if (b == 0) {
-          const double* th = a.theta + (int64_t)s * a.n_theta;
-          const int64_t i = a.L.offsets[bi] + rl;
-          for (int kk = 0; kk < d; ++kk) {
-            float v = 0.f;
-            if (valid) {
-              const float sc = (float)(sqrt(2.0 * kHalfLog2e) * exp(-th[1 + (a.ard ? kk : 0)]));
-              v = xt_of(a.x[i * d + kk], sc);
+          mbar_arrive(&s_free[b]);
+          if (item.z + (h >> 1) == item.y) {
+            // diagonal tile of the upper triangle: counted once, off-diagonal tiles twice
+#pragma unroll
+            for (int q = 0; q < 32; ++q) {
+              w0[q] = __float_as_uint(0.5f * __uint_as_float(w0[q]));
+              w1[q] = __float_as_uint(0.5f * __uint_as_float(w1[q]));
             }
-            sxt[kk * 128 + row] = v;
-            sdacc[kk * 128 + row] = 0.0;
           }
-        }
-        for (int h = b; h < nH; h += 2, ++uses) {
-          bool ok = mbar_wait(&s_full[b], sph, abort, a.err, 28);
-          if (!__all_sync(0xffffffffu, ok)) goto exp_out;
-          sph ^= 1;
-          tc_fence_after();
-          {
-            // the whole half of S and W in registers with one wait, so S_b, W_b
-            // are released at once and the next MMAs into them can start
-            uint32_t s0[32], s1[32], w0[32], w1[32], qq[32];
-            tmem_ld32(tS, s0);
-            tmem_ld32(tS + 32, s1);
-            tmem_ld32(tS + 64, w0);
-            tmem_ld32(tS + 96, w1);
-            tmem_ld_wait_regs(s0, s1, w0, w1);
-            tc_fence_before();
-            mbar_arrive(&s_free[b]);
-            if (a.sym && item.z + (h >> 1) == item.y + g) {
-              // diagonal tile of the upper triangle: counted once, off-diagonal tiles twice
 #pragma unroll
-              for (int q = 0; q < 32; ++q) {
-                w0[q] = __float_as_uint(0.5f * __uint_as_float(w0[q]));
-                w1[q] = __float_as_uint(0.5f * __uint_as_float(w1[q]));
-              }
-            }
+          for (int q = 0; q < 16; ++q)
+            qq[q] = pack_f16x2(ex2(__uint_as_float(s0[2 * q])) * __uint_as_float(w0[2 * q]),
+                               ex2(__uint_as_float(s0[2 * q + 1])) * __uint_as_float(w0[2 * q + 1]));
 #pragma unroll
-            for (int q = 0; q < 16; ++q)
-              qq[q] = pack_f16x2(ex2(__uint_as_float(s0[2 * q])) * __uint_as_float(w0[2 * q]),
-                                 ex2(__uint_as_float(s0[2 * q + 1])) * __uint_as_float(w0[2 * q + 1]));
-#pragma unroll
-            for (int q = 0; q < 16; ++q)
-              qq[16 + q] = pack_f16x2(ex2(__uint_as_float(s1[2 * q])) * __uint_as_float(w1[2 * q]),
-                                      ex2(__uint_as_float(s1[2 * q + 1])) * __uint_as_float(w1[2 * q + 1]));
-            if (uses > 0) {
-              // Q_b of this warpgroup's previous half must have been consumed
-              ok = mbar_wait(&q_free[b], (uint32_t)((uses - 1) & 1), abort, a.err, 30);
-              if (!__all_sync(0xffffffffu, ok)) goto exp_out;
-              tc_fence_after();
-            }
-            tmem_st32(tQ, qq);
-          }
-          tmem_st_wait();
-          tc_fence_before();
-          mbar_arrive(&q_ready[b]);
-          // warpgroup 0 folds the accumulator after the fold's last (odd) half
-          if (b == 0 && (((h + 1) % kFoldH) == kFoldH - 1 || h + 1 == nH - 1)) {
-            ok = mbar_wait(o_ready, oph, abort, a.err, 29);
+          for (int q = 0; q < 16; ++q)
+            qq[16 + q] = pack_f16x2(ex2(__uint_as_float(s1[2 * q])) * __uint_as_float(w1[2 * q]),
+                                    ex2(__uint_as_float(s1[2 * q + 1])) * __uint_as_float(w1[2 * q + 1]));
+          if (uses > 0) {
+            // Q_b of this warpgroup's previous half must have been consumed
+            ok = mbar_wait(&q_free[b], (uint32_t)((uses - 1) & 1), abort, a.err, 30);
             if (!__all_sync(0xffffffffu, ok)) goto exp_out;
-            oph ^= 1;
             tc_fence_after();
-            uint32_t oq[16];
-            tmem_ld16(tACC + 16 * (qc >> 4), oq);
-            tmem_ld_wait_regs(oq);
-            const float qs = __uint_as_float(oq[qc & 15]);
-            dq += (double)qs;
+          }
+          tmem_st32(tQ, qq);
+        }
+        tmem_st_wait();
+        tc_fence_before();
+        mbar_arrive(&q_ready[b]);
+        // warpgroup 0 folds the accumulator after the fold's last (odd) half:
+        // per row x~^2 q - 2 x~ R + T, summed over the warp's 32 rows in FP64
+        if (b == 0 && (((h + 1) % kFoldH) == kFoldH - 1 || h + 1 == nH - 1)) {
+          ok = mbar_wait(o_ready, oph, abort, a.err, 29);
+          if (!__all_sync(0xffffffffu, ok)) goto exp_out;
+          oph ^= 1;
+          tc_fence_after();
+          uint32_t oq[16];
+          tmem_ld16(tACC + 16 * (qc >> 4), oq);
+          tmem_ld_wait_regs(oq);
+          const float qs = __uint_as_float(oq[qc & 15]);
+          // per-row terms summed over the warp's 32 rows in FP32, the warp sums
+          // accumulated in FP64 across folds
+          float v = qs;
 #pragma unroll
-            for (int c4 = 0; c4 < (kMaxDT + 3) / 4; ++c4) {
-              if (4 * c4 < d) {
-                uint32_t o[16];
-                tmem_ld16(tACC + 16 * c4, o);
-                tmem_ld_wait_regs(o);
+          for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+          if (lane == 0) wp[0] += (double)v;
+          for (int c4 = 0; c4 < (kMaxDT + 3) / 4; ++c4) {
+            if (4 * c4 < d) {
+              uint32_t o[16];
+              tmem_ld16(tACC + 16 * c4, o);
+              tmem_ld_wait_regs(o);
 #pragma unroll
-                for (int uu = 0; uu < 4; ++uu) {
-                  const int kk = 4 * c4 + uu;
-                  if (kk < d) {
-                    const float R = __uint_as_float(o[4 * uu]) + __uint_as_float(o[4 * uu + 1]);
-                    const float T = __uint_as_float(o[4 * uu + 2]) + __uint_as_float(o[4 * uu + 3]);
-                    const float x = sxt[kk * 128 + row];
-                    sdacc[kk * 128 + row] += (double)fmaf(x, fmaf(x, qs, -2.f * R), T);
-                  }
+              for (int uu = 0; uu < 4; ++uu) {
+                const int kk = 4 * c4 + uu;
+                if (kk < d) {
+                  const float R = __uint_as_float(o[4 * uu]) + __uint_as_float(o[4 * uu + 1]);
+                  const float T = __uint_as_float(o[4 * uu + 2]) + __uint_as_float(o[4 * uu + 3]);
+                  const float sc = __shfl_sync(0xffffffffu, sc_lane, kk);
+                  const float x = valid ? xt_of(a.x[i * d + kk], sc) : 0.f;
+                  float e = valid ? fmaf(x, fmaf(x, qs, -2.f * R), T) : 0.f;
+#pragma unroll
+                  for (int sft = 16; sft > 0; sft >>= 1) e += __shfl_down_sync(0xffffffffu, e, sft);
+                  if (lane == 0) wp[1 + kk] += (double)e;
                 }
               }
             }
-            tc_fence_before();
-            mbar_arrive(o_free);
           }
+          tc_fence_before();
+          mbar_arrive(o_free);
         }
-        if (b == 0) {
-          // per-warp partial of this sub-item: [q, contrib_0 .. contrib_{d-1}]
-          double* out = a.gpart + ((size_t)t * (4 * nsub) + g * 4 + w) * kGW;
-          double v = dq;
-#pragma unroll
-          for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-          if (lane == 0) out[0] = v;
-          for (int kk = 0; kk < d; ++kk) {
-            {
-              double uu = sdacc[kk * 128 + row];
-#pragma unroll
-              for (int o = 16; o > 0; o >>= 1) uu += __shfl_down_sync(0xffffffffu, uu, o);
-              if (lane == 0) out[1 + kk] = uu;
-            }
-          }
-        }
+      }
+      if (b == 0 && lane == 0) {
+        // per-warp partial of this item: [q, contrib_0 .. contrib_{d-1}]
+        double* out = a.gpart + (((size_t)a.chunk * a.n_items + t) * 4 + w) * kGW;
+        for (int v = 0; v <= d; ++v) out[v] = wp[v];
       }
     }
   exp_out:;
@@ -485,8 +497,11 @@ __global__ void tc_bwd_norms_kernel(DevLayout L, int chains, int64_t n_total, co
 }
 
 // GI, VJ and BG operand tiles of every (chain, padded tile).
+// G and V enter by columns [c0, c0 + mc) of their m; GI rows [gh gh gl vh vh vl],
+// VJ rows [vh vl vh gh gl gh] (BF16 hi/lo, G scaled by a power of two), so that
+// GI VJ^T = G_i . V_j + V_i . G_j over the block.
 __global__ void tc_prep_bwd_kernel(DevLayout L, TcTables T, int chains, int d, int ard, int n_theta, int m,
-                                   int KG, int nparts, int NB, int qcol, int T_total, const float* x,
+                                   int c0, int mc, int KG, int NB, int qcol, int T_total, const float* x,
                                    const double* theta,
                                    const float* V, const float* G, int64_t n_total, const uint32_t* gmax,
                                    const uint32_t* vmax, const int32_t* sys_active, uint8_t* GI, uint8_t* VJ,
@@ -507,9 +522,9 @@ __global__ void tc_prep_bwd_kernel(DevLayout L, TcTables T, int chains, int d, i
   const __nv_bfloat16 zb = __float2bfloat16_rn(0.f);
   for (int q = 0; q < KG; ++q) {
     __nv_bfloat16 gval = zb, vval = zb;
-    if (valid && q < nparts * m) {
-      const int col = q % m, part = q / m;
-      const int64_t idx = ((int64_t)c * n_total + i) * m + col;
+    if (valid && q < 6 * mc) {
+      const int col = q % mc, part = q / mc;
+      const int64_t idx = ((int64_t)c * n_total + i) * m + c0 + col;
       const float gq = G[idx] * gs, vq = V[idx];
       const __nv_bfloat16 gh = __float2bfloat16_rn(gq), vh = __float2bfloat16_rn(vq);
       const __nv_bfloat16 gl = __float2bfloat16_rn(gq - __bfloat162float(gh));
@@ -554,21 +569,23 @@ __global__ void tc_prep_bwd_kernel(DevLayout L, TcTables T, int chains, int d, i
 constexpr int kFinThreads = 256;
 
 __global__ void __launch_bounds__(kFinThreads) tc_bwd_finalize_kernel(
-    DevLayout L, const int32_t* pref, int wpi, int chains, int n_theta, int ard, int d, const double* theta,
-    const double* gpart, const double* gvpart, const uint32_t* gmax, const uint32_t* vmax,
+    DevLayout L, const int32_t* pref, int n_items, int n_chunks, int chains, int n_theta, int ard, int d,
+    const double* theta, const double* gpart, const double* gvpart, const uint32_t* gmax, const uint32_t* vmax,
     const int32_t* sys_active, const int* err, double* grad) {
   __shared__ double red[kFinThreads / 32][kGW + 1];
   const int s = blockIdx.x;
   if (sys_active && !sys_active[s]) return;
   const int b = s / chains, c = s - b * chains;
-  const int64_t n_rows = (int64_t)(pref[s + 1] - pref[s]) * wpi;   // (item, warp) partial rows
-  const int64_t r0 = (int64_t)pref[s] * wpi;
+  const int64_t n_rows = (int64_t)(pref[s + 1] - pref[s]) * 4;   // (item, warp) partial rows per block
   double acc[kGW + 1];
 #pragma unroll
   for (int v = 0; v <= kGW; ++v) acc[v] = 0.0;
-  for (int64_t r = threadIdx.x; r < n_rows; r += kFinThreads) {
-    const double* row = gpart + (r0 + r) * kGW;
-    for (int v = 0; v <= d; ++v) acc[v] += row[v];
+  for (int ch = 0; ch < n_chunks; ++ch) {
+    const int64_t r0 = ((int64_t)ch * n_items + pref[s]) * 4;
+    for (int64_t r = threadIdx.x; r < n_rows; r += kFinThreads) {
+      const double* row = gpart + (r0 + r) * kGW;
+      for (int v = 0; v <= d; ++v) acc[v] += row[v];
+    }
   }
   for (int it = L.inst_item0[b] + threadIdx.x; it < L.inst_item0[b + 1]; it += kFinThreads)
     acc[kGW] += gvpart[(int64_t)it * chains + c];
@@ -609,29 +626,45 @@ __global__ void __launch_bounds__(kFinThreads) tc_bwd_finalize_kernel(
 
 kmv_status tc_backward(kmv_handle h, const KmvArgs& a, double* grad, cudaStream_t st) {
   const Layout& L = h->layout;
-  if (a.d > kMaxDT) return tc_fail(h, KMV_EUNSUPPORTED, "tensor-core adjoint supports d <= 15");
+  if (a.d > kMaxDT) return tc_fail(h, KMV_EUNSUPPORTED, "tensor-core adjoint supports d <= 32");
   TcState* S = tc_state(h);
   kmv_status stt = tc_build_plan(h, S, st);
   if (stt != KMV_OK) return stt;
   const int n_sys = L.n_inst * L.chains;
   const int KX = x_width(a.d);
-  // The TMEM-resident form while XA, GI and a round16(4 d + 1)-column accumulator
-  // fit; symmetrised (upper-triangle tiles, GI of depth 6 m) when that fits too.
-  const int NBt = round16(4 * a.d + 1);
-  const int KGs = round16(6 * a.m), KGp = round16(3 * a.m);
-  const bool sym = KX / 2 + KGs / 2 + NBt <= kTsCols;
-  if (!sym && KX / 2 + KGp / 2 + NBt > kTsCols)
-    return tc_fail(h, KMV_EUNSUPPORTED, "tensor-core adjoint operands do not fit in tensor memory");
-  const int KG = sym ? KGs : KGp;
-  const int n_items = sym ? S->sym_n_items : S->n_items;
-  const int wpi = sym ? 4 : 8;   // per-warp partial rows per item
-  const int NB = NBt, qcol = 4 * a.d;
+  const int NB = round16(4 * a.d + 1), qcol = 4 * a.d;
+  const size_t fixed = 1024 + kTsBarBytes + kTsFoldBytes;
+  // Columns of G, V per launch (mc) and where XA lives: the depth-6 mc GI rows,
+  // the accumulator and (unless XS) the XA rows must fit the TMEM columns left
+  // by S, W and Q, and the stages shared memory.  Fewer launches first, then
+  // XA in TMEM.
+  auto stages_for = [&](bool xs, int mc) -> int {
+    const size_t KG = round16(6 * mc);
+    const size_t stg = (size_t)(KX + KG + NB) * 256;
+    const size_t xa = xs ? (((size_t)KX * 256 + 1023) & ~size_t(1023)) : 0;
+    if (kMaxSmem < fixed + xa + 2 * stg) return 0;
+    return (int)std::min<size_t>(6, (kMaxSmem - fixed - xa) / stg);
+  };
+  auto max_mc = [&](bool xs) -> int {
+    for (int mc = a.m; mc >= 1; --mc) {
+      const int cols = (xs ? 0 : KX / 2) + round16(6 * mc) / 2 + NB;
+      if (cols <= kTsCols && stages_for(xs, mc) >= 2) return mc;
+    }
+    return 0;
+  };
+  const int mc0 = max_mc(false), mc1 = max_mc(true);
+  if (mc0 == 0 && mc1 == 0)
+    return tc_fail(h, KMV_EUNSUPPORTED, "tensor-core adjoint operands do not fit in tensor/shared memory");
+  const int nc0 = mc0 ? (a.m + mc0 - 1) / mc0 : INT32_MAX, nc1 = mc1 ? (a.m + mc1 - 1) / mc1 : INT32_MAX;
+  const bool xs = nc1 < nc0;
+  const int mc = xs ? mc1 : mc0, n_chunks = xs ? nc1 : nc0;
+  const int KG = round16(6 * mc);
+  const int stages = stages_for(xs, mc);
   const size_t XT = (size_t)KX * 256, GT = (size_t)KG * 256, BT = (size_t)NB * 256;
   const size_t STG = XT + GT + BT;
-  const size_t fixed = 1024 + kTsBarBytes;
-  const int stages = (int)std::min<size_t>(6, (kMaxSmem - fixed - kTsRowBytes) / STG);
-  if (stages < 2) return tc_fail(h, KMV_EUNSUPPORTED, "tensor-core adjoint tiles do not fit in shared memory");
-  const size_t smem = std::max(kMinSmem, fixed + stages * STG + kTsRowBytes);
+  const size_t smem =
+      std::max(kMinSmem, fixed + (xs ? ((XT + 1023) & ~size_t(1023)) : 0) + stages * STG);
+  const int n_items = S->sym_n_items;
 
   auto al = [](size_t v) { return (v + 255) & ~size_t(255); };
   const size_t tiles = (size_t)L.chains * S->T_total;
@@ -639,7 +672,7 @@ kmv_status tc_backward(kmv_handle h, const KmvArgs& a, double* grad, cudaStream_
   const size_t o_vj = o_gi + al(tiles * GT), o_bg = o_vj + al(tiles * GT), o_mx = o_bg + al(tiles * BT);
   const size_t o_gv = o_mx + al(sizeof(uint32_t) * 2 * n_sys);
   const size_t o_gp = o_gv + al(sizeof(double) * (size_t)std::max(1, L.n_items) * L.chains);
-  const size_t o_er = o_gp + al(sizeof(double) * (size_t)std::max(1, n_items) * wpi * kGW);
+  const size_t o_er = o_gp + al(sizeof(double) * (size_t)n_chunks * std::max(1, n_items) * 4 * kGW);
   stt = tc_ensure_buf(h, S, o_er + 256);
   if (stt != KMV_OK) return stt;
   uint8_t* base = static_cast<uint8_t*>(S->buf);
@@ -650,8 +683,10 @@ kmv_status tc_backward(kmv_handle h, const KmvArgs& a, double* grad, cudaStream_
   int* err = reinterpret_cast<int*>(base + o_er);
 
   if (!S->bwd_attr_set) {
-    if (cudaFuncSetAttribute(tc_bwd_ts_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem) !=
-        cudaSuccess)
+    if (cudaFuncSetAttribute(tc_bwd_ts_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kMaxSmem) != cudaSuccess ||
+        cudaFuncSetAttribute(tc_bwd_ts_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kMaxSmem) != cudaSuccess)
       return tc_fail(h, KMV_ECUDA, "cudaFuncSetAttribute failed");
     S->bwd_attr_set = true;
   }
@@ -663,13 +698,9 @@ kmv_status tc_backward(kmv_handle h, const KmvArgs& a, double* grad, cudaStream_
                                                                      gmax, vmax, gvpart, a.sys_active);
   if (n_items > 0) {
     tc_launch_prep_x(h, S, a, KX, 2, base + o_xa, base + o_xb, st);
-    tc_prep_bwd_kernel<<<dim3(S->T_total, L.chains), 128, 0, st>>>(
-        h->dev, S->dev, L.chains, a.d, a.ard, a.n_theta, a.m, KG, sym ? 6 : 3, NB, qcol, S->T_total, a.x, a.theta,
-        a.V, a.G, L.n_total, gmax, vmax, a.sys_active, base + o_gi, base + o_vj, base + o_bg, err);
     TcBwdArgs ba;
-    ba.items = sym ? S->d_sym_items : S->d_items;
+    ba.items = S->d_sym_items;
     ba.n_items = n_items;
-    ba.sym = sym ? 1 : 0;
     ba.chains = L.chains;
     ba.T_total = S->T_total;
     ba.KX = KX;
@@ -694,12 +725,25 @@ kmv_status tc_backward(kmv_handle h, const KmvArgs& a, double* grad, cudaStream_
     ba.sys_active = a.sys_active;
     ba.err = err;
     const int grid = std::min(n_items, S->num_sms);
-    ProfScope prof(h, KMV_KERNEL_ADJOINT, st);
-    tc_bwd_ts_kernel<<<grid, kTsThreads, smem, st>>>(ba);
+    // One launch per block of mc columns of G, V: the gradient is a sum over
+    // columns, so the blocks' partials are summed by the finalize.  Stream order
+    // keeps each block's operand tiles until its launch has read them.
+    for (int ch = 0; ch < n_chunks; ++ch) {
+      const int c0 = ch * mc, mcc = std::min(mc, a.m - c0);
+      tc_prep_bwd_kernel<<<dim3(S->T_total, L.chains), 128, 0, st>>>(
+          h->dev, S->dev, L.chains, a.d, a.ard, a.n_theta, a.m, c0, mcc, KG, NB, qcol, S->T_total, a.x, a.theta,
+          a.V, a.G, L.n_total, gmax, vmax, a.sys_active, base + o_gi, base + o_vj, base + o_bg, err);
+      ba.chunk = ch;
+      ProfScope prof(h, KMV_KERNEL_ADJOINT, st);
+      if (xs)
+        tc_bwd_ts_kernel<true><<<grid, kTsThreads, smem, st>>>(ba);
+      else
+        tc_bwd_ts_kernel<false><<<grid, kTsThreads, smem, st>>>(ba);
+    }
   }
-  tc_bwd_finalize_kernel<<<n_sys, kFinThreads, 0, st>>>(h->dev, sym ? S->dev.sym_pref : S->dev.sys_pref, wpi,
-                                                         L.chains, a.n_theta, a.ard, a.d, a.theta, gpart, gvpart,
-                                                         gmax, vmax, a.sys_active, err, grad);
+  tc_bwd_finalize_kernel<<<n_sys, kFinThreads, 0, st>>>(h->dev, S->dev.sym_pref, n_items, n_chunks, L.chains,
+                                                         a.n_theta, a.ard, a.d, a.theta, gpart, gvpart, gmax, vmax,
+                                                         a.sys_active, err, grad);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return tc_fail(h, KMV_ECUDA, cudaGetErrorString(e));
   if (a.Y != nullptr) {
