@@ -214,8 +214,10 @@ kmv_status kmv_energy(kmv_handle h, const kmv_points* pts, int32_t chains,
  * with weights and shifts from Jacobi elliptic functions on the spectral
  * interval [sigma_s^2, M_s], M_s = 1.01 max_i (A 1)_i (the largest row sum
  * bounds lambda_max because K0 >= 0 entrywise; 1% covers rounding).  The
- * n_poles shifted systems of every system are solved together by CG to cg_tol
- * (as kmv_cg_solve, cold start; the BF16 form by iterative refinement).
+ * n_poles shifted systems of every system are the n_poles columns of one
+ * multi-column CG: one product with per-column shifts per iteration, each
+ * column with its own CG scalars and its own stop at cg_tol (cold start; the
+ * BF16 form by iterative refinement with FP32 residuals, as kmv_cg_solve).
  *
  *   xi          DEVICE FP32 (chains, N_total): the caller's N(0, I) draw.
  *   phi         DEVICE FP32 (chains, N_total), written (must not alias xi).
@@ -225,8 +227,8 @@ kmv_status kmv_energy(kmv_handle h, const kmv_points* pts, int32_t chains,
  *   cg_iters    DEVICE int32 (n_inst * chains) or NULL: the largest iteration count.
  *   poles_out   DEVICE FP64 (n_inst * chains, 2 + 2 n_poles) or NULL:
  *               [sigma^2, M, w_1..w_Np, lambda_1..lambda_Np] per system.
- * Work: one N^2 pass for A 1, then n_poles * chains systems per CG iteration
- * (converged shifts drop out).  Allocates workspace; not for use while the
+ * Work: one N^2 pass for A 1, then one n_poles-column N^2 product per CG
+ * iteration (a system drops out when all its columns have stopped).  Allocates workspace; not for use while the
  * stream is being captured (the work plan changes between the two phases).
  */
 kmv_status kmv_phi_refresh(kmv_handle h, const kmv_points* pts, int32_t chains,

@@ -428,6 +428,137 @@ kmv_status run_solve(kmv_handle h, const kmv_points* pts, const double* theta, c
   return run_cg(h, pts, theta, rhs, rhs_stride, x, tol, maxiter, warm, status, iters, cg_bufs(h, S.cg), prec, st);
 }
 
+// --- multi-column CG: the shifted systems of the pole expansion ---------------------
+
+struct McgBufs {
+  float *r, *p, *q;
+  double *partial, *partial2;
+  McgCol* cols;
+  int32_t *sys_any, *n_active;
+};
+
+void mcg_layout(const Layout& L, int m, Arena& ar, size_t off[8]) {
+  const size_t vec = sizeof(float) * (size_t)L.chains * std::max<int64_t>(1, L.n_total) * m;
+  const size_t items = (size_t)std::max(1, L.n_items) * L.chains * m;
+  const size_t n_sys = (size_t)L.n_inst * L.chains;
+  off[0] = ar.take(vec);
+  off[1] = ar.take(vec);
+  off[2] = ar.take(vec);
+  off[3] = ar.take(sizeof(double) * items);
+  off[4] = ar.take(sizeof(double) * items * 2);
+  off[5] = ar.take(sizeof(McgCol) * n_sys * m);
+  off[6] = ar.take(sizeof(int32_t) * n_sys);
+  off[7] = ar.take(sizeof(double) * 2);   // n_active (int32) + worst rr/bb (double at +8)
+}
+
+McgBufs mcg_bufs(kmv_handle h, const size_t off[8]) {
+  McgBufs b;
+  b.r = at<float>(h, off[0]);
+  b.p = at<float>(h, off[1]);
+  b.q = at<float>(h, off[2]);
+  b.partial = at<double>(h, off[3]);
+  b.partial2 = at<double>(h, off[4]);
+  b.cols = at<McgCol>(h, off[5]);
+  b.sys_any = at<int32_t>(h, off[6]);
+  b.n_active = at<int32_t>(h, off[7]);
+  return b;
+}
+
+// CG on (A(theta_s) + shift[s m + q] I) x_q = b_q for the m columns q of every
+// system s, one m-column product per iteration; the column results stay in B.cols.
+// b is (chains, N) shared by the columns (b_cols == 0) or (chains, N, m).
+kmv_status run_mcg(kmv_handle h, const kmv_points* pts, const double* theta, const float* shifts, int m,
+                   const float* b, int b_cols, float* x, double tol, int maxiter, int warm, const McgBufs& B,
+                   kmv_precision prec, cudaStream_t st) {
+  const Layout& L = h->layout;
+  KmvArgs a = base_args(h, pts, theta);
+  a.m = m;
+  a.col_shift = shifts;
+  a.col_shift_stride = m;
+  if (warm) {
+    a.V = x;
+    a.Y = B.q;
+    KMV_TRY(run_forward(h, a, prec, st));
+  }
+  KMV_CUDA(h, launch_mcg_init(h->dev, L.n_items, L.chains, L.n_total, m, b, b_cols, B.q, warm, x, B.r, B.p,
+                              B.partial2, st));
+  KMV_CUDA(h, cudaMemsetAsync(B.n_active, 0, sizeof(int32_t), st));
+  KMV_CUDA(h, launch_mcg_reduce_init(h->dev, L.n_inst, L.chains, m, B.partial2, tol, B.cols, B.sys_any,
+                                     B.n_active, st));
+  a.V = B.p;
+  a.Y = B.q;
+  a.sys_active = B.sys_any;
+  const int check_every = 4;
+  for (int it = 0; it < maxiter; ++it) {
+    if (it % check_every == 0) {
+      KMV_CUDA(h, cudaMemcpyAsync(h->host_flag, B.n_active, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+      KMV_CUDA(h, cudaStreamSynchronize(st));
+      if (*h->host_flag == 0) break;
+    }
+    KMV_TRY(run_forward(h, a, prec, st));
+    KMV_CUDA(h, launch_mcg_dot(h->dev, L.n_items, L.chains, L.n_total, m, B.p, B.q, B.sys_any, B.partial, st));
+    KMV_CUDA(h, launch_mcg_alpha(h->dev, L.n_inst, L.chains, m, B.partial, B.cols, B.sys_any, st));
+    KMV_CUDA(h, launch_mcg_update_xr(h->dev, L.n_items, L.chains, L.n_total, m, B.cols, B.sys_any, x, B.r, B.p,
+                                     B.q, B.partial, st));
+    KMV_CUDA(h, cudaMemsetAsync(B.n_active, 0, sizeof(int32_t), st));
+    KMV_CUDA(h, launch_mcg_beta(h->dev, L.n_inst, L.chains, m, B.partial, tol, maxiter, B.cols, B.sys_any,
+                                B.n_active, st));
+    KMV_CUDA(h, launch_mcg_update_p(h->dev, L.n_items, L.chains, L.n_total, m, B.cols, B.sys_any, B.r, B.p, st));
+  }
+  return KMV_OK;
+}
+
+// The multi-column solve with the KMV_BF16_HILO operator to FP32 accuracy, by
+// the iterative refinement of run_cg_refined applied per column: true residual
+// with the FP32 operator, correction by multi-column CG with the tensor-core
+// operator, until every column has converged or stagnated.
+kmv_status run_mcg_refined(kmv_handle h, const kmv_points* pts, const double* theta, const float* shifts, int m,
+                           const float* b, float* x, double tol, int maxiter, int32_t* col_status,
+                           int32_t* col_iters, const McgBufs& B, const McgBufs& R, float* dx, double* prev_rr,
+                           cudaStream_t st) {
+  const Layout& L = h->layout;
+  const int64_t n_cols = (int64_t)L.n_inst * L.chains * m;
+  const int64_t nvec = (int64_t)L.chains * L.n_total * m;
+  // the relative accuracy of the m-column tensor-core product: the FMA-pipe form
+  // with the three-way split for m <= 2, else the two-way split
+  const double floor_tol = (m <= 2 && x_width_fma_ok(pts->d)) ? 1e-5 : 1e-3;
+  double* worst = reinterpret_cast<double*>(reinterpret_cast<char*>(R.n_active) + 8);
+  const int max_outer = 12;
+  if (nvec > 0) KMV_CUDA(h, cudaMemsetAsync(x, 0, sizeof(float) * nvec, st));
+  KMV_CUDA(h, cudaMemsetAsync(col_status, 0, sizeof(int32_t) * n_cols, st));
+  KMV_CUDA(h, cudaMemsetAsync(col_iters, 0, sizeof(int32_t) * n_cols, st));
+  KmvArgs a = base_args(h, pts, theta);
+  a.m = m;
+  a.col_shift = shifts;
+  a.col_shift_stride = m;
+  for (int outer = 0; outer <= max_outer; ++outer) {
+    // r = b - (A + shift) x with the FP32 operator; per-column stopping test
+    a.V = x;
+    a.Y = R.q;
+    if (L.n_items > 0) KMV_CUDA(h, launch_forward_simt(a, L.n_items, st));
+    KMV_CUDA(h, launch_mcg_init(h->dev, L.n_items, L.chains, L.n_total, m, b, 0, R.q, 1, x, R.r, R.p, R.partial2,
+                                st));
+    KMV_CUDA(h, launch_mcg_reduce_init(h->dev, L.n_inst, L.chains, m, R.partial2, tol, R.cols, R.sys_any,
+                                       R.n_active, st));
+    KMV_CUDA(h, launch_mcg_refine(n_cols, outer, R.cols, prev_rr, R.n_active, worst, st));
+    if (outer > 0) KMV_CUDA(h, launch_mcg_undo(h->dev, L.n_items, L.chains, L.n_total, m, R.cols, dx, x, st));
+    KMV_CUDA(h, cudaMemcpyAsync(h->host_flag, R.n_active, 16, cudaMemcpyDeviceToHost, st));
+    KMV_CUDA(h, cudaStreamSynchronize(st));
+    if (*h->host_flag == 0 || outer == max_outer) break;
+    double wr;
+    std::memcpy(&wr, reinterpret_cast<const char*>(h->host_flag) + 8, sizeof(double));
+    const double ratio = wr > 0.0 ? std::sqrt(wr) : 1.0;
+    const double inner_tol = std::min(0.5, std::max(floor_tol, 0.5 * tol / ratio));
+    // correction of the columns still active (the others get a zero right-hand side)
+    KMV_CUDA(h, launch_mcg_mask(h->dev, L.n_items, L.chains, L.n_total, m, R.cols, R.r, st));
+    KMV_TRY(run_mcg(h, pts, theta, shifts, m, R.r, 1, dx, inner_tol, maxiter, 0, B, KMV_BF16_HILO, st));
+    KMV_CUDA(h, launch_axpy(nvec, dx, x, st));
+    KMV_CUDA(h, launch_mcg_finish(n_cols, B.cols, 1, col_status, col_iters, st));
+  }
+  KMV_CUDA(h, launch_mcg_refine_finish(n_cols, R.cols, col_status, st));
+  return KMV_OK;
+}
+
 kmv_status check_prec(kmv_handle h, kmv_precision prec) {
   if (prec != KMV_FP32 && prec != KMV_BF16_HILO) return fail(h, KMV_EINVAL, "unknown precision");
   return KMV_OK;
@@ -562,38 +693,41 @@ kmv_status kmv_phi_refresh(kmv_handle h, const kmv_points* pts, int32_t chains, 
   if ((int64_t)chains * n_poles > (int64_t)1 << 20) return fail(h, KMV_EINVAL, "chains * n_poles too large");
   if (!(cg_tol > 0.0) || cg_maxiter < 1) return fail(h, KMV_EINVAL, "cg_tol must be > 0 and cg_maxiter >= 1");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  const int cp = chains * n_poles;
-  // size everything with the layout of the shifted systems (system s p = s N_p + p)
-  KMV_TRY(prepare_layout(h, pts, cp, st));
-  const int n_theta = h->layout.n_theta, n_items = h->layout.n_items;
-  const int64_t n_total = h->layout.n_total;
-  const int n_sys = h->layout.n_inst * chains, n_sysp = n_sys * n_poles;
+  KMV_TRY(prepare_layout(h, pts, chains, st));
+  const Layout& L = h->layout;
+  const int n_theta = L.n_theta, n_items = L.n_items;
+  const int64_t n_total = L.n_total;
+  const int n_sys = L.n_inst * chains;
+  const int64_t n_cols = (int64_t)n_sys * n_poles;
+  const bool refined = prec == KMV_BF16_HILO;
   Arena ar;
-  SolveLayout SL;
-  solve_layout(h->layout, ar, prec, SL);
-  const size_t vecp = sizeof(float) * (size_t)cp * std::max<int64_t>(1, n_total);
+  size_t ob[8], orf[8];
+  mcg_layout(L, n_poles, ar, ob);
+  if (refined) mcg_layout(L, n_poles, ar, orf);
   const size_t vec1 = sizeof(float) * (size_t)chains * std::max<int64_t>(1, n_total);
-  const size_t o_rhs = ar.take(vecp), o_x = ar.take(vecp);
-  const size_t o_thp = ar.take(sizeof(double) * (size_t)n_sysp * n_theta);
-  const size_t o_w = ar.take(sizeof(double) * (size_t)n_sysp);
+  const size_t o_x = ar.take(sizeof(float) * (size_t)chains * std::max<int64_t>(1, n_total) * n_poles);
+  const size_t o_sh = ar.take(sizeof(float) * (size_t)n_cols);
+  const size_t o_w = ar.take(sizeof(double) * (size_t)n_cols);
   const size_t o_bnd = ar.take(sizeof(double) * (size_t)n_sys);
-  const size_t o_stp = ar.take(sizeof(int32_t) * (size_t)n_sysp), o_itp = ar.take(sizeof(int32_t) * (size_t)n_sysp);
+  const size_t o_cst = ar.take(sizeof(int32_t) * (size_t)n_cols), o_cit = ar.take(sizeof(int32_t) * (size_t)n_cols);
+  const size_t o_prev = ar.take(sizeof(double) * (size_t)n_cols);
+  const size_t o_dx = refined ? ar.take(sizeof(float) * (size_t)chains * std::max<int64_t>(1, n_total) * n_poles) : 0;
   const size_t o_one = ar.take(vec1), o_y = ar.take(vec1);
   KMV_TRY(reserve(h, ar.used));
   char* base = static_cast<char*>(h->ws);
-  float* rhs_p = reinterpret_cast<float*>(base + o_rhs);
   float* x_p = reinterpret_cast<float*>(base + o_x);
-  double* theta_p = reinterpret_cast<double*>(base + o_thp);
+  float* shifts = reinterpret_cast<float*>(base + o_sh);
   double* weights = reinterpret_cast<double*>(base + o_w);
   double* bounds = reinterpret_cast<double*>(base + o_bnd);
-  int32_t* st_p = reinterpret_cast<int32_t*>(base + o_stp);
-  int32_t* it_p = reinterpret_cast<int32_t*>(base + o_itp);
+  int32_t* col_status = reinterpret_cast<int32_t*>(base + o_cst);
+  int32_t* col_iters = reinterpret_cast<int32_t*>(base + o_cit);
+  double* prev_rr = reinterpret_cast<double*>(base + o_prev);
+  float* dx = refined ? reinterpret_cast<float*>(base + o_dx) : nullptr;
   float* ones = reinterpret_cast<float*>(base + o_one);
   float* y1 = reinterpret_cast<float*>(base + o_y);
 
   // spectral interval [sigma^2, max row sum of A] from A 1 (App. A, read with the
   // exact row-sum bound); 1% slack covers the rounding of the product
-  KMV_TRY(prepare_layout(h, pts, chains, st));
   KMV_CUDA(h, launch_phi_fill(ones, (int64_t)chains * n_total, 1.0f, st));
   {
     KmvArgs a = base_args(h, pts, theta);
@@ -603,14 +737,18 @@ kmv_status kmv_phi_refresh(kmv_handle h, const kmv_points* pts, int32_t chains, 
     KMV_TRY(run_forward(h, a, prec, st));
   }
   KMV_CUDA(h, launch_phi_bounds(h->dev, n_sys, chains, n_total, y1, 1.01, bounds, st));
-  KMV_CUDA(h, launch_phi_poles(n_sys, n_theta, n_poles, theta, bounds, theta_p, weights, poles_out, st));
-  KMV_CUDA(h, launch_phi_rhs(h->dev, n_items, chains, n_poles, n_total, xi, rhs_p, st));
-  // the N_p shifted systems of every (instance, chain) in one batched solve
-  KMV_TRY(prepare_layout(h, pts, cp, st));
-  KMV_TRY(run_solve(h, pts, theta_p, rhs_p, n_total, x_p, cg_tol, cg_maxiter, 0, st_p, it_p, SL, prec, st));
-  KMV_TRY(prepare_layout(h, pts, chains, st));
+  KMV_CUDA(h, launch_phi_poles(n_sys, n_theta, n_poles, theta, bounds, shifts, weights, poles_out, st));
+  // the n_poles shifted systems of every (instance, chain) as the columns of one solve
+  if (refined) {
+    KMV_TRY(run_mcg_refined(h, pts, theta, shifts, n_poles, xi, x_p, cg_tol, cg_maxiter, col_status, col_iters,
+                            mcg_bufs(h, ob), mcg_bufs(h, orf), dx, prev_rr, st));
+  } else {
+    const McgBufs B = mcg_bufs(h, ob);
+    KMV_TRY(run_mcg(h, pts, theta, shifts, n_poles, xi, 0, x_p, cg_tol, cg_maxiter, 0, B, KMV_FP32, st));
+    KMV_CUDA(h, launch_mcg_finish(n_cols, B.cols, 0, col_status, col_iters, st));
+  }
   KMV_CUDA(h, launch_phi_combine(h->dev, n_items, chains, n_poles, n_total, weights, x_p, phi, st));
-  KMV_CUDA(h, launch_phi_status(n_sys, n_poles, st_p, it_p, chain_status, cg_iters, st));
+  KMV_CUDA(h, launch_phi_status(n_sys, n_poles, col_status, col_iters, chain_status, cg_iters, st));
   return KMV_OK;
 }
 

@@ -44,6 +44,13 @@ struct DevLayout {
   const int32_t* inst_item0 = nullptr;
 };
 
+// Per-(system, column) state of the multi-column CG (kmv_mcg.cu).
+struct McgCol {
+  double rr, bb, alpha, beta;
+  int32_t iters, status, active;
+  int32_t pad;  // refinement: 1 when the column's last correction is to be taken back
+};
+
 // Per-system CG state, kept in the handle workspace.
 struct CgSys {
   double rr, bb, pq, alpha, beta;
@@ -63,6 +70,7 @@ struct KmvArgs {
   const float* G;       // backward seed (chains, N, m)
   int m;
   const float* col_shift;
+  int col_shift_stride;  // 0: col_shift[c] for every system; else col_shift[s * stride + c]
   float* Y;             // forward output / backward dL/dV
   double* Y64;
   const int32_t* sys_active;   // optional mask: skip systems with 0
@@ -112,19 +120,45 @@ cudaError_t launch_refine_stagnation(int n_sys, int outer, const CgSys* sys, dou
                                      int32_t* n_active, double* worst, cudaStream_t st);
 cudaError_t launch_refine_finish(int n_sys, const int32_t* active, const CgSys* sys, int32_t* status,
                                  cudaStream_t st);
-// phi refresh (kmv_phi.cu): spectral interval, pole weights/shifts, replicated
-// right-hand sides, weighted sum of the shifted solutions, per-system status
+// phi refresh (kmv_phi.cu): spectral interval, pole weights/shifts, weighted
+// sum of the shifted solutions, per-system status
 cudaError_t launch_phi_fill(float* v, int64_t n, float val, cudaStream_t st);
 cudaError_t launch_phi_bounds(DevLayout L, int n_sys, int chains, int64_t n_total, const float* Y, double slack,
                               double* bounds, cudaStream_t st);
 cudaError_t launch_phi_poles(int n_sys, int n_theta, int n_poles, const double* theta, const double* bounds,
-                             double* theta_p, double* weights, double* poles_out, cudaStream_t st);
-cudaError_t launch_phi_rhs(DevLayout L, int n_items, int chains, int n_poles, int64_t n_total, const float* xi,
-                           float* rhs_p, cudaStream_t st);
+                             float* shifts, double* weights, double* poles_out, cudaStream_t st);
 cudaError_t launch_phi_combine(DevLayout L, int n_items, int chains, int n_poles, int64_t n_total,
                                const double* weights, const float* x_p, float* phi, cudaStream_t st);
-cudaError_t launch_phi_status(int n_sys, int n_poles, const int32_t* st_p, const int32_t* it_p, int32_t* status,
-                              int32_t* iters, cudaStream_t st);
+cudaError_t launch_phi_status(int n_sys, int n_poles, const int32_t* col_status, const int32_t* col_iters,
+                              int32_t* status, int32_t* iters, cudaStream_t st);
+
+// multi-column CG (kmv_mcg.cu)
+cudaError_t launch_mcg_init(const DevLayout& L, int n_items, int chains, int64_t n_total, int m, const float* b,
+                            int b_cols, const float* q, int warm, float* x, float* r, float* p, double* partial2,
+                            cudaStream_t st);
+cudaError_t launch_mcg_reduce_init(const DevLayout& L, int n_inst, int chains, int m, const double* partial2,
+                                   double tol, McgCol* st, int32_t* sys_any, int32_t* n_active, cudaStream_t s);
+cudaError_t launch_mcg_dot(const DevLayout& L, int n_items, int chains, int64_t n_total, int m, const float* p,
+                           const float* q, const int32_t* sys_any, double* partial, cudaStream_t st);
+cudaError_t launch_mcg_alpha(const DevLayout& L, int n_inst, int chains, int m, const double* partial, McgCol* st,
+                             const int32_t* sys_any, cudaStream_t s);
+cudaError_t launch_mcg_update_xr(const DevLayout& L, int n_items, int chains, int64_t n_total, int m,
+                                 const McgCol* stt, const int32_t* sys_any, float* x, float* r, const float* p,
+                                 const float* q, double* partial, cudaStream_t st);
+cudaError_t launch_mcg_beta(const DevLayout& L, int n_inst, int chains, int m, const double* partial, double tol,
+                            int maxiter, McgCol* st, int32_t* sys_any, int32_t* n_active, cudaStream_t s);
+cudaError_t launch_mcg_finish(int64_t n_cols, const McgCol* cols, int accumulate, int32_t* col_status,
+                              int32_t* col_iters, cudaStream_t st);
+cudaError_t launch_mcg_mask(const DevLayout& L, int n_items, int chains, int64_t n_total, int m, const McgCol* cols,
+                            float* r, cudaStream_t st);
+cudaError_t launch_mcg_refine(int64_t n_cols, int outer, McgCol* cols, double* prev_rr, int32_t* n_active,
+                              double* worst, cudaStream_t st);
+cudaError_t launch_mcg_undo(const DevLayout& L, int n_items, int chains, int64_t n_total, int m, const McgCol* cols,
+                            const float* dx, float* x, cudaStream_t st);
+cudaError_t launch_mcg_refine_finish(int64_t n_cols, const McgCol* cols, int32_t* col_status, cudaStream_t st);
+cudaError_t launch_mcg_update_p(const DevLayout& L, int n_items, int chains, int64_t n_total, int m,
+                                const McgCol* stt, const int32_t* sys_any, const float* r, float* p,
+                                cudaStream_t st);
 
 
 cudaError_t launch_lf_drift(int n_sys, int n_theta, const double* theta, const double* pi,

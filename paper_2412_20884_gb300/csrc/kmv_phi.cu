@@ -1,7 +1,7 @@
 // The Gibbs draw of the auxiliary variable, phi = A^{-1/2} xi (Sec. 3.1), by
 // the pole expansion of App. A: A^{-1/2} xi ~ sum_p w_p (A + lambda_p I)^{-1} xi.
 // Device kernels of kmv_phi_refresh (kmv_api.cu): the spectral interval, the
-// weights and shifts, the replicated right-hand sides and the weighted sum.
+// weights and shifts, and the weighted sum of the shifted solutions.
 #include <algorithm>
 #include <cmath>
 
@@ -77,11 +77,10 @@ __global__ void phi_bounds_kernel(DevLayout L, int chains, int64_t n_total, cons
 
 // Weights and shifts of App. A on [m, M] = [sigma_s^2, bounds[s]] (k^2 = m / M,
 // K' = K(1 - k^2), u_p = (p + 1/2) K' / N_p, (sn, cn, dn) at (u_p | 1 - k^2)):
-//   lambda_p = m (sn / cn)^2,  w_p = 2 K' sqrt(m) / (pi N_p) dn / cn^2,
-// and the parameters of the shifted systems: theta with sigma^2 -> sigma^2 + lambda_p.
-// One thread per system.
+//   lambda_p = m (sn / cn)^2,  w_p = 2 K' sqrt(m) / (pi N_p) dn / cn^2.
+// The shifts go to the column-shift table of the m = N_p product.  One thread per system.
 __global__ void phi_poles_kernel(int n_sys, int n_theta, int n_poles, const double* theta, const double* bounds,
-                                 double* theta_p, double* weights, double* poles_out) {
+                                 float* shifts, double* weights, double* poles_out) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= n_sys) return;
   const double* th = theta + (int64_t)s * n_theta;
@@ -100,8 +99,7 @@ __global__ void phi_poles_kernel(int n_sys, int n_theta, int n_poles, const doub
     const double lam = m_lo * (sn / cn) * (sn / cn);
     const double wgt = scale * dn / (cn * cn);
     const int64_t sp = (int64_t)s * n_poles + p;
-    for (int k = 0; k < n_theta - 1; ++k) theta_p[sp * n_theta + k] = th[k];
-    theta_p[sp * n_theta + n_theta - 1] = log(m_lo + lam);
+    shifts[sp] = (float)lam;
     weights[sp] = wgt;
     if (poles_out) {
       poles_out[(int64_t)s * (2 + 2 * n_poles) + 2 + p] = wgt;
@@ -115,17 +113,7 @@ __global__ void phi_fill_kernel(float* v, int64_t n, float val) {
     v[i] = val;
 }
 
-// rhs_p[c N_p + p, i] = xi[c, i]
-__global__ void phi_rhs_kernel(DevLayout L, int n_poles, int64_t n_total, const float* xi, float* rhs_p) {
-  const int item = blockIdx.x, c = blockIdx.y;
-  const int b = L.item_inst[item];
-  const int64_t i = L.item_row0[item] + threadIdx.x;
-  if (i >= L.offsets[b + 1]) return;
-  const float v = xi[(int64_t)c * n_total + i];
-  for (int p = 0; p < n_poles; ++p) rhs_p[((int64_t)c * n_poles + p) * n_total + i] = v;
-}
-
-// phi[c, i] = sum_p w_{s p} x_p[c N_p + p, i], summed in FP64 in the order p = 0, 1, ...
+// phi[c, i] = sum_p w_{s p} x[c, i, p], summed in FP64 in the order p = 0, 1, ...
 __global__ void phi_combine_kernel(DevLayout L, int chains, int n_poles, int64_t n_total, const double* weights,
                                    const float* x_p, float* phi) {
   const int item = blockIdx.x, c = blockIdx.y;
@@ -135,21 +123,21 @@ __global__ void phi_combine_kernel(DevLayout L, int chains, int n_poles, int64_t
   const int64_t s = (int64_t)b * chains + c;
   double acc = 0.0;
   for (int p = 0; p < n_poles; ++p)
-    acc += weights[s * n_poles + p] * (double)x_p[((int64_t)c * n_poles + p) * n_total + i];
+    acc += weights[s * n_poles + p] * (double)x_p[((int64_t)c * n_total + i) * n_poles + p];
   phi[(int64_t)c * n_total + i] = (float)acc;
 }
 
 // A system's draw is KMV_OK only if all its shifted solves converged; its
 // iteration count is the largest among them.
-__global__ void phi_status_kernel(int n_sys, int n_poles, const int32_t* st_p, const int32_t* it_p,
+__global__ void phi_status_kernel(int n_sys, int n_poles, const int32_t* col_status, const int32_t* col_iters,
                                   int32_t* status, int32_t* iters) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= n_sys) return;
   int32_t st = KMV_OK, it = 0;
   for (int p = 0; p < n_poles; ++p) {
-    const int32_t v = st_p[(int64_t)s * n_poles + p];
+    const int32_t v = col_status[(int64_t)s * n_poles + p];
     if (v != KMV_OK && st == KMV_OK) st = v;
-    it = max(it, it_p[(int64_t)s * n_poles + p]);
+    it = max(it, col_iters[(int64_t)s * n_poles + p]);
   }
   status[s] = st;
   if (iters) iters[s] = it;
@@ -171,16 +159,9 @@ cudaError_t launch_phi_bounds(DevLayout L, int n_sys, int chains, int64_t n_tota
 }
 
 cudaError_t launch_phi_poles(int n_sys, int n_theta, int n_poles, const double* theta, const double* bounds,
-                             double* theta_p, double* weights, double* poles_out, cudaStream_t st) {
-  phi_poles_kernel<<<(n_sys + 63) / 64, 64, 0, st>>>(n_sys, n_theta, n_poles, theta, bounds, theta_p, weights,
+                             float* shifts, double* weights, double* poles_out, cudaStream_t st) {
+  phi_poles_kernel<<<(n_sys + 63) / 64, 64, 0, st>>>(n_sys, n_theta, n_poles, theta, bounds, shifts, weights,
                                                      poles_out);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_phi_rhs(DevLayout L, int n_items, int chains, int n_poles, int64_t n_total, const float* xi,
-                           float* rhs_p, cudaStream_t st) {
-  if (n_items == 0) return cudaSuccess;
-  phi_rhs_kernel<<<dim3(n_items, chains), kTile, 0, st>>>(L, n_poles, n_total, xi, rhs_p);
   return cudaGetLastError();
 }
 
@@ -191,9 +172,9 @@ cudaError_t launch_phi_combine(DevLayout L, int n_items, int chains, int n_poles
   return cudaGetLastError();
 }
 
-cudaError_t launch_phi_status(int n_sys, int n_poles, const int32_t* st_p, const int32_t* it_p, int32_t* status,
-                              int32_t* iters, cudaStream_t st) {
-  phi_status_kernel<<<(n_sys + 127) / 128, 128, 0, st>>>(n_sys, n_poles, st_p, it_p, status, iters);
+cudaError_t launch_phi_status(int n_sys, int n_poles, const int32_t* col_status, const int32_t* col_iters,
+                              int32_t* status, int32_t* iters, cudaStream_t st) {
+  phi_status_kernel<<<(n_sys + 127) / 128, 128, 0, st>>>(n_sys, n_poles, col_status, col_iters, status, iters);
   return cudaGetLastError();
 }
 

@@ -96,7 +96,8 @@ __global__ void __launch_bounds__(kTile) fwd_simt_kernel(KmvArgs a) {
     for (int q = 0; q < MP; ++q) {
       if (q < mc) {
         const int64_t idx = (vbase + i) * a.m + c0 + q;
-        const double shift = a.col_shift ? (double)a.col_shift[c0 + q] : 0.0;
+        const double shift =
+            a.col_shift ? (double)a.col_shift[(int64_t)s * a.col_shift_stride + c0 + q] : 0.0;
         const double vi = (double)a.V[idx];
         const double y = alpha * acc64[q] + (s2 + shift) * vi;
         a.Y[idx] = (float)y;

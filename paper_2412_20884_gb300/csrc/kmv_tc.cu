@@ -807,7 +807,7 @@ __global__ void tc_fwd_epilogue_kernel(DevLayout L, TcTables T, KmvArgs a, int c
       for (int k = 0; k < nk; ++k) acc += part[((it0 + k) * 256 + rowp) * mz + q];
       const int col = c0 + q;
       const int64_t idx = ((int64_t)c * a.n_total + i) * a.m + col;
-      const double shift = a.col_shift ? (double)a.col_shift[col] : 0.0;
+      const double shift = a.col_shift ? (double)a.col_shift[(int64_t)s * a.col_shift_stride + col] : 0.0;
       const double vi = (double)a.V[idx];
       double y = alpha * acc / (double)col_scale(vmax[(int64_t)s * mz + q]) + (s2 + shift) * vi;
       if (bad) y = __longlong_as_double(0x7ff8000000000000ll);

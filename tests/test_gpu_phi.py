@@ -75,6 +75,34 @@ def test_phi_matches_inverse_square_root(kmv_handle, prec, n_poles):
             assert np.linalg.norm(phi[c, r0:r1] - exact) <= bound, (s, np.linalg.norm(phi[c, r0:r1] - exact), bound)
 
 
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("n_poles", [1, 2, 15])
+def test_phi_several_tiles_matches_pole_oracle(kmv_handle, prec, n_poles):
+    """Several row tiles with ragged tails, an empty instance and three chains:
+    phi against the oracle's expansion on the device's interval (dense FP64
+    solves of the n_poles shifted systems), within the CG tolerance's effect
+    and FP32 rounding.  n_poles 1 and 2 take the few-column product forms."""
+    w = wl.ragged([700, 0, 333], d=4, chains=3, m=1, ard=True, seed=57)
+    tol = 1e-6
+    xi, phi, st, it, pl = _draw(kmv_handle, w, prec, n_poles=n_poles, tol=tol)
+    assert np.all(st == 0)
+    X = f32(w.X)
+    for b in range(w.n_inst):
+        r0, r1 = w.offsets[b], w.offsets[b + 1]
+        for c in range(w.chains):
+            s = b * w.chains + c
+            if r1 == r0:
+                assert it[s] == 0
+                continue
+            assert it[s] > 0
+            A = sk.A_matrix(X[r0:r1], w.theta[s], True)
+            ref = poles.inv_sqrt_apply(A, xi[c, r0:r1].astype(np.float64), pl[s, 0], pl[s, 1], n_poles)
+            xn = np.linalg.norm(xi[c, r0:r1])
+            bound = 20 * tol * xn / math.sqrt(pl[s, 0]) + 1e-5 * np.linalg.norm(ref)
+            err = np.linalg.norm(phi[c, r0:r1] - ref)
+            assert err <= bound, (s, err, bound)
+
+
 def test_phi_invalid_arguments(kmv_handle):
     from paper_2412_20884_gb300 import KmvError
     w = wl.ragged([64], d=2, chains=1, m=1, ard=True, seed=55)
