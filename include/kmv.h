@@ -214,10 +214,12 @@ kmv_status kmv_energy(kmv_handle h, const kmv_points* pts, int32_t chains,
  * with weights and shifts from Jacobi elliptic functions on the spectral
  * interval [sigma_s^2, M_s], M_s = 1.01 max_i (A 1)_i (the largest row sum
  * bounds lambda_max because K0 >= 0 entrywise; 1% covers rounding).  The
- * n_poles shifted systems of every system are the n_poles columns of one
- * multi-column CG: one product with per-column shifts per iteration, each
- * column with its own CG scalars and its own stop at cg_tol (cold start; the
- * BF16 form by iterative refinement with FP32 residuals, as kmv_cg_solve).
+ * n_poles shifted systems of every system share xi, so one CG sequence on the
+ * smallest shift carries them all (multi-shift CG: the shifted iterates follow
+ * from its scalars), each shift stopping at cg_tol.  The BF16 form then checks
+ * every shifted solution with the FP32 operator and polishes those above
+ * cg_tol by refinement (FP32 residuals, corrections by a multi-column CG whose
+ * one product per iteration applies all the shifts as column shifts).
  *
  *   xi          DEVICE FP32 (chains, N_total): the caller's N(0, I) draw.
  *   phi         DEVICE FP32 (chains, N_total), written (must not alias xi).
@@ -227,8 +229,10 @@ kmv_status kmv_energy(kmv_handle h, const kmv_points* pts, int32_t chains,
  *   cg_iters    DEVICE int32 (n_inst * chains) or NULL: the largest iteration count.
  *   poles_out   DEVICE FP64 (n_inst * chains, 2 + 2 n_poles) or NULL:
  *               [sigma^2, M, w_1..w_Np, lambda_1..lambda_Np] per system.
- * Work: one N^2 pass for A 1, then one n_poles-column N^2 product per CG
- * iteration (a system drops out when all its columns have stopped).  Allocates workspace; not for use while the
+ * Work: one N^2 pass for A 1, then one single-column N^2 product per CG
+ * iteration (a system drops out when all its shifts have stopped); the BF16
+ * check costs one n_poles-column FP32 product per refinement step.
+ * cg_iters counts the multi-shift iterations plus the polishing ones.  Allocates workspace; not for use while the
  * stream is being captured (the work plan changes between the two phases).
  */
 kmv_status kmv_phi_refresh(kmv_handle h, const kmv_points* pts, int32_t chains,

@@ -513,7 +513,7 @@ kmv_status run_mcg(kmv_handle h, const kmv_points* pts, const double* theta, con
 // with the FP32 operator, correction by multi-column CG with the tensor-core
 // operator, until every column has converged or stagnated.
 kmv_status run_mcg_refined(kmv_handle h, const kmv_points* pts, const double* theta, const float* shifts, int m,
-                           const float* b, float* x, double tol, int maxiter, int32_t* col_status,
+                           const float* b, float* x, int warm, double tol, int maxiter, int32_t* col_status,
                            int32_t* col_iters, const McgBufs& B, const McgBufs& R, float* dx, double* prev_rr,
                            cudaStream_t st) {
   const Layout& L = h->layout;
@@ -524,9 +524,11 @@ kmv_status run_mcg_refined(kmv_handle h, const kmv_points* pts, const double* th
   const double floor_tol = (m <= 2 && x_width_fma_ok(pts->d)) ? 1e-5 : 1e-3;
   double* worst = reinterpret_cast<double*>(reinterpret_cast<char*>(R.n_active) + 8);
   const int max_outer = 12;
-  if (nvec > 0) KMV_CUDA(h, cudaMemsetAsync(x, 0, sizeof(float) * nvec, st));
-  KMV_CUDA(h, cudaMemsetAsync(col_status, 0, sizeof(int32_t) * n_cols, st));
-  KMV_CUDA(h, cudaMemsetAsync(col_iters, 0, sizeof(int32_t) * n_cols, st));
+  if (!warm) {
+    if (nvec > 0) KMV_CUDA(h, cudaMemsetAsync(x, 0, sizeof(float) * nvec, st));
+    KMV_CUDA(h, cudaMemsetAsync(col_status, 0, sizeof(int32_t) * n_cols, st));
+    KMV_CUDA(h, cudaMemsetAsync(col_iters, 0, sizeof(int32_t) * n_cols, st));
+  }
   KmvArgs a = base_args(h, pts, theta);
   a.m = m;
   a.col_shift = shifts;
@@ -556,6 +558,90 @@ kmv_status run_mcg_refined(kmv_handle h, const kmv_points* pts, const double* th
     KMV_CUDA(h, launch_mcg_finish(n_cols, B.cols, 1, col_status, col_iters, st));
   }
   KMV_CUDA(h, launch_mcg_refine_finish(n_cols, R.cols, col_status, st));
+  return KMV_OK;
+}
+
+// --- multi-shift CG: all shifts from one Krylov sequence per system ------------------
+
+struct MscgBufs {
+  float *r, *p, *q, *ps;
+  double* partial;
+  MscgSys* sys;
+  MscgShift* sh;
+  float* base;
+  int32_t *sys_active, *n_active;
+};
+
+void mscg_layout(const Layout& L, int m, Arena& ar, size_t off[10]) {
+  const size_t vec = sizeof(float) * (size_t)L.chains * std::max<int64_t>(1, L.n_total);
+  const size_t items = (size_t)std::max(1, L.n_items) * L.chains;
+  const size_t n_sys = (size_t)L.n_inst * L.chains;
+  off[0] = ar.take(vec);
+  off[1] = ar.take(vec);
+  off[2] = ar.take(vec);
+  off[3] = ar.take(vec * m);
+  off[4] = ar.take(sizeof(double) * items);
+  off[5] = ar.take(sizeof(MscgSys) * n_sys);
+  off[6] = ar.take(sizeof(MscgShift) * n_sys * m);
+  off[7] = ar.take(sizeof(float) * n_sys);
+  off[8] = ar.take(sizeof(int32_t) * n_sys);
+  off[9] = ar.take(sizeof(int32_t) * 4);
+}
+
+MscgBufs mscg_bufs(kmv_handle h, const size_t off[10]) {
+  MscgBufs b;
+  b.r = at<float>(h, off[0]);
+  b.p = at<float>(h, off[1]);
+  b.q = at<float>(h, off[2]);
+  b.ps = at<float>(h, off[3]);
+  b.partial = at<double>(h, off[4]);
+  b.sys = at<MscgSys>(h, off[5]);
+  b.sh = at<MscgShift>(h, off[6]);
+  b.base = at<float>(h, off[7]);
+  b.sys_active = at<int32_t>(h, off[8]);
+  b.n_active = at<int32_t>(h, off[9]);
+  return b;
+}
+
+// (A(theta_s) + shifts[s m + j] I) x_j = b for the m shifts of every system,
+// cold start, by multi-shift CG: one m = 1 product with the base (smallest)
+// shift per iteration.  x is (chains, N, m); per-shift results go to
+// col_status / col_iters (n_sys * m).
+kmv_status run_mscg(kmv_handle h, const kmv_points* pts, const double* theta, const float* shifts, int m,
+                    const float* b, float* x, double tol, int maxiter, int32_t* col_status, int32_t* col_iters,
+                    const MscgBufs& B, kmv_precision prec, cudaStream_t st) {
+  const Layout& L = h->layout;
+  const int64_t n_cols = (int64_t)L.n_inst * L.chains * m;
+  KMV_CUDA(h, launch_mscg_init(h->dev, L.n_items, L.chains, L.n_total, m, b, B.r, B.p, x, B.ps, B.partial, st));
+  KMV_CUDA(h, cudaMemsetAsync(B.n_active, 0, sizeof(int32_t), st));
+  KMV_CUDA(h, launch_mscg_setup(h->dev, L.n_inst, L.chains, m, B.partial, shifts, tol, B.sys, B.sh, B.base,
+                                B.sys_active, B.n_active, st));
+  KmvArgs a = base_args(h, pts, theta);
+  a.m = 1;
+  a.col_shift = B.base;
+  a.col_shift_stride = 1;
+  a.V = B.p;
+  a.Y = B.q;
+  a.sys_active = B.sys_active;
+  a.dot_partial = B.partial;
+  const int check_every = 4;
+  for (int it = 0; it < maxiter; ++it) {
+    if (it % check_every == 0) {
+      KMV_CUDA(h, cudaMemcpyAsync(h->host_flag, B.n_active, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+      KMV_CUDA(h, cudaStreamSynchronize(st));
+      if (*h->host_flag == 0) break;
+    }
+    KMV_TRY(run_forward(h, a, prec, st));
+    KMV_CUDA(h, launch_mscg_alpha(h->dev, L.n_inst, L.chains, m, B.partial, B.sys, B.sh, B.sys_active, st));
+    KMV_CUDA(h, launch_mscg_update_xr(h->dev, L.n_items, L.chains, L.n_total, m, B.sys, B.sh, B.sys_active, B.r,
+                                      B.q, x, B.ps, B.partial, st));
+    KMV_CUDA(h, cudaMemsetAsync(B.n_active, 0, sizeof(int32_t), st));
+    KMV_CUDA(h, launch_mscg_beta(h->dev, L.n_inst, L.chains, m, B.partial, tol, maxiter, B.sys, B.sh, B.sys_active,
+                                 B.n_active, st));
+    KMV_CUDA(h, launch_mscg_update_p(h->dev, L.n_items, L.chains, L.n_total, m, B.sys, B.sh, B.sys_active, B.r, B.p,
+                                     B.ps, st));
+  }
+  KMV_CUDA(h, launch_mscg_finish(n_cols, B.sh, col_status, col_iters, st));
   return KMV_OK;
 }
 
@@ -701,9 +787,12 @@ kmv_status kmv_phi_refresh(kmv_handle h, const kmv_points* pts, int32_t chains, 
   const int64_t n_cols = (int64_t)n_sys * n_poles;
   const bool refined = prec == KMV_BF16_HILO;
   Arena ar;
-  size_t ob[8], orf[8];
-  mcg_layout(L, n_poles, ar, ob);
-  if (refined) mcg_layout(L, n_poles, ar, orf);
+  size_t ob[8], orf[8], oms[10];
+  mscg_layout(L, n_poles, ar, oms);
+  if (refined) {
+    mcg_layout(L, n_poles, ar, ob);
+    mcg_layout(L, n_poles, ar, orf);
+  }
   const size_t vec1 = sizeof(float) * (size_t)chains * std::max<int64_t>(1, n_total);
   const size_t o_x = ar.take(sizeof(float) * (size_t)chains * std::max<int64_t>(1, n_total) * n_poles);
   const size_t o_sh = ar.take(sizeof(float) * (size_t)n_cols);
@@ -738,14 +827,14 @@ kmv_status kmv_phi_refresh(kmv_handle h, const kmv_points* pts, int32_t chains, 
   }
   KMV_CUDA(h, launch_phi_bounds(h->dev, n_sys, chains, n_total, y1, 1.01, bounds, st));
   KMV_CUDA(h, launch_phi_poles(n_sys, n_theta, n_poles, theta, bounds, shifts, weights, poles_out, st));
-  // the n_poles shifted systems of every (instance, chain) as the columns of one solve
+  // the n_poles shifted systems of every (instance, chain) from one Krylov sequence
+  KMV_TRY(run_mscg(h, pts, theta, shifts, n_poles, xi, x_p, cg_tol, cg_maxiter, col_status, col_iters,
+                   mscg_bufs(h, oms), prec, st));
   if (refined) {
-    KMV_TRY(run_mcg_refined(h, pts, theta, shifts, n_poles, xi, x_p, cg_tol, cg_maxiter, col_status, col_iters,
+    // the BF16 operator leaves the shifted solves at its own accuracy: polish each
+    // to cg_tol by refinement with FP32 residuals (a check only, where they are there)
+    KMV_TRY(run_mcg_refined(h, pts, theta, shifts, n_poles, xi, x_p, 1, cg_tol, cg_maxiter, col_status, col_iters,
                             mcg_bufs(h, ob), mcg_bufs(h, orf), dx, prev_rr, st));
-  } else {
-    const McgBufs B = mcg_bufs(h, ob);
-    KMV_TRY(run_mcg(h, pts, theta, shifts, n_poles, xi, 0, x_p, cg_tol, cg_maxiter, 0, B, KMV_FP32, st));
-    KMV_CUDA(h, launch_mcg_finish(n_cols, B.cols, 0, col_status, col_iters, st));
   }
   KMV_CUDA(h, launch_phi_combine(h->dev, n_items, chains, n_poles, n_total, weights, x_p, phi, st));
   KMV_CUDA(h, launch_phi_status(n_sys, n_poles, col_status, col_iters, chain_status, cg_iters, st));

@@ -51,6 +51,17 @@ struct McgCol {
   int32_t pad;  // refinement: 1 when the column's last correction is to be taken back
 };
 
+// Multi-shift CG state (kmv_mscg.cu): per system, and per (system, shift).
+constexpr int kMaxShifts = 32;
+struct MscgSys {
+  double rr, bb, alpha, beta, alpha_prev, beta_prev;
+  int32_t iters, pad;
+};
+struct MscgShift {
+  double sigma, zeta, zeta_prev, zeta_next, alpha_s, beta_s;
+  int32_t active, iters, status, pad;
+};
+
 // Per-system CG state, kept in the handle workspace.
 struct CgSys {
   double rr, bb, pq, alpha, beta;
@@ -131,6 +142,26 @@ cudaError_t launch_phi_combine(DevLayout L, int n_items, int chains, int n_poles
                                const double* weights, const float* x_p, float* phi, cudaStream_t st);
 cudaError_t launch_phi_status(int n_sys, int n_poles, const int32_t* col_status, const int32_t* col_iters,
                               int32_t* status, int32_t* iters, cudaStream_t st);
+
+// multi-shift CG (kmv_mscg.cu)
+cudaError_t launch_mscg_init(const DevLayout& L, int n_items, int chains, int64_t n_total, int m, const float* b,
+                             float* r, float* p, float* xs, float* ps, double* partial, cudaStream_t st);
+cudaError_t launch_mscg_setup(const DevLayout& L, int n_inst, int chains, int m, const double* partial,
+                              const float* shifts, double tol, MscgSys* sys, MscgShift* sh, float* base_shift,
+                              int32_t* sys_active, int32_t* n_active, cudaStream_t st);
+cudaError_t launch_mscg_alpha(const DevLayout& L, int n_inst, int chains, int m, const double* partial, MscgSys* sys,
+                              MscgShift* sh, int32_t* sys_active, cudaStream_t st);
+cudaError_t launch_mscg_update_xr(const DevLayout& L, int n_items, int chains, int64_t n_total, int m,
+                                  const MscgSys* sys, const MscgShift* sh, const int32_t* sys_active, float* r,
+                                  const float* q, float* xs, const float* ps, double* partial, cudaStream_t st);
+cudaError_t launch_mscg_beta(const DevLayout& L, int n_inst, int chains, int m, const double* partial, double tol,
+                             int maxiter, MscgSys* sys, MscgShift* sh, int32_t* sys_active, int32_t* n_active,
+                             cudaStream_t st);
+cudaError_t launch_mscg_update_p(const DevLayout& L, int n_items, int chains, int64_t n_total, int m,
+                                 const MscgSys* sys, const MscgShift* sh, const int32_t* sys_active, const float* r,
+                                 float* p, float* ps, cudaStream_t st);
+cudaError_t launch_mscg_finish(int64_t n_cols, const MscgShift* sh, int32_t* col_status, int32_t* col_iters,
+                               cudaStream_t st);
 
 // multi-column CG (kmv_mcg.cu)
 cudaError_t launch_mcg_init(const DevLayout& L, int n_items, int chains, int64_t n_total, int m, const float* b,
