@@ -19,6 +19,10 @@ Definitions followed:
   * Algorithm 1      : one update = draw xi, form phi, draw pi, integrate N_int steps,
                        Metropolis test against a uniform X <= acceptance.
 
+Kernel family: ``kern`` = None is the stationary SE kernel of oracle/se_kernel.py;
+otherwise a pair (A_fn, dA_fn) of callables (X, theta) -> A and -> [dA/dtheta_p]
+(e.g. the Chebyshev-amplitude family of oracle/cheb_kernel.py).
+
 Prior: ``None`` is the paper's flat prior (S = 0).  A dict {"mu", "prec"} gives
 the diagonal Gaussian S = sum prec (theta - mu)^2 / 2 used by the tiny-N test.
 ``free`` marks which components move (the paper fixes sigma or l at times);
@@ -34,6 +38,14 @@ import numpy as np
 import scipy.linalg as sla
 
 from .se_kernel import A_matrix, dA_dtheta
+
+
+def _A(X, theta, ard, kern):
+    return A_matrix(X, theta, ard) if kern is None else kern[0](X, theta)
+
+
+def _dA(X, theta, ard, kern):
+    return dA_dtheta(X, theta, ard) if kern is None else kern[1](X, theta)
 
 
 def prior_S(theta, prior):
@@ -56,37 +68,37 @@ def solve(X, theta, y, ard):
     return sla.cho_solve(sla.cho_factor(A, lower=True), np.asarray(y, np.float64))
 
 
-def potential(X, y, phi, theta, ard, prior=None):
+def potential(X, y, phi, theta, ard, prior=None, kern=None):
     """U_phi(theta) of Eq. U."""
-    A = A_matrix(X, theta, ard)
+    A = _A(X, theta, ard, kern)
     x = sla.cho_solve(sla.cho_factor(A, lower=True), y)
     return prior_S(theta, prior) + 0.5 * float(y @ x) + 0.5 * float(phi @ A @ phi)
 
 
-def force(X, y, phi, theta, ard, prior=None):
+def force(X, y, phi, theta, ard, prior=None, kern=None):
     """F_phi(theta) = grad U by the direct expression of Sec. 3.2.1."""
-    A = A_matrix(X, theta, ard)
+    A = _A(X, theta, ard, kern)
     x = sla.cho_solve(sla.cho_factor(A, lower=True), y)
-    mats = dA_dtheta(X, theta, ard)
+    mats = _dA(X, theta, ard, kern)
     F = prior_grad(theta, prior)
     for p, M in enumerate(mats):
         F[p] += -0.5 * float(x @ M @ x) + 0.5 * float(phi @ M @ phi)
     return F
 
 
-def hamiltonian(X, y, phi, theta, pi, ard, prior=None):
+def hamiltonian(X, y, phi, theta, pi, ard, prior=None, kern=None):
     pi = np.asarray(pi, np.float64)
-    return potential(X, y, phi, theta, ard, prior) + 0.5 * float(pi @ pi)
+    return potential(X, y, phi, theta, ard, prior, kern) + 0.5 * float(pi @ pi)
 
 
-def leapfrog(X, y, phi, theta, pi, dt, ard, prior=None, free=None, n_steps=1):
+def leapfrog(X, y, phi, theta, pi, dt, ard, prior=None, free=None, n_steps=1, kern=None):
     """n_steps of the drift-kick-drift map of Sec. 3.2.2, drifts not merged."""
     theta = np.array(theta, np.float64)
     pi = np.array(pi, np.float64)
     mask = np.ones_like(theta) if free is None else np.asarray(free, np.float64)
     for _ in range(n_steps):
         theta_half = theta + 0.5 * dt * pi * mask
-        F = force(X, y, phi, theta_half, ard, prior)
+        F = force(X, y, phi, theta_half, ard, prior, kern)
         pi = pi - dt * F * mask
         theta = theta_half + 0.5 * dt * pi * mask
     return theta, pi
