@@ -13,6 +13,17 @@
  *     theta[s, :] = [log alpha, log l_1 .. log l_k, log sigma^2],
  *     n_theta = 2 + (ard ? d : 1),   s = b * chains + c.
  *
+ * Kernel family of Sec. 4 (kmv_points.cheb = N_cheb >= 1): the squared
+ * exponential with a non-stationary vertical scale,
+ *     K_ij = exp(C(x_i)) exp(C(x_j)) exp(-1/2 sum_k (x_ik - x_jk)^2 / l_k^2),
+ *     C(x) = sum_t Theta_t T_{t_1}(x_1) .. T_{t_d}(x_d),  t in [0, N_cheb)^d,
+ * T_n the Chebyshev polynomials of the first kind (points meant to lie in
+ * [-1, 1]^d), with
+ *     theta[s, :] = [Theta (N_cheb^d, row-major, t_1 slowest), log l_1 .. log l_k,
+ *                    log sigma^2],   n_theta = N_cheb^d + (ard ? d : 1) + 1.
+ * Every entry point takes this family; gradients give d/dTheta_t =
+ * sum_ij (G V^T)_ij (T_t(x_i) + T_t(x_j)) K_ij in place of d/dlog alpha.
+ *
  * Common conventions
  *   - Every pointer documented DEVICE is caller-owned device memory on the
  *     handle's device; HOST pointers are read during the call only.  The
@@ -75,6 +86,9 @@ typedef struct {
   int32_t d;               /* input dimension, 1 <= d <= 64 */
   int32_t ard;             /* 0: isotropic kernel, 1: one lengthscale per dimension */
   const float* x;          /* DEVICE, (N_total, d) row-major input points */
+  int32_t cheb;            /* 0: the SE kernel of Sec. 1; N_cheb in [1, 32]: the
+                              Chebyshev-amplitude family above (N_cheb^d <= 1024,
+                              d <= 8 when N_cheb >= 2) */
 } kmv_points;
 
 /* Create a handle bound to CUDA device `device` (made current by every call). */
@@ -284,7 +298,8 @@ kmv_status kmv_profile_read(kmv_handle h, int32_t kind, double* total_ms, int64_
  *   Concurrency: every call on a device shares the one array; calls whose
  *     work overlaps on the GPU (other streams, other host threads) race and
  *     must be ordered by the caller.
- *   Errors: KMV_EINVAL (bad argument or scratch limit exceeded), KMV_ECUDA.
+ *   Errors: KMV_EINVAL (bad argument or scratch limit exceeded), KMV_ECUDA,
+ *     KMV_EUNSUPPORTED for the Chebyshev-amplitude family (pts->cheb != 0).
  */
 kmv_status kmv_backward_noalloc(const kmv_points* pts, int32_t chains, const double* theta,
                                 const float* V, const float* G, int32_t m, double* grad_theta,

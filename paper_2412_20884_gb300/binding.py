@@ -33,7 +33,7 @@ class KmvError(RuntimeError):
 
 class _Points(C.Structure):
     _fields_ = [("n_inst", C.c_int32), ("offsets", C.POINTER(C.c_int64)), ("d", C.c_int32),
-                ("ard", C.c_int32), ("x", C.c_void_p)]
+                ("ard", C.c_int32), ("x", C.c_void_p), ("cheb", C.c_int32)]
 
 
 _P = C.c_void_p
@@ -103,9 +103,12 @@ def _need(t, dtype, name, shape=None):
 
 
 class Points:
-    """A point set: instances concatenated along rows of x (N_total, d)."""
+    """A point set: instances concatenated along rows of x (N_total, d).
 
-    def __init__(self, x: torch.Tensor, offsets=None, ard: bool = True):
+    cheb = N_cheb >= 1 selects the Chebyshev log-amplitude kernel of Sec. 4, with
+    theta rows [Theta (N_cheb^d), log l (1 or d), log sigma^2]; 0 is the SE kernel."""
+
+    def __init__(self, x: torch.Tensor, offsets=None, ard: bool = True, cheb: int = 0):
         _need(x, torch.float32, "x")
         if x.dim() != 2:
             raise ValueError("x must be (N_total, d)")
@@ -119,9 +122,11 @@ class Points:
         self.d = x.shape[1]
         self.n_inst = len(off) - 1
         self.n_total = n
-        self.n_theta = 2 + (self.d if self.ard else 1)
+        self.cheb = int(cheb)
+        k = self.d if self.ard else 1
+        self.n_theta = (self.cheb ** self.d + k + 1) if self.cheb else 2 + k
         self._c = _Points(self.n_inst, self.offsets.ctypes.data_as(C.POINTER(C.c_int64)), self.d,
-                          int(self.ard), C.c_void_p(x.data_ptr()))
+                          int(self.ard), C.c_void_p(x.data_ptr()), self.cheb)
 
     @property
     def c(self):

@@ -83,6 +83,10 @@ kmv_status check_points(kmv_handle h, const kmv_points* pts, int32_t chains) {
   if (n > (int64_t(1) << 40)) return fail(h, KMV_EINVAL, "too many rows");
   if (n > 0 && !pts->x) return fail(h, KMV_EINVAL, "x is NULL");
   if ((int64_t)pts->n_inst * chains > (int64_t(1) << 30)) return fail(h, KMV_EINVAL, "too many systems");
+  if (pts->cheb < 0 || pts->cheb > kMaxChebOrder) return fail(h, KMV_EINVAL, "cheb must be in [0, 32]");
+  if (pts->cheb > 1 && pts->d > kMaxChebDims) return fail(h, KMV_EINVAL, "cheb >= 2 needs d <= 8");
+  if (pts->cheb > 0 && cheb_n_coef(pts->cheb, pts->d) < 0)
+    return fail(h, KMV_EINVAL, "cheb^d must be <= 1024");
   return KMV_OK;
 }
 
@@ -99,7 +103,10 @@ kmv_status prepare_layout(kmv_handle h, const kmv_points* pts, int32_t chains, c
   L.chains = chains;
   L.d = pts->d;
   L.ard = pts->ard;
-  L.n_theta = 2 + (pts->ard ? pts->d : 1);
+  L.cheb = pts->cheb;
+  L.n_coef = pts->cheb > 0 ? cheb_n_coef(pts->cheb, pts->d) : 0;
+  L.n_theta_int = 2 + (pts->ard ? pts->d : 1);
+  L.n_theta = L.cheb ? L.n_coef + L.n_theta_int - 1 : L.n_theta_int;
   if (same) return KMV_OK;
   if (h->capturing)
     return fail(h, KMV_EINVAL, "new point layout during stream capture: make the same call once before capturing");
@@ -179,7 +186,58 @@ KmvArgs base_args(kmv_handle h, const kmv_points* pts, const double* theta) {
   a.x = pts->x;
   a.theta = theta;
   a.n_z = 1;
+  if (h->layout.cheb) {
+    // the Chebyshev family runs as the stationary kernel between amplitudes,
+    // prepared from this theta by cheb_prepare
+    a.theta = h->cheb_theta;
+    a.n_theta = h->layout.n_theta_int;
+    a.amp = h->cheb_amp;
+  }
   return a;
+}
+
+// For the Chebyshev family: the internal stationary parameters and the per-point
+// amplitudes exp(C_theta(x)) of theta (user layout), plus the backward's scratch
+// for up to m_bwd columns.  A no-op for the SE kernel.
+kmv_status cheb_prepare(kmv_handle h, const kmv_points* pts, const double* theta, int m_bwd, cudaStream_t st) {
+  const Layout& L = h->layout;
+  if (!L.cheb) return KMV_OK;
+  const size_t n_sys = (size_t)L.n_inst * L.chains;
+  const size_t vec = (size_t)L.chains * std::max<int64_t>(1, L.n_total);
+  const size_t items = (size_t)std::max(1, L.n_items) * L.chains;
+  Arena ar;
+  const size_t o_th = ar.take(sizeof(double) * n_sys * L.n_theta_int);
+  const size_t o_amp = ar.take(sizeof(float) * vec);
+  const size_t o_gi = ar.take(sizeof(double) * n_sys * L.n_theta_int);
+  const size_t o_pt = ar.take(sizeof(double) * items * L.n_coef);
+  const size_t o_kv = ar.take(sizeof(float) * vec * std::max(1, m_bwd));
+  const size_t o_kg = ar.take(sizeof(float) * vec * std::max(1, m_bwd));
+  if (ar.used > h->cheb_bytes) {
+    if (h->capturing)
+      return fail(h, KMV_EINVAL, "workspace would grow during stream capture: make the same call once before capturing");
+    if (h->cheb_buf) {
+      KMV_CUDA(h, cudaDeviceSynchronize());
+      KMV_CUDA(h, cudaFree(h->cheb_buf));
+      h->cheb_buf = nullptr;
+      h->cheb_bytes = 0;
+    }
+    if (cudaMalloc(&h->cheb_buf, ar.used) != cudaSuccess) {
+      cudaGetLastError();
+      h->cheb_buf = nullptr;
+      return fail(h, KMV_ENOMEM, "amplitude buffer allocation failed");
+    }
+    h->cheb_bytes = ar.used;
+  }
+  char* base = static_cast<char*>(h->cheb_buf);
+  h->cheb_theta = reinterpret_cast<double*>(base + o_th);
+  h->cheb_amp = reinterpret_cast<float*>(base + o_amp);
+  h->cheb_gint = reinterpret_cast<double*>(base + o_gi);
+  h->cheb_part = reinterpret_cast<double*>(base + o_pt);
+  h->cheb_kv = reinterpret_cast<float*>(base + o_kv);
+  h->cheb_kg = reinterpret_cast<float*>(base + o_kg);
+  KMV_CUDA(h, launch_cheb_prepare(h->dev, L.n_items, (int)n_sys, L.chains, L.n_total, L.d, L.cheb, L.n_coef,
+                                  L.n_theta, L.n_theta_int, pts->x, theta, h->cheb_theta, h->cheb_amp, st));
+  return KMV_OK;
 }
 
 // --- building blocks used by several entry points -------------------------------------
@@ -203,8 +261,8 @@ size_t backward_ws_bytes(const Layout& L, int m) {
   return sizeof(double) * (size_t)std::max(1, L.n_items) * L.chains * nz * L.n_theta;
 }
 
-kmv_status run_backward(kmv_handle h, KmvArgs a, double* grad, double* partial,
-                        kmv_precision prec, cudaStream_t st) {
+kmv_status run_backward_stationary(kmv_handle h, KmvArgs a, double* grad, double* partial,
+                                   kmv_precision prec, cudaStream_t st) {
   const Layout& L = h->layout;
   if (prec == KMV_BF16_HILO) {
     // shapes outside the tensor-core adjoint's range (d > 15, or operand
@@ -219,8 +277,36 @@ kmv_status run_backward(kmv_handle h, KmvArgs a, double* grad, double* partial,
     ProfScope prof(h, KMV_KERNEL_ADJOINT, st);
     KMV_CUDA(h, launch_backward_simt(a, L.n_items, st));
   }
-  KMV_CUDA(h, launch_grad_finalize(h->dev, L.n_inst, L.chains, L.n_theta, L.ard, L.d, a.n_z,
+  KMV_CUDA(h, launch_grad_finalize(h->dev, L.n_inst, L.chains, a.n_theta, L.ard, L.d, a.n_z,
                                    a.theta, partial, grad, st));
+  return KMV_OK;
+}
+
+// Adjoint of sum G o (A V) with args from base_args; grad in the caller's theta layout.
+// For the Chebyshev family the stationary adjoint (with amplitudes) gives the
+// lengthscale and noise entries, and the Theta entries are sum_i T_t(x_i) h_i with
+// h = G o (K V) + V o (K G) summed over columns (K without the noise term).
+kmv_status run_backward(kmv_handle h, KmvArgs a, double* grad, double* partial,
+                        kmv_precision prec, cudaStream_t st) {
+  const Layout& L = h->layout;
+  if (!L.cheb) return run_backward_stationary(h, a, grad, partial, prec, st);
+  KMV_TRY(run_backward_stationary(h, a, h->cheb_gint, partial, prec, st));
+  KmvArgs f = a;
+  f.G = nullptr;
+  f.col_shift = nullptr;
+  f.Y64 = nullptr;
+  f.dot_partial = nullptr;
+  f.grad_partial = nullptr;
+  f.no_diag = 1;
+  f.V = a.V;
+  f.Y = h->cheb_kv;
+  KMV_TRY(run_forward(h, f, prec, st));
+  f.V = a.G;
+  f.Y = h->cheb_kg;
+  KMV_TRY(run_forward(h, f, prec, st));
+  KMV_CUDA(h, launch_cheb_grad(h->dev, L.n_items, L.n_inst, L.chains, L.n_total, L.d, L.cheb, L.n_coef, L.n_theta,
+                               L.n_theta_int, a.m, a.x, a.V, a.G, h->cheb_kv, h->cheb_kg, a.sys_active,
+                               h->cheb_part, h->cheb_gint, grad, st));
   return KMV_OK;
 }
 
@@ -684,6 +770,7 @@ kmv_status kmv_destroy(kmv_handle h) {
   tc_release(h);
   if (h->ws) cudaFree(h->ws);
   if (h->tables) cudaFree(h->tables);
+  if (h->cheb_buf) cudaFree(h->cheb_buf);
   if (h->host_flag) cudaFreeHost(h->host_flag);
   kmv_profile_enable(h, 0);
   for (cudaEvent_t e : h->prof_pool) cudaEventDestroy(e);
@@ -708,7 +795,7 @@ const char* kmv_status_string(kmv_status s) {
 const char* kmv_last_error(kmv_handle h) { return h ? h->last_error.c_str() : ""; }
 
 int64_t kmv_workspace_bytes(kmv_handle h) {
-  return h ? (int64_t)(h->ws_bytes + h->tables_bytes + tc_workspace_bytes(h)) : 0;
+  return h ? (int64_t)(h->ws_bytes + h->tables_bytes + h->cheb_bytes + tc_workspace_bytes(h)) : 0;
 }
 
 kmv_status kmv_forward(kmv_handle h, const kmv_points* pts, int32_t chains, const double* theta,
@@ -721,6 +808,7 @@ kmv_status kmv_forward(kmv_handle h, const kmv_points* pts, int32_t chains, cons
   if ((const void*)V == (const void*)Y) return fail(h, KMV_EINVAL, "Y must not alias V");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   KMV_TRY(prepare_layout(h, pts, chains, st));
+  KMV_TRY(cheb_prepare(h, pts, theta, 0, st));
   KmvArgs a = base_args(h, pts, theta);
   a.V = V;
   a.m = m;
@@ -742,6 +830,7 @@ kmv_status kmv_backward(kmv_handle h, const kmv_points* pts, int32_t chains, con
   Arena ar;
   const size_t o_part = ar.take(backward_ws_bytes(h->layout, m));
   KMV_TRY(reserve(h, ar.used));
+  KMV_TRY(cheb_prepare(h, pts, theta, m, st));
   KmvArgs a = base_args(h, pts, theta);
   a.V = V;
   a.G = G;
@@ -764,6 +853,7 @@ kmv_status kmv_cg_solve(kmv_handle h, const kmv_points* pts, int32_t chains, con
   SolveLayout SL;
   solve_layout(h->layout, ar, prec, SL);
   KMV_TRY(reserve(h, ar.used));
+  KMV_TRY(cheb_prepare(h, pts, theta, 0, st));
   const int64_t stride = rhs_per_chain ? h->layout.n_total : 0;
   return run_solve(h, pts, theta, rhs, stride, x, tol, maxiter, warm_start, chain_status, iters, SL, prec, st);
 }
@@ -814,6 +904,7 @@ kmv_status kmv_phi_refresh(kmv_handle h, const kmv_points* pts, int32_t chains, 
   float* dx = refined ? reinterpret_cast<float*>(base + o_dx) : nullptr;
   float* ones = reinterpret_cast<float*>(base + o_one);
   float* y1 = reinterpret_cast<float*>(base + o_y);
+  KMV_TRY(cheb_prepare(h, pts, theta, 0, st));
 
   // spectral interval [sigma^2, max row sum of A] from A 1 (App. A, read with the
   // exact row-sum bound); 1% slack covers the rounding of the product
@@ -873,6 +964,7 @@ kmv_status leapfrog_step(kmv_handle h, const kmv_points* pts, int32_t chains, co
 
   // drift: theta_h = theta + dt/2 pi
   KMV_CUDA(h, launch_lf_drift(n_sys, L.n_theta, theta, pi, free_mask, 0.5 * dt, theta_h, st));
+  KMV_TRY(cheb_prepare(h, pts, theta_h, 2, st));
   // x = A(theta_h)^{-1} y, cold start (keeps the force a function of theta_h only)
   KMV_TRY(run_solve(h, pts, theta_h, y, 0, x_work, cg_tol, cg_maxiter, 0, chain_status, cg_iters, SL, prec, st));
   // force: d/dtheta [-x^T A x / 2 + phi^T A phi / 2] at frozen x (Eq. u)
@@ -916,6 +1008,7 @@ kmv_status kmv_energy(kmv_handle h, const kmv_points* pts, int32_t chains, const
   const size_t o_p1 = ar.take(sizeof(double) * items);
   const size_t o_p2 = ar.take(sizeof(double) * items);
   KMV_TRY(reserve(h, ar.used));
+  KMV_TRY(cheb_prepare(h, pts, theta, 0, st));
   KMV_TRY(run_solve(h, pts, theta, y, 0, x_work, cg_tol, cg_maxiter, 0, chain_status, cg_iters, SL, prec, st));
   KmvArgs a = base_args(h, pts, theta);
   a.V = phi;

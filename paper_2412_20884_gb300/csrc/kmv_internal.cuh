@@ -27,6 +27,9 @@ constexpr int kFoldTiles = 4;
 // Host description of one call's point set and its row-tile work items.
 struct Layout {
   int n_inst = 0, chains = 0, d = 0, ard = 0, n_theta = 0;
+  // Chebyshev-amplitude family (Sec. 4): N_cheb (0: the SE kernel of Sec. 1),
+  // N_cheb^d coefficients, and the stationary parameter count used inside
+  int cheb = 0, n_coef = 0, n_theta_int = 0;
   int64_t n_total = 0;
   int n_items = 0;
   int max_items_per_inst = 0;
@@ -88,6 +91,10 @@ struct KmvArgs {
   double* dot_partial;         // forward m == 1: per-item sum_i V_i Y_i
   double* grad_partial;        // backward: per-(item, chain, z) partial sums
   int n_z;                     // column chunks
+  // Chebyshev-amplitude family (Sec. 4): K_ij = amp_i amp_j K0_ij with
+  // amp = exp(C_theta(x)) per (chain, point), laid out (chains, N_total); NULL = 1.
+  const float* amp;
+  int no_diag;                 // forward: leave out the (sigma^2 + shift) V term
 };
 
 // SIMT kernels (kmv_simt.cu)
@@ -142,6 +149,20 @@ cudaError_t launch_phi_combine(DevLayout L, int n_items, int chains, int n_poles
                                const double* weights, const float* x_p, float* phi, cudaStream_t st);
 cudaError_t launch_phi_status(int n_sys, int n_poles, const int32_t* col_status, const int32_t* col_iters,
                               int32_t* status, int32_t* iters, cudaStream_t st);
+
+// Chebyshev-amplitude kernel family (kmv_cheb.cu)
+constexpr int kMaxChebOrder = 32;   // N_cheb
+constexpr int kMaxChebDims = 8;     // d when N_cheb >= 2
+constexpr int kMaxChebCoef = 1024;  // N_cheb^d
+int cheb_n_coef(int n_cheb, int d);  // N_cheb^d, or -1 above kMaxChebCoef
+cudaError_t launch_cheb_prepare(const DevLayout& L, int n_items, int n_sys, int chains, int64_t n_total, int d,
+                                int n_cheb, int n_coef, int n_theta, int n_theta_int, const float* x,
+                                const double* theta, double* theta_int, float* amp, cudaStream_t st);
+cudaError_t launch_cheb_grad(const DevLayout& L, int n_items, int n_inst, int chains, int64_t n_total, int d,
+                             int n_cheb, int n_coef, int n_theta, int n_theta_int, int m, const float* x,
+                             const float* V, const float* G, const float* KV, const float* KG,
+                             const int32_t* sys_active, double* partial, const double* grad_int, double* grad,
+                             cudaStream_t st);
 
 // multi-shift CG (kmv_mscg.cu)
 cudaError_t launch_mscg_init(const DevLayout& L, int n_items, int chains, int64_t n_total, int m, const float* b,
@@ -227,6 +248,14 @@ struct kmv_handle_s {
   size_t ws_bytes = 0;
   int32_t* host_flag = nullptr;   // pinned, for convergence checks
   void* tc = nullptr;             // tensor-core path state (kmv_tc.cu)
+  // Chebyshev-amplitude family: internal parameters, amplitudes and the
+  // backward's scratch for the current theta (kmv_api.cu, cheb_prepare)
+  void* cheb_buf = nullptr;
+  size_t cheb_bytes = 0;
+  double* cheb_theta = nullptr;
+  float* cheb_amp = nullptr;
+  float *cheb_kv = nullptr, *cheb_kg = nullptr;
+  double *cheb_part = nullptr, *cheb_gint = nullptr;
   // true while the current call's stream is being captured into a CUDA graph:
   // no allocation, no table upload, no host synchronisation may happen then
   bool capturing = false;

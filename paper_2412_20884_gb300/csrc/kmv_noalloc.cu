@@ -68,6 +68,7 @@ extern "C" kmv_status kmv_backward_noalloc(const kmv_points* pts, int32_t chains
   if (!pts || pts->n_inst < 1 || !pts->offsets || pts->d < 1 || pts->d > kMaxD ||
       (pts->ard != 0 && pts->ard != 1) || chains < 1 || m < 1 || !theta || !V || !G || !grad_theta)
     return KMV_EINVAL;
+  if (pts->cheb != 0) return KMV_EUNSUPPORTED;   // the amplitudes would need scratch per point
   if (pts->offsets[0] != 0) return KMV_EINVAL;
   int64_t n_items = 0;
   for (int b = 0; b < pts->n_inst; ++b) {

@@ -9,6 +9,7 @@
 //   sum_j Q_ij                                   -> d/dlog alpha
 //   sum_j Q_ij (xh_ik - xh_jk)^2 (per k, or r^2) -> d/dlog l_k
 //   sum_j K0_ij G_j                              -> dL/dV = A G
+// With per-point amplitudes (Sec. 4) G and V enter as amp o G, amp o V.
 // Because every dA/dtheta_p is symmetric, summing W_ij over all ordered
 // pairs (i, j) gives the gradient without symmetrising W.  Per-CTA FP64
 // partials go to a buffer that launch_grad_finalize reduces in a fixed order.
@@ -51,11 +52,12 @@ __global__ void __launch_bounds__(kTile) bwd_simt_kernel(KmvArgs a) {
   for (int k = 0; k < DA; ++k) xi[k] = 0.f;
 #pragma unroll
   for (int q = 0; q < MP; ++q) gi[q] = 0.f;
+  const float amp_i = (a.amp && valid) ? a.amp[vbase + i] : 1.f;
   if (valid) {
     for (int k = 0; k < dd; ++k) xi[k] = a.x[i * dd + k] * sc[k];
 #pragma unroll
     for (int q = 0; q < MP; ++q)
-      if (q < mc) gi[q] = a.G[(vbase + i) * a.m + c0 + q];
+      if (q < mc) gi[q] = a.G[(vbase + i) * a.m + c0 + q] * amp_i;
   }
 
   float accq = 0.f, accg[DG], accv[MP];
@@ -76,8 +78,9 @@ __global__ void __launch_bounds__(kTile) bwd_simt_kernel(KmvArgs a) {
       const int r = e / MP, q = e - r * MP;
       const bool in = r < nj && q < mc;
       const int64_t idx = (vbase + jt + r) * a.m + c0 + q;
-      sv[e] = in ? a.V[idx] : 0.f;
-      sg[e] = (in && want_gv) ? a.G[idx] : 0.f;
+      const float am = (in && a.amp) ? a.amp[vbase + jt + r] : 1.f;
+      sv[e] = in ? a.V[idx] * am : 0.f;
+      sg[e] = (in && want_gv) ? a.G[idx] * am : 0.f;
     }
     __syncthreads();
 #pragma unroll 2
@@ -145,8 +148,9 @@ __global__ void __launch_bounds__(kTile) bwd_simt_kernel(KmvArgs a) {
     for (int q = 0; q < MP; ++q) {
       if (q < mc) {
         const int64_t idx = (vbase + i) * a.m + c0 + q;
-        noise += (double)gi[q] * (double)a.V[idx];
-        if (want_gv) a.Y[idx] = (float)(alpha * accv64[q] + s2 * (double)gi[q]);
+        const double g = (double)a.G[idx];
+        noise += g * (double)a.V[idx];
+        if (want_gv) a.Y[idx] = (float)(alpha * (double)amp_i * accv64[q] + s2 * g);
       }
     }
   }

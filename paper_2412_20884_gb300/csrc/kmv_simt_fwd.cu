@@ -6,7 +6,9 @@
 //   K0_ij = 2^(-sum_k (xh_ik - xh_jk)^2),  xh = x sqrt(log2(e)/2) / l,
 // from direct differences (no |x|^2 expansion, so no cancellation), then
 // accumulates K0_ij V_j in FP32, folded into FP64 every 512 columns.
-// Epilogue (Eq. kerdef): Y_i = alpha * acc_i + (sigma^2 + shift) V_i.
+// Epilogue (Eq. kerdef): Y_i = alpha * acc_i + (sigma^2 + shift) V_i.  With
+// per-point amplitudes (the kernel family of Sec. 4) V_j enters as amp_j V_j
+// and acc_i is scaled by amp_i.
 #include "simt_common.cuh"
 
 namespace kmv {
@@ -57,7 +59,8 @@ __global__ void __launch_bounds__(kTile) fwd_simt_kernel(KmvArgs a) {
     }
     for (int e = threadIdx.x; e < kJT * MP; e += kTile) {
       const int r = e / MP, q = e - r * MP;
-      sv[e] = (r < nj && q < mc) ? a.V[(vbase + jt + r) * a.m + c0 + q] : 0.f;
+      sv[e] = (r < nj && q < mc) ? a.V[(vbase + jt + r) * a.m + c0 + q] * (a.amp ? a.amp[vbase + jt + r] : 1.f)
+                                 : 0.f;
     }
     __syncthreads();
 #pragma unroll 4
@@ -92,6 +95,7 @@ __global__ void __launch_bounds__(kTile) fwd_simt_kernel(KmvArgs a) {
   const double s2 = exp(th[a.n_theta - 1]);
   double dot = 0.0;
   if (valid) {
+    const double ai = a.amp ? alpha * (double)a.amp[vbase + i] : alpha;
 #pragma unroll
     for (int q = 0; q < MP; ++q) {
       if (q < mc) {
@@ -99,7 +103,7 @@ __global__ void __launch_bounds__(kTile) fwd_simt_kernel(KmvArgs a) {
         const double shift =
             a.col_shift ? (double)a.col_shift[(int64_t)s * a.col_shift_stride + c0 + q] : 0.0;
         const double vi = (double)a.V[idx];
-        const double y = alpha * acc64[q] + (s2 + shift) * vi;
+        const double y = ai * acc64[q] + (a.no_diag ? 0.0 : (s2 + shift) * vi);
         a.Y[idx] = (float)y;
         if (a.Y64) a.Y64[idx] = y;
         dot += vi * y;

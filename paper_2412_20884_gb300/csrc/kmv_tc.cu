@@ -647,7 +647,7 @@ __global__ void __launch_bounds__(kFwdThreads, 1) tc_fwd_fma_kernel(TcFwdArgs a)
 
 // V tiles as FP32 columns for the FMA-pipe product: VF[c][t] = MZ x 128 floats.
 __global__ void tc_prep_vf_kernel(DevLayout L, TcTables T, int chains, int64_t n_total, const float* V, int m,
-                                  int mz, int T_total, const int32_t* sys_active, float* VF) {
+                                  int mz, int T_total, const int32_t* sys_active, const float* amp, float* VF) {
   const int t = blockIdx.x, c = blockIdx.y, r = threadIdx.x;
   const int b = T.tile_inst[t];
   const int s = b * chains + c;
@@ -657,7 +657,8 @@ __global__ void tc_prep_vf_kernel(DevLayout L, TcTables T, int chains, int64_t n
   const bool valid = rl < nb;
   const int64_t i = L.offsets[b] + rl;
   float* dst = VF + ((size_t)c * T_total + t) * (size_t)mz * 128;
-  for (int q = 0; q < mz; ++q) dst[q * 128 + r] = valid ? V[((int64_t)c * n_total + i) * m + q] : 0.f;
+  const float am = (valid && amp) ? amp[(int64_t)c * n_total + i] : 1.f;
+  for (int q = 0; q < mz; ++q) dst[q * 128 + r] = valid ? V[((int64_t)c * n_total + i) * m + q] * am : 0.f;
 }
 
 // ------------------------------------------------------------------ prep kernels
@@ -750,22 +751,23 @@ __global__ void tc_prep_x_kernel(DevLayout L, TcTables T, int chains, int d, int
 
 // Per (system, column) max |V| over the instance (as float bits; values >= 0 order like uints).
 __global__ void tc_vmax_kernel(DevLayout L, int chains, int64_t n_total, const float* V, int m, int c0,
-                               int mz, const int32_t* sys_active, uint32_t* vmax) {
+                               int mz, const int32_t* sys_active, const float* amp, uint32_t* vmax) {
   const int item = blockIdx.x, c = blockIdx.y;
   const int b = L.item_inst[item];
   const int s = b * chains + c;
   if (sys_active && !sys_active[s]) return;
   const int64_t i = L.item_row0[item] + threadIdx.x;
   if (i >= L.offsets[b + 1]) return;
+  const float am = amp ? amp[(int64_t)c * n_total + i] : 1.f;
   for (int q = 0; q < mz; ++q) {
-    const float v = fabsf(V[((int64_t)c * n_total + i) * m + c0 + q]);
+    const float v = fabsf(V[((int64_t)c * n_total + i) * m + c0 + q] * am);
     atomicMax(&vmax[(int64_t)s * mz + q], __float_as_uint(v));
   }
 }
 
 __global__ void tc_prep_v_kernel(DevLayout L, TcTables T, int chains, int64_t n_total, const float* V, int m,
                                  int c0, int mz, int MP, int T_total, const uint32_t* vmax,
-                                 const int32_t* sys_active, uint8_t* VT) {
+                                 const int32_t* sys_active, const float* amp, uint8_t* VT) {
   const int t = blockIdx.x, c = blockIdx.y, r = threadIdx.x;
   const int b = T.tile_inst[t];
   const int s = b * chains + c;
@@ -775,9 +777,11 @@ __global__ void tc_prep_v_kernel(DevLayout L, TcTables T, int chains, int64_t n_
   const bool valid = rl < nb;
   __half* dst = reinterpret_cast<__half*>(VT + ((size_t)c * T_total + t) * (size_t)MP * 256);
   const int64_t i = L.offsets[b] + rl;
+  const float am = (valid && amp) ? amp[(int64_t)c * n_total + i] : 1.f;
   for (int q = 0; q < MP; ++q) {
     float v = 0.f;
-    if (valid && q < mz) v = V[((int64_t)c * n_total + i) * m + c0 + q] * col_scale(vmax[(int64_t)s * mz + q]);
+    if (valid && q < mz)
+      v = V[((int64_t)c * n_total + i) * m + c0 + q] * am * col_scale(vmax[(int64_t)s * mz + q]);
     dst[t_off(q, r) / 2] = __float2half_rn(v);
   }
 }
@@ -802,6 +806,7 @@ __global__ void tc_fwd_epilogue_kernel(DevLayout L, TcTables T, KmvArgs a, int c
   const bool bad = *err != 0;
   double dot = 0.0;
   if (valid) {
+    const double ai = a.amp ? alpha * (double)a.amp[(int64_t)c * a.n_total + i] : alpha;
     for (int q = 0; q < mz; ++q) {
       double acc = 0.0;
       for (int k = 0; k < nk; ++k) acc += part[((it0 + k) * 256 + rowp) * mz + q];
@@ -809,7 +814,7 @@ __global__ void tc_fwd_epilogue_kernel(DevLayout L, TcTables T, KmvArgs a, int c
       const int64_t idx = ((int64_t)c * a.n_total + i) * a.m + col;
       const double shift = a.col_shift ? (double)a.col_shift[(int64_t)s * a.col_shift_stride + col] : 0.0;
       const double vi = (double)a.V[idx];
-      double y = alpha * acc / (double)col_scale(vmax[(int64_t)s * mz + q]) + (s2 + shift) * vi;
+      double y = ai * acc / (double)col_scale(vmax[(int64_t)s * mz + q]) + (a.no_diag ? 0.0 : (s2 + shift) * vi);
       if (bad) y = __longlong_as_double(0x7ff8000000000000ll);
       a.Y[idx] = (float)y;
       if (a.Y64) a.Y64[idx] = y;
@@ -1065,7 +1070,7 @@ kmv_status tc_forward(kmv_handle h, const KmvArgs& a, cudaStream_t st) {
     if (cudaMemsetAsync(vmax, 0, sizeof(uint32_t) * (size_t)n_sys * mz, st) != cudaSuccess)
       return tc_fail(h, KMV_ECUDA, "memset failed");
     tc_prep_vf_kernel<<<dim3(S->T_total, L.chains), 128, 0, st>>>(h->dev, S->dev, L.chains, L.n_total, a.V, a.m,
-                                                                  mz, S->T_total, a.sys_active,
+                                                                  mz, S->T_total, a.sys_active, a.amp,
                                                                   reinterpret_cast<float*>(VT));
     TcFwdArgs fa;
     fa.items = S->d_items;
@@ -1105,9 +1110,9 @@ kmv_status tc_forward(kmv_handle h, const KmvArgs& a, cudaStream_t st) {
     if (cudaMemsetAsync(vmax, 0, sizeof(uint32_t) * (size_t)n_sys * mz, st) != cudaSuccess)
       return tc_fail(h, KMV_ECUDA, "memset failed");
     tc_vmax_kernel<<<dim3(L.n_items, L.chains), kTile, 0, st>>>(h->dev, L.chains, L.n_total, a.V, a.m, c0, mz,
-                                                                a.sys_active, vmax);
+                                                                a.sys_active, a.amp, vmax);
     tc_prep_v_kernel<<<dim3(S->T_total, L.chains), 128, 0, st>>>(h->dev, S->dev, L.chains, L.n_total, a.V, a.m, c0,
-                                                                 mz, MP, S->T_total, vmax, a.sys_active, VT);
+                                                                 mz, MP, S->T_total, vmax, a.sys_active, a.amp, VT);
     TcFwdArgs fa;
     fa.items = S->d_items;
     fa.n_items = S->n_items;

@@ -472,7 +472,7 @@ __global__ void __launch_bounds__(kTsThreads, 1) tc_bwd_ts_kernel(TcBwdArgs a) {
 // max |G_i| and max |V_j| per system (row norms) and sum_i G_i . V_i.
 __global__ void tc_bwd_norms_kernel(DevLayout L, int chains, int64_t n_total, const float* V, const float* G,
                                     int m, uint32_t* gmax, uint32_t* vmax, double* gvpart,
-                                    const int32_t* sys_active) {
+                                    const int32_t* sys_active, const float* amp) {
   __shared__ double red[kTile / 32];
   const int item = blockIdx.x, c = blockIdx.y;
   const int b = L.item_inst[item];
@@ -489,8 +489,9 @@ __global__ void tc_bwd_norms_kernel(DevLayout L, int chains, int64_t n_total, co
       v2 = fmaf(vq, vq, v2);
       gv += (double)gq * (double)vq;
     }
-    atomicMax(&gmax[s], __float_as_uint(sqrtf(g2)));
-    atomicMax(&vmax[s], __float_as_uint(sqrtf(v2)));
+    const float am = amp ? amp[(int64_t)c * n_total + i] : 1.f;
+    atomicMax(&gmax[s], __float_as_uint(sqrtf(g2) * am));
+    atomicMax(&vmax[s], __float_as_uint(sqrtf(v2) * am));
   }
   const double t = block_sum(gv, red);
   if (threadIdx.x == 0) gvpart[(int64_t)item * chains + c] = t;
@@ -504,8 +505,8 @@ __global__ void tc_prep_bwd_kernel(DevLayout L, TcTables T, int chains, int d, i
                                    int c0, int mc, int KG, int NB, int qcol, int T_total, const float* x,
                                    const double* theta,
                                    const float* V, const float* G, int64_t n_total, const uint32_t* gmax,
-                                   const uint32_t* vmax, const int32_t* sys_active, uint8_t* GI, uint8_t* VJ,
-                                   uint8_t* BG, int* err) {
+                                   const uint32_t* vmax, const int32_t* sys_active, const float* amp,
+                                   uint8_t* GI, uint8_t* VJ, uint8_t* BG, int* err) {
   const int t = blockIdx.x, c = blockIdx.y, r = threadIdx.x;
   const int b = T.tile_inst[t];
   const int s = b * chains + c;
@@ -518,14 +519,15 @@ __global__ void tc_prep_bwd_kernel(DevLayout L, TcTables T, int chains, int d, i
   __nv_bfloat16* gi = reinterpret_cast<__nv_bfloat16*>(GI + tile * (size_t)KG * 256);
   __nv_bfloat16* vj = reinterpret_cast<__nv_bfloat16*>(VJ + tile * (size_t)KG * 256);
   __half* bg = reinterpret_cast<__half*>(BG + tile * (size_t)NB * 256);
-  const float gs = (float)w_scale(gmax[s], vmax[s]);
+  const float am = (valid && amp) ? amp[(int64_t)c * n_total + i] : 1.f;
+  const float gs = (float)w_scale(gmax[s], vmax[s]) * am;
   const __nv_bfloat16 zb = __float2bfloat16_rn(0.f);
   for (int q = 0; q < KG; ++q) {
     __nv_bfloat16 gval = zb, vval = zb;
     if (valid && q < 6 * mc) {
       const int col = q % mc, part = q / mc;
       const int64_t idx = ((int64_t)c * n_total + i) * m + c0 + col;
-      const float gq = G[idx] * gs, vq = V[idx];
+      const float gq = G[idx] * gs, vq = V[idx] * am;
       const __nv_bfloat16 gh = __float2bfloat16_rn(gq), vh = __float2bfloat16_rn(vq);
       const __nv_bfloat16 gl = __float2bfloat16_rn(gq - __bfloat162float(gh));
       const __nv_bfloat16 vl = __float2bfloat16_rn(vq - __bfloat162float(vh));
@@ -695,7 +697,7 @@ kmv_status tc_backward(kmv_handle h, const KmvArgs& a, double* grad, cudaStream_
     return tc_fail(h, KMV_ECUDA, "memset failed");
   if (L.n_items > 0)
     tc_bwd_norms_kernel<<<dim3(L.n_items, L.chains), kTile, 0, st>>>(h->dev, L.chains, L.n_total, a.V, a.G, a.m,
-                                                                     gmax, vmax, gvpart, a.sys_active);
+                                                                     gmax, vmax, gvpart, a.sys_active, a.amp);
   if (n_items > 0) {
     tc_launch_prep_x(h, S, a, KX, 2, base + o_xa, base + o_xb, st);
     TcBwdArgs ba;
@@ -732,7 +734,7 @@ kmv_status tc_backward(kmv_handle h, const KmvArgs& a, double* grad, cudaStream_
       const int c0 = ch * mc, mcc = std::min(mc, a.m - c0);
       tc_prep_bwd_kernel<<<dim3(S->T_total, L.chains), 128, 0, st>>>(
           h->dev, S->dev, L.chains, a.d, a.ard, a.n_theta, a.m, c0, mcc, KG, NB, qcol, S->T_total, a.x, a.theta,
-          a.V, a.G, L.n_total, gmax, vmax, a.sys_active, base + o_gi, base + o_vj, base + o_bg, err);
+          a.V, a.G, L.n_total, gmax, vmax, a.sys_active, a.amp, base + o_gi, base + o_vj, base + o_bg, err);
       ba.chunk = ch;
       ProfScope prof(h, KMV_KERNEL_ADJOINT, st);
       if (xs)

@@ -197,6 +197,30 @@ def ragged(sizes, d: int = 3, chains: int = 2, m: int = 2, ard: bool = True,
     return Workload("ragged", x, offsets, y, theta, ard, chains, V, G)
 
 
+def cheb(sizes, d: int = 2, n_cheb: int = 3, chains: int = 2, m: int = 2, ard: bool = False,
+         seed: int = 0, ell_range=(0.3, 1.0), sigma2: float = 0.05, theta_scale: float = 0.3) -> Workload:
+    """Instances for the Chebyshev log-amplitude kernel of Sec. 4: points uniform in
+    [-1, 1]^d, theta rows [Theta (n_cheb^d, N(0, theta_scale^2) / (1 + |t|_1)), log l, log sigma^2]."""
+    rng = rng_for(seed)
+    sizes = np.asarray(sizes, dtype=np.int64)
+    offsets = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    n = int(offsets[-1])
+    x = rng.uniform(-1.0, 1.0, size=(n, d))
+    y = np.cos(2.0 * x).prod(axis=1) + 0.1 * rng.standard_normal(n)
+    deg = np.indices((n_cheb,) * d).reshape(d, -1).sum(axis=0)
+    thetas = []
+    for _b in range(len(sizes)):
+        for _c in range(chains):
+            k = d if ard else 1
+            coef = theta_scale * rng.standard_normal(deg.size) / (1.0 + deg)
+            ells = log_uniform(rng, ell_range[0], ell_range[1], k)
+            thetas.append(np.concatenate([coef, np.log(ells), [math.log(sigma2)]]))
+    theta = np.stack(thetas)
+    V = _vectors(rng, chains, n, m)
+    G = _vectors(rng, chains, n, m)
+    return Workload("cheb", x, offsets, y, theta, ard, chains, V, G, meta={"cheb": n_cheb})
+
+
 def tiny_verification(n: int = 10) -> Workload:
     """Sec. 4.1's verification data: N equispaced points on [-1, 1), y_i = 1."""
     x = (-1.0 + 2.0 * np.arange(n) / n)[:, None]
