@@ -233,13 +233,16 @@ def main():
     ap.add_argument("--cpu-rows", type=int, default=512, help="rows of the oracle sample for cpu_baseline")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-leapfrog", action="store_true")
-    ap.add_argument("--suite", default=None, choices=["c3c4"],
-                    help="instead of the headline line: time the C3 products and the C4 leapfrog batch")
+    ap.add_argument("--suite", default=None, choices=["c3c4", "cheb"],
+                    help="instead of the headline line: time the C3 products and the C4 leapfrog batch (c3c4), "
+                         "or the Chebyshev-amplitude kernel family of Sec. 4 (cheb)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
     if args.suite == "c3c4":
         return run_suite_c3c4(args)
+    if args.suite == "cheb":
+        return run_suite_cheb(args)
 
     import torch
     import torch.distributed as dist
@@ -509,11 +512,97 @@ def leapfrog_rates(h, dev, rank, world):
     return res
 
 
+def run_suite_cheb(args):
+    """The Chebyshev log-amplitude kernel family of Sec. 4 (one GPU, one JSON line):
+    products  N = 65,536 points in [-1, 1]^2, N_cheb = 8 (64 coefficients), m = 16:
+              forward and backward (with the Theta gradients) against the stationary
+              SE kernel of the same shape, both forms;
+    E3 shape  N = 1,500 points, d = 2, 10 chains, N_cheb in {2, 4, 8}, every theta entry
+              0.01 at the start (the initialisation of Sec. 4): leapfrog steps/s
+              (FP32 and BF16, eager, after 3 warm-up steps) and the phi draw
+              (15 poles, cg_tol 1e-6)."""
+    import torch
+    import workloads as wl
+    from paper_2412_20884_gb300 import Kmv, Points
+    dev = torch.device("cuda", 0)
+    h = Kmv(0)
+    out = {"suite": "cheb", "data": "synthetic"}
+
+    def timed(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    n = 65536
+    w = wl.cheb([n], d=2, n_cheb=8, chains=1, m=16, seed=71)
+    x = torch.tensor(w.X, dtype=torch.float32, device=dev)
+    V = torch.tensor(w.V, dtype=torch.float32, device=dev)
+    G = torch.tensor(w.G, dtype=torch.float32, device=dev)
+    pc = Points(x, w.offsets, ard=False, cheb=8)
+    ps = Points(x, w.offsets, ard=False)
+    thc = torch.tensor(w.theta, dtype=torch.float64, device=dev)
+    ths = torch.tensor([[0.0, float(w.theta[0, -2]), float(w.theta[0, -1])]], dtype=torch.float64, device=dev)
+    prod = {"workload": f"N={n} x~U[-1,1]^2, iso, N_cheb=8 (64 coefficients), m=16"}
+    for prec in ("bf16_hilo", "fp32"):
+        r = {}
+        for name, pts, th in (("cheb", pc, thc), ("se", ps, ths)):
+            fm = timed(lambda: h.kmv_forward(pts, th, V, prec=prec), 3)
+            bm = timed(lambda: h.kmv_backward(pts, th, V, G, prec=prec), 2)
+            r[name] = {"fwd_ms": fm, "bwd_ms": bm, "fwd_gpair_s": n * n / fm / 1e6, "bwd_gpair_s": n * n / bm / 1e6}
+        r["fwd_overhead"] = r["cheb"]["fwd_ms"] / r["se"]["fwd_ms"]
+        r["bwd_overhead"] = r["cheb"]["bwd_ms"] / r["se"]["bwd_ms"]
+        prod[prec] = r
+    out["products"] = prod
+    del x, V, G, pc, ps
+
+    e3 = {"workload": "N=1500 x~U[-1,1]^2, iso, 10 chains, theta_0 = 0.01, dt=0.01, cg_tol=1e-6"}
+    for nc in (2, 4, 8):
+        w = wl.cheb([1500], d=2, n_cheb=nc, chains=10, m=1, seed=72 + nc, sigma2=0.05)
+        pts = Points(torch.tensor(w.X, dtype=torch.float32, device=dev), w.offsets, ard=False, cheb=nc)
+        th0 = torch.full(w.theta.shape, 0.01, dtype=torch.float64, device=dev)
+        y = torch.tensor(w.y, dtype=torch.float32, device=dev)
+        xi = torch.tensor(np.random.default_rng(73).standard_normal((10, 1500)), dtype=torch.float32, device=dev)
+        r = {"n_theta": int(w.n_theta)}
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        phi, st, its = h.phi_refresh(pts, th0, xi, n_poles=15, cg_tol=1e-6, cg_maxiter=5000)
+        torch.cuda.synchronize()
+        r["phi_refresh_ms"] = 1e3 * (time.perf_counter() - t0)
+        r["phi_ok"] = bool((st == 0).all())
+        pi0 = torch.tensor(0.1 * np.random.default_rng(74).standard_normal(w.theta.shape), dtype=torch.float64,
+                           device=dev)
+        for prec in ("fp32", "bf16_hilo"):
+            th, pi = th0.clone(), pi0.clone()
+            xw = torch.empty_like(phi)
+            thw, piw = th0.clone(), pi0.clone()
+            for _ in range(3):
+                h.leapfrog_step(pts, y, phi, thw, piw, 0.01, cg_maxiter=5000, x_work=xw, prec=prec)
+            torch.cuda.synchronize()
+            steps = 10
+            t0 = time.perf_counter()
+            its = []
+            for _ in range(steps):
+                st, it, _ = h.leapfrog_step(pts, y, phi, th, pi, 0.01, cg_maxiter=5000, x_work=xw, prec=prec)
+                its.append(it.float().mean().item())
+            torch.cuda.synchronize()
+            r[prec] = {"steps_per_s": steps / (time.perf_counter() - t0), "mean_cg_iters": float(np.mean(its)),
+                       "ok": bool((st == 0).all()), "status_counts": np.bincount(st.cpu().numpy(), minlength=8).tolist(),
+                       "theta_max_abs": float(th.abs().max())}
+        e3[f"n_cheb_{nc}"] = r
+    out["e3_shape"] = e3
+    print(json.dumps(out))
+
+
 def run_suite_c3c4(args):
     """Secondary configurations (one GPU, one JSON line):
     C3  N = 262,144, d = 32, ARD, m = 64: forward and backward times of both forms
-        (the tensor-core adjoint covers d <= 15, so the BF16 backward here is the
-        FP32 adjoint; the BF16 forward is the tensor-core kernel);
+        (the BF16 backward is the tensor-core adjoint, which covers d <= 32);
     C4  256 instances of 1e3..2e4 points, d = 4, 4 chains (1024 systems): leapfrog
         steps/s over the whole batch for both forms, eager and as a CUDA graph of
         the same steps (a fixed number of masked CG iterations per solve)."""
