@@ -256,6 +256,51 @@ kmv_status kmv_phi_refresh(kmv_handle h, const kmv_points* pts, int32_t chains,
                            kmv_precision prec, void* stream);
 
 /*
+ * Randomized Nystrom preconditioner (Frangella, Tropp and Udell), which the
+ * paper uses for its linear solves (Sec. 3.1, end; Sec. 3.2.3; Sec. 4): a
+ * rank-r factorisation K(theta) ~ U diag(lambda) U^T per system, used through
+ * the Woodbury form for A = K + sigma^2 I,
+ *     P^{-1} = (lambda_r + sigma^2) U (diag(lambda) + sigma^2)^{-1} U^T + (I - U U^T),
+ * with sigma^2 taken from the theta of each solve, so one factorisation can
+ * serve the solves at later theta (the paper rebuilds it every few updates).
+ *
+ * kmv_nystrom_build - Y = K Omega (one r-column product without the noise
+ * term), nu = sqrt(N_b) 2^-23 |Y|_F, Y_nu = Y + nu Omega, Omega^T Y_nu = L L^T,
+ * B = Y_nu L^{-T} = U S W^T, lambda = max(S^2 - nu, 0).
+ *   rank        1..128 (the paper uses 5 and 500).
+ *   omega       DEVICE FP32 (chains, N_total, rank): the caller's N(0, 1) draws.
+ *   U           DEVICE FP32 (chains, rank, N_total), written: the orthonormal
+ *               columns, stored column after column.
+ *   lam         DEVICE FP64 (n_inst * chains, rank), written, descending.
+ *   chain_status DEVICE int32 (n_inst * chains): KMV_OK, or KMV_ENOTCONV when the
+ *               r x r Cholesky failed (e.g. an instance with fewer than rank
+ *               points); that system then gets lam = 0, U = 0 (P = I).
+ * Work: one rank-column N^2 product, O(N rank^2) Gram and U passes, O(rank^3)
+ * per system in FP64.  Allocates workspace; not for use during capture.
+ *
+ * kmv_set_preconditioner - from the next call on, every CG solve on this
+ * handle (kmv_cg_solve, leapfrog_step, kmv_energy, both precisions) runs
+ * preconditioned CG with pc, until it is called with NULL.  The arrays are the
+ * caller's and must stay valid while set; a solve whose layout (n_inst,
+ * chains, N_total) differs from pc's returns KMV_EINVAL.  kmv_phi_refresh keeps
+ * its multi-shift CG, which a preconditioner would break.
+ */
+typedef struct {
+  int32_t rank;
+  int32_t n_inst;
+  int32_t chains;
+  int64_t n_total;
+  const float* U;      /* DEVICE (chains, rank, N_total) */
+  const double* lam;   /* DEVICE (n_inst * chains, rank) */
+} kmv_nystrom;
+
+kmv_status kmv_nystrom_build(kmv_handle h, const kmv_points* pts, int32_t chains,
+                             const double* theta, int32_t rank, const float* omega,
+                             float* U, double* lam, int32_t* chain_status,
+                             kmv_precision prec, void* stream);
+kmv_status kmv_set_preconditioner(kmv_handle h, const kmv_nystrom* pc);
+
+/*
  * Kernel timing.  Instrumentation for measuring the library on a device; the
  * paper has no counterpart.  While enabled, every launch of a main product
  * kernel is bracketed by two CUDA events recorded on the call's stream:

@@ -31,6 +31,11 @@ class KmvError(RuntimeError):
         self.status = status
 
 
+class _Nystrom(C.Structure):
+    _fields_ = [("rank", C.c_int32), ("n_inst", C.c_int32), ("chains", C.c_int32), ("n_total", C.c_int64),
+                ("U", C.c_void_p), ("lam", C.c_void_p)]
+
+
 class _Points(C.Structure):
     _fields_ = [("n_inst", C.c_int32), ("offsets", C.POINTER(C.c_int64)), ("d", C.c_int32),
                 ("ard", C.c_int32), ("x", C.c_void_p), ("cheb", C.c_int32)]
@@ -54,6 +59,9 @@ _SIGS = {
     "kmv_backward_noalloc": (C.c_int, [C.POINTER(_Points), C.c_int32, _P, _P, _P, C.c_int32, _P, _P, _P]),
     "kmv_phi_refresh": (C.c_int, [_P, C.POINTER(_Points), C.c_int32, _P, _P, _P, C.c_int32, C.c_double,
                                   C.c_int32, _P, _P, _P, C.c_int, _P]),
+    "kmv_nystrom_build": (C.c_int, [_P, C.POINTER(_Points), C.c_int32, _P, C.c_int32, _P, _P, _P, _P, C.c_int,
+                                    _P]),
+    "kmv_set_preconditioner": (C.c_int, [_P, _P]),
     "kmv_profile_enable": (C.c_int, [_P, C.c_int32]),
     "kmv_profile_read": (C.c_int, [_P, C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
 }
@@ -243,6 +251,35 @@ class Kmv:
                                         _ptr(x), float(tol), int(maxiter), int(bool(warm_start)),
                                         _ptr(status), _ptr(iters), self._prec(prec), _stream(stream)))
         return x, status, iters
+
+    def nystrom_build(self, pts: Points, theta, omega, prec="fp32", stream=None):
+        """Randomized Nystrom factorisation K ~ U diag(lam) U^T per system (kmv_nystrom_build).
+        omega: (chains, N_total, rank) N(0, 1) draws.  Returns (U (chains, rank, N_total), lam, status)."""
+        chains = self._chains(pts, theta)
+        n_sys = pts.n_inst * chains
+        _need(theta, torch.float64, "theta", (n_sys, pts.n_theta))
+        rank = omega.shape[-1]
+        _need(omega, torch.float32, "omega", (chains, pts.n_total, rank))
+        U = torch.empty((chains, rank, pts.n_total), dtype=torch.float32, device=omega.device)
+        lam = torch.empty((n_sys, rank), dtype=torch.float64, device=omega.device)
+        status = torch.empty(n_sys, dtype=torch.int32, device=omega.device)
+        self._check(self.L.kmv_nystrom_build(self.h, pts.c, chains, _ptr(theta), int(rank), _ptr(omega), _ptr(U),
+                                             _ptr(lam), _ptr(status), self._prec(prec), _stream(stream)))
+        return U, lam, status
+
+    def set_preconditioner(self, pts: Points, U=None, lam=None):
+        """Precondition every later CG solve on this handle with (U, lam) (kmv_set_preconditioner);
+        U = None clears it.  The tensors are kept referenced while set."""
+        if U is None:
+            self._pc = None
+            self._check(self.L.kmv_set_preconditioner(self.h, None))
+            return
+        chains, rank, n = U.shape
+        _need(U, torch.float32, "U", (chains, rank, pts.n_total))
+        _need(lam, torch.float64, "lam", (pts.n_inst * chains, rank))
+        self._pc = (U, lam, _Nystrom(rank, pts.n_inst, chains, n, C.c_void_p(U.data_ptr()),
+                                     C.c_void_p(lam.data_ptr())))
+        self._check(self.L.kmv_set_preconditioner(self.h, C.byref(self._pc[2])))
 
     def phi_refresh(self, pts: Points, theta, xi, n_poles=15, cg_tol=1e-6, cg_maxiter=1000, phi=None,
                     want_poles=False, prec="fp32", stream=None):

@@ -391,6 +391,96 @@ kmv_status run_cg(kmv_handle h, const kmv_points* pts, const double* theta, cons
   return KMV_OK;
 }
 
+// --- preconditioned CG (randomized Nystrom, set by kmv_set_preconditioner) -----------
+
+struct PcgBufs {
+  float *r, *p, *q, *z;
+  double *partial, *partial2, *prz, *proj, *coef;
+  PcgSys* sys;
+  int32_t *active, *n_active;
+};
+
+void pcg_layout(const Layout& L, int rank, Arena& ar, size_t off[12]) {
+  const size_t vec = sizeof(float) * (size_t)L.chains * std::max<int64_t>(1, L.n_total);
+  const size_t items = (size_t)std::max(1, L.n_items) * L.chains;
+  const size_t n_sys = (size_t)L.n_inst * L.chains;
+  for (int k = 0; k < 4; ++k) off[k] = ar.take(vec);
+  off[4] = ar.take(sizeof(double) * items);
+  off[5] = ar.take(sizeof(double) * items * 2);
+  off[6] = ar.take(sizeof(double) * items);
+  off[7] = ar.take(sizeof(double) * items * rank);
+  off[8] = ar.take(sizeof(double) * n_sys * rank);
+  off[9] = ar.take(sizeof(PcgSys) * n_sys);
+  off[10] = ar.take(sizeof(int32_t) * n_sys);
+  off[11] = ar.take(sizeof(int32_t) * 4);
+}
+
+PcgBufs pcg_bufs(kmv_handle h, const size_t off[12]) {
+  PcgBufs b;
+  b.r = at<float>(h, off[0]);
+  b.p = at<float>(h, off[1]);
+  b.q = at<float>(h, off[2]);
+  b.z = at<float>(h, off[3]);
+  b.partial = at<double>(h, off[4]);
+  b.partial2 = at<double>(h, off[5]);
+  b.prz = at<double>(h, off[6]);
+  b.proj = at<double>(h, off[7]);
+  b.coef = at<double>(h, off[8]);
+  b.sys = at<PcgSys>(h, off[9]);
+  b.active = at<int32_t>(h, off[10]);
+  b.n_active = at<int32_t>(h, off[11]);
+  return b;
+}
+
+// Batched preconditioned CG on A(theta_s) x = rhs with the handle's preconditioner;
+// arguments and stopping rule as run_cg (under capture: exactly maxiter masked iterations).
+kmv_status run_pcg(kmv_handle h, const kmv_points* pts, const double* theta, const float* rhs, int64_t rhs_stride,
+                   float* x, double tol, int maxiter, int warm, int32_t* status, int32_t* iters, const PcgBufs& B,
+                   kmv_precision prec, cudaStream_t st) {
+  const Layout& L = h->layout;
+  const int n_sys = L.n_inst * L.chains;
+  const PcgPrecond P{h->pc.rank, h->pc.U, h->pc.lam};
+  KmvArgs a = base_args(h, pts, theta);
+  a.m = 1;
+  if (warm) {
+    a.V = x;
+    a.Y = B.q;
+    KMV_TRY(run_forward(h, a, prec, st));
+  }
+  KMV_CUDA(h, launch_pcg_init(h->dev, L.n_items, L.chains, L.n_total, rhs, rhs_stride, B.q, x, B.r, warm,
+                              B.partial2, st));
+  KMV_CUDA(h, launch_pcg_precond(h->dev, L.n_items, L.n_inst, L.chains, L.n_total, P, a.theta, a.n_theta, B.r, B.z,
+                                 nullptr, B.proj, B.coef, B.prz, st));
+  KMV_CUDA(h, cudaMemsetAsync(B.n_active, 0, sizeof(int32_t), st));
+  KMV_CUDA(h, launch_pcg_setup(h->dev, L.n_inst, L.chains, B.partial2, B.prz, tol, B.sys, B.active, B.n_active, st));
+  const size_t vbytes = sizeof(float) * (size_t)L.chains * L.n_total;
+  if (vbytes) KMV_CUDA(h, cudaMemcpyAsync(B.p, B.z, vbytes, cudaMemcpyDeviceToDevice, st));
+  a.V = B.p;
+  a.Y = B.q;
+  a.sys_active = B.active;
+  a.dot_partial = B.partial;
+  const int check_every = 4;
+  for (int it = 0; it < maxiter; ++it) {
+    if (!h->capturing && it % check_every == 0) {
+      KMV_CUDA(h, cudaMemcpyAsync(h->host_flag, B.n_active, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+      KMV_CUDA(h, cudaStreamSynchronize(st));
+      if (*h->host_flag == 0) break;
+    }
+    KMV_TRY(run_forward(h, a, prec, st));
+    KMV_CUDA(h, launch_pcg_alpha(h->dev, L.n_inst, L.chains, B.partial, B.sys, B.active, st));
+    KMV_CUDA(h, launch_pcg_update_xr(h->dev, L.n_items, L.chains, L.n_total, B.sys, B.active, x, B.r, B.p, B.q,
+                                     B.partial, st));
+    KMV_CUDA(h, launch_pcg_precond(h->dev, L.n_items, L.n_inst, L.chains, L.n_total, P, a.theta, a.n_theta, B.r,
+                                   B.z, B.active, B.proj, B.coef, B.prz, st));
+    KMV_CUDA(h, cudaMemsetAsync(B.n_active, 0, sizeof(int32_t), st));
+    KMV_CUDA(h, launch_pcg_beta(h->dev, L.n_inst, L.chains, B.partial, B.prz, tol, maxiter, B.sys, B.active,
+                                B.n_active, st));
+    KMV_CUDA(h, launch_pcg_update_p(h->dev, L.n_items, L.chains, L.n_total, B.sys, B.active, B.z, B.p, st));
+  }
+  KMV_CUDA(h, launch_pcg_finish(n_sys, B.sys, B.active, status, iters, st));
+  return KMV_OK;
+}
+
 // Extra buffers of the refined (KMV_BF16_HILO) solve.
 struct RefineBufs {
   float *q32, *r, *dx, *pdummy;
@@ -442,7 +532,8 @@ RefineBufs refine_bufs(kmv_handle h, const size_t off[11]) {
 // Returns the summed inner iterations.
 kmv_status run_cg_refined(kmv_handle h, const kmv_points* pts, const double* theta, const float* rhs,
                           int64_t rhs_stride, float* x, double tol, int maxiter, int warm, int32_t* status,
-                          int32_t* iters, const CgBufs& B, const RefineBufs& R, cudaStream_t st) {
+                          int32_t* iters, const CgBufs& B, const RefineBufs& R, const PcgBufs* PB,
+                          cudaStream_t st) {
   const Layout& L = h->layout;
   const int n_sys = L.n_inst * L.chains;
   const int64_t nvec = (int64_t)L.chains * L.n_total;
@@ -483,8 +574,12 @@ kmv_status run_cg_refined(kmv_handle h, const kmv_points* pts, const double* the
     }
     // correction from the tensor-core operator, on the systems still active
     if (L.n_items > 0) KMV_CUDA(h, launch_mask_rows(h->dev, L.n_items, L.chains, L.n_total, R.active, R.r, st));
-    KMV_TRY(run_cg(h, pts, theta, R.r, L.n_total, R.dx, inner_tol, maxiter, 0, R.in_status, R.in_iters, B,
-                   KMV_BF16_HILO, st));
+    if (PB)
+      KMV_TRY(run_pcg(h, pts, theta, R.r, L.n_total, R.dx, inner_tol, maxiter, 0, R.in_status, R.in_iters, *PB,
+                      KMV_BF16_HILO, st));
+    else
+      KMV_TRY(run_cg(h, pts, theta, R.r, L.n_total, R.dx, inner_tol, maxiter, 0, R.in_status, R.in_iters, B,
+                     KMV_BF16_HILO, st));
     KMV_CUDA(h, launch_axpy(nvec, R.dx, x, st));
     KMV_CUDA(h, launch_refine_merge(n_sys, R.in_status, R.in_iters, status, iters, st));
   }
@@ -492,25 +587,35 @@ kmv_status run_cg_refined(kmv_handle h, const kmv_points* pts, const double* the
   return KMV_OK;
 }
 
-// Buffers of a solve in either precision.
+// Buffers of a solve in either precision, with or without the preconditioner.
 struct SolveLayout {
   size_t cg[8];
   size_t rf[11];
-  bool refined;
+  size_t pcg[12];
+  bool refined, pc;
 };
 
-void solve_layout(const Layout& L, Arena& ar, kmv_precision prec, SolveLayout& S) {
+void solve_layout(kmv_handle h, Arena& ar, kmv_precision prec, SolveLayout& S) {
+  const Layout& L = h->layout;
   cg_layout(L, ar, S.cg);
   S.refined = prec == KMV_BF16_HILO;
   if (S.refined) refine_layout(L, ar, S.rf);
+  S.pc = h->pc_on;
+  if (S.pc) pcg_layout(L, h->pc.rank, ar, S.pcg);
 }
 
 kmv_status run_solve(kmv_handle h, const kmv_points* pts, const double* theta, const float* rhs, int64_t rhs_stride,
                      float* x, double tol, int maxiter, int warm, int32_t* status, int32_t* iters,
                      const SolveLayout& S, kmv_precision prec, cudaStream_t st) {
+  const Layout& L = h->layout;
+  if (S.pc && (h->pc.n_inst != L.n_inst || h->pc.chains != L.chains || h->pc.n_total != L.n_total))
+    return fail(h, KMV_EINVAL, "the preconditioner was built for another layout (n_inst, chains, N_total)");
+  PcgBufs pb;
+  if (S.pc) pb = pcg_bufs(h, S.pcg);
   if (S.refined)
     return run_cg_refined(h, pts, theta, rhs, rhs_stride, x, tol, maxiter, warm, status, iters, cg_bufs(h, S.cg),
-                          refine_bufs(h, S.rf), st);
+                          refine_bufs(h, S.rf), S.pc ? &pb : nullptr, st);
+  if (S.pc) return run_pcg(h, pts, theta, rhs, rhs_stride, x, tol, maxiter, warm, status, iters, pb, prec, st);
   return run_cg(h, pts, theta, rhs, rhs_stride, x, tol, maxiter, warm, status, iters, cg_bufs(h, S.cg), prec, st);
 }
 
@@ -851,7 +956,7 @@ kmv_status kmv_cg_solve(kmv_handle h, const kmv_points* pts, int32_t chains, con
   KMV_TRY(prepare_layout(h, pts, chains, st));
   Arena ar;
   SolveLayout SL;
-  solve_layout(h->layout, ar, prec, SL);
+  solve_layout(h, ar, prec, SL);
   KMV_TRY(reserve(h, ar.used));
   KMV_TRY(cheb_prepare(h, pts, theta, 0, st));
   const int64_t stride = rhs_per_chain ? h->layout.n_total : 0;
@@ -932,6 +1037,55 @@ kmv_status kmv_phi_refresh(kmv_handle h, const kmv_points* pts, int32_t chains, 
   return KMV_OK;
 }
 
+kmv_status kmv_nystrom_build(kmv_handle h, const kmv_points* pts, int32_t chains, const double* theta,
+                             int32_t rank, const float* omega, float* U, double* lam, int32_t* chain_status,
+                             kmv_precision prec, void* stream) {
+  KMV_TRY(check_points(h, pts, chains));
+  KMV_TRY(check_prec(h, prec));
+  if (!theta || !omega || !U || !lam || !chain_status) return fail(h, KMV_EINVAL, "NULL argument");
+  if (rank < 1 || rank > kMaxRank) return fail(h, KMV_EINVAL, "rank must be in [1, 128]");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  KMV_TRY(prepare_layout(h, pts, chains, st));
+  if (h->capturing) return fail(h, KMV_EINVAL, "kmv_nystrom_build cannot run during stream capture");
+  const Layout& L = h->layout;
+  const size_t n_sys = (size_t)L.n_inst * L.chains;
+  const size_t rr = (size_t)rank * rank;
+  Arena ar;
+  const size_t o_y = ar.take(sizeof(float) * (size_t)L.chains * std::max<int64_t>(1, L.n_total) * rank);
+  const size_t o_g = ar.take(sizeof(double) * n_sys * 3 * rr);
+  const size_t o_s = ar.take(sizeof(double) * n_sys * 4 * rr);
+  const size_t o_t = ar.take(sizeof(double) * n_sys * rr);
+  const size_t o_nu = ar.take(sizeof(double) * n_sys);
+  KMV_TRY(reserve(h, ar.used));
+  KMV_TRY(cheb_prepare(h, pts, theta, 0, st));
+  // Y = K Omega: the product without the noise term
+  KmvArgs a = base_args(h, pts, theta);
+  a.V = omega;
+  a.m = rank;
+  a.Y = at<float>(h, o_y);
+  a.no_diag = 1;
+  KMV_TRY(run_forward(h, a, prec, st));
+  KMV_CUDA(h, launch_nystrom_finish(h->dev, L.n_items, L.n_inst, L.chains, L.n_total, rank, omega, at<float>(h, o_y),
+                                    at<double>(h, o_g), at<double>(h, o_s), at<double>(h, o_t), at<double>(h, o_nu), U,
+                                    lam, chain_status, st));
+  return KMV_OK;
+}
+
+kmv_status kmv_set_preconditioner(kmv_handle h, const kmv_nystrom* pc) {
+  if (!h) return KMV_EINVAL;
+  if (!pc) {
+    h->pc_on = false;
+    h->pc = kmv_nystrom{};
+    return KMV_OK;
+  }
+  if (pc->rank < 1 || pc->rank > kMaxRank || !pc->U || !pc->lam || pc->n_inst < 1 || pc->chains < 1 ||
+      pc->n_total < 0)
+    return fail(h, KMV_EINVAL, "bad preconditioner (rank in [1, 128], U and lam non-NULL, sizes)");
+  h->pc = *pc;
+  h->pc_on = true;
+  return KMV_OK;
+}
+
 kmv_status leapfrog_step(kmv_handle h, const kmv_points* pts, int32_t chains, const float* y,
                          const float* phi, double* theta, double* pi, double dt,
                          const double* prior_mu, const double* prior_prec, const uint8_t* free_mask,
@@ -949,7 +1103,7 @@ kmv_status leapfrog_step(kmv_handle h, const kmv_points* pts, int32_t chains, co
   const int n_sys = L.n_inst * L.chains;
   Arena ar;
   SolveLayout SL;
-  solve_layout(L, ar, prec, SL);
+  solve_layout(h, ar, prec, SL);
   const size_t o_th = ar.take(sizeof(double) * n_sys * L.n_theta);
   const size_t o_gr = ar.take(sizeof(double) * n_sys * L.n_theta);
   const size_t vec2 = sizeof(float) * 2 * (size_t)L.chains * std::max<int64_t>(1, L.n_total);
@@ -1000,7 +1154,7 @@ kmv_status kmv_energy(kmv_handle h, const kmv_points* pts, int32_t chains, const
   const Layout& L = h->layout;
   Arena ar;
   SolveLayout SL;
-  solve_layout(L, ar, prec, SL);
+  solve_layout(h, ar, prec, SL);
   const size_t vec = (size_t)L.chains * std::max<int64_t>(1, L.n_total);
   const size_t o_y = ar.take(sizeof(float) * vec);
   const size_t o_y64 = ar.take(sizeof(double) * vec);

@@ -150,6 +150,41 @@ cudaError_t launch_phi_combine(DevLayout L, int n_items, int chains, int n_poles
 cudaError_t launch_phi_status(int n_sys, int n_poles, const int32_t* col_status, const int32_t* col_iters,
                               int32_t* status, int32_t* iters, cudaStream_t st);
 
+// Randomized Nystrom preconditioner (kmv_nystrom.cu) and preconditioned CG (kmv_pcg.cu)
+constexpr int kMaxRank = 128;
+struct PcgSys {
+  double rr, bb, rz, alpha, beta;
+  int32_t iters, status;
+};
+struct PcgPrecond {
+  int rank;
+  const float* U;     // (chains, rank, N_total)
+  const double* lam;  // (n_sys, rank), descending
+};
+cudaError_t launch_nystrom_finish(const DevLayout& L, int n_items, int n_inst, int chains, int64_t n_total, int r,
+                                  const float* Om, const float* Y, double* grams, double* scratch, double* T,
+                                  double* nu, float* U, double* lam, int32_t* status, cudaStream_t st);
+cudaError_t launch_pcg_init(const DevLayout& L, int n_items, int chains, int64_t n_total, const float* rhs,
+                            int64_t rhs_stride, const float* q, float* x, float* r, int warm, double* partial2,
+                            cudaStream_t st);
+cudaError_t launch_pcg_precond(const DevLayout& L, int n_items, int n_inst, int chains, int64_t n_total,
+                               const PcgPrecond& P, const double* theta, int n_theta, const float* r, float* z,
+                               const int32_t* active, double* proj, double* coef, double* prz, cudaStream_t st);
+cudaError_t launch_pcg_setup(const DevLayout& L, int n_inst, int chains, const double* partial2, const double* prz,
+                             double tol, PcgSys* sys, int32_t* active, int32_t* n_active, cudaStream_t st);
+cudaError_t launch_pcg_alpha(const DevLayout& L, int n_inst, int chains, const double* partial, PcgSys* sys,
+                             int32_t* active, cudaStream_t st);
+cudaError_t launch_pcg_update_xr(const DevLayout& L, int n_items, int chains, int64_t n_total, const PcgSys* sys,
+                                 const int32_t* active, float* x, float* r, const float* p, const float* q,
+                                 double* partial, cudaStream_t st);
+cudaError_t launch_pcg_beta(const DevLayout& L, int n_inst, int chains, const double* prr, const double* prz,
+                            double tol, int maxiter, PcgSys* sys, int32_t* active, int32_t* n_active,
+                            cudaStream_t st);
+cudaError_t launch_pcg_update_p(const DevLayout& L, int n_items, int chains, int64_t n_total, const PcgSys* sys,
+                                const int32_t* active, const float* z, float* p, cudaStream_t st);
+cudaError_t launch_pcg_finish(int n_sys, const PcgSys* sys, const int32_t* active, int32_t* status, int32_t* iters,
+                              cudaStream_t st);
+
 // Chebyshev-amplitude kernel family (kmv_cheb.cu)
 constexpr int kMaxChebOrder = 32;   // N_cheb
 constexpr int kMaxChebDims = 8;     // d when N_cheb >= 2
@@ -256,6 +291,9 @@ struct kmv_handle_s {
   float* cheb_amp = nullptr;
   float *cheb_kv = nullptr, *cheb_kg = nullptr;
   double *cheb_part = nullptr, *cheb_gint = nullptr;
+  // preconditioner set by kmv_set_preconditioner (caller-owned arrays)
+  bool pc_on = false;
+  kmv_nystrom pc = {};
   // true while the current call's stream is being captured into a CUDA graph:
   // no allocation, no table upload, no host synchronisation may happen then
   bool capturing = false;
