@@ -233,9 +233,10 @@ def main():
     ap.add_argument("--cpu-rows", type=int, default=512, help="rows of the oracle sample for cpu_baseline")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-leapfrog", action="store_true")
-    ap.add_argument("--suite", default=None, choices=["c3c4", "cheb"],
+    ap.add_argument("--suite", default=None, choices=["c3c4", "cheb", "precond"],
                     help="instead of the headline line: time the C3 products and the C4 leapfrog batch (c3c4), "
-                         "or the Chebyshev-amplitude kernel family of Sec. 4 (cheb)")
+                         "the Chebyshev-amplitude kernel family of Sec. 4 (cheb), or the leapfrog step with "
+                         "the randomized Nystrom preconditioner (precond)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -243,6 +244,8 @@ def main():
         return run_suite_c3c4(args)
     if args.suite == "cheb":
         return run_suite_cheb(args)
+    if args.suite == "precond":
+        return run_suite_precond(args)
 
     import torch
     import torch.distributed as dist
@@ -512,6 +515,66 @@ def leapfrog_rates(h, dev, rank, world):
     return res
 
 
+def run_suite_precond(args):
+    """Leapfrog steps with the randomized Nystrom preconditioner (one GPU, one JSON line):
+    for c1 (N = 2048), the 16,384-point 8-chain c5 copy and C4 (1024 systems), the
+    step rate and CG iterations without and with a rank-r factorisation built once at
+    the starting theta (and reused, as the paper does between rebuilds), plus the
+    build time.  phi is a fixed N(0, 1) vector here: the solve is y's, not phi's."""
+    import torch
+    import workloads as wl
+    from paper_2412_20884_gb300 import Kmv, Points
+    dev = torch.device("cuda", 0)
+    h = Kmv(0)
+    out = {"suite": "precond", "data": "synthetic"}
+    cases = [("c1", wl.c1(), 0.01, 10, (16, 64)),
+             ("c5_n16384", wl.c5(n=16384, chains=8), 0.002, 4, (32, 128)),
+             ("c4", wl.c4(), 0.01, 1, (64,))]
+    for name, w, dt, steps, ranks in cases:
+        pts = Points(torch.tensor(w.X, dtype=torch.float32, device=dev), w.offsets, ard=w.ard)
+        th0 = torch.tensor(w.theta, dtype=torch.float64, device=dev)
+        y = torch.tensor(w.y, dtype=torch.float32, device=dev)
+        rng = np.random.default_rng(7)
+        phi = torch.tensor(rng.standard_normal((w.chains, w.n_total)), dtype=torch.float32, device=dev)
+        pi0 = torch.tensor(0.1 * rng.standard_normal(w.theta.shape), dtype=torch.float64, device=dev)
+        r = {"workload": f"{w.n_inst} instance(s), N_total={w.n_total}, d={w.d}, {w.chains} chains, dt={dt}, "
+                         f"cg_tol=1e-6", "steps_timed": steps}
+        for rank in (0,) + tuple(ranks):
+            key = f"rank_{rank}" if rank else "none"
+            rr = {}
+            if rank:
+                om = torch.randn((w.chains, w.n_total, rank), dtype=torch.float32, device=dev,
+                                 generator=torch.Generator(device=dev).manual_seed(8))
+                h.nystrom_build(pts, th0, om)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                U, lam, st = h.nystrom_build(pts, th0, om)
+                torch.cuda.synchronize()
+                rr["build_ms"] = 1e3 * (time.perf_counter() - t0)
+                rr["build_ok_fraction"] = float((st == 0).float().mean())
+                h.set_preconditioner(pts, U, lam)
+            for prec in ("fp32", "bf16_hilo"):
+                xw = torch.empty_like(phi)
+                th, pi = th0.clone(), pi0.clone()
+                h.leapfrog_step(pts, y, phi, th0.clone(), pi0.clone(), dt, cg_maxiter=5000, x_work=xw, prec=prec)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                its, mx = [], 0
+                for _ in range(steps):
+                    st, it, _ = h.leapfrog_step(pts, y, phi, th, pi, dt, cg_maxiter=5000, x_work=xw, prec=prec)
+                    its.append(it.float().mean().item())
+                    mx = max(mx, int(it.max().item()))
+                torch.cuda.synchronize()
+                rr[prec] = {"steps_per_s": steps / (time.perf_counter() - t0), "mean_cg_iters": float(np.mean(its)),
+                            "max_cg_iters": mx, "ok": bool((st == 0).all())}
+            if rank:
+                h.set_preconditioner(pts)
+            r[key] = rr
+        out[name] = r
+        print(json.dumps({name: r}), file=sys.stderr, flush=True)
+    print(json.dumps(out))
+
+
 def run_suite_cheb(args):
     """The Chebyshev log-amplitude kernel family of Sec. 4 (one GPU, one JSON line):
     products  N = 65,536 points in [-1, 1]^2, N_cheb = 8 (64 coefficients), m = 16:
@@ -519,7 +582,7 @@ def run_suite_cheb(args):
               SE kernel of the same shape, both forms;
     E3 shape  N = 1,500 points, d = 2, 10 chains, N_cheb in {2, 4, 8}, every theta entry
               0.01 at the start (the initialisation of Sec. 4): leapfrog steps/s
-              (FP32 and BF16, eager, after 3 warm-up steps) and the phi draw
+              (FP32 and BF16, eager, after 13 warm-up steps) and the phi draw
               (15 poles, cg_tol 1e-6)."""
     import torch
     import workloads as wl
@@ -581,7 +644,7 @@ def run_suite_cheb(args):
             th, pi = th0.clone(), pi0.clone()
             xw = torch.empty_like(phi)
             thw, piw = th0.clone(), pi0.clone()
-            for _ in range(3):
+            for _ in range(13):
                 h.leapfrog_step(pts, y, phi, thw, piw, 0.01, cg_maxiter=5000, x_work=xw, prec=prec)
             torch.cuda.synchronize()
             steps = 10

