@@ -520,7 +520,9 @@ def run_suite_precond(args):
     for c1 (N = 2048), the 16,384-point 8-chain c5 copy and C4 (1024 systems), the
     step rate and CG iterations without and with a rank-r factorisation built once at
     the starting theta (and reused, as the paper does between rebuilds), plus the
-    build time.  phi is a fixed N(0, 1) vector here: the solve is y's, not phi's."""
+    build time, and the phi draw (15 poles, cg_tol 1e-6: multi-shift CG without a
+    preconditioner, preconditioned multi-column CG with one).  phi in the leapfrog
+    is a fixed N(0, 1) vector: the solve is y's, not phi's."""
     import torch
     import workloads as wl
     from paper_2412_20884_gb300 import Kmv, Points
@@ -567,6 +569,16 @@ def run_suite_precond(args):
                 torch.cuda.synchronize()
                 rr[prec] = {"steps_per_s": steps / (time.perf_counter() - t0), "mean_cg_iters": float(np.mean(its)),
                             "max_cg_iters": mx, "ok": bool((st == 0).all())}
+            if rank or name != "c4":   # C4's unpreconditioned draw: 31 s (BF16), measured by --suite c3c4
+                xi = torch.tensor(rng.standard_normal((w.chains, w.n_total)), dtype=torch.float32, device=dev)
+                for prec in ("fp32", "bf16_hilo"):
+                    torch.cuda.synchronize()
+                    t0 = time.perf_counter()
+                    _, st, its = h.phi_refresh(pts, th0, xi, n_poles=15, cg_tol=1e-6, cg_maxiter=5000, prec=prec)
+                    torch.cuda.synchronize()
+                    rr[prec]["phi_refresh_ms"] = 1e3 * (time.perf_counter() - t0)
+                    rr[prec]["phi_max_cg_iters"] = int(its.max())
+                    rr[prec]["phi_ok"] = bool((st == 0).all())
             if rank:
                 h.set_preconditioner(pts)
             r[key] = rr

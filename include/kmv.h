@@ -282,8 +282,12 @@ kmv_status kmv_phi_refresh(kmv_handle h, const kmv_points* pts, int32_t chains,
  * handle (kmv_cg_solve, leapfrog_step, kmv_energy, both precisions) runs
  * preconditioned CG with pc, until it is called with NULL.  The arrays are the
  * caller's and must stay valid while set; a solve whose layout (n_inst,
- * chains, N_total) differs from pc's returns KMV_EINVAL.  kmv_phi_refresh keeps
- * its multi-shift CG, which a preconditioner would break.
+ * chains, N_total) differs from pc's returns KMV_EINVAL.  kmv_phi_refresh then
+ * solves its shifted systems as preconditioned columns of one multi-column CG
+ * (mu = sigma^2 + lambda_p per column: the same factors serve every shift)
+ * instead of multi-shift CG, whose shift invariance a preconditioner breaks;
+ * that solve takes FP32 products in both forms (the many-column tensor-core
+ * product is too coarse to refine the small shifts when sigma^2 << |K|).
  */
 typedef struct {
   int32_t rank;

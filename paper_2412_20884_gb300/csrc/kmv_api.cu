@@ -655,12 +655,40 @@ McgBufs mcg_bufs(kmv_handle h, const size_t off[8]) {
   return b;
 }
 
+// Preconditioner of the multi-column CG: the handle's Nystrom factors, applied per
+// column with mu_q = sigma^2 + shift_q (the Woodbury form for each shifted system).
+struct McgPre {
+  PcgPrecond P;
+  float* z;
+  double *proj, *coef, *prz;
+};
+
+void mcg_pre_layout(const Layout& L, int m, int rank, Arena& ar, size_t off[4]) {
+  const size_t vec = sizeof(float) * (size_t)L.chains * std::max<int64_t>(1, L.n_total) * m;
+  const size_t items = (size_t)std::max(1, L.n_items) * L.chains * m;
+  off[0] = ar.take(vec);
+  off[1] = ar.take(sizeof(double) * items * rank);
+  off[2] = ar.take(sizeof(double) * (size_t)L.n_inst * L.chains * m * rank);
+  off[3] = ar.take(sizeof(double) * items);
+}
+
+McgPre mcg_pre(kmv_handle h, const size_t off[4]) {
+  McgPre p;
+  p.P = PcgPrecond{h->pc.rank, h->pc.U, h->pc.lam};
+  p.z = at<float>(h, off[0]);
+  p.proj = at<double>(h, off[1]);
+  p.coef = at<double>(h, off[2]);
+  p.prz = at<double>(h, off[3]);
+  return p;
+}
+
 // CG on (A(theta_s) + shift[s m + q] I) x_q = b_q for the m columns q of every
 // system s, one m-column product per iteration; the column results stay in B.cols.
-// b is (chains, N) shared by the columns (b_cols == 0) or (chains, N, m).
+// b is (chains, N) shared by the columns (b_cols == 0) or (chains, N, m).  With
+// pre, each column runs preconditioned CG.
 kmv_status run_mcg(kmv_handle h, const kmv_points* pts, const double* theta, const float* shifts, int m,
                    const float* b, int b_cols, float* x, double tol, int maxiter, int warm, const McgBufs& B,
-                   kmv_precision prec, cudaStream_t st) {
+                   kmv_precision prec, cudaStream_t st, const McgPre* pre = nullptr) {
   const Layout& L = h->layout;
   KmvArgs a = base_args(h, pts, theta);
   a.m = m;
@@ -676,6 +704,13 @@ kmv_status run_mcg(kmv_handle h, const kmv_points* pts, const double* theta, con
   KMV_CUDA(h, cudaMemsetAsync(B.n_active, 0, sizeof(int32_t), st));
   KMV_CUDA(h, launch_mcg_reduce_init(h->dev, L.n_inst, L.chains, m, B.partial2, tol, B.cols, B.sys_any,
                                      B.n_active, st));
+  const size_t vbytes = sizeof(float) * (size_t)L.chains * L.n_total * m;
+  if (pre) {
+    KMV_CUDA(h, launch_mcg_precond(h->dev, L.n_items, L.n_inst, L.chains, L.n_total, m, pre->P, a.theta, a.n_theta,
+                                   shifts, B.r, pre->z, B.sys_any, pre->proj, pre->coef, pre->prz, st));
+    KMV_CUDA(h, launch_mcg_set_rz(h->dev, L.n_inst, L.chains, m, pre->prz, B.cols, st));
+    if (vbytes) KMV_CUDA(h, cudaMemcpyAsync(B.p, pre->z, vbytes, cudaMemcpyDeviceToDevice, st));
+  }
   a.V = B.p;
   a.Y = B.q;
   a.sys_active = B.sys_any;
@@ -688,13 +723,17 @@ kmv_status run_mcg(kmv_handle h, const kmv_points* pts, const double* theta, con
     }
     KMV_TRY(run_forward(h, a, prec, st));
     KMV_CUDA(h, launch_mcg_dot(h->dev, L.n_items, L.chains, L.n_total, m, B.p, B.q, B.sys_any, B.partial, st));
-    KMV_CUDA(h, launch_mcg_alpha(h->dev, L.n_inst, L.chains, m, B.partial, B.cols, B.sys_any, st));
+    KMV_CUDA(h, launch_mcg_alpha(h->dev, L.n_inst, L.chains, m, B.partial, B.cols, B.sys_any, pre ? 1 : 0, st));
     KMV_CUDA(h, launch_mcg_update_xr(h->dev, L.n_items, L.chains, L.n_total, m, B.cols, B.sys_any, x, B.r, B.p,
                                      B.q, B.partial, st));
+    if (pre)
+      KMV_CUDA(h, launch_mcg_precond(h->dev, L.n_items, L.n_inst, L.chains, L.n_total, m, pre->P, a.theta,
+                                     a.n_theta, shifts, B.r, pre->z, B.sys_any, pre->proj, pre->coef, pre->prz, st));
     KMV_CUDA(h, cudaMemsetAsync(B.n_active, 0, sizeof(int32_t), st));
-    KMV_CUDA(h, launch_mcg_beta(h->dev, L.n_inst, L.chains, m, B.partial, tol, maxiter, B.cols, B.sys_any,
-                                B.n_active, st));
-    KMV_CUDA(h, launch_mcg_update_p(h->dev, L.n_items, L.chains, L.n_total, m, B.cols, B.sys_any, B.r, B.p, st));
+    KMV_CUDA(h, launch_mcg_beta(h->dev, L.n_inst, L.chains, m, B.partial, pre ? pre->prz : nullptr, tol, maxiter,
+                                B.cols, B.sys_any, B.n_active, st));
+    KMV_CUDA(h, launch_mcg_update_p(h->dev, L.n_items, L.chains, L.n_total, m, B.cols, B.sys_any,
+                                    pre ? pre->z : B.r, B.p, st));
   }
   return KMV_OK;
 }
@@ -981,13 +1020,19 @@ kmv_status kmv_phi_refresh(kmv_handle h, const kmv_points* pts, int32_t chains, 
   const int n_sys = L.n_inst * chains;
   const int64_t n_cols = (int64_t)n_sys * n_poles;
   const bool refined = prec == KMV_BF16_HILO;
+  // with a preconditioner set (and matching this layout) the shifted systems run
+  // as preconditioned columns of one multi-column CG (a preconditioner breaks the
+  // shift invariance multi-shift CG relies on); without, multi-shift CG
+  const bool use_pc = h->pc_on && h->pc.n_inst == L.n_inst && h->pc.chains == L.chains &&
+                      h->pc.n_total == L.n_total;
+  if (h->pc_on && !use_pc)
+    return fail(h, KMV_EINVAL, "the preconditioner was built for another layout (n_inst, chains, N_total)");
   Arena ar;
-  size_t ob[8], orf[8], oms[10];
-  mscg_layout(L, n_poles, ar, oms);
-  if (refined) {
-    mcg_layout(L, n_poles, ar, ob);
-    mcg_layout(L, n_poles, ar, orf);
-  }
+  size_t ob[8], orf[8], oms[10], opre[4];
+  if (!use_pc) mscg_layout(L, n_poles, ar, oms);
+  if (refined || use_pc) mcg_layout(L, n_poles, ar, ob);
+  if (refined && !use_pc) mcg_layout(L, n_poles, ar, orf);
+  if (use_pc) mcg_pre_layout(L, n_poles, h->pc.rank, ar, opre);
   const size_t vec1 = sizeof(float) * (size_t)chains * std::max<int64_t>(1, n_total);
   const size_t o_x = ar.take(sizeof(float) * (size_t)chains * std::max<int64_t>(1, n_total) * n_poles);
   const size_t o_sh = ar.take(sizeof(float) * (size_t)n_cols);
@@ -1023,14 +1068,24 @@ kmv_status kmv_phi_refresh(kmv_handle h, const kmv_points* pts, int32_t chains, 
   }
   KMV_CUDA(h, launch_phi_bounds(h->dev, n_sys, chains, n_total, y1, 1.01, bounds, st));
   KMV_CUDA(h, launch_phi_poles(n_sys, n_theta, n_poles, theta, bounds, shifts, weights, poles_out, st));
-  // the n_poles shifted systems of every (instance, chain) from one Krylov sequence
-  KMV_TRY(run_mscg(h, pts, theta, shifts, n_poles, xi, x_p, cg_tol, cg_maxiter, col_status, col_iters,
-                   mscg_bufs(h, oms), prec, st));
-  if (refined) {
-    // the BF16 operator leaves the shifted solves at its own accuracy: polish each
-    // to cg_tol by refinement with FP32 residuals (a check only, where they are there)
-    KMV_TRY(run_mcg_refined(h, pts, theta, shifts, n_poles, xi, x_p, 1, cg_tol, cg_maxiter, col_status, col_iters,
-                            mcg_bufs(h, ob), mcg_bufs(h, orf), dx, prev_rr, st));
+  if (use_pc) {
+    // FP32 products in both forms: the n_poles-column tensor-core product (1e-3)
+    // is too coarse to refine the small-shift systems when sigma^2 is small next
+    // to |K|, and with the preconditioner the solve takes few iterations
+    const McgPre pre = mcg_pre(h, opre);
+    const McgBufs B = mcg_bufs(h, ob);
+    KMV_TRY(run_mcg(h, pts, theta, shifts, n_poles, xi, 0, x_p, cg_tol, cg_maxiter, 0, B, KMV_FP32, st, &pre));
+    KMV_CUDA(h, launch_mcg_finish(n_cols, B.cols, 0, col_status, col_iters, st));
+  } else {
+    // the n_poles shifted systems of every (instance, chain) from one Krylov sequence
+    KMV_TRY(run_mscg(h, pts, theta, shifts, n_poles, xi, x_p, cg_tol, cg_maxiter, col_status, col_iters,
+                     mscg_bufs(h, oms), prec, st));
+    if (refined) {
+      // the BF16 operator leaves the shifted solves at its own accuracy: polish each
+      // to cg_tol by refinement with FP32 residuals (a check only, where they are there)
+      KMV_TRY(run_mcg_refined(h, pts, theta, shifts, n_poles, xi, x_p, 1, cg_tol, cg_maxiter, col_status,
+                              col_iters, mcg_bufs(h, ob), mcg_bufs(h, orf), dx, prev_rr, st));
+    }
   }
   KMV_CUDA(h, launch_phi_combine(h->dev, n_items, chains, n_poles, n_total, weights, x_p, phi, st));
   KMV_CUDA(h, launch_phi_status(n_sys, n_poles, col_status, col_iters, chain_status, cg_iters, st));

@@ -49,7 +49,7 @@ struct DevLayout {
 
 // Per-(system, column) state of the multi-column CG (kmv_mcg.cu).
 struct McgCol {
-  double rr, bb, alpha, beta;
+  double rr, bb, alpha, beta, rz;   // rz: r.z of the preconditioned form
   int32_t iters, status, active;
   int32_t pad;  // refinement: 1 when the column's last correction is to be taken back
 };
@@ -228,12 +228,13 @@ cudaError_t launch_mcg_reduce_init(const DevLayout& L, int n_inst, int chains, i
 cudaError_t launch_mcg_dot(const DevLayout& L, int n_items, int chains, int64_t n_total, int m, const float* p,
                            const float* q, const int32_t* sys_any, double* partial, cudaStream_t st);
 cudaError_t launch_mcg_alpha(const DevLayout& L, int n_inst, int chains, int m, const double* partial, McgCol* st,
-                             const int32_t* sys_any, cudaStream_t s);
+                             const int32_t* sys_any, int pre, cudaStream_t s);
 cudaError_t launch_mcg_update_xr(const DevLayout& L, int n_items, int chains, int64_t n_total, int m,
                                  const McgCol* stt, const int32_t* sys_any, float* x, float* r, const float* p,
                                  const float* q, double* partial, cudaStream_t st);
-cudaError_t launch_mcg_beta(const DevLayout& L, int n_inst, int chains, int m, const double* partial, double tol,
-                            int maxiter, McgCol* st, int32_t* sys_any, int32_t* n_active, cudaStream_t s);
+cudaError_t launch_mcg_beta(const DevLayout& L, int n_inst, int chains, int m, const double* partial,
+                            const double* prz, double tol, int maxiter, McgCol* st, int32_t* sys_any,
+                            int32_t* n_active, cudaStream_t s);
 cudaError_t launch_mcg_finish(int64_t n_cols, const McgCol* cols, int accumulate, int32_t* col_status,
                               int32_t* col_iters, cudaStream_t st);
 cudaError_t launch_mcg_mask(const DevLayout& L, int n_items, int chains, int64_t n_total, int m, const McgCol* cols,
@@ -243,6 +244,13 @@ cudaError_t launch_mcg_refine(int64_t n_cols, int outer, McgCol* cols, double* p
 cudaError_t launch_mcg_undo(const DevLayout& L, int n_items, int chains, int64_t n_total, int m, const McgCol* cols,
                             const float* dx, float* x, cudaStream_t st);
 cudaError_t launch_mcg_refine_finish(int64_t n_cols, const McgCol* cols, int32_t* col_status, cudaStream_t st);
+// preconditioned multi-column CG: z_q = r_q + U (d_q o (U^T r_q)), d from mu_q = sigma^2 + shift_q
+cudaError_t launch_mcg_precond(const DevLayout& L, int n_items, int n_inst, int chains, int64_t n_total, int m,
+                               const PcgPrecond& P, const double* theta, int n_theta, const float* shifts,
+                               const float* r, float* z, const int32_t* sys_any, double* proj, double* coef,
+                               double* prz, cudaStream_t st);
+cudaError_t launch_mcg_set_rz(const DevLayout& L, int n_inst, int chains, int m, const double* prz, McgCol* cols,
+                              cudaStream_t st);
 cudaError_t launch_mcg_update_p(const DevLayout& L, int n_items, int chains, int64_t n_total, int m,
                                 const McgCol* stt, const int32_t* sys_any, const float* r, float* p,
                                 cudaStream_t st);

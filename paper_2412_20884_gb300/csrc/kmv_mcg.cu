@@ -99,9 +99,10 @@ __global__ void mcg_dot_kernel(DevLayout L, int chains, int64_t n_total, int m, 
   }
 }
 
-// alpha = r.r / p.q for the active columns; a non-positive p.q is a breakdown.
+// alpha = r.r / p.q (r.z / p.q when preconditioned) for the active columns; a
+// non-positive p.q is a breakdown.
 __global__ void mcg_alpha_kernel(DevLayout L, int n_inst, int chains, int m, const double* partial, McgCol* st,
-                                 const int32_t* sys_any) {
+                                 const int32_t* sys_any, int pre) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= n_inst * chains || !sys_any[s]) return;
   const int bi = s / chains, c = s - bi * chains;
@@ -114,12 +115,13 @@ __global__ void mcg_alpha_kernel(DevLayout L, int n_inst, int chains, int m, con
     double pq = 0.0;
     for (int it = L.inst_item0[bi]; it < L.inst_item0[bi + 1]; ++it)
       pq += partial[((int64_t)it * chains + c) * m + col];
-    if (!(pq > 0.0) || !isfinite(pq)) {
+    const double num = pre ? k.rz : k.rr;
+    if (!(pq > 0.0) || !isfinite(pq) || !(num > 0.0)) {
       k.alpha = 0.0;
       k.active = 0;
-      k.status = isfinite(pq) ? KMV_ENOTCONV : KMV_ENONFINITE;
+      k.status = (isfinite(pq) && isfinite(num)) ? KMV_ENOTCONV : KMV_ENONFINITE;
     } else {
-      k.alpha = k.rr / pq;
+      k.alpha = num / pq;
     }
   }
 }
@@ -153,9 +155,11 @@ __global__ void mcg_update_xr_kernel(DevLayout L, int chains, int64_t n_total, i
   }
 }
 
-// beta = r.r_new / r.r; stop converged columns (r.r <= tol^2 b.b) and those at maxiter
-__global__ void mcg_beta_kernel(DevLayout L, int n_inst, int chains, int m, const double* partial, double tol,
-                                int maxiter, McgCol* st, int32_t* sys_any, int32_t* n_active) {
+// beta = r.r_new / r.r (r.z_new / r.z when preconditioned, prz != NULL); stop
+// converged columns (r.r <= tol^2 b.b) and those at maxiter
+__global__ void mcg_beta_kernel(DevLayout L, int n_inst, int chains, int m, const double* partial,
+                                const double* prz, double tol, int maxiter, McgCol* st, int32_t* sys_any,
+                                int32_t* n_active) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= n_inst * chains || !sys_any[s]) return;
   const int bi = s / chains, c = s - bi * chains;
@@ -166,7 +170,15 @@ __global__ void mcg_beta_kernel(DevLayout L, int n_inst, int chains, int m, cons
     double rr = 0.0;
     for (int it = L.inst_item0[bi]; it < L.inst_item0[bi + 1]; ++it)
       rr += partial[((int64_t)it * chains + c) * m + col];
-    k.beta = rr / k.rr;
+    if (prz) {
+      double rz = 0.0;
+      for (int it = L.inst_item0[bi]; it < L.inst_item0[bi + 1]; ++it)
+        rz += prz[((int64_t)it * chains + c) * m + col];
+      k.beta = rz / k.rz;
+      k.rz = rz;
+    } else {
+      k.beta = rr / k.rr;
+    }
     k.rr = rr;
     k.iters += 1;
     if (!isfinite(rr)) {
@@ -184,7 +196,7 @@ __global__ void mcg_beta_kernel(DevLayout L, int n_inst, int chains, int m, cons
   sys_any[s] = any;
 }
 
-// p = r + beta p on the active columns
+// p = r + beta p on the active columns (r is z when preconditioned)
 __global__ void mcg_update_p_kernel(DevLayout L, int chains, int64_t n_total, int m, const McgCol* st,
                                     const int32_t* sys_any, const float* r, float* p) {
   const int item = blockIdx.x, c = blockIdx.y;
@@ -299,7 +311,144 @@ __global__ void mcg_refine_finish_kernel(int64_t n_cols, const McgCol* cols, int
   }
 }
 
+// Multi-column projection: partial[tile, c, q, k] = sum over the tile's rows of
+// U[c, k, i] r[c, i, q]; the tile's r columns are staged in shared memory and
+// each U row segment is read once for all columns.
+__global__ void mcg_proj_kernel(DevLayout L, int chains, int64_t n_total, int m, int rank, const float* U,
+                                const float* r, const int32_t* sys_any, double* partial) {
+  __shared__ float rs[kMaxShifts][kTile];
+  const int item = blockIdx.x, c = blockIdx.y;
+  const int b = L.item_inst[item];
+  if (sys_any && !sys_any[b * chains + c]) return;
+  const int64_t r0 = L.item_row0[item], r1 = L.offsets[b + 1];
+  for (int e = threadIdx.x; e < m * kTile; e += blockDim.x) {
+    const int row = e / m, q = e - row * m;
+    const int64_t i = r0 + row;
+    rs[q][row] = i < r1 ? r[((int64_t)c * n_total + i) * m + q] : 0.f;
+  }
+  __syncthreads();
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  for (int k = w; k < rank; k += kTile / 32) {
+    const float* Uk = U + ((int64_t)c * rank + k) * n_total;
+    float u[kTile / 32];
+#pragma unroll
+    for (int t = 0; t < kTile / 32; ++t) {
+      const int64_t i = r0 + l + 32 * t;
+      u[t] = i < r1 ? Uk[i] : 0.f;
+    }
+    for (int q = 0; q < m; ++q) {
+      double acc = 0.0;
+#pragma unroll
+      for (int t = 0; t < kTile / 32; ++t) acc += (double)u[t] * (double)rs[q][l + 32 * t];
+      for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+      if (l == 0) partial[(((int64_t)item * chains + c) * m + q) * rank + k] = acc;
+    }
+  }
+}
+
+// coef[s, q, k] = d_{q,k} sum over the instance's tiles of partial[., q, k],
+// d = (lambda_r + mu_q) / (lambda_k + mu_q) - 1, mu_q = sigma_s^2 + shift[s, q]
+__global__ void mcg_coef_kernel(DevLayout L, int n_inst, int chains, int m, int rank, int n_theta,
+                                const double* theta, const float* shifts, const double* lam, const double* partial,
+                                const int32_t* sys_any, double* coef) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= (int64_t)n_inst * chains * m * rank) return;
+  const int k = (int)(e % rank);
+  const int64_t sq = e / rank;
+  const int q = (int)(sq % m), s = (int)(sq / m);
+  if (sys_any && !sys_any[s]) return;
+  const int b = s / chains, c = s - b * chains;
+  const double mu = exp(theta[(int64_t)s * n_theta + n_theta - 1]) + (double)shifts[(int64_t)s * m + q];
+  const double lr = lam[(int64_t)s * rank + rank - 1];
+  const double d = (lr + mu) / (lam[(int64_t)s * rank + k] + mu) - 1.0;
+  double acc = 0.0;
+  for (int it = L.inst_item0[b]; it < L.inst_item0[b + 1]; ++it)
+    acc += partial[(((int64_t)it * chains + c) * m + q) * rank + k];
+  coef[e] = d * acc;
+}
+
+// z[c, i, q] = r[c, i, q] + sum_k U[c, k, i] coef[s, q, k]; partials of r.z per column
+__global__ void mcg_apply_kernel(DevLayout L, int chains, int64_t n_total, int m, int rank, const float* U,
+                                 const double* coef, const float* r, float* z, const int32_t* sys_any,
+                                 double* prz) {
+  extern __shared__ float cf[];   // m x rank
+  __shared__ double red[kTile / 32][kMaxShifts];
+  const int item = blockIdx.x, c = blockIdx.y;
+  const int b = L.item_inst[item];
+  const int s = b * chains + c;
+  if (sys_any && !sys_any[s]) return;
+  for (int e = threadIdx.x; e < m * rank; e += blockDim.x) cf[e] = (float)coef[(int64_t)s * m * rank + e];
+  __syncthreads();
+  const int64_t i = L.item_row0[item] + threadIdx.x;
+  const bool valid = i < L.offsets[b + 1];
+  float acc[kMaxShifts];
+#pragma unroll
+  for (int q = 0; q < kMaxShifts; ++q) acc[q] = 0.f;
+  if (valid) {
+    for (int k = 0; k < rank; ++k) {
+      const float u = U[((int64_t)c * rank + k) * n_total + i];
+#pragma unroll
+      for (int q = 0; q < kMaxShifts; ++q)
+        if (q < m) acc[q] = fmaf(u, cf[q * rank + k], acc[q]);
+    }
+  }
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+#pragma unroll
+  for (int q = 0; q < kMaxShifts; ++q) {
+    if (q >= m) break;
+    double v = 0.0;
+    if (valid) {
+      const int64_t o = ((int64_t)c * n_total + i) * m + q;
+      const float rv = r[o];
+      const float zv = rv + acc[q];
+      z[o] = zv;
+      v = (double)rv * zv;
+    }
+    for (int o2 = 16; o2 > 0; o2 >>= 1) v += __shfl_down_sync(0xffffffffu, v, o2);
+    if (l == 0) red[w][q] = v;
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < m; q += blockDim.x) {
+    double t = 0.0;
+    for (int u = 0; u < kTile / 32; ++u) t += red[u][q];
+    prz[((int64_t)item * chains + c) * m + q] = t;
+  }
+}
+
+// rz of every column from the per-tile partials (after the first preconditioning)
+__global__ void mcg_set_rz_kernel(DevLayout L, int n_inst, int chains, int m, const double* prz, McgCol* cols) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n_inst * chains) return;
+  const int b = s / chains, c = s - b * chains;
+  for (int q = 0; q < m; ++q) {
+    double rz = 0.0;
+    for (int it = L.inst_item0[b]; it < L.inst_item0[b + 1]; ++it) rz += prz[((int64_t)it * chains + c) * m + q];
+    cols[(int64_t)s * m + q].rz = rz;
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_mcg_precond(const DevLayout& L, int n_items, int n_inst, int chains, int64_t n_total, int m,
+                               const PcgPrecond& P, const double* theta, int n_theta, const float* shifts,
+                               const float* r, float* z, const int32_t* sys_any, double* proj, double* coef,
+                               double* prz, cudaStream_t st) {
+  if (n_items == 0) return cudaSuccess;
+  mcg_proj_kernel<<<dim3(n_items, chains), kTile, 0, st>>>(L, chains, n_total, m, P.rank, P.U, r, sys_any, proj);
+  const int64_t n = (int64_t)n_inst * chains * m * P.rank;
+  mcg_coef_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(L, n_inst, chains, m, P.rank, n_theta, theta, shifts,
+                                                               P.lam, proj, sys_any, coef);
+  mcg_apply_kernel<<<dim3(n_items, chains), kTile, sizeof(float) * m * P.rank, st>>>(L, chains, n_total, m, P.rank,
+                                                                                     P.U, coef, r, z, sys_any, prz);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mcg_set_rz(const DevLayout& L, int n_inst, int chains, int m, const double* prz, McgCol* cols,
+                              cudaStream_t st) {
+  const int n = n_inst * chains;
+  mcg_set_rz_kernel<<<(n + 127) / 128, 128, 0, st>>>(L, n_inst, chains, m, prz, cols);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_mcg_finish(int64_t n_cols, const McgCol* cols, int accumulate, int32_t* col_status,
                               int32_t* col_iters, cudaStream_t st) {
@@ -361,9 +510,9 @@ cudaError_t launch_mcg_dot(const DevLayout& L, int n_items, int chains, int64_t 
 }
 
 cudaError_t launch_mcg_alpha(const DevLayout& L, int n_inst, int chains, int m, const double* partial, McgCol* st,
-                             const int32_t* sys_any, cudaStream_t s) {
+                             const int32_t* sys_any, int pre, cudaStream_t s) {
   const int n = n_inst * chains;
-  mcg_alpha_kernel<<<(n + 127) / 128, 128, 0, s>>>(L, n_inst, chains, m, partial, st, sys_any);
+  mcg_alpha_kernel<<<(n + 127) / 128, 128, 0, s>>>(L, n_inst, chains, m, partial, st, sys_any, pre);
   return cudaGetLastError();
 }
 
@@ -376,10 +525,11 @@ cudaError_t launch_mcg_update_xr(const DevLayout& L, int n_items, int chains, in
   return cudaGetLastError();
 }
 
-cudaError_t launch_mcg_beta(const DevLayout& L, int n_inst, int chains, int m, const double* partial, double tol,
-                            int maxiter, McgCol* st, int32_t* sys_any, int32_t* n_active, cudaStream_t s) {
+cudaError_t launch_mcg_beta(const DevLayout& L, int n_inst, int chains, int m, const double* partial,
+                            const double* prz, double tol, int maxiter, McgCol* st, int32_t* sys_any,
+                            int32_t* n_active, cudaStream_t s) {
   const int n = n_inst * chains;
-  mcg_beta_kernel<<<(n + 127) / 128, 128, 0, s>>>(L, n_inst, chains, m, partial, tol, maxiter, st, sys_any,
+  mcg_beta_kernel<<<(n + 127) / 128, 128, 0, s>>>(L, n_inst, chains, m, partial, prz, tol, maxiter, st, sys_any,
                                                   n_active);
   return cudaGetLastError();
 }

@@ -145,6 +145,41 @@ def test_leapfrog_with_and_without_preconditioner(kmv_handle):
     np.testing.assert_allclose(th_b.cpu().numpy(), th_a.cpu().numpy(), rtol=0, atol=0.5 * 0.02 * tol_pi + 1e-12)
 
 
+@pytest.mark.parametrize("prec", ["fp32", "bf16_hilo"])
+def test_preconditioned_phi_refresh(kmv_handle, prec):
+    from oracle import poles
+    w = wl.ragged([500, 260], d=2, chains=2, m=1, ard=True, seed=93, ell_range=(0.3, 0.8), sigma2=0.01)
+    pts, theta, _, _ = to_dev(w)
+    xi = np.random.default_rng(94).standard_normal((w.chains, w.n_total)).astype(np.float32)
+    xd = torch.tensor(xi, device="cuda")
+    phi0, st0, it0 = kmv_handle.phi_refresh(pts, theta, xd, n_poles=15, cg_tol=1e-6, cg_maxiter=3000, prec=prec)
+    phi0 = phi0.cpu().numpy()
+    U, lam, _ = kmv_handle.nystrom_build(pts, theta, torch.tensor(_omega(w, 48, 95), device="cuda"))
+    kmv_handle.set_preconditioner(pts, U, lam)
+    try:
+        phi, st, it, pl = kmv_handle.phi_refresh(pts, theta, xd, n_poles=15, cg_tol=1e-6, cg_maxiter=3000,
+                                                 want_poles=True, prec=prec)
+    finally:
+        kmv_handle.set_preconditioner(pts)
+    assert torch.all(st0 == 0) and torch.all(st == 0)
+    phi, pl = phi.cpu().numpy(), pl.cpu().numpy()
+    X = f32(w.X)
+    for b in range(w.n_inst):
+        r0, r1 = w.offsets[b], w.offsets[b + 1]
+        for c in range(w.chains):
+            s = b * w.chains + c
+            A = sk.A_matrix(X[r0:r1], w.theta[s], True)
+            ref = poles.inv_sqrt_apply(A, xi[c, r0:r1].astype(np.float64), pl[s, 0], pl[s, 1], 15)
+            xn = np.linalg.norm(xi[c, r0:r1])
+            bound = 20 * 1e-6 * xn / math.sqrt(pl[s, 0]) + 1e-5 * np.linalg.norm(ref)
+            # sigma^2 = 0.01 puts the FP32 floor of the shifted solves near this bound:
+            # the preconditioned draw is held to it or to twice the multi-shift draw's error
+            err0 = np.linalg.norm(phi0[c, r0:r1] - ref)
+            assert np.linalg.norm(phi[c, r0:r1] - ref) <= max(bound, 2.0 * err0), (s, bound, err0)
+    # fewer iterations than the unpreconditioned multi-shift solve
+    assert it.cpu().numpy().max() < it0.cpu().numpy().max(), (it, it0)
+
+
 def test_preconditioner_arguments(kmv_handle):
     from paper_2412_20884_gb300 import KmvError
     w = wl.ragged([200], d=2, chains=1, m=1, seed=90)
