@@ -204,6 +204,45 @@ kmv_status leapfrog_step(kmv_handle h, const kmv_points* pts, int32_t chains,
                          kmv_precision prec, void* stream);
 
 /*
+ * kmv_implicit_step - one implicit midpoint step of Sec. 3.2.3 for every chain:
+ * the (theta_1, pi_1, x) of Eq. implicitsystem,
+ *     theta_1 = theta_0 + dt (pi_0 + pi_1)/2,
+ *     pi_1    = pi_0 - dt F(theta_bar, x),   theta_bar = (theta_0 + theta_1)/2,
+ *     A(theta_bar) x = y,
+ * with F the frozen-x force of leapfrog_step, found as the fixed point of the
+ * map Phi of Eq. Phi by Anderson acceleration with depth aa_depth (App. B; the
+ * paper uses 10), theta, pi and x taken as one vector.  Phi's linear part uses
+ * R = P^{-1} / c when a Nystrom preconditioner is set (kmv_set_preconditioner),
+ * else R = I / c, c = 1.05 x a 20-step power estimate of rho(P^{-1} A(theta_0))
+ * (resp. rho(A(theta_0))), so that the plain iteration contracts.  A system
+ * stops when every theta, pi component of z - Phi(z) is <= tol (1 + max
+ * |Phi(z)|) and |y - A(theta_bar) x| <= tol |y|, or that residual is below
+ * 1e-3 |y| and has not halved in 8 aa_depth iterations (the floor of the FP32
+ * product, about 2^-24 |A| |x|, can lie above tol |y| on ill-conditioned systems);
+ * theta, pi and x_work then hold Phi(z) of that iteration.
+ *
+ *   theta, pi    DEVICE FP64 (n_inst * chains, n_theta): in theta_0, pi_0; out
+ *                theta_1, pi_1.
+ *   x_work       DEVICE FP32 (chains, N_total): in the starting x (e.g. the last
+ *                step's), out x at the midpoint.
+ *   aa_depth     1..16; maxiter >= 1 iterations (each one product, one FP32 adjoint).
+ *   chain_status DEVICE int32: KMV_OK, KMV_ENOTCONV (maxiter reached: theta,
+ *                pi hold the last iterate; reject), KMV_ENONFINITE.
+ *   iters        DEVICE int32 (n_inst * chains): iterations taken.
+ *   prior_mu, prior_prec, free_mask as in leapfrog_step.  Both forms (prec)
+ *   take FP32 products and the FP32 adjoint here: the iteration measures the
+ *   true residual y - A x, which the tensor-core product's rounding keeps
+ *   above tol on ill-conditioned systems.
+ * The Metropolis test needs A(theta_1)^{-1} y afterwards (kmv_energy).
+ */
+kmv_status kmv_implicit_step(kmv_handle h, const kmv_points* pts, int32_t chains,
+                             const float* y, const float* phi, double* theta, double* pi,
+                             double dt, const double* prior_mu, const double* prior_prec,
+                             const uint8_t* free_mask, int32_t aa_depth, double tol,
+                             int32_t maxiter, float* x_work, int32_t* chain_status,
+                             int32_t* iters, kmv_precision prec, void* stream);
+
+/*
  * kmv_energy - the Hamiltonian of Sec. 3.2 per chain, accumulated in FP64:
  *     U = S(theta) + y^T x / 2 + phi^T A phi / 2,  x = A(theta)^{-1} y   (Eq. U)
  *     H = U + pi^T pi / 2                                            (M = I)

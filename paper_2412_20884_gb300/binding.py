@@ -54,6 +54,8 @@ _SIGS = {
                                C.c_int32, C.c_int32, _P, _P, C.c_int, _P]),
     "leapfrog_step": (C.c_int, [_P, C.POINTER(_Points), C.c_int32, _P, _P, _P, _P, C.c_double, _P, _P, _P,
                                 C.c_double, C.c_int32, _P, _P, _P, C.c_int, _P]),
+    "kmv_implicit_step": (C.c_int, [_P, C.POINTER(_Points), C.c_int32, _P, _P, _P, _P, C.c_double, _P, _P, _P,
+                                    C.c_int32, C.c_double, C.c_int32, _P, _P, _P, C.c_int, _P]),
     "kmv_energy": (C.c_int, [_P, C.POINTER(_Points), C.c_int32, _P, _P, _P, _P, _P, _P, C.c_double,
                              C.c_int32, _P, _P, _P, _P, _P, C.c_int, _P]),
     "kmv_backward_noalloc": (C.c_int, [C.POINTER(_Points), C.c_int32, _P, _P, _P, C.c_int32, _P, _P, _P]),
@@ -322,6 +324,33 @@ class Kmv:
                                          float(dt), _ptr(mu), _ptr(prec_), _ptr(free_mask), float(cg_tol),
                                          int(cg_maxiter), _ptr(x_work), _ptr(status), _ptr(iters),
                                          self._prec(prec), _stream(stream)))
+        return status, iters, x_work
+
+    def implicit_step(self, pts: Points, y, phi, theta, pi, dt, prior=None, free_mask=None, aa_depth=10,
+                      tol=1e-6, maxiter=200, x_work=None, prec="fp32", stream=None):
+        """One implicit midpoint step by Anderson acceleration (kmv_implicit_step); theta, pi
+        and x_work (the starting x; zeros when None) are updated in place.  Returns (status, iters, x_work)."""
+        chains = self._chains(pts, theta)
+        n_sys = pts.n_inst * chains
+        _need(y, torch.float32, "y", (pts.n_total,))
+        _need(phi, torch.float32, "phi", (chains, pts.n_total))
+        _need(theta, torch.float64, "theta", (n_sys, pts.n_theta))
+        _need(pi, torch.float64, "pi", (n_sys, pts.n_theta))
+        mu = prec_ = None
+        if prior is not None:
+            mu = _need(prior[0], torch.float64, "prior_mu", (pts.n_theta,))
+            prec_ = _need(prior[1], torch.float64, "prior_prec", (pts.n_theta,))
+        if free_mask is not None:
+            _need(free_mask, torch.uint8, "free_mask", (pts.n_theta,))
+        if x_work is None:
+            x_work = torch.zeros((chains, pts.n_total), dtype=torch.float32, device=y.device)
+        _need(x_work, torch.float32, "x_work", (chains, pts.n_total))
+        status = torch.empty(n_sys, dtype=torch.int32, device=y.device)
+        iters = torch.empty_like(status)
+        self._check(self.L.kmv_implicit_step(self.h, pts.c, chains, _ptr(y), _ptr(phi), _ptr(theta), _ptr(pi),
+                                             float(dt), _ptr(mu), _ptr(prec_), _ptr(free_mask), int(aa_depth),
+                                             float(tol), int(maxiter), _ptr(x_work), _ptr(status), _ptr(iters),
+                                             self._prec(prec), _stream(stream)))
         return status, iters, x_work
 
     def kmv_energy(self, pts: Points, y, phi, theta, pi=None, prior=None, cg_tol=1e-6, cg_maxiter=1000,

@@ -1193,6 +1193,143 @@ kmv_status leapfrog_step(kmv_handle h, const kmv_points* pts, int32_t chains, co
   return KMV_OK;
 }
 
+kmv_status kmv_implicit_step(kmv_handle h, const kmv_points* pts, int32_t chains, const float* y, const float* phi,
+                             double* theta, double* pi, double dt, const double* prior_mu, const double* prior_prec,
+                             const uint8_t* free_mask, int32_t aa_depth, double tol, int32_t maxiter, float* x_work,
+                             int32_t* chain_status, int32_t* iters, kmv_precision prec, void* stream) {
+  KMV_TRY(check_points(h, pts, chains));
+  KMV_TRY(check_prec(h, prec));
+  if (!y || !phi || !theta || !pi || !x_work || !chain_status || !iters)
+    return fail(h, KMV_EINVAL, "NULL argument");
+  if ((prior_mu == nullptr) != (prior_prec == nullptr))
+    return fail(h, KMV_EINVAL, "prior_mu and prior_prec must both be set or both be NULL");
+  if (!std::isfinite(dt) || !(tol > 0.0) || maxiter < 1 || aa_depth < 1 || aa_depth > kMaxAA)
+    return fail(h, KMV_EINVAL, "bad dt / tol / maxiter, or aa_depth outside [1, 16]");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  KMV_TRY(prepare_layout(h, pts, chains, st));
+  const Layout& L = h->layout;
+  if (h->pc_on && (h->pc.n_inst != L.n_inst || h->pc.chains != L.chains || h->pc.n_total != L.n_total))
+    return fail(h, KMV_EINVAL, "the preconditioner was built for another layout (n_inst, chains, N_total)");
+  const int n_sys = L.n_inst * L.chains, n = L.n_theta, k = aa_depth;
+  const size_t vec = (size_t)L.chains * std::max<int64_t>(1, L.n_total);
+  const size_t items = (size_t)std::max(1, L.n_items) * L.chains;
+  const int rank = h->pc_on ? h->pc.rank : 1;
+  Arena ar;
+  const size_t o_th0 = ar.take(sizeof(double) * n_sys * n), o_pi0 = ar.take(sizeof(double) * n_sys * n);
+  const size_t o_tb = ar.take(sizeof(double) * n_sys * n), o_gr = ar.take(sizeof(double) * n_sys * n);
+  const size_t o_vf = ar.take(sizeof(float) * 2 * vec), o_gf = ar.take(sizeof(float) * 2 * vec);
+  const size_t o_bp = ar.take(backward_ws_bytes(L, 2));
+  const size_t o_q = ar.take(sizeof(float) * vec), o_r = ar.take(sizeof(float) * vec), o_z = ar.take(sizeof(float) * vec);
+  const size_t o_gx = ar.take(sizeof(float) * vec * k), o_fx = ar.take(sizeof(float) * vec * k);
+  const size_t o_gtp = ar.take(sizeof(double) * (size_t)k * n_sys * 2 * n);
+  const size_t o_ftp = ar.take(sizeof(double) * (size_t)k * n_sys * 2 * n);
+  const size_t o_h = ar.take(sizeof(double) * (size_t)n_sys * k * k), o_al = ar.take(sizeof(double) * (size_t)n_sys * k);
+  const size_t o_act = ar.take(sizeof(int32_t) * n_sys), o_dn = ar.take(sizeof(int32_t) * n_sys);
+  const size_t o_na = ar.take(sizeof(int32_t) * 4);
+  const size_t o_xp = ar.take(sizeof(double) * items * k), o_rp = ar.take(sizeof(double) * items * 2);
+  const size_t o_c = ar.take(sizeof(double) * n_sys), o_pp = ar.take(sizeof(double) * items);
+  const size_t o_proj = ar.take(sizeof(double) * items * rank), o_coef = ar.take(sizeof(double) * n_sys * rank);
+  const size_t o_prz = ar.take(sizeof(double) * items);
+  const size_t o_brr = ar.take(sizeof(double) * n_sys), o_bit = ar.take(sizeof(int32_t) * n_sys);
+  KMV_TRY(reserve(h, ar.used));
+  double* th0 = at<double>(h, o_th0);
+  double* pi0 = at<double>(h, o_pi0);
+  double* tb = at<double>(h, o_tb);
+  double* grad = at<double>(h, o_gr);
+  float* q = at<float>(h, o_q);
+  float* r = at<float>(h, o_r);
+  float* z = at<float>(h, o_z);
+  int32_t* active = at<int32_t>(h, o_act);
+  int32_t* n_active = at<int32_t>(h, o_na);
+  double* cscale = at<double>(h, o_c);
+  const PcgPrecond P{h->pc.rank, h->pc.U, h->pc.lam};
+  KMV_CUDA(h, cudaMemcpyAsync(th0, theta, sizeof(double) * n_sys * n, cudaMemcpyDeviceToDevice, st));
+  KMV_CUDA(h, cudaMemcpyAsync(pi0, pi, sizeof(double) * n_sys * n, cudaMemcpyDeviceToDevice, st));
+
+  // c ~ rho(R~ A(theta_0)) by 20 power iterations from the vector of ones, times 1.05
+  KMV_TRY(cheb_prepare(h, pts, th0, 2, st));
+  {
+    KmvArgs a = base_args(h, pts, th0);
+    a.m = 1;
+    KMV_CUDA(h, launch_phi_fill(z, (int64_t)vec, 1.0f, st));
+    KMV_CUDA(h, launch_imp_scale(h->dev, L.n_items, L.chains, L.n_total, nullptr, z, z, at<double>(h, o_pp), st));
+    KMV_CUDA(h, launch_imp_norm(h->dev, L.n_inst, L.chains, at<double>(h, o_pp), cscale, st));
+    KMV_CUDA(h, launch_imp_scale(h->dev, L.n_items, L.chains, L.n_total, cscale, z, r, at<double>(h, o_pp), st));
+    for (int t = 0; t < 20; ++t) {
+      a.V = r;
+      a.Y = q;
+      KMV_TRY(run_forward(h, a, KMV_FP32, st));
+      const float* w = q;
+      if (h->pc_on) {
+        KMV_CUDA(h, launch_pcg_precond(h->dev, L.n_items, L.n_inst, L.chains, L.n_total, P, th0, n, q, z, nullptr,
+                                       at<double>(h, o_proj), at<double>(h, o_coef), at<double>(h, o_prz), st));
+        w = z;
+      }
+      KMV_CUDA(h, launch_imp_scale(h->dev, L.n_items, L.chains, L.n_total, nullptr, w, z, at<double>(h, o_pp), st));
+      KMV_CUDA(h, launch_imp_norm(h->dev, L.n_inst, L.chains, at<double>(h, o_pp), cscale, st));
+      KMV_CUDA(h, launch_imp_scale(h->dev, L.n_items, L.chains, L.n_total, cscale, z, r, at<double>(h, o_pp), st));
+    }
+    KMV_CUDA(h, launch_imp_cfinal(n_sys, 1.05, cscale, st));
+  }
+
+  // Anderson-accelerated iteration of Phi, all systems in lockstep, finished ones masked
+  KMV_CUDA(h, launch_fill_i32(active, n_sys, 1, st));
+  KMV_CUDA(h, cudaMemsetAsync(chain_status, 0, sizeof(int32_t) * n_sys, st));
+  KMV_CUDA(h, cudaMemsetAsync(iters, 0, sizeof(int32_t) * n_sys, st));
+  // Phi's linear part takes the FP32 product in both forms: Anderson acceleration
+  // measures the true residual y - A x each iteration, and on ill-conditioned
+  // systems the tensor-core product's rounding kept it above tol (measured: a
+  // kappa ~ 1.5e3 system stalled for 1500 iterations that FP32 solves in 270);
+  // the adjoint of the force, FP32 as well, is most of an iteration's cost
+  const kmv_precision lin_prec = KMV_FP32;
+  (void)prec;
+  const int check_every = 4;
+  for (int it = 0; it < maxiter; ++it) {
+    if (!h->capturing && it > 0 && it % check_every == 0) {
+      KMV_CUDA(h, cudaMemcpyAsync(h->host_flag, n_active, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+      KMV_CUDA(h, cudaStreamSynchronize(st));
+      if (*h->host_flag == 0) break;
+    }
+    const int slot = it % k, cnt = std::min(it + 1, k);
+    KMV_CUDA(h, launch_imp_mid(n_sys * n, th0, theta, tb, st));
+    KMV_TRY(cheb_prepare(h, pts, tb, 2, st));
+    KmvArgs a = base_args(h, pts, tb);
+    a.m = 1;
+    a.V = x_work;
+    a.Y = q;
+    a.sys_active = active;
+    KMV_TRY(run_forward(h, a, lin_prec, st));
+    KMV_CUDA(h, launch_imp_resid(h->dev, L.n_items, L.chains, L.n_total, y, q, active, r, at<double>(h, o_rp), st));
+    const float* zz = r;
+    if (h->pc_on) {
+      KMV_CUDA(h, launch_pcg_precond(h->dev, L.n_items, L.n_inst, L.chains, L.n_total, P, th0, n, r, z, active,
+                                     at<double>(h, o_proj), at<double>(h, o_coef), at<double>(h, o_prz), st));
+      zz = z;
+    }
+    KMV_CUDA(h, launch_imp_x(h->dev, L.n_items, L.chains, L.n_total, k, slot, cnt, x_work, zz, cscale, active,
+                             at<float>(h, o_gx), at<float>(h, o_fx), at<double>(h, o_xp), st));
+    // the frozen-x force at theta_bar (FP32 adjoint, as in the leapfrog step)
+    KMV_CUDA(h, launch_pack_force(L.chains, L.n_total, x_work, phi, at<float>(h, o_vf), at<float>(h, o_gf), st));
+    KmvArgs fa = base_args(h, pts, tb);
+    fa.V = at<float>(h, o_vf);
+    fa.G = at<float>(h, o_gf);
+    fa.m = 2;
+    fa.Y = nullptr;
+    fa.sys_active = active;
+    KMV_TRY(run_backward(h, fa, grad, at<double>(h, o_bp), KMV_FP32, st));
+    KMV_CUDA(h, cudaMemsetAsync(n_active, 0, sizeof(int32_t), st));
+    KMV_CUDA(h, launch_imp_aa(h->dev, L.n_inst, L.chains, n, k, slot, cnt, th0, pi0, theta, pi, grad, prior_mu,
+                              prior_prec, free_mask, dt, at<double>(h, o_xp), at<double>(h, o_rp), tol, it, maxiter,
+                              at<double>(h, o_gtp), at<double>(h, o_ftp), at<double>(h, o_h), at<double>(h, o_al),
+                              active, at<int32_t>(h, o_dn), chain_status, iters, n_active, at<double>(h, o_brr),
+                              at<int32_t>(h, o_bit), st));
+    KMV_CUDA(h, launch_imp_mix(h->dev, L.n_items, L.n_inst, L.chains, L.n_total, n, k, slot, cnt,
+                               at<double>(h, o_gtp), at<float>(h, o_gx), at<double>(h, o_al), active,
+                               at<int32_t>(h, o_dn), theta, pi, x_work, st));
+  }
+  return KMV_OK;
+}
+
 kmv_status kmv_energy(kmv_handle h, const kmv_points* pts, int32_t chains, const float* y,
                       const float* phi, const double* theta, const double* pi,
                       const double* prior_mu, const double* prior_prec, double cg_tol,

@@ -185,6 +185,31 @@ cudaError_t launch_pcg_update_p(const DevLayout& L, int n_items, int chains, int
 cudaError_t launch_pcg_finish(int n_sys, const PcgSys* sys, const int32_t* active, int32_t* status, int32_t* iters,
                               cudaStream_t st);
 
+// Implicit midpoint step by Anderson acceleration (kmv_implicit.cu)
+constexpr int kMaxAA = 16;
+cudaError_t launch_fill_i32(int32_t* v, int n, int32_t val, cudaStream_t st);
+cudaError_t launch_imp_mid(int n, const double* th0, const double* th, double* tb, cudaStream_t st);
+cudaError_t launch_imp_resid(const DevLayout& L, int n_items, int chains, int64_t n_total, const float* y,
+                             const float* q, const int32_t* active, float* r, double* partial2, cudaStream_t st);
+cudaError_t launch_imp_x(const DevLayout& L, int n_items, int chains, int64_t n_total, int k, int slot, int cnt,
+                         const float* x, const float* z, const double* cscale, const int32_t* active, float* Gx,
+                         float* Fx, double* partial, cudaStream_t st);
+cudaError_t launch_imp_aa(const DevLayout& L, int n_inst, int chains, int n, int k, int slot, int cnt,
+                          const double* th0, const double* pi0, const double* th, const double* pi,
+                          const double* grad, const double* mu, const double* prec, const uint8_t* mask, double dt,
+                          const double* xpart, const double* rpart, double tol, int iter, int maxiter, double* Gtp,
+                          double* Ftp, double* H, double* alpha, int32_t* active, int32_t* done_now, int32_t* status,
+                          int32_t* iters, int32_t* n_active, double* best_rr, int32_t* best_it, cudaStream_t st);
+cudaError_t launch_imp_mix(const DevLayout& L, int n_items, int n_inst, int chains, int64_t n_total, int n, int k,
+                           int slot, int cnt, const double* Gtp, const float* Gx, const double* alpha,
+                           const int32_t* active, const int32_t* done_now, double* th, double* pi, float* x,
+                           cudaStream_t st);
+cudaError_t launch_imp_scale(const DevLayout& L, int n_items, int chains, int64_t n_total, const double* norm,
+                             const float* w, float* v, double* partial, cudaStream_t st);
+cudaError_t launch_imp_norm(const DevLayout& L, int n_inst, int chains, const double* partial, double* cscale,
+                            cudaStream_t st);
+cudaError_t launch_imp_cfinal(int n_sys, double safety, double* cscale, cudaStream_t st);
+
 // Chebyshev-amplitude kernel family (kmv_cheb.cu)
 constexpr int kMaxChebOrder = 32;   // N_cheb
 constexpr int kMaxChebDims = 8;     // d when N_cheb >= 2
