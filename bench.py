@@ -233,10 +233,10 @@ def main():
     ap.add_argument("--cpu-rows", type=int, default=512, help="rows of the oracle sample for cpu_baseline")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-leapfrog", action="store_true")
-    ap.add_argument("--suite", default=None, choices=["c3c4", "cheb", "precond"],
+    ap.add_argument("--suite", default=None, choices=["c3c4", "cheb", "precond", "implicit"],
                     help="instead of the headline line: time the C3 products and the C4 leapfrog batch (c3c4), "
                          "the Chebyshev-amplitude kernel family of Sec. 4 (cheb), or the leapfrog step with "
-                         "the randomized Nystrom preconditioner (precond)")
+                         "the randomized Nystrom preconditioner (precond), or the implicit midpoint step (implicit)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -246,6 +246,8 @@ def main():
         return run_suite_cheb(args)
     if args.suite == "precond":
         return run_suite_precond(args)
+    if args.suite == "implicit":
+        return run_suite_implicit(args)
 
     import torch
     import torch.distributed as dist
@@ -513,6 +515,64 @@ def leapfrog_rates(h, dev, rank, world):
                     r[prec]["graph_unavailable"] = str(e)[:200]
         res["c1" if w.n_total == 2048 else "c5_n16384"] = r
     return res
+
+
+def run_suite_implicit(args):
+    """The implicit midpoint step (Anderson acceleration, depth 10, tol 1e-5; one
+    GPU, one JSON line) on c1 and the 16,384-point 8-chain c5 copy, without and
+    with a rank-r Nystrom factorisation built at the starting theta: steps/s and
+    Anderson iterations, beside the leapfrog step at the same dt."""
+    import torch
+    import workloads as wl
+    from paper_2412_20884_gb300 import Kmv, Points
+    dev = torch.device("cuda", 0)
+    h = Kmv(0)
+    out = {"suite": "implicit", "data": "synthetic"}
+    for name, w, dt, steps, rank in (("c1", wl.c1(), 0.01, 5, 64), ("c5_n16384", wl.c5(n=16384, chains=8), 0.002, 2,
+                                                                     128)):
+        pts = Points(torch.tensor(w.X, dtype=torch.float32, device=dev), w.offsets, ard=w.ard)
+        th0 = torch.tensor(w.theta, dtype=torch.float64, device=dev)
+        y = torch.tensor(w.y, dtype=torch.float32, device=dev)
+        rng = np.random.default_rng(9)
+        phi = torch.tensor(rng.standard_normal((w.chains, w.n_total)), dtype=torch.float32, device=dev)
+        pi0 = torch.tensor(0.1 * rng.standard_normal(w.theta.shape), dtype=torch.float64, device=dev)
+        r = {"workload": f"N_total={w.n_total}, d={w.d}, {w.chains} chains, dt={dt}", "steps_timed": steps}
+        for key in ("none", f"rank_{rank}"):
+            if key != "none":
+                om = torch.randn((w.chains, w.n_total, rank), dtype=torch.float32, device=dev,
+                                 generator=torch.Generator(device=dev).manual_seed(8))
+                U, lam, _ = h.nystrom_build(pts, th0, om)
+                h.set_preconditioner(pts, U, lam)
+            rr = {}
+            th, pi = th0.clone(), pi0.clone()
+            xw = torch.zeros_like(phi)
+            st, it, _ = h.implicit_step(pts, y, phi, th0.clone(), pi0.clone(), dt, tol=1e-5, maxiter=2000,
+                                        x_work=torch.zeros_like(phi))
+            it.float().mean().item()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            its, mx, ok = [], 0, True
+            for _ in range(steps):
+                st, it, _ = h.implicit_step(pts, y, phi, th, pi, dt, tol=1e-5, maxiter=2000, x_work=xw)
+                its.append(it.float().mean().item())
+                mx = max(mx, int(it.max().item()))
+                ok = ok and bool((st == 0).all())
+            torch.cuda.synchronize()
+            rr["implicit"] = {"steps_per_s": steps / (time.perf_counter() - t0), "mean_aa_iters": float(np.mean(its)),
+                              "max_aa_iters": mx, "ok": ok}
+            th, pi = th0.clone(), pi0.clone()
+            t0 = time.perf_counter()
+            its = []
+            for _ in range(steps):
+                st, it, _ = h.leapfrog_step(pts, y, phi, th, pi, dt, cg_maxiter=5000)
+                its.append(it.float().mean().item())
+            torch.cuda.synchronize()
+            rr["leapfrog_fp32"] = {"steps_per_s": steps / (time.perf_counter() - t0), "mean_cg_iters": float(np.mean(its))}
+            if key != "none":
+                h.set_preconditioner(pts)
+            r[key] = rr
+        out[name] = r
+    print(json.dumps(out))
 
 
 def run_suite_precond(args):
