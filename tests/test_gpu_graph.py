@@ -73,3 +73,53 @@ def test_graph_replay_equals_eager(kmv_handle, prec):
     graph.replay()
     torch.cuda.synchronize()
     assert torch.equal(th_g, th_first)
+
+
+def test_preconditioned_graph_replay_equals_eager(kmv_handle):
+    """Preconditioned leapfrog steps (Nystrom factors set on the handle) and an
+    implicit midpoint step, captured and replayed, equal their eager runs."""
+    pts, theta0, y, phi, pi0 = _inputs(81)
+    om = torch.tensor(np.random.default_rng(82).standard_normal((2, pts.n_total, 16)), dtype=torch.float32,
+                      device="cuda")
+    U, lam, _ = kmv_handle.nystrom_build(pts, theta0, om)
+    kmv_handle.set_preconditioner(pts, U, lam)
+    try:
+        steps, dt, maxit = 3, 0.02, 60
+        th_e, pi_e = theta0.clone(), pi0.clone()
+        xw_e = torch.empty_like(phi)
+        for _ in range(steps):
+            st, _, _ = kmv_handle.leapfrog_step(pts, y, phi, th_e, pi_e, dt, cg_maxiter=maxit, x_work=xw_e)
+            assert torch.all(st == 0)
+        xi_e = torch.zeros_like(phi)
+        th_ie, pi_ie = theta0.clone(), pi0.clone()
+        st, _, _ = kmv_handle.implicit_step(pts, y, phi, th_ie, pi_ie, dt, tol=1e-5, maxiter=300, x_work=xi_e)
+        assert torch.all(st == 0)
+        th_g, pi_g = theta0.clone(), pi0.clone()
+        xw_g = torch.empty_like(phi)
+        th_ig, pi_ig = theta0.clone(), pi0.clone()
+        xi_g = torch.zeros_like(phi)
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):      # eager warm-up sizes the workspace
+            kmv_handle.leapfrog_step(pts, y, phi, theta0.clone(), pi0.clone(), dt, cg_maxiter=maxit, x_work=xw_g)
+            kmv_handle.implicit_step(pts, y, phi, theta0.clone(), pi0.clone(), dt, tol=1e-5, maxiter=300,
+                                     x_work=torch.zeros_like(phi))
+        torch.cuda.current_stream().wait_stream(side)
+        torch.cuda.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            for _ in range(steps):
+                kmv_handle.leapfrog_step(pts, y, phi, th_g, pi_g, dt, cg_maxiter=maxit, x_work=xw_g)
+            kmv_handle.implicit_step(pts, y, phi, th_ig, pi_ig, dt, tol=1e-5, maxiter=300, x_work=xi_g)
+        th_g.copy_(theta0)
+        pi_g.copy_(pi0)
+        th_ig.copy_(theta0)
+        pi_ig.copy_(pi0)
+        xi_g.zero_()
+        graph.replay()
+        torch.cuda.synchronize()
+        # masked iterations past convergence change nothing: the same results as eager
+        assert torch.equal(th_g, th_e) and torch.equal(pi_g, pi_e)
+        assert torch.equal(th_ig, th_ie) and torch.equal(pi_ig, pi_ie)
+    finally:
+        kmv_handle.set_preconditioner(pts)
