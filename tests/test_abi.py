@@ -45,3 +45,48 @@ def test_binding_signatures_cover_header():
     from paper_2412_20884_gb300 import binding
     for n in declared_functions():
         assert n in binding._SIGS, n
+
+
+def _declaration_arities():
+    text = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    out = {}
+    for m in re.finditer(r"^\s*(?:const\s+)?[a-z_0-9]+\s*\*?\s*([a-z_][a-z_0-9]*)\s*\(([^)]*)\)\s*;", text, flags=re.M):
+        args = m.group(2).strip()
+        out[m.group(1)] = 0 if args in ("", "void") else args.count(",") + 1
+    return out
+
+
+def test_binding_argument_counts_match_header():
+    from paper_2412_20884_gb300 import binding
+    for name, n in _declaration_arities().items():
+        assert len(binding._SIGS[name][1]) == n, (name, len(binding._SIGS[name][1]), n)
+
+
+def test_struct_layouts_match_ctypes(tmp_path):
+    """kmv_points and kmv_nystrom as the C compiler lays them out (gcc on the
+    header) against the binding's ctypes structures: field order, offsets, size."""
+    import shutil
+    import subprocess
+    from paper_2412_20884_gb300 import binding
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = {"kmv_points": binding._Points, "kmv_nystrom": binding._Nystrom}
+    lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "kmv.h"', "int main(void) {"]
+    for cname, ct in structs.items():
+        lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
+        for fname, _ in ct._fields_:
+            lines.append(f'  printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.dirname(HEADER), str(src), "-o", str(exe)], check=True)
+    got = {}
+    for line in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.splitlines():
+        cname, field, val = line.split()
+        got[(cname, field)] = int(val)
+    for cname, ct in structs.items():
+        assert got[(cname, "size")] == ctypes.sizeof(ct), cname
+        for fname, _ in ct._fields_:
+            assert got[(cname, fname)] == getattr(ct, fname).offset, (cname, fname)
