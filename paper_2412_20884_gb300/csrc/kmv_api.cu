@@ -175,8 +175,7 @@ kmv_status prepare_layout(kmv_handle h, const kmv_points* pts, int32_t chains, c
 }
 
 KmvArgs base_args(kmv_handle h, const kmv_points* pts, const double* theta) {
-  KmvArgs a;
-  std::memset(&a, 0, sizeof(a));
+  KmvArgs a{};
   a.L = h->dev;
   a.chains = h->layout.chains;
   a.d = pts->d;

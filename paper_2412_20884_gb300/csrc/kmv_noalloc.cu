@@ -116,8 +116,7 @@ extern "C" kmv_status kmv_backward_noalloc(const kmv_points* pts, int32_t chains
       pts->n_inst, L.offsets, reinterpret_cast<int32_t*>(base + o_ii), reinterpret_cast<int32_t*>(base + o_inst),
       reinterpret_cast<int64_t*>(base + o_row0));
 
-  KmvArgs a;
-  std::memset(&a, 0, sizeof(a));
+  KmvArgs a{};
   a.L = L;
   a.chains = chains;
   a.d = pts->d;
