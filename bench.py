@@ -203,6 +203,21 @@ def kernel_roof(prec, kind, d, m, n, clock_mhz, tensor_tflops, ms):
     return r
 
 
+def max_over_ranks(x: float, world: int, device) -> float:
+    """The largest of every rank's x (all ranks take part when world > 1)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_rate(units_per_rank: float, world: int, ms_max: float) -> float:
+    """Whole-job throughput: the units all ranks processed over the slowest rank's time (G units/s)."""
+    return world * units_per_rank / (ms_max * 1e-3) / 1e9
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -315,11 +330,8 @@ def main():
     t_f = [ev[k][0].elapsed_time(ev[k][1]) for k in range(args.steps)]
     t_b = [ev[k][1].elapsed_time(ev[k][2]) for k in range(args.steps)]
     ms = (sum(t_f) + sum(t_b)) / args.steps
-    ms_t = torch.tensor([ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
-    ms_max = float(ms_t.item())
-    value = world * pairs / (ms_max * 1e-3) / 1e9
+    ms_max = max_over_ranks(ms, world, dev)
+    value = aggregate_rate(pairs, world, ms_max)
     # our kernels per step: FP32 form = forward, adjoint, finalize; BF16 form =
     # forward (prep_x, vmax, prep_v, main, epilogue) + adjoint (norms, prep_x,
     # prep, main, finalize) + dL/dV = A G through the forward (5 more)
@@ -356,10 +368,7 @@ def main():
         torch.cuda.synchronize()
         if k >= 2:
             e2e_ms.append(e0.elapsed_time(e1))
-    e2e_t = torch.tensor([float(np.mean(e2e_ms))], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
-    e2e_value = world * pairs / (float(e2e_t.item()) * 1e-3) / 1e9
+    e2e_value = aggregate_rate(pairs, world, max_over_ranks(float(np.mean(e2e_ms)), world, dev))
 
     out = None
     if rank == 0:
