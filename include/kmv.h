@@ -261,6 +261,23 @@ kmv_status kmv_energy(kmv_handle h, const kmv_points* pts, int32_t chains,
                       kmv_precision prec, void* stream);
 
 /*
+ * kmv_accept - the Metropolis test of Algorithm 1 for every system: accept iff
+ * status[s] == KMV_OK (status may be NULL), both energies are finite and
+ * log u[s] <= H_old[s] - H_new[s] (the event u <= min(1, exp(H_old - H_new))
+ * for u in (0, 1]); a rejected system's theta gets theta_old back.
+ *   H_old, H_new, u  DEVICE FP64 (n_sys); u the caller's U(0, 1] draws.
+ *   theta_old        DEVICE FP64 (n_sys, n_theta); theta DEVICE FP64, in/out.
+ *   accepted         DEVICE int32 (n_sys): 1 accepted, 0 rejected.
+ * kmv_status_merge - dst[s] = src[s] where dst[s] is KMV_OK and src[s] is not
+ * (collects the first failure of a trajectory's steps for kmv_accept).
+ * Neither needs a handle; both are stream-ordered on `stream`.
+ */
+kmv_status kmv_accept(int32_t n_sys, int32_t n_theta, const double* H_old, const double* H_new,
+                      const double* u, const int32_t* status, const double* theta_old,
+                      double* theta, int32_t* accepted, void* stream);
+kmv_status kmv_status_merge(int32_t n, const int32_t* src, int32_t* dst, void* stream);
+
+/*
  * kmv_phi_refresh - the Gibbs draw of the auxiliary variable of Sec. 3.1,
  * phi = A(theta_s)^{-1/2} xi for every system s, by the pole expansion of
  * App. A (Eq. pex):  phi = sum_p w_p (A + lambda_p I)^{-1} xi, p = 1..n_poles,

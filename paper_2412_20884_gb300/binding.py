@@ -64,6 +64,8 @@ _SIGS = {
     "kmv_nystrom_build": (C.c_int, [_P, C.POINTER(_Points), C.c_int32, _P, C.c_int32, _P, _P, _P, _P, C.c_int,
                                     _P]),
     "kmv_set_preconditioner": (C.c_int, [_P, _P]),
+    "kmv_accept": (C.c_int, [C.c_int32, C.c_int32, _P, _P, _P, _P, _P, _P, _P, _P]),
+    "kmv_status_merge": (C.c_int, [C.c_int32, _P, _P, _P]),
     "kmv_profile_enable": (C.c_int, [_P, C.c_int32]),
     "kmv_profile_read": (C.c_int, [_P, C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
 }
@@ -413,6 +415,36 @@ def kmv_backward_noalloc(pts: Points, theta, V, G, want_grad_V=True, grad_theta=
 
 
 _DEFAULT = {}
+
+
+def accept(H_old, H_new, u, theta_old, theta, status=None, stream=None):
+    """The Metropolis test of Algorithm 1 (kmv_accept): theta of rejected systems is
+    restored from theta_old in place.  Returns accepted (n_sys int32)."""
+    L = lib()
+    n_sys, n_theta = theta.shape
+    for t, nm in ((H_old, "H_old"), (H_new, "H_new"), (u, "u")):
+        _need(t, torch.float64, nm, (n_sys,))
+    _need(theta_old, torch.float64, "theta_old", theta.shape)
+    _need(theta, torch.float64, "theta", theta.shape)
+    if status is not None:
+        _need(status, torch.int32, "status", (n_sys,))
+    accepted = torch.empty(n_sys, dtype=torch.int32, device=theta.device)
+    st = L.kmv_accept(n_sys, n_theta, _ptr(H_old), _ptr(H_new), _ptr(u), _ptr(status), _ptr(theta_old),
+                      _ptr(theta), _ptr(accepted), _stream(stream))
+    if st != KMV_OK:
+        raise KmvError(st, "kmv_accept: " + L.kmv_status_string(st).decode())
+    return accepted
+
+
+def status_merge(src, dst, stream=None):
+    """dst = the first failure of src and dst, per system, in place (kmv_status_merge)."""
+    L = lib()
+    _need(src, torch.int32, "src", dst.shape)
+    _need(dst, torch.int32, "dst", src.shape)
+    st = L.kmv_status_merge(int(dst.numel()), _ptr(src), _ptr(dst), _stream(stream))
+    if st != KMV_OK:
+        raise KmvError(st, "kmv_status_merge: " + L.kmv_status_string(st).decode())
+    return dst
 
 
 def default_handle(device: int = 0) -> Kmv:

@@ -1329,6 +1329,22 @@ kmv_status kmv_implicit_step(kmv_handle h, const kmv_points* pts, int32_t chains
   return KMV_OK;
 }
 
+kmv_status kmv_status_merge(int32_t n, const int32_t* src, int32_t* dst, void* stream) {
+  if (n < 0 || (n > 0 && (!src || !dst))) return KMV_EINVAL;
+  return launch_status_merge(n, src, dst, static_cast<cudaStream_t>(stream)) == cudaSuccess ? KMV_OK : KMV_ECUDA;
+}
+
+kmv_status kmv_accept(int32_t n_sys, int32_t n_theta, const double* H_old, const double* H_new, const double* u,
+                      const int32_t* status, const double* theta_old, double* theta, int32_t* accepted,
+                      void* stream) {
+  if (n_sys < 0 || n_theta < 1) return KMV_EINVAL;
+  if (n_sys > 0 && (!H_old || !H_new || !u || !theta_old || !theta || !accepted)) return KMV_EINVAL;
+  return launch_accept(n_sys, n_theta, H_old, H_new, u, status, theta_old, theta, accepted,
+                       static_cast<cudaStream_t>(stream)) == cudaSuccess
+             ? KMV_OK
+             : KMV_ECUDA;
+}
+
 kmv_status kmv_energy(kmv_handle h, const kmv_points* pts, int32_t chains, const float* y,
                       const float* phi, const double* theta, const double* pi,
                       const double* prior_mu, const double* prior_prec, double cg_tol,

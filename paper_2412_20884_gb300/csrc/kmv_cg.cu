@@ -472,4 +472,40 @@ cudaError_t launch_energy_finalize(const DevLayout& L, int n_inst, int chains, i
   return cudaGetLastError();
 }
 
+// --- Metropolis test (Algorithm 1) ----------------------------------------------
+
+// fail[s] = the first non-OK status seen (keeps an earlier failure)
+__global__ void status_merge_kernel(int n, const int32_t* src, int32_t* dst) {
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x)
+    if (dst[s] == KMV_OK && src[s] != KMV_OK) dst[s] = src[s];
+}
+
+cudaError_t launch_status_merge(int n, const int32_t* src, int32_t* dst, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  status_merge_kernel<<<(n + 255) / 256, 256, 0, st>>>(n, src, dst);
+  return cudaGetLastError();
+}
+
+// accept iff the trajectory's status is OK and log u <= H_old - H_new (the event
+// u <= min(1, exp(H_old - H_new)) for u in (0, 1]); a rejected system gets theta_old
+__global__ void accept_kernel(int n_sys, int n_theta, const double* H_old, const double* H_new, const double* u,
+                              const int32_t* status, const double* theta_old, double* theta, int32_t* accepted) {
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n_sys; s += gridDim.x * blockDim.x) {
+    const bool ok = (status == nullptr || status[s] == KMV_OK) && isfinite(H_new[s]) && isfinite(H_old[s]);
+    const bool acc = ok && log(u[s]) <= H_old[s] - H_new[s];
+    accepted[s] = acc ? 1 : 0;
+    if (!acc)
+      for (int p = 0; p < n_theta; ++p) theta[(int64_t)s * n_theta + p] = theta_old[(int64_t)s * n_theta + p];
+  }
+}
+
+cudaError_t launch_accept(int n_sys, int n_theta, const double* H_old, const double* H_new, const double* u,
+                          const int32_t* status, const double* theta_old, double* theta, int32_t* accepted,
+                          cudaStream_t st) {
+  if (n_sys == 0) return cudaSuccess;
+  accept_kernel<<<(n_sys + 127) / 128, 128, 0, st>>>(n_sys, n_theta, H_old, H_new, u, status, theta_old, theta,
+                                                     accepted);
+  return cudaGetLastError();
+}
+
 }  // namespace kmv

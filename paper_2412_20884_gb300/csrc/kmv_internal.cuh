@@ -185,6 +185,12 @@ cudaError_t launch_pcg_update_p(const DevLayout& L, int n_items, int chains, int
 cudaError_t launch_pcg_finish(int n_sys, const PcgSys* sys, const int32_t* active, int32_t* status, int32_t* iters,
                               cudaStream_t st);
 
+// Metropolis test (kmv_cg.cu)
+cudaError_t launch_status_merge(int n, const int32_t* src, int32_t* dst, cudaStream_t st);
+cudaError_t launch_accept(int n_sys, int n_theta, const double* H_old, const double* H_new, const double* u,
+                          const int32_t* status, const double* theta_old, double* theta, int32_t* accepted,
+                          cudaStream_t st);
+
 // Implicit midpoint step by Anderson acceleration (kmv_implicit.cu)
 constexpr int kMaxAA = 16;
 cudaError_t launch_fill_i32(int32_t* v, int n, int32_t val, cudaStream_t st);
