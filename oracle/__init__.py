@@ -20,6 +20,13 @@ are used only to bound memory; every block evaluates the same formula):
   * ``poles``      - the pole expansion of A^{-1/2} (Eq. pex, App. A, Eq. msqdisc).
   * ``diagnostics``- moving-window means (Sec. 4.1) and the integrated
                      autocorrelation time (App. C).
+  * ``cheb_kernel``- the Chebyshev log-amplitude kernel family of Sec. 4, its
+                     dense A and derivatives.
+  * ``nystrom``    - the randomized Nystrom approximation and preconditioner
+                     (Frangella, Tropp and Udell) the paper uses for its
+                     solves, and preconditioned CG.
+  * ``implicit``   - the implicit midpoint step (Sec. 3.2.3, Eq. Phi) solved
+                     by Anderson acceleration (App. B).
 
 Pins (tests/test_oracle_*.py) tie each function to values fixed by the paper
 or by mathematics rather than to itself.  Parity status per function is listed

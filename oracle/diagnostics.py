@@ -8,7 +8,7 @@
   * marginal_cdf_grid  : trapezoid-rule marginal CDFs of P(theta) on a grid (Sec. 4.1).
 
 Parity status: pinned (AR(1) autocorrelation time (1+rho)/(1-rho); the CDF of
-a Gaussian density) - see tests/test_oracle_diagnostics.py.
+a Gaussian density) - see tests/test_oracle_poles_diag.py.
 """
 from __future__ import annotations
 
