@@ -234,6 +234,7 @@ kmv_status cheb_prepare(kmv_handle h, const kmv_points* pts, const double* theta
   h->cheb_part = reinterpret_cast<double*>(base + o_pt);
   h->cheb_kv = reinterpret_cast<float*>(base + o_kv);
   h->cheb_kg = reinterpret_cast<float*>(base + o_kg);
+  h->cheb_mcap = std::max(1, m_bwd);
   KMV_CUDA(h, launch_cheb_prepare(h->dev, L.n_items, (int)n_sys, L.chains, L.n_total, L.d, L.cheb, L.n_coef,
                                   L.n_theta, L.n_theta_int, pts->x, theta, h->cheb_theta, h->cheb_amp, st));
   return KMV_OK;
@@ -289,6 +290,7 @@ kmv_status run_backward(kmv_handle h, KmvArgs a, double* grad, double* partial,
                         kmv_precision prec, cudaStream_t st) {
   const Layout& L = h->layout;
   if (!L.cheb) return run_backward_stationary(h, a, grad, partial, prec, st);
+  if (a.m > h->cheb_mcap) return fail(h, KMV_EINVAL, "internal: amplitude scratch prepared for fewer columns");
   KMV_TRY(run_backward_stationary(h, a, h->cheb_gint, partial, prec, st));
   KmvArgs f = a;
   f.G = nullptr;

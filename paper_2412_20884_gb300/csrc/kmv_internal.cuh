@@ -329,6 +329,7 @@ struct kmv_handle_s {
   double* cheb_theta = nullptr;
   float* cheb_amp = nullptr;
   float *cheb_kv = nullptr, *cheb_kg = nullptr;
+  int cheb_mcap = 0;   // columns cheb_kv / cheb_kg hold
   double *cheb_part = nullptr, *cheb_gint = nullptr;
   // preconditioner set by kmv_set_preconditioner (caller-owned arrays)
   bool pc_on = false;
