@@ -105,7 +105,8 @@ int64_t kmv_workspace_bytes(kmv_handle h);
  * kmv_forward - Y = A(theta) V (+ col_shift o V), the matrix-free product of
  * Eq. kerdef; col_shift gives the shifted operators A + lambda_p I of Eq. pex.
  *
- *   chains     >= 1 independent hyperparameter sets per instance.
+ *   chains     1..65535 independent hyperparameter sets per instance (the
+ *              limit holds for every entry point).
  *   theta      DEVICE FP64 (n_inst * chains, n_theta).
  *   V          DEVICE FP32 (chains, N_total, m), m >= 1.
  *   col_shift  DEVICE FP32 (m) or NULL: column c uses A + col_shift[c] I.

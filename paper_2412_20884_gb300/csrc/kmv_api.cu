@@ -75,7 +75,7 @@ kmv_status check_points(kmv_handle h, const kmv_points* pts, int32_t chains) {
   if (!pts->offsets) return fail(h, KMV_EINVAL, "offsets is NULL");
   if (pts->d < 1 || pts->d > kMaxD) return fail(h, KMV_EINVAL, "d must be in [1, 64]");
   if (pts->ard != 0 && pts->ard != 1) return fail(h, KMV_EINVAL, "ard must be 0 or 1");
-  if (chains < 1) return fail(h, KMV_EINVAL, "chains must be >= 1");
+  if (chains < 1 || chains > 65535) return fail(h, KMV_EINVAL, "chains must be in [1, 65535]");
   if (pts->offsets[0] != 0) return fail(h, KMV_EINVAL, "offsets[0] must be 0");
   for (int b = 0; b < pts->n_inst; ++b)
     if (pts->offsets[b + 1] < pts->offsets[b]) return fail(h, KMV_EINVAL, "offsets must be non-decreasing");
