@@ -1011,7 +1011,6 @@ kmv_status kmv_phi_refresh(kmv_handle h, const kmv_points* pts, int32_t chains, 
   KMV_TRY(check_prec(h, prec));
   if (!theta || !xi || !phi || !chain_status) return fail(h, KMV_EINVAL, "NULL argument");
   if (n_poles < 1 || n_poles > kMaxPoles) return fail(h, KMV_EINVAL, "n_poles must be in [1, 32]");
-  if ((int64_t)chains * n_poles > (int64_t)1 << 20) return fail(h, KMV_EINVAL, "chains * n_poles too large");
   if (!(cg_tol > 0.0) || cg_maxiter < 1) return fail(h, KMV_EINVAL, "cg_tol must be > 0 and cg_maxiter >= 1");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   KMV_TRY(prepare_layout(h, pts, chains, st));

@@ -66,7 +66,7 @@ extern "C" kmv_status kmv_backward_noalloc(const kmv_points* pts, int32_t chains
                                            const float* V, const float* G, int32_t m, double* grad_theta,
                                            float* grad_V, void* stream) {
   if (!pts || pts->n_inst < 1 || !pts->offsets || pts->d < 1 || pts->d > kMaxD ||
-      (pts->ard != 0 && pts->ard != 1) || chains < 1 || m < 1 || !theta || !V || !G || !grad_theta)
+      (pts->ard != 0 && pts->ard != 1) || chains < 1 || chains > 65535 || m < 1 || !theta || !V || !G || !grad_theta)
     return KMV_EINVAL;
   if (pts->cheb != 0) return KMV_EUNSUPPORTED;   // the amplitudes would need scratch per point
   if (pts->offsets[0] != 0) return KMV_EINVAL;
