@@ -152,8 +152,12 @@ kmv_status kmv_backward(kmv_handle h, const kmv_points* pts, int32_t chains,
  *   iters        DEVICE int32 (n_inst * chains) or NULL: iterations used.
  * KMV_BF16_HILO solves by mixed-precision iterative refinement: the residual
  * rhs - A x is formed with the FP32 operator and each correction is solved by
- * CG with the tensor-core operator to 1e-3, so the result meets `tol` against
- * the FP32 operator; `iters` then counts the tensor-core CG iterations.
+ * CG with the tensor-core operator (to 1e-5 where the one-column product takes
+ * the FMA-pipe form, else 1e-3), so the result meets `tol` against the FP32
+ * operator, or stops where the residual no longer falls (its FP32 floor);
+ * `iters` then counts the tensor-core CG iterations.  With a Nystrom
+ * preconditioner set on the handle (kmv_set_preconditioner) the CG, and the
+ * refinement's inner CG, are preconditioned.
  * Outside stream capture, the call synchronises `stream` every few iterations
  * to test convergence on the host.  While `stream` is being captured into a
  * CUDA graph it records exactly cg_maxiter iterations instead (KMV_BF16_HILO:
