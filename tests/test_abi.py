@@ -90,3 +90,21 @@ def test_struct_layouts_match_ctypes(tmp_path):
         assert got[(cname, "size")] == ctypes.sizeof(ct), cname
         for fname, _ in ct._fields_:
             assert got[(cname, fname)] == getattr(ct, fname).offset, (cname, fname)
+
+
+def test_argument_errors_need_no_device(so):
+    """Entry points reject bad arguments before any CUDA call (no GPU needed)."""
+    from paper_2412_20884_gb300 import binding
+    for name, (res, args) in binding._SIGS.items():
+        getattr(so, name).restype = res
+        getattr(so, name).argtypes = args
+    EINVAL = 1
+    # a NULL handle
+    assert so.kmv_forward(None, None, 1, None, None, 1, None, None, None, 0, None) == EINVAL
+    assert so.kmv_set_preconditioner(None, None) == EINVAL
+    assert so.kmv_profile_enable(None, 1) == EINVAL
+    # handle-free calls with bad sizes
+    assert so.kmv_accept(4, 0, None, None, None, None, None, None, None, None) == EINVAL
+    assert so.kmv_accept(4, 3, None, None, None, None, None, None, None, None) == EINVAL
+    assert so.kmv_status_merge(-1, None, None, None) == EINVAL
+    assert so.kmv_backward_noalloc(None, 1, None, None, None, 1, None, None, None) == EINVAL
