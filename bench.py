@@ -35,7 +35,7 @@ WORKLOAD = "kmv fwd+bwd, N=65536 points x~N(0,I) in d=8, ARD SE (10 hyperparamet
 #   fp32      : FMA-pipe ops per pair (fwd 2d + m, bwd 4d + 2m + 2) -> roof = FMA rate / ops
 SM_COUNT = 152
 FMA_LANES = 128        # FP32 FMA lanes per SM per clock
-MUFU_EX2_LANES = 32    # ex2 per SM per clock on GB300 (measured by probes/ex2_ffma_rate.cu)
+MUFU_EX2_LANES = 32    # ex2 per SM per clock on GB300 (measured by an ex2 issue-rate micro-benchmark, profiles/issue_rates_gb300.md)
 # dram__bytes_read.sum + dram__bytes_write.sum per launch of the main loop, from an
 # ncu capture of the same workload; absent once the kernel changes after that capture.
 DRAM_TRAFFIC = {("bf16_hilo", "fwd"): 10542080}
