@@ -158,24 +158,23 @@ def cpu_oracle_rate(rows_per_step: int, steps: int, seed: int = 0):
 
 def kernel_work(prec, kind, d, m, n):
     """Algorithmic work of one launch of a main kernel on one N x N system:
-    (ex2 count, tensor-core FLOPs, FMA-pipe ops).
+    (ex2 count, tensor-core FLOPs, FMA-pipe ops), counted as the method's own
+    work, not the implementation's split or padded operand depths.
 
-    Forward (one pass of Eq. kerdef over all N^2 pairs): one ex2 per pair; the
-    BF16 form contracts the cross term with its hi/lo split and folded biases
-    (3d + 6 products) and P.V (m).  Adjoint (the quadratic-form gradient of
-    Sec. 3.2.1): the BF16 form evaluates the upper triangle of tiles only
-    (T (T + 1) / 2 tiles of 128 x 128 pairs, half the logical pairs) with the
-    symmetrised G.V product of depth 6 m, the cross term and the 4 d + 1
-    feature sums.  The FP32 forms are FMA-pipe bound: 2 d + m operations per
-    pair forward, 4 d + 2 m + 2 adjoint."""
+    Forward (one pass of Eq. kerdef over all N^2 pairs): one ex2 per pair, the
+    cross term x_i . x_j (2 d FLOPs) and P.V (2 m).  Adjoint (the quadratic-form
+    gradient of Sec. 3.2.1): K and the distances are symmetric, so the method
+    needs the N (N + 1) / 2 pairs j >= i, each with one ex2, the cross term
+    (2 d), the symmetrised G_i.V_j + V_i.G_j (4 m) and the feature sums
+    Q [x, x^2, 1] (2 (2 d + 1)).  The FP32 forms are FMA-pipe bound: 2 d + m
+    operations per pair forward, 4 d + 2 m + 2 adjoint (all N^2 pairs)."""
     if prec == "bf16_hilo":
-        if kind == "fwd":
+        if kind in ("fwd", "fwd_m1"):
             pairs = n * n
-            return pairs, pairs * (2 * (3 * d + 6) + 2 * m), 0
-        t = -(-n // 128)
-        comp = t * (t + 1) // 2 * 128 * 128
-        return comp, comp * (2 * (3 * d + 6) + 2 * 6 * m + 2 * (4 * d + 1)), 0
-    ops = 2 * d + m if kind == "fwd" else 4 * d + 2 * m + 2
+            return pairs, pairs * (2 * d + 2 * m), 0
+        half = n * (n + 1) // 2
+        return half, half * (2 * d + 4 * m + 2 * (2 * d + 1)), 0
+    ops = 2 * d + m if kind in ("fwd", "fwd_m1") else 4 * d + 2 * m + 2
     return 0, 0, n * n * ops
 
 
@@ -248,7 +247,7 @@ def main():
     ap.add_argument("--cpu-rows", type=int, default=512, help="rows of the oracle sample for cpu_baseline")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-leapfrog", action="store_true")
-    ap.add_argument("--suite", default=None, choices=["c3c4", "cheb", "precond", "implicit"],
+    ap.add_argument("--suite", default=None, choices=["c3c4", "cheb", "precond", "implicit", "adjoint"],
                     help="instead of the headline line: time the C3 products and the C4 leapfrog batch (c3c4), "
                          "the Chebyshev-amplitude kernel family of Sec. 4 (cheb), or the leapfrog step with "
                          "the randomized Nystrom preconditioner (precond), or the implicit midpoint step (implicit)")
@@ -263,6 +262,8 @@ def main():
         return run_suite_precond(args)
     if args.suite == "implicit":
         return run_suite_implicit(args)
+    if args.suite == "adjoint":
+        return run_suite_adjoint(args)
 
     import torch
     import torch.distributed as dist
@@ -324,6 +325,18 @@ def main():
         torch.cuda.synchronize()
         t_wall = time.perf_counter() - t_wall0
     prof = {"fwd": h.profile_read(KMV_KERNEL_FORWARD), "adj": h.profile_read(KMV_KERNEL_ADJOINT)}
+    # the CG iterations' product (m = 1: P.v on the FMA pipe) on the same points,
+    # timed by itself after the step loop; not part of the step
+    V1 = V[:, :, :1].contiguous()
+    Y1 = torch.empty_like(V1)
+    for _ in range(3):
+        h.kmv_forward(pts, theta, V1, Y=Y1, prec=prec)
+    torch.cuda.synchronize()
+    for _ in range(args.steps):
+        flush.zero_()
+        h.kmv_forward(pts, theta, V1, Y=Y1, prec=prec)
+    torch.cuda.synchronize()
+    prof_m1 = h.profile_read(KMV_KERNEL_FORWARD)
     h.profile_enable(False)
     if world > 1:
         dist.barrier()
@@ -386,6 +399,12 @@ def main():
                              "share_of_step": tot_ms / args.steps / ms_max,
                              "roofline": kernel_roof(prec, kind, w.d, w.m, n, clock, tflops, per)}
         dom = max(kernels, key=lambda k: kernels[k]["ms_per_launch"] * kernels[k]["launches_per_step"])
+        if prof_m1[1] > 0:
+            per = prof_m1[0] / prof_m1[1]
+            kernels["fwd_m1"] = {"kernel": "tc_fwd_fma_kernel<1>" if prec == "bf16_hilo" else "simt_fwd_kernel",
+                                 "what": "the CG product A v (m = 1) on the same points, timed outside the step",
+                                 "launches_per_step": 0, "ms_per_launch": per,
+                                 "roofline": kernel_roof(prec, "fwd_m1", w.d, 1, n, clock, tflops, per)}
         roof_out = dict(kernels[dom]["roofline"])
         roof_out.update({"traffic": DRAM_TRAFFIC.get((prec, dom)),
                          "kernel": {"fwd": "tc_fwd_kernel", "adj": "tc_bwd_ts_kernel"}[dom] if prec == "bf16_hilo"
@@ -522,8 +541,104 @@ def leapfrog_rates(h, dev, rank, world):
                         r[prec]["graph_theta_maxdiff_vs_eager"] = float(np.abs(th_g.cpu().numpy() - finals[prec]).max())
                 except Exception as e:  # capture needs a CUDA-graph capable torch build
                     r[prec]["graph_unavailable"] = str(e)[:200]
+        if w.n_total == 2048:
+            r["hmc"] = c1_hmc(h, dev, w, pts, y)
         res["c1" if w.n_total == 2048 else "c5_n16384"] = r
     return res
+
+
+def c1_hmc(h, dev, w, pts, y):
+    """Algorithm 1 on the N = 2048 workload (sampler.hmc_update: phi draw by the
+    pole expansion, FP32 energies, n_int leapfrog steps, Metropolis test), both
+    forms: the acceptance rate reached and the whole loop's leapfrog steps per
+    second, at dt = 0.01 (200 updates x 10 steps) and at the configuration's
+    dt = 0.05 (20 updates x 10 steps)."""
+    import torch
+    from paper_2412_20884_gb300.sampler import hmc_update
+    out = {}
+    for dt, updates in ((0.01, 200), (0.05, 20)):
+        for prec in ("fp32", "bf16_hilo"):
+            rng = np.random.default_rng(11)
+            th = torch.tensor(w.theta, dtype=torch.float64, device=dev)
+            acc, fails = [], 0
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(updates):
+                xi = torch.tensor(rng.standard_normal((1, w.n_total)), dtype=torch.float32, device=dev)
+                pi = torch.tensor(rng.standard_normal(w.theta.shape), dtype=torch.float64, device=dev)
+                u = torch.tensor(1.0 - rng.uniform(size=1), dtype=torch.float64, device=dev)
+                ok, fail = hmc_update(h, pts, y, th, dt, 10, xi, pi, u, prec=prec, cg_maxiter=5000)
+                acc.append(int(ok.item()))
+                fails += int((fail != 0).sum().item())
+            torch.cuda.synchronize()
+            sec = time.perf_counter() - t0
+            out[f"dt{dt}_{prec}"] = {"updates": updates, "n_int": 10, "acceptance": float(np.mean(acc)),
+                                     "failed_systems": fails, "leapfrog_steps_per_s_incl_phi_and_energy":
+                                     updates * 10 / sec, "theta_final": th.cpu().numpy()[0].round(4).tolist()}
+    return out
+
+
+def run_suite_adjoint(args):
+    """Accuracy and time of the adjoint of the build as it stands (one GPU, one
+    JSON line): on the batching workload (256 instances, d = 4, 4 chains, m = 2)
+    the sampled-row gradients of 8 random instances against the FP64 oracle
+    (relative error per component, worst over the 32 systems) in both forms,
+    and the adjoint kernel's time per launch on the N = 65,536, d = 8, m = 16
+    workload (CUDA events).  Rebuilding with -DKMV_BWD_FOLD_HALVES=F sets how
+    many 64-column halves the tensor-core accumulator takes before each FP64 fold."""
+    import torch
+    import workloads as wl
+    from oracle import se_kernel as sk
+    from paper_2412_20884_gb300 import Kmv, Points
+    from paper_2412_20884_gb300.binding import KMV_KERNEL_ADJOINT
+    dev = torch.device("cuda", 0)
+    h = Kmv(0)
+    w = wl.c4(m=2)
+    rng = np.random.default_rng(7)
+    chosen = np.sort(rng.choice(w.n_inst, 8, replace=False))
+    Gs = np.zeros_like(w.G)
+    rows = {}
+    for b in chosen:
+        r0, r1 = w.offsets[b], w.offsets[b + 1]
+        rows[b] = np.sort(rng.choice(r1 - r0, 128, replace=False))
+        Gs[:, r0 + rows[b]] = w.G[:, r0 + rows[b]]
+    X = w.X.astype(np.float32).astype(np.float64)
+    pts = Points(torch.tensor(w.X, dtype=torch.float32, device=dev), w.offsets, ard=True)
+    th = torch.tensor(w.theta, dtype=torch.float64, device=dev)
+    V = torch.tensor(w.V, dtype=torch.float32, device=dev)
+    G = torch.tensor(Gs, dtype=torch.float32, device=dev)
+    grads = {p: h.kmv_backward(pts, th, V, G, want_grad_V=False, prec=p)[0].cpu().numpy()
+             for p in ("fp32", "bf16_hilo")}
+    errs = {p: [] for p in grads}
+    for b in chosen:
+        r0, r1 = w.offsets[b], w.offsets[b + 1]
+        for c in range(w.chains):
+            s = b * w.chains + c
+            g_ref, _ = sk.kmv_adjoint(X[r0:r1], w.theta[s], w.V[c, r0:r1].astype(np.float32).astype(np.float64),
+                                      Gs[c, r0:r1].astype(np.float32).astype(np.float64), True, rows=rows[b])
+            floor = 1e-3 * np.abs(g_ref).max()
+            for p, g in grads.items():
+                errs[p].append(float(np.max(np.abs(g[s] - g_ref) / np.maximum(np.abs(g_ref), floor))))
+    w2 = wl.c2()
+    pts2 = Points(torch.tensor(w2.X, dtype=torch.float32, device=dev), w2.offsets, ard=True)
+    th2 = torch.tensor(w2.theta, dtype=torch.float64, device=dev)
+    V2 = torch.tensor(w2.V, dtype=torch.float32, device=dev)
+    G2 = torch.tensor(w2.G, dtype=torch.float32, device=dev)
+    for _ in range(3):
+        h.kmv_backward(pts2, th2, V2, G2, want_grad_V=False, prec="bf16_hilo")
+    torch.cuda.synchronize()
+    h.profile_enable(True)
+    for _ in range(10):
+        h.kmv_backward(pts2, th2, V2, G2, want_grad_V=False, prec="bf16_hilo")
+    ms, nl = h.profile_read(KMV_KERNEL_ADJOINT)
+    h.profile_enable(False)
+    out = {"suite": "adjoint", "data": "synthetic",
+           "batching_sampled_rows": {p: {"worst_gradient_error": max(e), "median": float(np.median(e))}
+                                     for p, e in errs.items()},
+           "adjoint_kernel_ms_n65536_d8_m16": ms / nl}
+    print(json.dumps(out))
+    h.close()
+    return 0
 
 
 def run_suite_implicit(args):

@@ -71,10 +71,17 @@ typedef enum {
    * products folded into FP64 accumulators every 512 columns.  Relative
    * error against FP64 <= 1e-5 on outputs, <= 1e-4 on gradients. */
   KMV_FP32 = 0,
-  /* Tensor-core form (tcgen05): cross term X_I X_J^T in BF16 with a hi/lo
-   * split (hi.hi + hi.lo + lo.hi) and the row biases folded into the same
-   * contraction, exp2 in FP32 registers, P.V in FP16 with FP32 accumulation
-   * folded into FP64.  Relative error against FP64 <= 2e-3. */
+  /* Tensor-core form (tcgen05).  Points are centred per instance (midrange,
+   * exact for a stationary kernel).  Products: cross term X_I X_J^T in BF16
+   * with a hi/lo split (hi.hi + hi.lo + lo.hi; a three-way split for m <= 2)
+   * and the row biases folded into the same contraction, exp2 in FP32
+   * registers, P.V in FP16 (FP32 on the FMA pipe for m <= 2) with FP32
+   * accumulation folded into FP64; relative error against FP64 <= 2e-3.
+   * Adjoint: the exponent and G.V from F16 hi/lo operands, Q = W o K0 kept
+   * exactly as two F16 parts, feature sums folded into FP64 every 1024
+   * columns; gradients to 1e-4 relative like KMV_FP32.  The adjoint needs
+   * |x_k - c_k| < 200 l_k and sum_k (x_k - c_k)^2 / l_k^2 < 2^16 / log2(e)
+   * (c the centre); beyond, its gradients are NaN (use KMV_FP32). */
   KMV_BF16_HILO = 1
 } kmv_precision;
 
@@ -386,12 +393,66 @@ kmv_status kmv_profile_enable(kmv_handle h, int32_t on);
 kmv_status kmv_profile_read(kmv_handle h, int32_t kind, double* total_ms, int64_t* launches);
 
 /*
+ * Tile choices of the tensor-core kernels (KMV_BF16_HILO) and an autotuner
+ * that picks them per call shape.  The paper has no counterpart (it leaves the
+ * GPU kernels to a library); these calls change speed only, never results
+ * beyond rounding.
+ *
+ *   kernel (kmv_tile_kernel):
+ *     KMV_TILES_FORWARD      products with m > 2 columns (P.V on the tensor cores)
+ *     KMV_TILES_FORWARD_FMA  products with m <= 2 (the CG iterations; P.v on the
+ *                            FMA pipe)
+ *     KMV_TILES_ADJOINT      the adjoint kernel of kmv_backward
+ *   kmv_tiles:
+ *     stages        operand-ring stages in shared memory, 2..8 (the adjoint uses
+ *                   at most 6); 0 = as many as shared memory holds
+ *     items_per_sm  work items per SM the work plan aims at, 1..64 (default 6)
+ *     exp_split     0: every exp2 on the MUFU (ex2.approx); 4 or 8: one element
+ *                   in 4 (8) by a range-reduced minimax polynomial on the FMA
+ *                   pipe (relative error 7.5e-5 for the F16 probabilities of
+ *                   KMV_TILES_FORWARD, 1.6e-7 for KMV_TILES_FORWARD_FMA); other
+ *                   values round to 0, 4 or 8.  Ignored by the adjoint.
+ *
+ * kmv_set_tiles sets the default of a kernel kind, used by every shape the
+ * autotuner has not recorded; kmv_get_tiles reads it.  Both are host-only and
+ * synchronous.  Errors: KMV_EINVAL (null argument, unknown kernel, a value
+ * out of range).
+ *
+ * kmv_autotune times candidate tiles for the shape of (pts, chains, m): the
+ * product kernel of kmv_forward with m columns and the adjoint kernel of
+ * kmv_backward with m columns, each with every candidate (3 exp splits x 2
+ * stage limits x 3 plan densities for the products, 2 x 3 for the adjoint),
+ * by CUDA events around the main kernel, and records the fastest for that
+ * shape: (kernel, d, m, floor(log2 of the largest instance's size)).  Later
+ * calls of that shape run with it; other shapes keep the defaults.  Timing
+ * runs on at most the first 65,536 rows of the largest instance with one
+ * chain and theta of its first system; values of V and G are synthetic.
+ *   cache_path  HOST string or NULL: a text file of recorded shapes, read first
+ *               (shapes it holds are not timed again) and rewritten with every
+ *               recorded shape afterwards.
+ * The call is synchronous, allocates scratch device memory (freed before it
+ * returns) and must not be made while `stream` is being captured.  Errors:
+ * KMV_EINVAL, KMV_ENOMEM, KMV_ECUDA, KMV_EUNSUPPORTED (no tensor-core form
+ * for this shape; nothing recorded).
+ */
+typedef enum { KMV_TILES_FORWARD = 0, KMV_TILES_FORWARD_FMA = 1, KMV_TILES_ADJOINT = 2 } kmv_tile_kernel;
+typedef struct {
+  int32_t stages;
+  int32_t items_per_sm;
+  int32_t exp_split;
+} kmv_tiles;
+kmv_status kmv_set_tiles(kmv_handle h, int32_t kernel, const kmv_tiles* t);
+kmv_status kmv_get_tiles(kmv_handle h, int32_t kernel, kmv_tiles* t);
+kmv_status kmv_autotune(kmv_handle h, const kmv_points* pts, int32_t chains, const double* theta, int32_t m,
+                        const char* cache_path, void* stream);
+
+/*
  * kmv_backward_noalloc - kmv_backward with KMV_FP32 arithmetic that allocates
  * no device memory and needs no handle.  The paper has no counterpart: this
  * entry point exists for callers that cannot call cudaMalloc, such as code
- * running while its stream is captured into a CUDA graph, code whose device
- * memory all belongs to its own pool, or loops that cannot take the
- * synchronisation an allocation may imply.
+ * whose device memory all belongs to its own pool or arena (memory taken
+ * behind the pool's back can make it fail), or loops that cannot take the
+ * device-wide synchronisation an allocation may imply.
  *
  *   Arguments and results as in kmv_backward (grad_V may be NULL).
  *   Scratch: a fixed 4 MiB device array inside the library, held by every
@@ -408,8 +469,11 @@ kmv_status kmv_profile_read(kmv_handle h, int32_t kind, double* total_ms, int64_
  *   Concurrency: every call on a device shares the one array; calls whose
  *     work overlaps on the GPU (other streams, other host threads) race and
  *     must be ordered by the caller.
- *   Errors: KMV_EINVAL (bad argument or scratch limit exceeded), KMV_ECUDA,
- *     KMV_EUNSUPPORTED for the Chebyshev-amplitude family (pts->cheb != 0).
+ *   Offsets: each call copies pts->offsets (HOST) to the array; the copy is
+ *     staged before the call returns, so the host array may change afterwards.
+ *   Errors: KMV_EINVAL (bad argument, by the rules of every other entry point,
+ *     or scratch limit exceeded), KMV_ECUDA, KMV_EUNSUPPORTED for the
+ *     Chebyshev-amplitude family (pts->cheb != 0).
  */
 kmv_status kmv_backward_noalloc(const kmv_points* pts, int32_t chains, const double* theta,
                                 const float* V, const float* G, int32_t m, double* grad_theta,

@@ -36,6 +36,10 @@ class _Nystrom(C.Structure):
                 ("U", C.c_void_p), ("lam", C.c_void_p)]
 
 
+class _Tiles(C.Structure):
+    _fields_ = [("stages", C.c_int32), ("items_per_sm", C.c_int32), ("exp_split", C.c_int32)]
+
+
 class _Points(C.Structure):
     _fields_ = [("n_inst", C.c_int32), ("offsets", C.POINTER(C.c_int64)), ("d", C.c_int32),
                 ("ard", C.c_int32), ("x", C.c_void_p), ("cheb", C.c_int32)]
@@ -67,10 +71,14 @@ _SIGS = {
     "kmv_accept": (C.c_int, [C.c_int32, C.c_int32, _P, _P, _P, _P, _P, _P, _P, _P]),
     "kmv_status_merge": (C.c_int, [C.c_int32, _P, _P, _P]),
     "kmv_profile_enable": (C.c_int, [_P, C.c_int32]),
+    "kmv_set_tiles": (C.c_int, [_P, C.c_int32, C.POINTER(_Tiles)]),
+    "kmv_get_tiles": (C.c_int, [_P, C.c_int32, C.POINTER(_Tiles)]),
+    "kmv_autotune": (C.c_int, [_P, C.POINTER(_Points), C.c_int32, _P, C.c_int32, C.c_char_p, _P]),
     "kmv_profile_read": (C.c_int, [_P, C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
 }
 
 KMV_KERNEL_FORWARD, KMV_KERNEL_ADJOINT = 0, 1
+KMV_TILES_FORWARD, KMV_TILES_FORWARD_FMA, KMV_TILES_ADJOINT = 0, 1, 2
 
 
 def lib_path() -> str:
@@ -189,6 +197,24 @@ class Kmv:
         ms, n = C.c_double(0.0), C.c_int64(0)
         self._check(self.L.kmv_profile_read(self.h, kind, C.byref(ms), C.byref(n)))
         return ms.value, n.value
+
+    def set_tiles(self, kernel: int, stages: int = 0, items_per_sm: int = 6, exp_split: int = 0):
+        """Default tile choices of one tensor-core kernel kind (kmv_set_tiles)."""
+        t = _Tiles(stages, items_per_sm, exp_split)
+        self._check(self.L.kmv_set_tiles(self.h, kernel, C.byref(t)))
+
+    def get_tiles(self, kernel: int) -> dict:
+        """Default tile choices of one kernel kind (kmv_get_tiles)."""
+        t = _Tiles()
+        self._check(self.L.kmv_get_tiles(self.h, kernel, C.byref(t)))
+        return {"stages": t.stages, "items_per_sm": t.items_per_sm, "exp_split": t.exp_split}
+
+    def autotune(self, pts: "Points", theta, m: int, cache_path=None, stream=None):
+        """Time candidate tiles for this call shape and record the fastest (kmv_autotune; synchronous)."""
+        chains = self._chains(pts, theta)
+        _need(theta, torch.float64, "theta", (pts.n_inst * chains, pts.n_theta))
+        path = None if cache_path is None else os.fsencode(cache_path)
+        self._check(self.L.kmv_autotune(self.h, pts.c, chains, _ptr(theta), int(m), path, _stream(stream)))
 
     @staticmethod
     def _prec(prec):
@@ -385,10 +411,11 @@ def kmv_backward_noalloc(pts: Points, theta, V, G, want_grad_V=True, grad_theta=
                          stream=None):
     """The FP32 adjoint without device allocation or handle (include/kmv.h).
 
-    For callers that cannot allocate device memory (stream capture, their own
-    memory pool, allocation-free loops); its scratch is a fixed 4 MiB array in
-    the library, shared by all calls on a device.  Raises KmvError with status
-    KMV_EINVAL when the problem does not fit that array.
+    For callers that cannot allocate device memory (device memory held by
+    their own pool or arena, loops that cannot take the synchronisation an
+    allocation may imply); its scratch is a fixed 4 MiB array in the library,
+    shared by all calls on a device.  Raises KmvError with status KMV_EINVAL
+    when the problem does not fit that array.
     """
     L = lib()
     n_sys = theta.shape[0]

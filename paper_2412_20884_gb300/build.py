@@ -54,10 +54,20 @@ def _compile(src, extra):
 
 
 def build_library(verbose: bool = False, extra_flags=None) -> str:
-    """Compile and link libkmv.so; returns its path."""
+    """Compile and link libkmv.so; returns its path.
+
+    extra_flags: further nvcc flags (e.g. ``["-DKMV_BWD_FOLD_HALVES=8"]``); a
+    change of flags since the last build rebuilds every object."""
     os.makedirs(BUILD, exist_ok=True)
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
     extra = list(extra_flags or [])
+    stamp = os.path.join(BUILD, "flags.txt")
+    flags_text = " ".join(FLAGS + extra + ARCH)
+    if not os.path.exists(stamp) or open(stamp).read() != flags_text:
+        for o in glob.glob(os.path.join(BUILD, "*.o")):
+            os.remove(o)
+        with open(stamp, "w") as fh:
+            fh.write(flags_text)
     with cf.ThreadPoolExecutor(max_workers=min(len(srcs), os.cpu_count() or 4)) as ex:
         objs = list(ex.map(lambda s: _compile(s, extra), srcs))
     if _stale(LIB, objs):

@@ -10,6 +10,28 @@
 
 using namespace kmv;
 
+namespace kmv {
+const char* points_error(const kmv_points* pts, int32_t chains) {
+  if (!pts) return "points is NULL";
+  if (pts->n_inst < 1) return "n_inst must be >= 1";
+  if (!pts->offsets) return "offsets is NULL";
+  if (pts->d < 1 || pts->d > kMaxD) return "d must be in [1, 64]";
+  if (pts->ard != 0 && pts->ard != 1) return "ard must be 0 or 1";
+  if (chains < 1 || chains > 65535) return "chains must be in [1, 65535]";
+  if (pts->offsets[0] != 0) return "offsets[0] must be 0";
+  for (int b = 0; b < pts->n_inst; ++b)
+    if (pts->offsets[b + 1] < pts->offsets[b]) return "offsets must be non-decreasing";
+  const int64_t n = pts->offsets[pts->n_inst];
+  if (n > (int64_t(1) << 40)) return "too many rows";
+  if (n > 0 && !pts->x) return "x is NULL";
+  if ((int64_t)pts->n_inst * chains > (int64_t(1) << 30)) return "too many systems";
+  if (pts->cheb < 0 || pts->cheb > kMaxChebOrder) return "cheb must be in [0, 32]";
+  if (pts->cheb > 1 && pts->d > kMaxChebDims) return "cheb >= 2 needs d <= 8";
+  if (pts->cheb > 0 && cheb_n_coef(pts->cheb, pts->d) < 0) return "cheb^d must be <= 1024";
+  return nullptr;
+}
+}  // namespace kmv
+
 namespace {
 
 kmv_status fail(kmv_handle h, kmv_status s, const std::string& msg) {
@@ -70,24 +92,8 @@ T* at(kmv_handle h, size_t off) {
 
 kmv_status check_points(kmv_handle h, const kmv_points* pts, int32_t chains) {
   if (!h) return KMV_EINVAL;
-  if (!pts) return fail(h, KMV_EINVAL, "points is NULL");
-  if (pts->n_inst < 1) return fail(h, KMV_EINVAL, "n_inst must be >= 1");
-  if (!pts->offsets) return fail(h, KMV_EINVAL, "offsets is NULL");
-  if (pts->d < 1 || pts->d > kMaxD) return fail(h, KMV_EINVAL, "d must be in [1, 64]");
-  if (pts->ard != 0 && pts->ard != 1) return fail(h, KMV_EINVAL, "ard must be 0 or 1");
-  if (chains < 1 || chains > 65535) return fail(h, KMV_EINVAL, "chains must be in [1, 65535]");
-  if (pts->offsets[0] != 0) return fail(h, KMV_EINVAL, "offsets[0] must be 0");
-  for (int b = 0; b < pts->n_inst; ++b)
-    if (pts->offsets[b + 1] < pts->offsets[b]) return fail(h, KMV_EINVAL, "offsets must be non-decreasing");
-  const int64_t n = pts->offsets[pts->n_inst];
-  if (n > (int64_t(1) << 40)) return fail(h, KMV_EINVAL, "too many rows");
-  if (n > 0 && !pts->x) return fail(h, KMV_EINVAL, "x is NULL");
-  if ((int64_t)pts->n_inst * chains > (int64_t(1) << 30)) return fail(h, KMV_EINVAL, "too many systems");
-  if (pts->cheb < 0 || pts->cheb > kMaxChebOrder) return fail(h, KMV_EINVAL, "cheb must be in [0, 32]");
-  if (pts->cheb > 1 && pts->d > kMaxChebDims) return fail(h, KMV_EINVAL, "cheb >= 2 needs d <= 8");
-  if (pts->cheb > 0 && cheb_n_coef(pts->cheb, pts->d) < 0)
-    return fail(h, KMV_EINVAL, "cheb^d must be <= 1024");
-  return KMV_OK;
+  const char* e = points_error(pts, chains);
+  return e ? fail(h, KMV_EINVAL, e) : KMV_OK;
 }
 
 // Builds (or reuses) the row-tile work items of this point set on the device.
@@ -311,6 +317,42 @@ kmv_status run_backward(kmv_handle h, KmvArgs a, double* grad, double* partial,
   return KMV_OK;
 }
 
+// While `st` is being captured: records the loop `while (*n_active > 0)
+// body(stream)` as a conditional WHILE node, so that a replayed solve stops
+// when its systems have converged, as the eager loop does.  The first test
+// is a kernel captured before the node; the body ends with the next test.
+// The body is captured on the handle's side stream into the node's graph.
+template <class Body>
+kmv_status capture_while(kmv_handle h, cudaStream_t st, const int32_t* n_active, Body&& body) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaGraph_t g = nullptr;
+  KMV_CUDA(h, cudaStreamGetCaptureInfo(st, &cs, nullptr, &g, nullptr, nullptr, nullptr));
+  if (cs != cudaStreamCaptureStatusActive) return fail(h, KMV_EINVAL, "internal: capture_while outside a capture");
+  cudaGraphConditionalHandle cond;
+  KMV_CUDA(h, cudaGraphConditionalHandleCreate(&cond, g, 0, cudaGraphCondAssignDefault));
+  KMV_CUDA(h, launch_loop_cond(cond, n_active, st));
+  const cudaGraphNode_t* deps = nullptr;
+  size_t n_deps = 0;
+  KMV_CUDA(h, cudaStreamGetCaptureInfo(st, &cs, nullptr, &g, &deps, nullptr, &n_deps));
+  cudaGraphNodeParams np{};
+  np.type = cudaGraphNodeTypeConditional;
+  np.conditional.handle = cond;
+  np.conditional.type = cudaGraphCondTypeWhile;
+  np.conditional.size = 1;
+  cudaGraphNode_t node = nullptr;
+  KMV_CUDA(h, cudaGraphAddNode(&node, g, deps, nullptr, n_deps, &np));
+  cudaGraph_t body_graph = np.conditional.phGraph_out[0];
+  KMV_CUDA(h, cudaStreamBeginCaptureToGraph(h->side, body_graph, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+  kmv_status s = body(h->side);
+  if (s == KMV_OK && launch_loop_cond(cond, n_active, h->side) != cudaSuccess) s = KMV_ECUDA;
+  cudaGraph_t captured = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(h->side, &captured);
+  if (s != KMV_OK) return s;
+  KMV_CUDA(h, e);
+  KMV_CUDA(h, cudaStreamUpdateCaptureDependencies(st, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+  return KMV_OK;
+}
+
 struct CgBufs {
   float *r, *p, *q;
   double *partial, *partial2;
@@ -370,23 +412,38 @@ kmv_status run_cg(kmv_handle h, const kmv_points* pts, const double* theta, cons
   a.Y = B.q;
   a.sys_active = B.active;
   a.dot_partial = B.partial;
-  // Under stream capture there is no host check: exactly maxiter masked
-  // iterations are recorded (converged systems idle on their device masks, so
-  // the result equals the eager solve that stops at convergence).
-  for (int it = 0; it < maxiter; ++it) {
-    if (!h->capturing && it % check_every == 0) {
-      KMV_CUDA(h, cudaMemcpyAsync(h->host_flag, B.n_active, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-      KMV_CUDA(h, cudaStreamSynchronize(st));
-      if (*h->host_flag == 0) break;
-    }
-    KMV_TRY(run_forward(h, a, prec, st));
-    KMV_CUDA(h, launch_cg_reduce_pq(h->dev, L.n_inst, L.chains, B.partial, B.sys, B.active, st));
+  // one CG iteration on every active system; theta is fixed within the solve,
+  // so the products after the first reuse its operand tiles
+  auto iteration = [&](cudaStream_t s, int reuse) -> kmv_status {
+    a.reuse_prep = reuse;
+    KMV_TRY(run_forward(h, a, prec, s));
+    KMV_CUDA(h, launch_cg_reduce_pq(h->dev, L.n_inst, L.chains, B.partial, B.sys, B.active, s));
     KMV_CUDA(h, launch_cg_update_xr(h->dev, L.n_items, L.chains, L.n_total, B.sys, B.active, x, B.r,
-                                    B.p, B.q, B.partial, st));
+                                    B.p, B.q, B.partial, s));
     KMV_CUDA(h, launch_cg_reduce_rr(h->dev, L.n_inst, L.chains, B.partial, tol, maxiter, B.sys,
-                                    B.active, B.n_active, st));
+                                    B.active, B.n_active, s));
     KMV_CUDA(h, launch_cg_update_p(h->dev, L.n_items, L.chains, L.n_total, B.sys, B.active, B.r,
-                                   B.p, st));
+                                   B.p, s));
+    return KMV_OK;
+  };
+  if (h->capturing) {
+    // Under stream capture: the first iteration (which prepares the operand
+    // tiles; on systems already converged it changes nothing), then a WHILE
+    // node repeating iterations while any system is active, so a replay stops
+    // at convergence (or at maxiter, which deactivates a system) like the eager loop.
+    if (maxiter > 0) {
+      KMV_TRY(iteration(st, warm ? 1 : 0));
+      KMV_TRY(capture_while(h, st, B.n_active, [&](cudaStream_t s2) { return iteration(s2, 1); }));
+    }
+  } else {
+    for (int it = 0; it < maxiter; ++it) {
+      if (it % check_every == 0) {
+        KMV_CUDA(h, cudaMemcpyAsync(h->host_flag, B.n_active, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        KMV_CUDA(h, cudaStreamSynchronize(st));
+        if (*h->host_flag == 0) break;
+      }
+      KMV_TRY(iteration(st, (it > 0 || warm) ? 1 : 0));
+    }
   }
   KMV_CUDA(h, launch_cg_finish(n_sys, B.sys, status, iters, st));
   return KMV_OK;
@@ -461,22 +518,35 @@ kmv_status run_pcg(kmv_handle h, const kmv_points* pts, const double* theta, con
   a.sys_active = B.active;
   a.dot_partial = B.partial;
   const int check_every = 4;
-  for (int it = 0; it < maxiter; ++it) {
-    if (!h->capturing && it % check_every == 0) {
-      KMV_CUDA(h, cudaMemcpyAsync(h->host_flag, B.n_active, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-      KMV_CUDA(h, cudaStreamSynchronize(st));
-      if (*h->host_flag == 0) break;
-    }
-    KMV_TRY(run_forward(h, a, prec, st));
-    KMV_CUDA(h, launch_pcg_alpha(h->dev, L.n_inst, L.chains, B.partial, B.sys, B.active, st));
+  auto iteration = [&](cudaStream_t s, int reuse) -> kmv_status {
+    a.reuse_prep = reuse;
+    KMV_TRY(run_forward(h, a, prec, s));
+    KMV_CUDA(h, launch_pcg_alpha(h->dev, L.n_inst, L.chains, B.partial, B.sys, B.active, s));
     KMV_CUDA(h, launch_pcg_update_xr(h->dev, L.n_items, L.chains, L.n_total, B.sys, B.active, x, B.r, B.p, B.q,
-                                     B.partial, st));
+                                     B.partial, s));
     KMV_CUDA(h, launch_pcg_precond(h->dev, L.n_items, L.n_inst, L.chains, L.n_total, P, a.theta, a.n_theta, B.r,
-                                   B.z, B.active, B.proj, B.coef, B.prz, st));
-    KMV_CUDA(h, cudaMemsetAsync(B.n_active, 0, sizeof(int32_t), st));
+                                   B.z, B.active, B.proj, B.coef, B.prz, s));
+    KMV_CUDA(h, cudaMemsetAsync(B.n_active, 0, sizeof(int32_t), s));
     KMV_CUDA(h, launch_pcg_beta(h->dev, L.n_inst, L.chains, B.partial, B.prz, tol, maxiter, B.sys, B.active,
-                                B.n_active, st));
-    KMV_CUDA(h, launch_pcg_update_p(h->dev, L.n_items, L.chains, L.n_total, B.sys, B.active, B.z, B.p, st));
+                                B.n_active, s));
+    KMV_CUDA(h, launch_pcg_update_p(h->dev, L.n_items, L.chains, L.n_total, B.sys, B.active, B.z, B.p, s));
+    return KMV_OK;
+  };
+  if (h->capturing) {
+    // as in run_cg: one iteration, then a WHILE node until no system is active
+    if (maxiter > 0) {
+      KMV_TRY(iteration(st, warm ? 1 : 0));
+      KMV_TRY(capture_while(h, st, B.n_active, [&](cudaStream_t s2) { return iteration(s2, 1); }));
+    }
+  } else {
+    for (int it = 0; it < maxiter; ++it) {
+      if (it % check_every == 0) {
+        KMV_CUDA(h, cudaMemcpyAsync(h->host_flag, B.n_active, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        KMV_CUDA(h, cudaStreamSynchronize(st));
+        if (*h->host_flag == 0) break;
+      }
+      KMV_TRY(iteration(st, (it > 0 || warm) ? 1 : 0));
+    }
   }
   KMV_CUDA(h, launch_pcg_finish(n_sys, B.sys, B.active, status, iters, st));
   return KMV_OK;
@@ -584,7 +654,7 @@ kmv_status run_cg_refined(kmv_handle h, const kmv_points* pts, const double* the
     KMV_CUDA(h, launch_axpy(nvec, R.dx, x, st));
     KMV_CUDA(h, launch_refine_merge(n_sys, R.in_status, R.in_iters, status, iters, st));
   }
-  KMV_CUDA(h, launch_refine_finish(n_sys, R.active, R.sys, status, st));
+  KMV_CUDA(h, launch_refine_finish(n_sys, R.active, R.sys, tol, status, st));
   return KMV_OK;
 }
 
@@ -599,7 +669,10 @@ struct SolveLayout {
 void solve_layout(kmv_handle h, Arena& ar, kmv_precision prec, SolveLayout& S) {
   const Layout& L = h->layout;
   cg_layout(L, ar, S.cg);
-  S.refined = prec == KMV_BF16_HILO;
+  // The single-column tensor-core product (three-way split exponent, FP32 P.v)
+  // is as accurate as the FP32 form, so the BF16 form solves with it directly;
+  // only shapes without that product (d > 17) solve by refinement.
+  S.refined = prec == KMV_BF16_HILO && !x_width_fma_ok(L.d);
   if (S.refined) refine_layout(L, ar, S.rf);
   S.pc = h->pc_on;
   if (S.pc) pcg_layout(L, h->pc.rank, ar, S.pcg);
@@ -899,8 +972,10 @@ kmv_status kmv_create(kmv_handle* out, int device) {
   if (!h) return KMV_ENOMEM;
   h->device = device;
   if (cudaSetDevice(device) != cudaSuccess ||
-      cudaMallocHost(reinterpret_cast<void**>(&h->host_flag), 64) != cudaSuccess) {
+      cudaMallocHost(reinterpret_cast<void**>(&h->host_flag), 64) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking) != cudaSuccess) {
     cudaGetLastError();
+    if (h->host_flag) cudaFreeHost(h->host_flag);
     delete h;
     return KMV_ECUDA;
   }
@@ -917,6 +992,7 @@ kmv_status kmv_destroy(kmv_handle h) {
   if (h->tables) cudaFree(h->tables);
   if (h->cheb_buf) cudaFree(h->cheb_buf);
   if (h->host_flag) cudaFreeHost(h->host_flag);
+  if (h->side) cudaStreamDestroy(h->side);
   kmv_profile_enable(h, 0);
   for (cudaEvent_t e : h->prof_pool) cudaEventDestroy(e);
   delete h;
@@ -1019,7 +1095,9 @@ kmv_status kmv_phi_refresh(kmv_handle h, const kmv_points* pts, int32_t chains, 
   const int64_t n_total = L.n_total;
   const int n_sys = L.n_inst * chains;
   const int64_t n_cols = (int64_t)n_sys * n_poles;
-  const bool refined = prec == KMV_BF16_HILO;
+  // the multi-shift solve's product is single-column: FP32-accurate in both
+  // forms where the three-way split fits, else the BF16 form polishes by refinement
+  const bool refined = prec == KMV_BF16_HILO && !x_width_fma_ok(L.d);
   // with a preconditioner set (and matching this layout) the shifted systems run
   // as preconditioned columns of one multi-column CG (a preconditioner breaks the
   // shift invariance multi-shift CG relies on); without, multi-shift CG
@@ -1183,10 +1261,11 @@ kmv_status leapfrog_step(kmv_handle h, const kmv_points* pts, int32_t chains, co
   a.G = Gf;
   a.m = 2;
   a.Y = nullptr;
-  // The two quadratic forms cancel to a small fraction of their size, below
-  // the F16 rounding of the tensor-core adjoint: the force is always FP32 (one
-  // N^2 pass per step, small next to the solve).
-  KMV_TRY(run_backward(h, a, grad, at<double>(h, o_bp), KMV_FP32, st));
+  // The two quadratic forms cancel to a small fraction of their size; both
+  // adjoint forms keep every pair's term to about FP32 accuracy (the
+  // tensor-core form from its split operands and exact Q = Qh + Ql), so the
+  // force follows the call's precision.
+  KMV_TRY(run_backward(h, a, grad, at<double>(h, o_bp), prec, st));
   // kick + drift
   KMV_CUDA(h, launch_lf_kick_drift(n_sys, L.n_theta, theta_h, grad, prior_mu, prior_prec, free_mask,
                                    chain_status, dt, theta, pi, st));

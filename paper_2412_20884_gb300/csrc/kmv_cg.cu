@@ -93,6 +93,15 @@ __global__ void cg_reduce_init_kernel(DevLayout L, int n_inst, int chains, const
   count_active(n_sys, active, n_active);
 }
 
+__global__ void loop_cond_kernel(cudaGraphConditionalHandle cond, const int32_t* n_active) {
+  cudaGraphSetConditional(cond, *n_active > 0 ? 1u : 0u);
+}
+
+cudaError_t launch_loop_cond(cudaGraphConditionalHandle cond, const int32_t* n_active, cudaStream_t st) {
+  loop_cond_kernel<<<1, 1, 0, st>>>(cond, n_active);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_cg_reduce_init(const DevLayout& L, int n_inst, int chains, const double* partial2,
                                   double tol, CgSys* sys, int32_t* active, int32_t* n_active,
                                   cudaStream_t st) {
@@ -263,7 +272,10 @@ __global__ void refine_merge_kernel(int n_sys, const int32_t* in_status, const i
                                     int32_t* status, int32_t* iters) {
   for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n_sys; s += gridDim.x * blockDim.x) {
     if (iters) iters[s] += in_iters[s];
+    // a correction solve that failed (non-finite, or cg_maxiter / breakdown) is
+    // remembered; refine_finish clears the latter if the final residual meets tol
     if (in_status[s] == KMV_ENONFINITE) status[s] = KMV_ENONFINITE;
+    else if (in_status[s] == KMV_ENOTCONV && status[s] == KMV_OK) status[s] = KMV_ENOTCONV;
   }
 }
 
@@ -318,18 +330,27 @@ cudaError_t launch_refine_stagnation(int n_sys, int outer, const CgSys* sys, dou
   return cudaGetLastError();
 }
 
-// Final outer status: still active after the last refinement -> not converged.
-__global__ void refine_finish_kernel(int n_sys, const int32_t* active, const CgSys* sys, int32_t* status) {
+// Final outer status from the last true residual rr (sys[s].rr): converged if
+// rr <= tol^2 bb; otherwise converged only when the residual stopped falling
+// with every correction solve converged (the floor of the FP32 operator),
+// and not converged when a correction solve failed or the system is still active.
+__global__ void refine_finish_kernel(int n_sys, const int32_t* active, const CgSys* sys, double tol,
+                                     int32_t* status) {
   for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n_sys; s += gridDim.x * blockDim.x) {
-    if (status[s] != KMV_OK) continue;
-    if (sys[s].status != KMV_OK) status[s] = sys[s].status;
-    else if (active[s]) status[s] = KMV_ENOTCONV;
+    if (status[s] == KMV_ENONFINITE) continue;
+    if (sys[s].status != KMV_OK) {
+      status[s] = sys[s].status;
+    } else if (sys[s].rr <= tol * tol * sys[s].bb) {
+      status[s] = KMV_OK;
+    } else if (active[s]) {
+      status[s] = KMV_ENOTCONV;
+    }
   }
 }
 
-cudaError_t launch_refine_finish(int n_sys, const int32_t* active, const CgSys* sys, int32_t* status,
+cudaError_t launch_refine_finish(int n_sys, const int32_t* active, const CgSys* sys, double tol, int32_t* status,
                                  cudaStream_t st) {
-  refine_finish_kernel<<<(n_sys + 255) / 256, 256, 0, st>>>(n_sys, active, sys, status);
+  refine_finish_kernel<<<(n_sys + 255) / 256, 256, 0, st>>>(n_sys, active, sys, tol, status);
   return cudaGetLastError();
 }
 

@@ -95,7 +95,14 @@ struct KmvArgs {
   // amp = exp(C_theta(x)) per (chain, point), laid out (chains, N_total); NULL = 1.
   const float* amp;
   int no_diag;                 // forward: leave out the (sigma^2 + shift) V term
+  // forward, tensor-core form: the operand tiles of (theta, x) prepared by the
+  // previous product of the same solve may be reused (theta and x unchanged)
+  int reuse_prep;
 };
+
+// The argument rules of a point set and chain count shared by every entry
+// point (kmv_api.cu): nullptr when they hold, else what is wrong.
+const char* points_error(const kmv_points* pts, int32_t chains);
 
 // SIMT kernels (kmv_simt.cu)
 cudaError_t launch_forward_simt(const KmvArgs& a, int n_items, cudaStream_t st);
@@ -128,6 +135,9 @@ cudaError_t launch_cg_update_p(const DevLayout& L, int n_items, int chains, int6
                                cudaStream_t st);
 cudaError_t launch_cg_finish(int n_sys, const CgSys* sys, int32_t* status, int32_t* iters,
                              cudaStream_t st);
+// Sets the value of a graph's conditional handle to (*n_active > 0): the test
+// of a captured solver loop (a WHILE node repeats its body while it is 1).
+cudaError_t launch_loop_cond(cudaGraphConditionalHandle cond, const int32_t* n_active, cudaStream_t st);
 
 cudaError_t launch_mask_rows(const DevLayout& L, int n_items, int chains, int64_t n_total, const int32_t* active,
                              float* r, cudaStream_t st);
@@ -136,7 +146,7 @@ cudaError_t launch_refine_merge(int n_sys, const int32_t* in_status, const int32
                                 int32_t* iters, cudaStream_t st);
 cudaError_t launch_refine_stagnation(int n_sys, int outer, const CgSys* sys, double* prev_rr, int32_t* active,
                                      int32_t* n_active, double* worst, cudaStream_t st);
-cudaError_t launch_refine_finish(int n_sys, const int32_t* active, const CgSys* sys, int32_t* status,
+cudaError_t launch_refine_finish(int n_sys, const int32_t* active, const CgSys* sys, double tol, int32_t* status,
                                  cudaStream_t st);
 // phi refresh (kmv_phi.cu): spectral interval, pole weights/shifts, weighted
 // sum of the shifted solutions, per-system status
@@ -337,6 +347,8 @@ struct kmv_handle_s {
   // true while the current call's stream is being captured into a CUDA graph:
   // no allocation, no table upload, no host synchronisation may happen then
   bool capturing = false;
+  // stream on which the bodies of conditional (WHILE) graph nodes are captured
+  cudaStream_t side = nullptr;
   // kernel timing (kmv_profile_enable): event pairs around the main product kernels
   bool prof = false;
   std::vector<cudaEvent_t> prof_pool;

@@ -1,18 +1,19 @@
 // kmv_backward_noalloc: the FP32 adjoint with its scratch in a fixed device
 // array, for callers that cannot allocate device memory.
 //
-// Who needs this: code that runs while a CUDA stream is being captured into a
-// graph (cudaMalloc is not allowed there and would break the capture), code
-// that hands the whole device to its own memory pool and must not take memory
-// behind the pool's back, and latency-critical loops that cannot afford the
-// device-wide synchronisation cudaMalloc/cudaFree can imply.  It needs no
-// handle either: kmv_create allocates, this entry point does not.
+// Who needs this: code that hands all of the device memory to its own pool
+// or arena (a framework's caching allocator, a fixed budget per process) and
+// must not take memory behind the pool's back, and latency-critical loops that
+// cannot afford the device-wide synchronisation that cudaMalloc and cudaFree
+// can imply.  It needs no handle either: kmv_create allocates, this entry
+// point does not.
 //
 // Scratch: the static array below, kNoAllocScratchBytes (4 MiB) per device
 // that loads the library, held until the process exits.  Host code may not
 // pass the array's name to a kernel (in host code it is only a stand-in for
 // the symbol); the device address comes from cudaGetSymbolAddress, looked up
 // once per device, with that device current, on the first call there.
+#include <atomic>
 #include <cstring>
 
 #include "kmv_internal.cuh"
@@ -26,16 +27,18 @@ constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
-unsigned char* g_scratch_addr[kMaxDevices] = {nullptr};
+// device address of the array per device, looked up on the first call there
+// (two threads making that first call at once both store the same address)
+std::atomic<unsigned char*> g_scratch_addr[kMaxDevices];
 
 size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
 
-// Fills item_inst / item_row0 / inst_item0 from the offsets already copied
-// into the scratch: one thread per instance.
+// Fills inst_item0 / item_inst / item_row0 from the offsets already copied
+// into the scratch.  One block: thread 0 forms the prefix over instances
+// once, then the block fills the items of every instance.
 __global__ void noalloc_items_kernel(int n_inst, const int64_t* offsets, int32_t* inst_item0,
                                      int32_t* item_inst, int64_t* item_row0) {
-  // prefix over instances, done by one thread (n_inst is small next to the N^2 work)
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
+  if (threadIdx.x == 0) {
     int32_t acc = 0;
     for (int b = 0; b < n_inst; ++b) {
       inst_item0[b] = acc;
@@ -44,13 +47,9 @@ __global__ void noalloc_items_kernel(int n_inst, const int64_t* offsets, int32_t
     inst_item0[n_inst] = acc;
   }
   __syncthreads();
-  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < n_inst; b += gridDim.x * blockDim.x) {
-    // recomputed here so the fill does not depend on the prefix thread
-    int32_t first = 0;
-    for (int q = 0; q < b; ++q) first += (int32_t)((offsets[q + 1] - offsets[q] + kTile - 1) / kTile);
-    const int64_t nb = offsets[b + 1] - offsets[b];
-    const int32_t tiles = (int32_t)((nb + kTile - 1) / kTile);
-    for (int32_t t = 0; t < tiles; ++t) {
+  for (int b = 0; b < n_inst; ++b) {
+    const int32_t first = inst_item0[b], tiles = inst_item0[b + 1] - first;
+    for (int32_t t = threadIdx.x; t < tiles; t += blockDim.x) {
       item_inst[first + t] = b;
       item_row0[first + t] = offsets[b] + (int64_t)t * kTile;
     }
@@ -65,19 +64,12 @@ using namespace kmv;
 extern "C" kmv_status kmv_backward_noalloc(const kmv_points* pts, int32_t chains, const double* theta,
                                            const float* V, const float* G, int32_t m, double* grad_theta,
                                            float* grad_V, void* stream) {
-  if (!pts || pts->n_inst < 1 || !pts->offsets || pts->d < 1 || pts->d > kMaxD ||
-      (pts->ard != 0 && pts->ard != 1) || chains < 1 || chains > 65535 || m < 1 || !theta || !V || !G || !grad_theta)
-    return KMV_EINVAL;
+  // the same rules as every entry point with a handle (points_error), then this one's own
+  if (points_error(pts, chains) != nullptr || m < 1 || !theta || !V || !G || !grad_theta) return KMV_EINVAL;
   if (pts->cheb != 0) return KMV_EUNSUPPORTED;   // the amplitudes would need scratch per point
-  if (pts->offsets[0] != 0) return KMV_EINVAL;
   int64_t n_items = 0;
-  for (int b = 0; b < pts->n_inst; ++b) {
-    const int64_t nb = pts->offsets[b + 1] - pts->offsets[b];
-    if (nb < 0) return KMV_EINVAL;
-    n_items += (nb + kTile - 1) / kTile;
-  }
+  for (int b = 0; b < pts->n_inst; ++b) n_items += (pts->offsets[b + 1] - pts->offsets[b] + kTile - 1) / kTile;
   const int64_t n_total = pts->offsets[pts->n_inst];
-  if (n_total > 0 && !pts->x) return KMV_EINVAL;
   const int n_theta = 2 + (pts->ard ? pts->d : 1);
   const int mp = backward_mp(m);
   const int n_z = (m + mp - 1) / mp;
@@ -93,15 +85,16 @@ extern "C" kmv_status kmv_backward_noalloc(const kmv_points* pts, int32_t chains
 
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return KMV_ECUDA;
-  if (!g_scratch_addr[dev]) {
+  unsigned char* base = g_scratch_addr[dev].load(std::memory_order_acquire);
+  if (!base) {
     void* p = nullptr;
     if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
       cudaGetLastError();
       return KMV_ECUDA;
     }
-    g_scratch_addr[dev] = static_cast<unsigned char*>(p);
+    base = static_cast<unsigned char*>(p);
+    g_scratch_addr[dev].store(base, std::memory_order_release);
   }
-  unsigned char* base = g_scratch_addr[dev];
   cudaStream_t st = static_cast<cudaStream_t>(stream);
 
   if (cudaMemcpyAsync(base + o_off, pts->offsets, sizeof(int64_t) * (pts->n_inst + 1), cudaMemcpyHostToDevice,
@@ -112,7 +105,7 @@ extern "C" kmv_status kmv_backward_noalloc(const kmv_points* pts, int32_t chains
   L.inst_item0 = reinterpret_cast<const int32_t*>(base + o_ii);
   L.item_inst = reinterpret_cast<const int32_t*>(base + o_inst);
   L.item_row0 = reinterpret_cast<const int64_t*>(base + o_row0);
-  noalloc_items_kernel<<<(pts->n_inst + 127) / 128, 128, 0, st>>>(
+  noalloc_items_kernel<<<1, 256, 0, st>>>(
       pts->n_inst, L.offsets, reinterpret_cast<int32_t*>(base + o_ii), reinterpret_cast<int32_t*>(base + o_inst),
       reinterpret_cast<int64_t*>(base + o_row0));
 

@@ -3,8 +3,8 @@
 // Layout in HBM (written per call by the prep kernels, per chain c, in
 // 128-row tiles that are byte-for-byte the shared-memory operand layout, so
 // each tile moves with one bulk copy):
-//   XA[c][t] : 128 x KX BF16, rows i:  [hi(xh), hi(xh), lo(xh), 1, 1, 1, bh, bm, bl, 0..]
-//   XB[c][t] : 128 x KX BF16, rows j:  [hi(xh), lo(xh), hi(xh), bh, bm, bl, 1, 1, 1, 0..]
+//   XA[c][t] : 128 x KX BF16, rows i:  per dimension [hi, lo, hi] of xh, then 1, 1, 1, bh, bm, bl, 0..
+//   XB[c][t] : 128 x KX BF16, rows j:  per dimension [hi, hi, lo] of xh, then bh, bm, bl, 1, 1, 1, 0..
 //   VT[c][t] : MP x 128 F16, V^T of the tile scaled by a per-column power of two
 // with xh = x sqrt(log2(e)) / l and b = -|xh|^2/2 (computed from the split
 // values, so the diagonal exponent is 0) split into three BF16 terms.  One
@@ -60,6 +60,14 @@ __device__ __forceinline__ void issue_pv(uint32_t d_tmem, uint32_t a_tmem, uint6
   for (int k = 0; k < 8; ++k) ptx::mma_ts(d_tmem, a_tmem + 8 * k, db + 16 * k, idesc, (k > 0) || acc);
 }
 
+// 2^s for element e of a 32-element chunk (e is a compile-time constant once
+// the loops are unrolled): one element in POLY on the FMA pipe (degree-DEG
+// polynomial), the rest on the MUFU; POLY = 0 puts every exp on the MUFU.
+template <int POLY, int DEG>
+__device__ __forceinline__ float exp2_mix(float s, int e) {
+  return (POLY > 0 && (e % POLY) == POLY - 1) ? exp2_fma<DEG>(s) : ptx::ex2(s);
+}
+
 struct TcFwdArgs {
   const int4* items;       // {system, I tile (first of 2), first J tile, number of J tiles}
   int n_items;
@@ -77,7 +85,7 @@ struct TcFwdArgs {
 
 // RM > 0: the FP64 fold accumulators of up to RM columns live in registers;
 // RM == 0: they live in the per-item partial (global read-modify-write).
-template <int RM>
+template <int RM, int POLY>
 __global__ void __launch_bounds__(kFwdThreads, 1) tc_fwd_kernel(TcFwdArgs a) {
   using namespace ptx;
   extern __shared__ uint8_t smem_raw[];
@@ -316,10 +324,12 @@ __global__ void __launch_bounds__(kFwdThreads, 1) tc_fwd_kernel(TcFwdArgs a) {
           tmem_ld32(tl + s_col + 96, b1);
 #pragma unroll
           for (int q = 0; q < 16; ++q)
-            pk[q] = pack_f16x2(ex2(__uint_as_float(a0[2 * q])), ex2(__uint_as_float(a0[2 * q + 1])));
+            pk[q] = pack_f16x2(exp2_mix<POLY, 3>(__uint_as_float(a0[2 * q]), 2 * q),
+                               exp2_mix<POLY, 3>(__uint_as_float(a0[2 * q + 1]), 2 * q + 1));
 #pragma unroll
           for (int q = 0; q < 16; ++q)
-            pk[16 + q] = pack_f16x2(ex2(__uint_as_float(a1[2 * q])), ex2(__uint_as_float(a1[2 * q + 1])));
+            pk[16 + q] = pack_f16x2(exp2_mix<POLY, 3>(__uint_as_float(a1[2 * q]), 2 * q),
+                               exp2_mix<POLY, 3>(__uint_as_float(a1[2 * q + 1]), 2 * q + 1));
           tmem_ld_wait_regs(b0, b1);
           // S(k) is fully in registers: the tensor core may overwrite it
           tc_fence_before();
@@ -334,10 +344,12 @@ __global__ void __launch_bounds__(kFwdThreads, 1) tc_fwd_kernel(TcFwdArgs a) {
           tmem_st32(tl + p_col, pk);
 #pragma unroll
           for (int q = 0; q < 16; ++q)
-            pk[q] = pack_f16x2(ex2(__uint_as_float(b0[2 * q])), ex2(__uint_as_float(b0[2 * q + 1])));
+            pk[q] = pack_f16x2(exp2_mix<POLY, 3>(__uint_as_float(b0[2 * q]), 2 * q),
+                               exp2_mix<POLY, 3>(__uint_as_float(b0[2 * q + 1]), 2 * q + 1));
 #pragma unroll
           for (int q = 0; q < 16; ++q)
-            pk[16 + q] = pack_f16x2(ex2(__uint_as_float(b1[2 * q])), ex2(__uint_as_float(b1[2 * q + 1])));
+            pk[16 + q] = pack_f16x2(exp2_mix<POLY, 3>(__uint_as_float(b1[2 * q]), 2 * q),
+                               exp2_mix<POLY, 3>(__uint_as_float(b1[2 * q + 1]), 2 * q + 1));
           tmem_st32(tl + p_col + 32, pk);
         }
         tmem_st_wait();
@@ -397,8 +409,9 @@ __global__ void __launch_bounds__(kFwdThreads, 1) tc_fwd_kernel(TcFwdArgs a) {
 // Forward for one or two columns (the CG product): S = XA XB^T on the tensor
 // core as above, but P.v on the FMA pipe with P kept in FP32 and v in FP32
 // (tile VF: MZ x 128 floats), so the tensor pipe only computes S and the
-// kernel is bound by the exps.  Warp roles as in tc_fwd_kernel.
-template <int MZ>
+// kernel is bound by the exps.  Warp roles as in tc_fwd_kernel; S is double
+// buffered in TMEM (512 columns), so the issuers run one tile ahead.
+template <int MZ, int POLY>
 __global__ void __launch_bounds__(kFwdThreads, 1) tc_fwd_fma_kernel(TcFwdArgs a) {
   using namespace ptx;
   extern __shared__ uint8_t smem_raw[];
@@ -412,9 +425,9 @@ __global__ void __launch_bounds__(kFwdThreads, 1) tc_fwd_fma_kernel(TcFwdArgs a)
   uint64_t* empty = full + S;        // released by the 2 issuers (S read XB) and 8 exp warps (read VF)
   uint64_t* a_full = empty + S;
   uint64_t* a_empty = a_full + 2;
-  uint64_t* s_full = a_empty + 2;
-  uint64_t* s_free = s_full + 2;
-  uint64_t* done = s_free + 2;
+  uint64_t* s_full = a_empty + 2;   // [g][buffer]
+  uint64_t* s_free = s_full + 4;    // [g][buffer]
+  uint64_t* done = s_free + 4;
   uint32_t* tslot = reinterpret_cast<uint32_t*>(done + 2);
   volatile int* abort = reinterpret_cast<volatile int*>(tslot + 1);
 
@@ -427,15 +440,17 @@ __global__ void __launch_bounds__(kFwdThreads, 1) tc_fwd_fma_kernel(TcFwdArgs a)
     for (int g = 0; g < 2; ++g) {
       mbar_init(&a_full[g], 1);
       mbar_init(&a_empty[g], 2);
-      mbar_init(&s_full[g], 1);
-      mbar_init(&s_free[g], 128);
       mbar_init(&done[g], 1);
+    }
+    for (int q = 0; q < 4; ++q) {
+      mbar_init(&s_full[q], 1);
+      mbar_init(&s_free[q], 128);
     }
     *abort = 0;
     fence_barrier_init();
   }
   if (warp == kMmaWarp) {
-    tmem_alloc(tslot, 256);
+    tmem_alloc(tslot, 512);
     tmem_relinquish();
   }
   tc_fence_before();
@@ -497,9 +512,12 @@ __global__ void __launch_bounds__(kFwdThreads, 1) tc_fwd_fma_kernel(TcFwdArgs a)
       const int nkx = a.KX / 16;
       const uint64_t dA = sdesc(smem_u32(sA + g * A_TILE), 128, sboX);
       const uint64_t dB = sdesc(smem_u32(sB), 128, sboX);
+      // S of I tile g, double-buffered: tile k goes to columns [256 (k & 1) + 128 g, +128),
+      // so the next tile's S is computed while the warpgroup still reads this one
       const uint32_t s_tmem = tbase + g * 128;
       int it = 0;
-      uint32_t stage = 0, sph = 0, sf_ph = 0;
+      uint32_t stage = 0, sph = 0;
+      uint32_t sf_ph[2] = {0u, 0u};
       long long k = 0;
       for (int t = blockIdx.x; t < a.n_items; t += gridDim.x) {
         const int4 item = a.items[t];
@@ -507,17 +525,18 @@ __global__ void __launch_bounds__(kFwdThreads, 1) tc_fwd_fma_kernel(TcFwdArgs a)
         const int ab = it & 1;
         const uint64_t dAg = sdesc_add(dA, 2 * ab * A_TILE);
         for (int j = 0; j < item.w; ++j, ++k) {
-          if (k > 0) {
-            if (!warp_wait(&s_free[g], sf_ph, abort, a.err, 13)) goto fma_mma_out;
-            sf_ph ^= 1;
+          const int buf = (int)(k & 1);
+          if (k >= 2) {
+            if (!warp_wait(&s_free[2 * g + buf], sf_ph[buf], abort, a.err, 13)) goto fma_mma_out;
+            sf_ph[buf] ^= 1;
           }
           if (j == 0 && !warp_wait(&a_full[ab], (it >> 1) & 1, abort, a.err, 14)) goto fma_mma_out;
           if (!warp_wait(&full[stage], sph, abort, a.err, 15)) goto fma_mma_out;
           tc_fence_after();
           const uint64_t db = sdesc_add(dB, stage * A_TILE);
           if (leader) {
-            issue_s(s_tmem, dAg, db, nkx, idS);
-            tc_commit(&s_full[g]);
+            issue_s(s_tmem + 256 * buf, dAg, db, nkx, idS);
+            tc_commit(&s_full[2 * g + buf]);
             tc_commit(&empty[stage]);
             if (j == item.w - 1) tc_commit(&a_empty[ab]);
           }
@@ -536,8 +555,8 @@ __global__ void __launch_bounds__(kFwdThreads, 1) tc_fwd_fma_kernel(TcFwdArgs a)
     const int g = warp >> 2, w = warp & 3;
     const int row = 32 * w + lane;
     const uint32_t tl = tbase + (static_cast<uint32_t>(32 * w) << 16);
-    const uint32_t s_col = g * 128;
-    uint32_t sph = 0, stage = 0, fph = 0;
+    uint32_t sph[2] = {0u, 0u}, stage = 0, fph = 0;
+    long long k = 0;
     for (int t = blockIdx.x; t < a.n_items; t += gridDim.x) {
       const int4 item = a.items[t];
       if (a.sys_active && !a.sys_active[item.x]) continue;
@@ -550,12 +569,14 @@ __global__ void __launch_bounds__(kFwdThreads, 1) tc_fwd_fma_kernel(TcFwdArgs a)
         acc64[q] = 0.0;
         acc[q][0] = acc[q][1] = acc[q][2] = acc[q][3] = 0.f;
       }
-      for (int j = 0; j < item.w; ++j) {
-        bool ok = mbar_wait(&s_full[g], sph, abort, a.err, 16);
+      for (int j = 0; j < item.w; ++j, ++k) {
+        const int buf = (int)(k & 1);
+        const uint32_t s_col = 256 * buf + g * 128;
+        bool ok = mbar_wait(&s_full[2 * g + buf], sph[buf], abort, a.err, 16);
         // the VF tile of this stage is visible once its copy has completed
         ok = ok && mbar_wait(&full[stage], fph, abort, a.err, 17);
         if (!__all_sync(0xffffffffu, ok)) goto fma_exp_out;
-        sph ^= 1;
+        sph[buf] ^= 1;
         tc_fence_after();
         const float4* vs = reinterpret_cast<const float4*>(sV + stage * V_TILE);
         {
@@ -567,8 +588,10 @@ __global__ void __launch_bounds__(kFwdThreads, 1) tc_fwd_fma_kernel(TcFwdArgs a)
           tmem_ld32(tl + s_col + 96, b1);
 #pragma unroll
           for (int u = 0; u < 8; ++u) {
-            const float p0 = ex2(__uint_as_float(a0[4 * u])), p1 = ex2(__uint_as_float(a0[4 * u + 1]));
-            const float p2 = ex2(__uint_as_float(a0[4 * u + 2])), p3 = ex2(__uint_as_float(a0[4 * u + 3]));
+            const float p0 = exp2_mix<POLY, 5>(__uint_as_float(a0[4 * u]), 4 * u);
+            const float p1 = exp2_mix<POLY, 5>(__uint_as_float(a0[4 * u + 1]), 4 * u + 1);
+            const float p2 = exp2_mix<POLY, 5>(__uint_as_float(a0[4 * u + 2]), 4 * u + 2);
+            const float p3 = exp2_mix<POLY, 5>(__uint_as_float(a0[4 * u + 3]), 4 * u + 3);
 #pragma unroll
             for (int q = 0; q < MZ; ++q) {
               const float4 v = vs[q * 32 + 0 + u];
@@ -580,8 +603,10 @@ __global__ void __launch_bounds__(kFwdThreads, 1) tc_fwd_fma_kernel(TcFwdArgs a)
           }
 #pragma unroll
           for (int u = 0; u < 8; ++u) {
-            const float p0 = ex2(__uint_as_float(a1[4 * u])), p1 = ex2(__uint_as_float(a1[4 * u + 1]));
-            const float p2 = ex2(__uint_as_float(a1[4 * u + 2])), p3 = ex2(__uint_as_float(a1[4 * u + 3]));
+            const float p0 = exp2_mix<POLY, 5>(__uint_as_float(a1[4 * u]), 4 * u);
+            const float p1 = exp2_mix<POLY, 5>(__uint_as_float(a1[4 * u + 1]), 4 * u + 1);
+            const float p2 = exp2_mix<POLY, 5>(__uint_as_float(a1[4 * u + 2]), 4 * u + 2);
+            const float p3 = exp2_mix<POLY, 5>(__uint_as_float(a1[4 * u + 3]), 4 * u + 3);
 #pragma unroll
             for (int q = 0; q < MZ; ++q) {
               const float4 v = vs[q * 32 + 8 + u];
@@ -593,11 +618,13 @@ __global__ void __launch_bounds__(kFwdThreads, 1) tc_fwd_fma_kernel(TcFwdArgs a)
           }
           tmem_ld_wait_regs(b0, b1);
           tc_fence_before();
-          mbar_arrive(&s_free[g]);
+          mbar_arrive(&s_free[2 * g + buf]);
 #pragma unroll
           for (int u = 0; u < 8; ++u) {
-            const float p0 = ex2(__uint_as_float(b0[4 * u])), p1 = ex2(__uint_as_float(b0[4 * u + 1]));
-            const float p2 = ex2(__uint_as_float(b0[4 * u + 2])), p3 = ex2(__uint_as_float(b0[4 * u + 3]));
+            const float p0 = exp2_mix<POLY, 5>(__uint_as_float(b0[4 * u]), 4 * u);
+            const float p1 = exp2_mix<POLY, 5>(__uint_as_float(b0[4 * u + 1]), 4 * u + 1);
+            const float p2 = exp2_mix<POLY, 5>(__uint_as_float(b0[4 * u + 2]), 4 * u + 2);
+            const float p3 = exp2_mix<POLY, 5>(__uint_as_float(b0[4 * u + 3]), 4 * u + 3);
 #pragma unroll
             for (int q = 0; q < MZ; ++q) {
               const float4 v = vs[q * 32 + 16 + u];
@@ -609,8 +636,10 @@ __global__ void __launch_bounds__(kFwdThreads, 1) tc_fwd_fma_kernel(TcFwdArgs a)
           }
 #pragma unroll
           for (int u = 0; u < 8; ++u) {
-            const float p0 = ex2(__uint_as_float(b1[4 * u])), p1 = ex2(__uint_as_float(b1[4 * u + 1]));
-            const float p2 = ex2(__uint_as_float(b1[4 * u + 2])), p3 = ex2(__uint_as_float(b1[4 * u + 3]));
+            const float p0 = exp2_mix<POLY, 5>(__uint_as_float(b1[4 * u]), 4 * u);
+            const float p1 = exp2_mix<POLY, 5>(__uint_as_float(b1[4 * u + 1]), 4 * u + 1);
+            const float p2 = exp2_mix<POLY, 5>(__uint_as_float(b1[4 * u + 2]), 4 * u + 2);
+            const float p3 = exp2_mix<POLY, 5>(__uint_as_float(b1[4 * u + 3]), 4 * u + 3);
 #pragma unroll
             for (int q = 0; q < MZ; ++q) {
               const float4 v = vs[q * 32 + 24 + u];
@@ -642,7 +671,7 @@ __global__ void __launch_bounds__(kFwdThreads, 1) tc_fwd_fma_kernel(TcFwdArgs a)
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  if (warp == kMmaWarp) tmem_dealloc(tbase, 256);
+  if (warp == kMmaWarp) tmem_dealloc(tbase, 512);
 }
 
 // V tiles as FP32 columns for the FMA-pipe product: VF[c][t] = MZ x 128 floats.
@@ -663,10 +692,34 @@ __global__ void tc_prep_vf_kernel(DevLayout L, TcTables T, int chains, int64_t n
 
 // ------------------------------------------------------------------ prep kernels
 
-// One thread per padded row: the A-side and B-side BF16 operand rows.
-__global__ void tc_prep_x_kernel(DevLayout L, TcTables T, int chains, int d, int ard, int n_theta, int KX,
-                                 int nsplit, int T_total, const float* x, const double* theta, uint8_t* XA,
-                                 uint8_t* XB) {
+// Per (instance, dimension) min and max of x as order-preserving keys; one
+// block per 128-row item of the layout, one atomic per warp and dimension.
+__global__ void tc_center_kernel(DevLayout L, int n_inst, int d, const float* x, uint32_t* keys) {
+  const int item = blockIdx.x;
+  const int b = L.item_inst[item];
+  const int64_t i = L.item_row0[item] + threadIdx.x;
+  const bool valid = i < L.offsets[b + 1];
+  const int lane = threadIdx.x & 31;
+  for (int k = 0; k < d; ++k) {
+    uint32_t kmin = 0xffffffffu, kmax = 0u;
+    if (valid) kmin = kmax = fkey(x[i * d + k]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      kmin = min(kmin, __shfl_xor_sync(0xffffffffu, kmin, o));
+      kmax = max(kmax, __shfl_xor_sync(0xffffffffu, kmax, o));
+    }
+    if (lane == 0 && kmax != 0u) {
+      atomicMin(&keys[(size_t)b * d + k], kmin);
+      atomicMax(&keys[((size_t)n_inst + b) * d + k], kmax);
+    }
+  }
+}
+
+// One thread per padded row: the A-side and B-side operand rows (16-bit
+// elements, BF16 or F16 by split mode) of the centred, scaled points.
+__global__ void tc_prep_x_kernel(DevLayout L, TcTables T, int n_inst, int chains, int d, int ard, int n_theta,
+                                 int KX, int nsplit, int T_total, const float* x, const double* theta,
+                                 const uint32_t* ckeys, uint8_t* XA, uint8_t* XB, int* err) {
   const int t = blockIdx.x, c = blockIdx.y, r = threadIdx.x;
   const int b = T.tile_inst[t];
   const int s = b * chains + c;
@@ -674,11 +727,19 @@ __global__ void tc_prep_x_kernel(DevLayout L, TcTables T, int chains, int d, int
   const int64_t rl = (int64_t)(t - T.inst_tile0[b]) * 128 + r;
   const bool valid = rl < nb;
   const size_t base = ((size_t)c * T_total + t) * (size_t)KX * 256;
-  __nv_bfloat16* A = reinterpret_cast<__nv_bfloat16*>(XA + base);
-  __nv_bfloat16* B = reinterpret_cast<__nv_bfloat16*>(XB + base);
-  auto putA = [&](int kk, __nv_bfloat16 v) { A[x_off(r, kk, KX) / 2] = v; };
-  auto putB = [&](int kk, __nv_bfloat16 v) { B[x_off(r, kk, KX) / 2] = v; };
-  const __nv_bfloat16 zero = __float2bfloat16_rn(0.f), one = __float2bfloat16_rn(1.f);
+  uint16_t* A = reinterpret_cast<uint16_t*>(XA + base);
+  uint16_t* B = reinterpret_cast<uint16_t*>(XB + base);
+  auto putA = [&](int kk, uint16_t v) { A[x_off(r, kk, KX) / 2] = v; };
+  auto putB = [&](int kk, uint16_t v) { B[x_off(r, kk, KX) / 2] = v; };
+  const bool f16 = nsplit == kSplitF16;
+  // 16-bit encodings of the operand type and their values back in FP32
+  auto enc = [&](float v) -> uint16_t {
+    return f16 ? __half_as_ushort(__float2half_rn(v)) : __bfloat16_as_ushort(__float2bfloat16_rn(v));
+  };
+  auto dec = [&](uint16_t u) -> float {
+    return f16 ? __half2float(__ushort_as_half(u)) : __bfloat162float(__ushort_as_bfloat16(u));
+  };
+  const uint16_t zero = 0, one = enc(1.f);
   if (!valid) {
     for (int kk = 0; kk < KX; ++kk) {
       putA(kk, zero);
@@ -689,27 +750,30 @@ __global__ void tc_prep_x_kernel(DevLayout L, TcTables T, int chains, int d, int
   const int64_t i = L.offsets[b] + rl;
   const double* th = theta + (int64_t)s * n_theta;
   double nrm = 0.0;
+  bool range_ok = true;
   for (int k = 0; k < d; ++k) {
-    // xh = x sqrt(log2 e) / l, so that -|xh_i - xh_j|^2 / 2 = -log2(e) r^2 / 2
+    // xh = (x - centre) sqrt(log2 e) / l, so that -|xh_i - xh_j|^2 / 2 = -log2(e) r^2 / 2
     const float sc = (float)(sqrt(2.0 * kHalfLog2e) * exp(-th[1 + (ard ? k : 0)]));
-    const float xh = x[i * d + k] * sc;
-    const __nv_bfloat16 hi = __float2bfloat16_rn(xh);
-    const float r1 = xh - __bfloat162float(hi);
-    const __nv_bfloat16 mid = __float2bfloat16_rn(r1);
-    const double hd = __bfloat162float(hi), md = __bfloat162float(mid);
-    if (nsplit == 2) {
-      // A: [hi, hi, lo]  B: [hi, lo, hi]
+    const float xh = (x[i * d + k] - center_of(ckeys, n_inst, d, b, k)) * sc;
+    if (f16 && !(fabsf(xh) < 240.f)) range_ok = false;
+    const uint16_t hi = enc(xh);
+    const float r1 = xh - dec(hi);
+    const uint16_t mid = enc(r1);
+    const double hd = dec(hi), md = dec(mid);
+    if (nsplit != kSplitBf3) {
+      // per dimension a triple, A: [hi, lo, hi]  B: [hi, hi, lo], so that
+      // column 3k of an A row holds hi and 3k + 1 holds lo of dimension k
       nrm += hd * hd + 2.0 * hd * md;
-      putA(k, hi);
-      putA(d + k, hi);
-      putA(2 * d + k, mid);
-      putB(k, hi);
-      putB(d + k, mid);
-      putB(2 * d + k, hi);
+      putA(3 * k, hi);
+      putA(3 * k + 1, mid);
+      putA(3 * k + 2, hi);
+      putB(3 * k, hi);
+      putB(3 * k + 1, hi);
+      putB(3 * k + 2, mid);
     } else {
       // A: [h, h, m, h, l, m]  B: [h, m, h, l, h, m]
-      const __nv_bfloat16 lo = __float2bfloat16_rn(r1 - __bfloat162float(mid));
-      const double ld = __bfloat162float(lo);
+      const uint16_t lo = enc(r1 - dec(mid));
+      const double ld = dec(lo);
       nrm += hd * hd + 2.0 * hd * md + 2.0 * hd * ld + md * md;
       putA(k, hi);
       putA(d + k, hi);
@@ -726,11 +790,13 @@ __global__ void tc_prep_x_kernel(DevLayout L, TcTables T, int chains, int d, int
     }
   }
   const double bias = -0.5 * nrm;
-  const __nv_bfloat16 bh = __float2bfloat16_rn((float)bias);
-  const double r1 = bias - (double)__bfloat162float(bh);
-  const __nv_bfloat16 bm = __float2bfloat16_rn((float)r1);
-  const __nv_bfloat16 bl = __float2bfloat16_rn((float)(r1 - (double)__bfloat162float(bm)));
-  const int o = (nsplit == 2 ? 3 : 6) * d;
+  if (f16 && !(-bias < (double)kF16BiasMax)) range_ok = false;
+  if (!range_ok && err) atomicCAS(err, 0, 101);
+  const uint16_t bh = enc((float)bias);
+  const double r1 = bias - (double)dec(bh);
+  const uint16_t bm = enc((float)r1);
+  const uint16_t bl = enc((float)(r1 - (double)dec(bm)));
+  const int o = (nsplit == kSplitBf3 ? 6 : 3) * d;
   putA(o + 0, one);
   putA(o + 1, one);
   putA(o + 2, one);
@@ -841,9 +907,29 @@ kmv_status tc_fail(kmv_handle h, kmv_status s, const char* msg) {
   return s;
 }
 
-kmv_status tc_build_plan(kmv_handle h, TcState* S, cudaStream_t st) {
+int size_class(const Layout& L) {
+  int64_t mx = 1;
+  for (int b = 0; b < L.n_inst; ++b) mx = std::max<int64_t>(mx, L.offsets[b + 1] - L.offsets[b]);
+  int k = 0;
+  while ((int64_t(1) << (k + 1)) <= mx) ++k;
+  return k;
+}
+
+TcTiles tc_tiles_for(kmv_handle h, int kind, int d, int m) {
+  TcState* S = tc_state(h);
+  const int nl = size_class(h->layout);
+  for (const TcTuned& e : S->tuned)
+    if (e.kind == kind && e.d == d && e.m == m && e.nlog2 == nl) return e.t;
+  return S->tiles[kind];
+}
+
+kmv_status tc_build_plan(kmv_handle h, TcState* S, int ipsm_fwd, int ipsm_adj, cudaStream_t st) {
   const Layout& L = h->layout;
-  if (S->chains == L.chains && S->offsets == L.offsets && S->tables) return KMV_OK;
+  if (ipsm_fwd <= 0) ipsm_fwd = S->plan_ipsm_fwd > 0 ? S->plan_ipsm_fwd : S->tiles[kTilesForward].items_per_sm;
+  if (ipsm_adj <= 0) ipsm_adj = S->plan_ipsm_adj > 0 ? S->plan_ipsm_adj : S->tiles[kTilesAdjoint].items_per_sm;
+  if (S->chains == L.chains && S->offsets == L.offsets && S->tables && S->plan_ipsm_fwd == ipsm_fwd &&
+      S->plan_ipsm_adj == ipsm_adj)
+    return KMV_OK;
   if (h->capturing)
     return tc_fail(h, KMV_EINVAL, "new work plan during stream capture: make the same call once before capturing");
   if (S->num_sms == 0) {
@@ -865,7 +951,7 @@ kmv_status tc_build_plan(kmv_handle h, TcState* S, cudaStream_t st) {
   }
   S->inst_tile0[n_inst] = (int32_t)S->tile_inst.size();
   S->T_total = (int)S->tile_inst.size();
-  const int64_t target = (int64_t)S->num_sms * 6;
+  const int64_t target = (int64_t)S->num_sms * ipsm_fwd;
   const int64_t nk_all = units > 0 ? std::max<int64_t>(1, (target + units - 1) / units) : 1;
   S->items.clear();
   S->sys_item0.assign((size_t)n_inst * chains, 0);
@@ -900,7 +986,8 @@ kmv_status tc_build_plan(kmv_handle h, TcState* S, cudaStream_t st) {
       const int64_t T = (L.offsets[b + 1] - L.offsets[b] + 127) / 128;
       pairs += (int64_t)chains * T * (T + 1) / 2;
     }
-    const int64_t C = std::max<int64_t>(8, (pairs + target - 1) / std::max<int64_t>(1, target));
+    const int64_t target_adj = (int64_t)S->num_sms * ipsm_adj;
+    const int64_t C = std::max<int64_t>(8, (pairs + target_adj - 1) / std::max<int64_t>(1, target_adj));
     S->sym_items.clear();
     S->sym_pref.assign((size_t)n_inst * chains + 1, 0);
     std::vector<int4> row;
@@ -969,6 +1056,9 @@ kmv_status tc_build_plan(kmv_handle h, TcState* S, cudaStream_t st) {
   if (cudaStreamSynchronize(st) != cudaSuccess) return tc_fail(h, KMV_ECUDA, "table upload failed");
   S->offsets = L.offsets;
   S->chains = L.chains;
+  S->prep_valid = false;
+  S->plan_ipsm_fwd = ipsm_fwd;
+  S->plan_ipsm_adj = ipsm_adj;
   return KMV_OK;
 }
 
@@ -983,6 +1073,7 @@ kmv_status tc_ensure_buf(kmv_handle h, TcState* S, size_t bytes) {
     S->buf = nullptr;
     S->buf_bytes = 0;
   }
+  S->prep_valid = false;
   const size_t want = bytes + bytes / 8 + (1 << 20);
   if (cudaMalloc(&S->buf, want) != cudaSuccess) {
     cudaGetLastError();
@@ -992,10 +1083,21 @@ kmv_status tc_ensure_buf(kmv_handle h, TcState* S, size_t bytes) {
   return KMV_OK;
 }
 
-void tc_launch_prep_x(kmv_handle h, TcState* S, const KmvArgs& a, int KX, int nsplit, uint8_t* XA, uint8_t* XB,
-                      cudaStream_t st) {
+size_t tc_center_bytes(const Layout& L) { return sizeof(uint32_t) * 2 * (size_t)L.n_inst * std::max(1, L.d); }
+
+void tc_launch_center(kmv_handle h, const KmvArgs& a, uint32_t* keys, cudaStream_t st) {
+  const Layout& L = h->layout;
+  const size_t half = sizeof(uint32_t) * (size_t)L.n_inst * a.d;
+  cudaMemsetAsync(keys, 0xff, half, st);
+  cudaMemsetAsync(reinterpret_cast<uint8_t*>(keys) + half, 0, half, st);
+  if (L.n_items > 0) tc_center_kernel<<<L.n_items, kTile, 0, st>>>(h->dev, L.n_inst, a.d, a.x, keys);
+}
+
+void tc_launch_prep_x(kmv_handle h, TcState* S, const KmvArgs& a, int KX, int nsplit, const uint32_t* ckeys,
+                      uint8_t* XA, uint8_t* XB, int* err, cudaStream_t st) {
   tc_prep_x_kernel<<<dim3(S->T_total, h->layout.chains), 128, 0, st>>>(
-      h->dev, S->dev, h->layout.chains, a.d, a.ard, a.n_theta, KX, nsplit, S->T_total, a.x, a.theta, XA, XB);
+      h->dev, S->dev, h->layout.n_inst, h->layout.chains, a.d, a.ard, a.n_theta, KX, nsplit, S->T_total, a.x,
+      a.theta, ckeys, XA, XB, err);
 }
 
 void tc_launch_epilogue(kmv_handle h, TcState* S, const KmvArgs& a, int c0, int mz, const double* part,
@@ -1004,19 +1106,48 @@ void tc_launch_epilogue(kmv_handle h, TcState* S, const KmvArgs& a, int c0, int 
                                                                                       part, colmax, err);
 }
 
+using FwdKernel = void (*)(TcFwdArgs);
+
+// The instantiation for RM (16: register fold accumulators, 0: global) or MZ
+// (FMA path) and the exp split; exp splits other than 0, 4 and 8 take the
+// nearest built one.
+FwdKernel fwd_kernel(bool fma, int cols, int split) {
+  const int sp = split <= 0 ? 0 : (split <= 5 ? 4 : 8);
+  if (fma) {
+    if (cols == 1) return sp == 0 ? tc_fwd_fma_kernel<1, 0> : sp == 4 ? tc_fwd_fma_kernel<1, 4> : tc_fwd_fma_kernel<1, 8>;
+    return sp == 0 ? tc_fwd_fma_kernel<2, 0> : sp == 4 ? tc_fwd_fma_kernel<2, 4> : tc_fwd_fma_kernel<2, 8>;
+  }
+  if (cols == 16) return sp == 0 ? tc_fwd_kernel<16, 0> : sp == 4 ? tc_fwd_kernel<16, 4> : tc_fwd_kernel<16, 8>;
+  return sp == 0 ? tc_fwd_kernel<0, 0> : sp == 4 ? tc_fwd_kernel<0, 4> : tc_fwd_kernel<0, 8>;
+}
+
+cudaError_t fwd_kernels_set_smem() {
+  for (bool fma : {false, true})
+    for (int cols : {0, 1, 2, 16})
+      for (int sp : {0, 4, 8}) {
+        if (fma != (cols == 1 || cols == 2)) continue;
+        const cudaError_t e =
+            cudaFuncSetAttribute(fwd_kernel(fma, cols, sp), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem);
+        if (e != cudaSuccess) return e;
+      }
+  return cudaSuccess;
+}
+
 kmv_status tc_forward(kmv_handle h, const KmvArgs& a, cudaStream_t st) {
   const Layout& L = h->layout;
   // one or two columns (the CG / energy products) take the FMA-pipe P.v path,
   // where the tensor pipe has room for the three-way split of the exponent
-  const bool fma_path = a.m <= 2 && x_width(a.d, 3) <= kMaxKX;
-  const int nsplit = fma_path ? 3 : 2;
+  const bool fma_path = a.m <= 2 && x_width(a.d, kSplitBf3) <= kMaxKX;
+  const int nsplit = fma_path ? kSplitBf3 : kSplitBf2;
   const int KX = x_width(a.d, nsplit);
   if (KX > kMaxKX) return tc_fail(h, KMV_EUNSUPPORTED, "KMV_BF16_HILO supports d <= 35");
   TcState* S = tc_state(h);
-  kmv_status stt = tc_build_plan(h, S, st);
+  const TcTiles tl = tc_tiles_for(h, fma_path ? kTilesForwardFma : kTilesForward, a.d, a.m);
+  kmv_status stt = tc_build_plan(h, S, tl.items_per_sm, 0, st);
   if (stt != KMV_OK) return stt;
   if (S->n_items == 0) return KMV_OK;
   const int n_sys = L.n_inst * L.chains;
+  const size_t max_stages = tl.stages > 0 ? (size_t)std::max(2, std::min(tl.stages, 8)) : 8;
   const size_t A_TILE = (size_t)KX * 256;
   auto al = [](size_t v) { return (v + 255) & ~size_t(255); };
   // column chunk: as wide as shared memory allows (at least two pipeline stages)
@@ -1024,7 +1155,7 @@ kmv_status tc_forward(kmv_handle h, const KmvArgs& a, cudaStream_t st) {
   int mz_max = std::min(a.m, kMaxMP);
   auto stages_for = [&](int mz) {
     const size_t vt = (size_t)std::max(16, (mz + 15) / 16 * 16) * 256;
-    return (int)std::min<size_t>(8, (kMaxSmem - fixed - 20 * 8) / (A_TILE + vt + 16));
+    return (int)std::min<size_t>(max_stages, (kMaxSmem - fixed - 20 * 8) / (A_TILE + vt + 16));
   };
   while (stages_for(mz_max) < 2 && mz_max > 16) mz_max = std::max(16, mz_max / 2);
   if (stages_for(mz_max) < 2) return tc_fail(h, KMV_EUNSUPPORTED, "tensor-core tiles do not fit in shared memory");
@@ -1033,7 +1164,8 @@ kmv_status tc_forward(kmv_handle h, const KmvArgs& a, cudaStream_t st) {
   const size_t vbytes = al((size_t)L.chains * S->T_total * MPmax * 256);
   const size_t mbytes = al(sizeof(uint32_t) * (size_t)n_sys * mz_max);
   const size_t pbytes = al(sizeof(double) * (size_t)S->n_items * 256 * mz_max);
-  const size_t total = 2 * xbytes + vbytes + mbytes + pbytes + 256;
+  const size_t cbytes = al(tc_center_bytes(L));
+  const size_t total = 2 * xbytes + vbytes + mbytes + pbytes + cbytes + 256;
   stt = tc_ensure_buf(h, S, total);
   if (stt != KMV_OK) return stt;
   uint8_t* base = static_cast<uint8_t*>(S->buf);
@@ -1042,31 +1174,32 @@ kmv_status tc_forward(kmv_handle h, const KmvArgs& a, cudaStream_t st) {
   uint8_t* VT = XB + xbytes;
   uint32_t* vmax = reinterpret_cast<uint32_t*>(VT + vbytes);
   double* part = reinterpret_cast<double*>(reinterpret_cast<uint8_t*>(vmax) + mbytes);
-  int* err = reinterpret_cast<int*>(reinterpret_cast<uint8_t*>(part) + pbytes);
+  uint32_t* ckeys = reinterpret_cast<uint32_t*>(reinterpret_cast<uint8_t*>(part) + pbytes);
+  int* err = reinterpret_cast<int*>(reinterpret_cast<uint8_t*>(ckeys) + cbytes);
   if (!S->attr_set) {
-    if (cudaFuncSetAttribute(tc_fwd_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem) !=
-            cudaSuccess ||
-        cudaFuncSetAttribute(tc_fwd_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem) !=
-            cudaSuccess)
-      return tc_fail(h, KMV_ECUDA, "cudaFuncSetAttribute failed");
+    if (fwd_kernels_set_smem() != cudaSuccess) return tc_fail(h, KMV_ECUDA, "cudaFuncSetAttribute failed");
     S->attr_set = true;
   }
   if (cudaMemsetAsync(err, 0, sizeof(int), st) != cudaSuccess) return tc_fail(h, KMV_ECUDA, "memset failed");
-  tc_launch_prep_x(h, S, a, KX, nsplit, XA, XB, st);
+  // the operand tiles depend on theta and x only: a solve's later products
+  // reuse those of its first one
+  const bool reuse = a.reuse_prep && S->prep_valid && S->prep_theta == a.theta && S->prep_x == a.x &&
+                     S->prep_nsplit == nsplit && S->prep_d == a.d;
+  if (!reuse) {
+    tc_launch_center(h, a, ckeys, st);
+    tc_launch_prep_x(h, S, a, KX, nsplit, ckeys, XA, XB, nullptr, st);
+    S->prep_valid = true;
+    S->prep_theta = a.theta;
+    S->prep_x = a.x;
+    S->prep_nsplit = nsplit;
+    S->prep_d = a.d;
+  }
   if (fma_path) {
     // one or two columns: P.v on the FMA pipe (FP32 P and v, no scaling)
     const int mz = a.m;
     const size_t V_TILE = (size_t)mz * 512;
-    const int stages = (int)std::min<size_t>(8, (kMaxSmem - fixed) / (A_TILE + V_TILE + 16));
+    const int stages = (int)std::max<size_t>(2, std::min<size_t>(max_stages, (kMaxSmem - fixed) / (A_TILE + V_TILE + 16)));
     const size_t smem = std::max(kMinSmem, fixed + stages * (A_TILE + V_TILE) + (2 * stages + 16) * 8);
-    if (!S->fma_attr_set) {
-      if (cudaFuncSetAttribute(tc_fwd_fma_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem) !=
-              cudaSuccess ||
-          cudaFuncSetAttribute(tc_fwd_fma_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem) !=
-              cudaSuccess)
-        return tc_fail(h, KMV_ECUDA, "cudaFuncSetAttribute failed");
-      S->fma_attr_set = true;
-    }
     if (cudaMemsetAsync(vmax, 0, sizeof(uint32_t) * (size_t)n_sys * mz, st) != cudaSuccess)
       return tc_fail(h, KMV_ECUDA, "memset failed");
     tc_prep_vf_kernel<<<dim3(S->T_total, L.chains), 128, 0, st>>>(h->dev, S->dev, L.chains, L.n_total, a.V, a.m,
@@ -1090,10 +1223,7 @@ kmv_status tc_forward(kmv_handle h, const KmvArgs& a, cudaStream_t st) {
     const int grid = std::min(S->n_items, S->num_sms);
     {
       ProfScope prof(h, KMV_KERNEL_FORWARD, st);
-      if (mz == 1)
-        tc_fwd_fma_kernel<1><<<grid, kFwdThreads, smem, st>>>(fa);
-      else
-        tc_fwd_fma_kernel<2><<<grid, kFwdThreads, smem, st>>>(fa);
+      fwd_kernel(true, mz, tl.exp_split)<<<grid, kFwdThreads, smem, st>>>(fa);
     }
     // vmax is zero: the epilogue's column scale is 1
     tc_launch_epilogue(h, S, a, 0, mz, part, vmax, err, st);
@@ -1131,10 +1261,7 @@ kmv_status tc_forward(kmv_handle h, const KmvArgs& a, cudaStream_t st) {
     const int grid = std::min(S->n_items, S->num_sms);
     {
       ProfScope prof(h, KMV_KERNEL_FORWARD, st);
-      if (MP <= 16)
-        tc_fwd_kernel<16><<<grid, kFwdThreads, smem, st>>>(fa);
-      else
-        tc_fwd_kernel<0><<<grid, kFwdThreads, smem, st>>>(fa);
+      fwd_kernel(false, MP <= 16 ? 16 : 0, tl.exp_split)<<<grid, kFwdThreads, smem, st>>>(fa);
     }
     tc_launch_epilogue(h, S, a, c0, mz, part, vmax, err, st);
     const cudaError_t e = cudaGetLastError();
@@ -1143,7 +1270,7 @@ kmv_status tc_forward(kmv_handle h, const KmvArgs& a, cudaStream_t st) {
   return KMV_OK;
 }
 
-bool x_width_fma_ok(int d) { return x_width(d, 3) <= kMaxKX; }
+bool x_width_fma_ok(int d) { return x_width(d, kSplitBf3) <= kMaxKX; }
 
 void tc_release(kmv_handle h) {
   if (!h->tc) return;

@@ -6,24 +6,29 @@
 // tile (J, I) equals the sum over tile (I, J): only the upper triangle of
 // tiles (J >= I) is evaluated, off-diagonal tiles weighted twice.  For a J
 // half tile (64 columns) of an I tile the MMA issuers write into TMEM
-//   S = XA_I XB_J^T           the base-2 exponent (BF16 hi/lo, as in the forward)
+//   S = XA_I XB_J^T           the base-2 exponent from F16 hi/lo operands of the
+//                             centred points (|dS| ~ 2^-24 |xh|^2)
 //   W = GI_I VJ_J^T           = G_i . V_j + V_i . G_j with GI rows
 //                             [gh gh gl vh vh vl] and VJ rows [vh vl vh gh gl gh]
-//                             (BF16 hi/lo, G scaled by a power of two)
-// an exp warpgroup forms Q = W 2^S (halved on the diagonal tile) as F16 in its
-// own TMEM columns, and the feature-sum issuer accumulates, per row i,
-//   ACC += Q BG               BG columns for dimension k: 4k..4k+3 = [xh, xl, sh, sl]
-//                             (F16 hi/lo of xt_jk and of xt_jk^2), column 4 d = 1;
-//                             giving R_ik = sum_j Q_ij xt_jk, T_ik = sum_j Q_ij xt_jk^2
-//                             and q_i = sum_j Q_ij
+//                             (F16 hi/lo, G and V each scaled by a power of two)
+// an exp warpgroup forms Q = W 2^S in FP32 (halved on the diagonal tile, and
+// zero for i = j, whose (xt_i - xt_i)^2 is 0), splits it exactly into
+// Q = Qh + Ql with Qh holding 11 significant bits (Veltkamp's splitting), and
+// stores both as F16; the feature-sum issuer accumulates, per row i,
+//   ACC += Qh BG + Ql BG      BG: F16 hi/lo of xt_jk and of xt_jk^2 and a ones column
+//                             (the hi and lo parts either in separate accumulator
+//                             columns, or, for large d, in the same columns by
+//                             splitting the K dimension), giving
+//                             R_ik = sum_j Q_ij xt_jk, T_ik = sum_j Q_ij xt_jk^2, q_i = sum_j Q_ij
 // Every kFoldH half tiles warpgroup 0 folds, per row,
 //   sum_j Q_ij (xt_ik - xt_jk)^2 = xt_ik^2 q_i - 2 xt_ik R_ik + T_ik
-// into FP64 sums.  Because q, R and T are formed from the same rounded Q, the
-// rounding of Q cancels in this combination exactly as in the exact sum; the
-// hi/lo splits keep xt and xt^2 to ~22 bits.  The scale of G is removed at the
-// end; per-warp FP64 partials are reduced per system in a fixed order.  When
-// the depth-6m operands do not fit in TMEM (large m), the same kernel runs on
-// all tiles with the plain W (GI [gh gh gl], VJ [vh vl vh]) and I-pair items.
+// into FP64 sums.  Because q, R and T are formed from the same Q, its rounding
+// cancels in this combination exactly as in the exact sum; leaving out the
+// diagonal keeps its large terms out of that cancellation, and its share of
+// the alpha gradient, sum_i G_i . V_i, is added exactly in FP64.  The scales of
+// G and V are removed at the end; per-warp FP64 partials are reduced per system
+// in a fixed order.  When the depth-6m operands do not fit in TMEM (large m),
+// G and V enter in blocks of columns, one launch per block.
 // dL/dV = A G is the forward product with G in place of V (kmv_tc.cu).
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
@@ -40,8 +45,17 @@
 namespace kmv {
 namespace {
 
-constexpr int kFoldH = 64;   // half tiles (64 columns) per FP32 accumulation (4096 columns)
+// Half tiles (64 columns) per FP32 accumulation of q, R, T in TMEM before the
+// FP64 fold: the tensor core's FP32 accumulation loses low bits at every K
+// step, so the sums are kept short (4 halves = 256 columns).  The two
+// warpgroups take turns at folding.
+#ifndef KMV_BWD_FOLD_HALVES
+#define KMV_BWD_FOLD_HALVES 4
+#endif
+constexpr int kFoldH = KMV_BWD_FOLD_HALVES;
+static_assert(kFoldH >= 2 && kFoldH % 2 == 0, "folds end on a half of warpgroup 1");
 constexpr int kGW = 34;      // doubles per (item, warp) gradient partial: [q, contrib_0..d-1]
+constexpr int kFoldWarps = 8;   // warps holding gradient partials (both warpgroups fold)
 
 struct TcBwdArgs {
   const int4* items;
@@ -49,9 +63,17 @@ struct TcBwdArgs {
   int chains;
   int T_total;
   int KX, KG, NB, S;
+  // Feature-sum layout.  ksplit = 0: BG has NB = NACC features, per dimension
+  // k the columns 4k..4k+3 = [xh, xl, sh, sl], and the ones column qcol = 4d;
+  // the accumulator has the same NACC columns.  ksplit = 1: BG has 2 NACC
+  // features, a hi block [xh_k at k, sh_k at toff + k, 1 at qcol = 2 toff] and a
+  // lo block of the same layout at feature NACC; the accumulator has NACC columns.
+  int ksplit, NACC, toff;
   int qcol;   // accumulator column of q_i (the ones column of BG)
   int chunk;  // index of this launch's block of G, V columns (partials are per block)
+  int n_inst;
   int d, n_theta, ard;
+  const uint32_t* ckeys;   // per-instance centre keys (tc_launch_center)
   DevLayout L;
   TcTables T;
   const float* x;
@@ -67,20 +89,25 @@ struct TcBwdArgs {
   int* err;
 };
 
-// Power-of-two factor putting max_i |G_i| max_j |V_j| (a bound on |W|) just below 2^14.
-__device__ __forceinline__ double w_scale(uint32_t gbits, uint32_t vbits) {
-  const double p = (double)__uint_as_float(gbits) * (double)__uint_as_float(vbits);
-  if (!(p > 0.0) || !isfinite(p)) return 1.0;
+// Power-of-two factor putting a largest row norm just below 2^7, so that the
+// F16 operands of G and V hold every element and |W^s| <= 2 2^7 2^7 = 2^15.
+__device__ __forceinline__ double row_scale(uint32_t bits) {
+  const double mx = (double)__uint_as_float(bits);
+  if (!(mx > 0.0) || !isfinite(mx)) return 1.0;
   int e;
-  frexp(p, &e);
-  return ldexp(1.0, 14 - e);
+  frexp(mx, &e);
+  return ldexp(1.0, 7 - e);
 }
 
-__device__ __forceinline__ float xt_of(float xv, float sc) {
-  const float xh = xv * sc;
-  const __half hi = __float2half_rn(xh);
-  const __half lo = __float2half_rn(xh - __half2float(hi));
-  return __half2float(hi) + __half2float(lo);
+// Exact split q = hi + lo with hi holding 11 significant bits (Veltkamp's
+// splitting with the factor 2^13 + 1), so that hi is an F16 value and lo
+// carries the next 11 bits when stored as F16.  The rounded intrinsics keep
+// the compiler from contracting the steps into FMAs, which would break the
+// split.
+__device__ __forceinline__ void split_q(float q, float& hi, float& lo) {
+  const float t = __fmul_rn(q, 8193.f);
+  hi = __fsub_rn(t, __fsub_rn(t, q));
+  lo = __fsub_rn(q, hi);
 }
 
 // K = 64 from TMEM (four K = 16 steps of 8 columns each).
@@ -101,16 +128,18 @@ constexpr int kBwdIssue1Warp = 10;
 // shared-memory tile loaded once per item.  Warps: 0-7 the warpgroups, 8 issues
 // S, W for buffer 0 (and owns TMEM), 9 is the producer, 10 issues S, W for
 // buffer 1, 11 issues the feature sums.  TMEM (512 columns):
-//   S_b [128 b, 128 b + 64), W_b [128 b + 64, 128 b + 128), Q_b [256 + 32 b, +32),
-//   XA [320, 320 + KX/2) unless XS, GI after it, ACC [512 - NB, 512);
+//   S_b [128 b, 128 b + 64), W_b [128 b + 64, 128 b + 128), Qh_b [256 + 32 b, +32),
+//   Ql_b [320 + 32 b, +32), XA [384, 384 + KX/2) unless XS, GI after it,
+//   ACC [512 - NACC, 512);
 // the host picks XS and the number of columns of G, V per launch so that these
 // fit.  Warpgroup 0 folds the accumulator into FP64 per-warp sums.
 constexpr int kTsThreads = 384;
 constexpr int kAccWarp = 11;
-constexpr int kTsCols = 192;   // columns for XA, GI and ACC
-constexpr int kMaxDT = 32;     // 4 d features + q in at most 144 accumulator columns
+constexpr int kTsCols = 128;   // columns for XA, GI and ACC
+constexpr int kMaxDT = 32;     // d <= 32
+constexpr int kXaRegs = 48;    // 32-bit words of an XA row holding the 3 d split values (d <= 32)
 constexpr int kTsBarBytes = 512;                       // mbarriers, TMEM slot, abort flag
-constexpr int kTsFoldBytes = 4 * kGW * 8;              // per-warp FP64 fold sums of warpgroup 0
+constexpr int kTsFoldBytes = kFoldWarps * kGW * 8;     // per-warp FP64 fold sums of both warpgroups
 
 template <bool XS>
 __global__ void __launch_bounds__(kTsThreads, 1) tc_bwd_ts_kernel(TcBwdArgs a) {
@@ -130,16 +159,16 @@ __global__ void __launch_bounds__(kTsThreads, 1) tc_bwd_ts_kernel(TcBwdArgs a) {
   uint64_t* s_free = s_full + 2;     // [b] S_b, W_b loaded into registers
   uint64_t* q_ready = s_free + 2;    // [b] Q_b written
   uint64_t* q_free = q_ready + 2;    // [b] Q_b consumed by the feature sums
-  uint64_t* o_ready = q_free + 2;    // accumulator of a fold complete
-  uint64_t* o_free = o_ready + 1;    // accumulator read
-  uint64_t* done = o_free + 1;       // [issuer], 3
+  uint64_t* o_ready = q_free + 2;    // [warpgroup] accumulator of a fold complete, for the folding warpgroup
+  uint64_t* o_free = o_ready + 2;    // [warpgroup] accumulator read
+  uint64_t* done = o_free + 2;       // [issuer], 3
   uint64_t* xa_full = done + 3;      // XS: XA tile landed
   uint64_t* xa_empty = xa_full + 1;  // XS: both S issuers done with it (2 arrivals)
   uint32_t* tslot = reinterpret_cast<uint32_t*>(xa_empty + 1);
   volatile int* abort = reinterpret_cast<volatile int*>(tslot + 1);
-  // FP64 fold sums of warpgroup 0, [warp][q, contrib_0 .. contrib_{d-1}]
+  // FP64 fold sums, [warpgroup * 4 + warp][q, contrib_0 .. contrib_{d-1}]
   double* wpart = reinterpret_cast<double*>(reinterpret_cast<uint8_t*>(full) + kTsBarBytes);
-  const uint32_t colA = 320, colG = XS ? 320 : 320 + a.KX / 2, colACC = 512 - a.NB;
+  const uint32_t colA = 384, colG = XS ? 384 : 384 + a.KX / 2, colACC = 512 - a.NACC;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
@@ -155,8 +184,10 @@ __global__ void __launch_bounds__(kTsThreads, 1) tc_bwd_ts_kernel(TcBwdArgs a) {
       mbar_init(&q_ready[b], 128);
       mbar_init(&q_free[b], 1);
     }
-    mbar_init(o_ready, 1);
-    mbar_init(o_free, 128);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&o_ready[b], 1);
+      mbar_init(&o_free[b], 128);
+    }
     for (int i = 0; i < 3; ++i) mbar_init(&done[i], 1);
     mbar_init(xa_full, 1);
     mbar_init(xa_empty, 2);
@@ -221,7 +252,7 @@ __global__ void __launch_bounds__(kTsThreads, 1) tc_bwd_ts_kernel(TcBwdArgs a) {
     // ------------------------------------------------------------ S, W issuer of buffer b
     const bool leader = elect_one();
     const int b = warp == kMmaWarp ? 0 : 1;
-    const uint32_t idSW = idesc_f16(128, 64, 1, 1);
+    const uint32_t idSW = idesc_f16(128, 64, 0, 0);
     const int nkx = a.KX / 16, nkg = a.KG / 16;
     const uint64_t dXA = sdesc(smem_u32(sXA), 128, a.KX * 16u);
     const uint64_t dXB = sdesc(smem_u32(sS + b * a.KX * 128u), 128, a.KX * 16u);
@@ -273,10 +304,13 @@ __global__ void __launch_bounds__(kTsThreads, 1) tc_bwd_ts_kernel(TcBwdArgs a) {
   } else if (warp == kAccWarp) {
     // ------------------------------------------------------------ feature-sum issuer
     const bool leader = elect_one();
-    const uint32_t idA = idesc_f16(128, a.NB, 0, 0);
+    const uint32_t idA = idesc_f16(128, a.NACC, 0, 0);
+    const uint32_t lo_bytes = (uint32_t)a.NACC * 256u;   // ksplit: the lo block of BG
     const uint64_t dBG = sdesc(smem_u32(sS + XT + GT), 128, 2048);
-    uint32_t stage = 0, of_ph = 0;
+    uint32_t stage = 0;
+    uint32_t of_ph[2] = {0u, 0u};
     uint32_t qr0 = 0, qr1 = 0;
+    long long fc = 0;   // folds committed: fold f is read by warpgroup f & 1
     bool open = false;
     for (int t = blockIdx.x; t < a.n_items; t += gridDim.x) {
       const int4 item = a.items[t];
@@ -291,22 +325,29 @@ __global__ void __launch_bounds__(kTsThreads, 1) tc_bwd_ts_kernel(TcBwdArgs a) {
         const uint32_t acc = (h % kFoldH) != 0;
         const bool fold_end = (h % kFoldH) == kFoldH - 1 || h == nH - 1;
         if (!acc && open) {
-          if (!warp_wait(o_free, of_ph, abort, a.err, 27)) goto acc_out;
-          of_ph ^= 1;
+          // the previous fold's accumulator must have been read by its warpgroup
+          const int rb = (int)((fc - 1) & 1);
+          if (!warp_wait(&o_free[rb], of_ph[rb], abort, a.err, 27)) goto acc_out;
+          of_ph[rb] ^= 1;
           open = false;
           tc_fence_after();
         }
         const uint64_t dbg = sdesc_add(dBG, stage * STG + b * 1024u);
-        const uint32_t tq = tbase + 256 + 32 * b, tacc = tbase + colACC;
+        const uint32_t tqh = tbase + 256 + 32 * b, tql = tbase + 320 + 32 * b, tacc = tbase + colACC;
         if (leader) {
-          issue_ts4(tacc, tq, dbg, idA, acc);
+          issue_ts4(tacc, tqh, dbg, idA, acc);
+          if (a.ksplit) issue_ts4(tacc, tqh, sdesc_add(dbg, lo_bytes), idA, 1);
+          issue_ts4(tacc, tql, dbg, idA, 1);
           tc_commit(&q_free[b]);
-          if (fold_end) tc_commit(o_ready);
+          if (fold_end) tc_commit(&o_ready[fc & 1]);
           // both halves of the stage read (their S, W MMAs completed before Q)
           if (b == 1) tc_commit(&empty[stage]);
         }
         __syncwarp();
-        if (fold_end) open = true;
+        if (fold_end) {
+          open = true;
+          ++fc;
+        }
         if (b == 1) {
           if (++stage == (uint32_t)S) stage = 0;
         }
@@ -321,22 +362,24 @@ __global__ void __launch_bounds__(kTsThreads, 1) tc_bwd_ts_kernel(TcBwdArgs a) {
     const int b = warp >> 2, w = warp & 3;
     const int row = 32 * w + lane;
     const uint32_t lofs = static_cast<uint32_t>(32 * w) << 16;
-    const uint32_t tS = tbase + lofs + 128 * b, tQ = tbase + lofs + 256 + 32 * b;
+    const uint32_t tS = tbase + lofs + 128 * b, tQh = tbase + lofs + 256 + 32 * b;
+    const uint32_t tQl = tQh + 64;
     const uint32_t tACC = tbase + lofs + colACC;
     const int d = a.d;
     const int qc = a.qcol;
-    double* wp = wpart + w * kGW;
+    double* wp = wpart + (b * 4 + w) * kGW;
     uint32_t sph = 0, oph = 0;
+    long long fcount = 0;   // fold ends passed (both warpgroups see every one)
     long long uses = 0;
     int u = 0;
     for (int t = blockIdx.x; t < a.n_items; t += gridDim.x) {
       const int4 item = a.items[t];
       if (a.sys_active && !a.sys_active[item.x]) continue;
-      const int s = item.x, bi = s / a.chains, c = s % a.chains;
+      const int c = item.x % a.chains;
       const int nH = 2 * item.w;
       if (u > 0) {
         // both warpgroups have waited for their last S, W of the previous
-        // item: no MMA reads XA or GI any more
+        // item and folded its accumulator: nothing reads XA or GI any more
         mbar_arrive(seg);
         const bool ok = mbar_wait(seg, (uint32_t)(u - 1) & 1u, abort, a.err, 32);
         if (!__all_sync(0xffffffffu, ok)) goto exp_out;
@@ -359,15 +402,7 @@ __global__ void __launch_bounds__(kTsThreads, 1) tc_bwd_ts_kernel(TcBwdArgs a) {
         tc_fence_before();
         mbar_arrive(a_ready);
       }
-      const int64_t nb = a.L.offsets[bi + 1] - a.L.offsets[bi];
-      const int64_t rl = (int64_t)(item.y - a.T.inst_tile0[bi]) * 128 + row;
-      const bool valid = rl < nb;
-      const int64_t i = a.L.offsets[bi] + rl;
-      const double* th = a.theta + (int64_t)s * a.n_theta;
-      // lane k holds the scale of dimension k (d <= 32): one exp per lane per item
-      const float sc_lane =
-          lane < d ? (float)(sqrt(2.0 * kHalfLog2e) * exp(-th[1 + (a.ard ? lane : 0)])) : 0.f;
-      if (b == 0 && lane == 0)
+      if (lane == 0)
         for (int v = 0; v <= d; ++v) wp[v] = 0.0;
       for (int h = b; h < nH; h += 2, ++uses) {
         bool ok = mbar_wait(&s_full[b], sph, abort, a.err, 28);
@@ -386,77 +421,142 @@ __global__ void __launch_bounds__(kTsThreads, 1) tc_bwd_ts_kernel(TcBwdArgs a) {
           tc_fence_before();
           mbar_arrive(&s_free[b]);
           if (item.z + (h >> 1) == item.y) {
-            // diagonal tile of the upper triangle: counted once, off-diagonal tiles twice
+            // diagonal tile of the upper triangle: counted once, off-diagonal
+            // tiles twice; the pair i = j is left out (its distance is 0, and its
+            // share of the alpha gradient is added exactly at the end)
+            const int e = row - 64 * b;
 #pragma unroll
             for (int q = 0; q < 32; ++q) {
-              w0[q] = __float_as_uint(0.5f * __uint_as_float(w0[q]));
-              w1[q] = __float_as_uint(0.5f * __uint_as_float(w1[q]));
+              w0[q] = __float_as_uint(q == e ? 0.f : 0.5f * __uint_as_float(w0[q]));
+              w1[q] = __float_as_uint(q + 32 == e ? 0.f : 0.5f * __uint_as_float(w1[q]));
             }
           }
+          // Q = W 2^S split into F16 hi and lo parts
+          uint32_t qh[32];
 #pragma unroll
-          for (int q = 0; q < 16; ++q)
-            qq[q] = pack_f16x2(ex2(__uint_as_float(s0[2 * q])) * __uint_as_float(w0[2 * q]),
-                               ex2(__uint_as_float(s0[2 * q + 1])) * __uint_as_float(w0[2 * q + 1]));
+          for (int q = 0; q < 16; ++q) {
+            float h0, l0, h1, l1;
+            split_q(ex2(__uint_as_float(s0[2 * q])) * __uint_as_float(w0[2 * q]), h0, l0);
+            split_q(ex2(__uint_as_float(s0[2 * q + 1])) * __uint_as_float(w0[2 * q + 1]), h1, l1);
+            qh[q] = pack_f16x2(h0, h1);
+            qq[q] = pack_f16x2(l0, l1);
+          }
 #pragma unroll
-          for (int q = 0; q < 16; ++q)
-            qq[16 + q] = pack_f16x2(ex2(__uint_as_float(s1[2 * q])) * __uint_as_float(w1[2 * q]),
-                                    ex2(__uint_as_float(s1[2 * q + 1])) * __uint_as_float(w1[2 * q + 1]));
+          for (int q = 0; q < 16; ++q) {
+            float h0, l0, h1, l1;
+            split_q(ex2(__uint_as_float(s1[2 * q])) * __uint_as_float(w1[2 * q]), h0, l0);
+            split_q(ex2(__uint_as_float(s1[2 * q + 1])) * __uint_as_float(w1[2 * q + 1]), h1, l1);
+            qh[16 + q] = pack_f16x2(h0, h1);
+            qq[16 + q] = pack_f16x2(l0, l1);
+          }
           if (uses > 0) {
             // Q_b of this warpgroup's previous half must have been consumed
             ok = mbar_wait(&q_free[b], (uint32_t)((uses - 1) & 1), abort, a.err, 30);
             if (!__all_sync(0xffffffffu, ok)) goto exp_out;
             tc_fence_after();
           }
-          tmem_st32(tQ, qq);
+          tmem_st32(tQh, qh);
+          tmem_st32(tQl, qq);
         }
         tmem_st_wait();
         tc_fence_before();
         mbar_arrive(&q_ready[b]);
-        // warpgroup 0 folds the accumulator after the fold's last (odd) half:
-        // per row x~^2 q - 2 x~ R + T, summed over the warp's 32 rows in FP64
-        if (b == 0 && (((h + 1) % kFoldH) == kFoldH - 1 || h + 1 == nH - 1)) {
-          ok = mbar_wait(o_ready, oph, abort, a.err, 29);
-          if (!__all_sync(0xffffffffu, ok)) goto exp_out;
-          oph ^= 1;
-          tc_fence_after();
-          uint32_t oq[16];
-          tmem_ld16(tACC + 16 * (qc >> 4), oq);
-          tmem_ld_wait_regs(oq);
-          const float qs = __uint_as_float(oq[qc & 15]);
-          // per-row terms summed over the warp's 32 rows in FP32, the warp sums
-          // accumulated in FP64 across folds
-          float v = qs;
+        // After the fold's last (odd) half the accumulator holds q, R, T of the
+        // fold; the warpgroups take turns at folding it: per row
+        // xt^2 q - 2 xt R + T, summed over the warp's 32 rows in FP32, the warp
+        // sums accumulated in FP64.  xt (the F16 hi + lo of the scaled, centred
+        // point, as in BG) is read back from the row's XA operand: columns 3k,
+        // 3k + 1 hold hi and lo of dimension k.
+        const int e_half = b == 0 ? h + 1 : h;
+        if ((e_half % kFoldH) == kFoldH - 1 || e_half == nH - 1) {
+          const bool mine = (fcount & 1) == b;
+          ++fcount;
+          if (mine) {
+            ok = mbar_wait(&o_ready[b], oph, abort, a.err, 29);
+            if (!__all_sync(0xffffffffu, ok)) goto exp_out;
+            oph ^= 1;
+            tc_fence_after();
+            // xt of this row, all dimensions (packed F16 pairs)
+            uint32_t xa[kXaRegs];
+            if (XS) {
+              // the shared-memory XA tile may already hold the next item's rows
+              // (it is released after the item's last S product): read the
+              // item's tile in global memory, which stays until the call ends
+              const uint8_t* gxa = a.XA + ((size_t)c * a.T_total + item.y) * XT;
 #pragma unroll
-          for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-          if (lane == 0) wp[0] += (double)v;
-          for (int c4 = 0; c4 < (kMaxDT + 3) / 4; ++c4) {
-            if (4 * c4 < d) {
-              uint32_t o[16];
-              tmem_ld16(tACC + 16 * c4, o);
-              tmem_ld_wait_regs(o);
+              for (int q = 0; q < kXaRegs; ++q) {
+                const int kk = 2 * q;
+                xa[q] = kk < 3 * d ? __ldg(reinterpret_cast<const uint32_t*>(gxa + x_off(row, kk, a.KX))) : 0u;
+              }
+            } else {
+              uint32_t t0[16], t1[16] = {};
+              tmem_ld16(tbase + lofs + colA, t0);
+              if (3 * d > 32) tmem_ld16(tbase + lofs + colA + 16, t1);
+              tmem_ld_wait_regs(t0, t1);
 #pragma unroll
-              for (int uu = 0; uu < 4; ++uu) {
-                const int kk = 4 * c4 + uu;
-                if (kk < d) {
-                  const float R = __uint_as_float(o[4 * uu]) + __uint_as_float(o[4 * uu + 1]);
-                  const float T = __uint_as_float(o[4 * uu + 2]) + __uint_as_float(o[4 * uu + 3]);
-                  const float sc = __shfl_sync(0xffffffffu, sc_lane, kk);
-                  const float x = valid ? xt_of(a.x[i * d + kk], sc) : 0.f;
-                  float e = valid ? fmaf(x, fmaf(x, qs, -2.f * R), T) : 0.f;
+              for (int c = 0; c < kXaRegs; ++c) xa[c] = c < 16 ? t0[c] : (c < 32 ? t1[c - 16] : 0u);
+            }
+            auto xt_dim = [&](int k) -> float {
+              const uint32_t wh = xa[(3 * k) >> 1], wl = xa[(3 * k + 1) >> 1];
+              const uint16_t hb = (uint16_t)(((3 * k) & 1) ? (wh >> 16) : (wh & 0xffffu));
+              const uint16_t lb = (uint16_t)(((3 * k + 1) & 1) ? (wl >> 16) : (wl & 0xffffu));
+              return __half2float(__ushort_as_half(hb)) + __half2float(__ushort_as_half(lb));
+            };
+            uint32_t oq[16];
+            tmem_ld16(tACC + 16 * (qc >> 4), oq);
+            tmem_ld_wait_regs(oq);
+            const float qs = __uint_as_float(oq[qc & 15]);
+            float v = qs;
 #pragma unroll
-                  for (int sft = 16; sft > 0; sft >>= 1) e += __shfl_down_sync(0xffffffffu, e, sft);
-                  if (lane == 0) wp[1 + kk] += (double)e;
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+            if (lane == 0) wp[0] += (double)v;
+            auto fold_dim = [&](int kk, float R, float T) {
+              const float x = xt_dim(kk);
+              float e = fmaf(x, fmaf(x, qs, -2.f * R), T);
+#pragma unroll
+              for (int sft = 16; sft > 0; sft >>= 1) e += __shfl_down_sync(0xffffffffu, e, sft);
+              if (lane == 0) wp[1 + kk] += (double)e;
+            };
+            if (!a.ksplit) {
+#pragma unroll
+              for (int c4 = 0; c4 < (kMaxDT + 3) / 4; ++c4) {
+                if (4 * c4 < d) {
+                  uint32_t o[16];
+                  tmem_ld16(tACC + 16 * c4, o);
+                  tmem_ld_wait_regs(o);
+#pragma unroll
+                  for (int uu = 0; uu < 4; ++uu) {
+                    const int kk = 4 * c4 + uu;
+                    if (kk < d)
+                      fold_dim(kk, __uint_as_float(o[4 * uu]) + __uint_as_float(o[4 * uu + 1]),
+                               __uint_as_float(o[4 * uu + 2]) + __uint_as_float(o[4 * uu + 3]));
+                  }
+                }
+              }
+            } else {
+#pragma unroll
+              for (int c16 = 0; c16 < kMaxDT / 16; ++c16) {
+                if (16 * c16 < d) {
+                  uint32_t oR[16], oT[16];
+                  tmem_ld16(tACC + 16 * c16, oR);
+                  tmem_ld16(tACC + a.toff + 16 * c16, oT);
+                  tmem_ld_wait_regs(oR, oT);
+#pragma unroll
+                  for (int uu = 0; uu < 16; ++uu) {
+                    const int kk = 16 * c16 + uu;
+                    if (kk < d) fold_dim(kk, __uint_as_float(oR[uu]), __uint_as_float(oT[uu]));
+                  }
                 }
               }
             }
+            tc_fence_before();
+            mbar_arrive(&o_free[b]);
           }
-          tc_fence_before();
-          mbar_arrive(o_free);
         }
       }
-      if (b == 0 && lane == 0) {
+      if (lane == 0) {
         // per-warp partial of this item: [q, contrib_0 .. contrib_{d-1}]
-        double* out = a.gpart + (((size_t)a.chunk * a.n_items + t) * 4 + w) * kGW;
+        double* out = a.gpart + (((size_t)a.chunk * a.n_items + t) * kFoldWarps + b * 4 + w) * kGW;
         for (int v = 0; v <= d; ++v) out[v] = wp[v];
       }
     }
@@ -469,9 +569,11 @@ __global__ void __launch_bounds__(kTsThreads, 1) tc_bwd_ts_kernel(TcBwdArgs a) {
   if (warp == kMmaWarp) tmem_dealloc(tbase, 512);
 }
 
-// max |G_i| and max |V_j| per system (row norms) and sum_i G_i . V_i.
+// max |G_i| and max |V_j| per system (row norms, with the amplitudes),
+// sum_i G_i . V_i (the noise gradient) and sum_i amp_i^2 G_i . V_i (the
+// diagonal's share of the alpha gradient).
 __global__ void tc_bwd_norms_kernel(DevLayout L, int chains, int64_t n_total, const float* V, const float* G,
-                                    int m, uint32_t* gmax, uint32_t* vmax, double* gvpart,
+                                    int m, uint32_t* gmax, uint32_t* vmax, double* gvpart, double* gvdiag,
                                     const int32_t* sys_active, const float* amp) {
   __shared__ double red[kTile / 32];
   const int item = blockIdx.x, c = blockIdx.y;
@@ -479,7 +581,7 @@ __global__ void tc_bwd_norms_kernel(DevLayout L, int chains, int64_t n_total, co
   const int s = b * chains + c;
   if (sys_active && !sys_active[s]) return;
   const int64_t i = L.item_row0[item] + threadIdx.x;
-  double gv = 0.0;
+  double gv = 0.0, am2 = 1.0;
   if (i < L.offsets[b + 1]) {
     float g2 = 0.f, v2 = 0.f;
     for (int q = 0; q < m; ++q) {
@@ -490,20 +592,27 @@ __global__ void tc_bwd_norms_kernel(DevLayout L, int chains, int64_t n_total, co
       gv += (double)gq * (double)vq;
     }
     const float am = amp ? amp[(int64_t)c * n_total + i] : 1.f;
+    am2 = (double)am * (double)am;
     atomicMax(&gmax[s], __float_as_uint(sqrtf(g2) * am));
     atomicMax(&vmax[s], __float_as_uint(sqrtf(v2) * am));
   }
   const double t = block_sum(gv, red);
-  if (threadIdx.x == 0) gvpart[(int64_t)item * chains + c] = t;
+  __syncthreads();
+  const double t2 = block_sum(gv * am2, red);
+  if (threadIdx.x == 0) {
+    gvpart[(int64_t)item * chains + c] = t;
+    gvdiag[(int64_t)item * chains + c] = t2;
+  }
 }
 
 // GI, VJ and BG operand tiles of every (chain, padded tile).
 // G and V enter by columns [c0, c0 + mc) of their m; GI rows [gh gh gl vh vh vl],
-// VJ rows [vh vl vh gh gl gh] (BF16 hi/lo, G scaled by a power of two), so that
-// GI VJ^T = G_i . V_j + V_i . G_j over the block.
-__global__ void tc_prep_bwd_kernel(DevLayout L, TcTables T, int chains, int d, int ard, int n_theta, int m,
-                                   int c0, int mc, int KG, int NB, int qcol, int T_total, const float* x,
-                                   const double* theta,
+// VJ rows [vh vl vh gh gl gh] (F16 hi/lo, G and V each scaled by a power of
+// two), so that GI VJ^T = G_i . V_j + V_i . G_j over the block.  BG carries the
+// F16 hi/lo parts of the centred xt and of xt^2 in the layout of TcBwdArgs.
+__global__ void tc_prep_bwd_kernel(DevLayout L, TcTables T, int n_inst, int chains, int d, int ard, int n_theta,
+                                   int m, int c0, int mc, int KG, int NB, int ksplit, int NACC, int toff, int qcol,
+                                   int T_total, const float* x, const double* theta, const uint32_t* ckeys,
                                    const float* V, const float* G, int64_t n_total, const uint32_t* gmax,
                                    const uint32_t* vmax, const int32_t* sys_active, const float* amp,
                                    uint8_t* GI, uint8_t* VJ, uint8_t* BG, int* err) {
@@ -516,21 +625,21 @@ __global__ void tc_prep_bwd_kernel(DevLayout L, TcTables T, int chains, int d, i
   const bool valid = rl < nb;
   const int64_t i = L.offsets[b] + rl;
   const size_t tile = (size_t)c * T_total + t;
-  __nv_bfloat16* gi = reinterpret_cast<__nv_bfloat16*>(GI + tile * (size_t)KG * 256);
-  __nv_bfloat16* vj = reinterpret_cast<__nv_bfloat16*>(VJ + tile * (size_t)KG * 256);
+  __half* gi = reinterpret_cast<__half*>(GI + tile * (size_t)KG * 256);
+  __half* vj = reinterpret_cast<__half*>(VJ + tile * (size_t)KG * 256);
   __half* bg = reinterpret_cast<__half*>(BG + tile * (size_t)NB * 256);
   const float am = (valid && amp) ? amp[(int64_t)c * n_total + i] : 1.f;
-  const float gs = (float)w_scale(gmax[s], vmax[s]) * am;
-  const __nv_bfloat16 zb = __float2bfloat16_rn(0.f);
+  const float gs = (float)row_scale(gmax[s]) * am, vs = (float)row_scale(vmax[s]) * am;
+  const __half zh = __float2half_rn(0.f);
   for (int q = 0; q < KG; ++q) {
-    __nv_bfloat16 gval = zb, vval = zb;
+    __half gval = zh, vval = zh;
     if (valid && q < 6 * mc) {
       const int col = q % mc, part = q / mc;
       const int64_t idx = ((int64_t)c * n_total + i) * m + c0 + col;
-      const float gq = G[idx] * gs, vq = V[idx] * am;
-      const __nv_bfloat16 gh = __float2bfloat16_rn(gq), vh = __float2bfloat16_rn(vq);
-      const __nv_bfloat16 gl = __float2bfloat16_rn(gq - __bfloat162float(gh));
-      const __nv_bfloat16 vl = __float2bfloat16_rn(vq - __bfloat162float(vh));
+      const float gq = G[idx] * gs, vq = V[idx] * vs;
+      const __half gh = __float2half_rn(gq), vh = __float2half_rn(vq);
+      const __half gl = __float2half_rn(gq - __half2float(gh));
+      const __half vl = __float2half_rn(vq - __half2float(vh));
       if (part < 3) {
         gval = part < 2 ? gh : gl;        // [gh, gh, gl]
         vval = part == 1 ? vl : vh;       // [vh, vl, vh]
@@ -544,11 +653,11 @@ __global__ void tc_prep_bwd_kernel(DevLayout L, TcTables T, int chains, int d, i
     vj[x_off(r, q, KG) / 2] = vval;
   }
   const double* th = theta + (int64_t)s * n_theta;
-  for (int f = 0; f < NB; ++f) bg[t_off(f, r) / 2] = __float2half_rn(0.f);
+  for (int f = 0; f < NB; ++f) bg[t_off(f, r) / 2] = zh;
   if (valid) {
     for (int k = 0; k < d; ++k) {
       const float sc = (float)(sqrt(2.0 * kHalfLog2e) * exp(-th[1 + (ard ? k : 0)]));
-      const float xh = x[i * d + k] * sc;
+      const float xh = (x[i * d + k] - center_of(ckeys, n_inst, d, b, k)) * sc;
       const __half hi = __float2half_rn(xh);
       const __half lo = __float2half_rn(xh - __half2float(hi));
       const float xtv = __half2float(hi) + __half2float(lo);
@@ -556,10 +665,17 @@ __global__ void tc_prep_bwd_kernel(DevLayout L, TcTables T, int chains, int d, i
       const float sq = xtv * xtv;
       const __half sh = __float2half_rn(sq);
       const __half sl = __float2half_rn(sq - __half2float(sh));
-      bg[t_off(4 * k, r) / 2] = hi;
-      bg[t_off(4 * k + 1, r) / 2] = lo;
-      bg[t_off(4 * k + 2, r) / 2] = sh;
-      bg[t_off(4 * k + 3, r) / 2] = sl;
+      if (!ksplit) {
+        bg[t_off(4 * k, r) / 2] = hi;
+        bg[t_off(4 * k + 1, r) / 2] = lo;
+        bg[t_off(4 * k + 2, r) / 2] = sh;
+        bg[t_off(4 * k + 3, r) / 2] = sl;
+      } else {
+        bg[t_off(k, r) / 2] = hi;
+        bg[t_off(toff + k, r) / 2] = sh;
+        bg[t_off(NACC + k, r) / 2] = lo;
+        bg[t_off(NACC + toff + k, r) / 2] = sl;
+      }
     }
     bg[t_off(qcol, r) / 2] = __float2half_rn(1.f);
   }
@@ -572,28 +688,30 @@ constexpr int kFinThreads = 256;
 
 __global__ void __launch_bounds__(kFinThreads) tc_bwd_finalize_kernel(
     DevLayout L, const int32_t* pref, int n_items, int n_chunks, int chains, int n_theta, int ard, int d,
-    const double* theta, const double* gpart, const double* gvpart, const uint32_t* gmax, const uint32_t* vmax,
-    const int32_t* sys_active, const int* err, double* grad) {
-  __shared__ double red[kFinThreads / 32][kGW + 1];
+    const double* theta, const double* gpart, const double* gvpart, const double* gvdiag, const uint32_t* gmax,
+    const uint32_t* vmax, const int32_t* sys_active, const int* err, double* grad) {
+  __shared__ double red[kFinThreads / 32][kGW + 2];
   const int s = blockIdx.x;
   if (sys_active && !sys_active[s]) return;
   const int b = s / chains, c = s - b * chains;
-  const int64_t n_rows = (int64_t)(pref[s + 1] - pref[s]) * 4;   // (item, warp) partial rows per block
-  double acc[kGW + 1];
+  const int64_t n_rows = (int64_t)(pref[s + 1] - pref[s]) * kFoldWarps;   // (item, warp) partial rows per block
+  double acc[kGW + 2];
 #pragma unroll
-  for (int v = 0; v <= kGW; ++v) acc[v] = 0.0;
+  for (int v = 0; v <= kGW + 1; ++v) acc[v] = 0.0;
   for (int ch = 0; ch < n_chunks; ++ch) {
-    const int64_t r0 = ((int64_t)ch * n_items + pref[s]) * 4;
+    const int64_t r0 = ((int64_t)ch * n_items + pref[s]) * kFoldWarps;
     for (int64_t r = threadIdx.x; r < n_rows; r += kFinThreads) {
       const double* row = gpart + (r0 + r) * kGW;
       for (int v = 0; v <= d; ++v) acc[v] += row[v];
     }
   }
-  for (int it = L.inst_item0[b] + threadIdx.x; it < L.inst_item0[b + 1]; it += kFinThreads)
+  for (int it = L.inst_item0[b] + threadIdx.x; it < L.inst_item0[b + 1]; it += kFinThreads) {
     acc[kGW] += gvpart[(int64_t)it * chains + c];
+    acc[kGW + 1] += gvdiag[(int64_t)it * chains + c];
+  }
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll
-  for (int v = 0; v <= kGW; ++v) {
+  for (int v = 0; v <= kGW + 1; ++v) {
     double u = acc[v];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) u += __shfl_down_sync(0xffffffffu, u, o);
@@ -601,18 +719,20 @@ __global__ void __launch_bounds__(kFinThreads) tc_bwd_finalize_kernel(
   }
   __syncthreads();
   if (threadIdx.x != 0) return;
-  double tot[kGW + 1];
-  for (int v = 0; v <= kGW; ++v) {
+  double tot[kGW + 2];
+  for (int v = 0; v <= kGW + 1; ++v) {
     tot[v] = 0.0;
     for (int ww = 0; ww < kFinThreads / 32; ++ww) tot[v] += red[ww][v];
   }
   const double* th = theta + (int64_t)s * n_theta;
   const double alpha = exp(th[0]), s2 = exp(th[n_theta - 1]);
-  const double gs = w_scale(gmax[s], vmax[s]);
+  // W^s carried the scales of G and V
+  const double gs = row_scale(gmax[s]) * row_scale(vmax[s]);
   const bool bad = *err != 0;
   const double nan = __longlong_as_double(0x7ff8000000000000ll);
   double* out = grad + (int64_t)s * n_theta;
-  out[0] = bad ? nan : alpha * tot[0] / gs;
+  // off-diagonal pairs from the kernel, the pairs i = j (K0_ii = 1) exactly
+  out[0] = bad ? nan : alpha * (tot[0] / gs + tot[kGW + 1]);
   const double ls = alpha / (gs * 2.0 * kHalfLog2e);
   if (ard) {
     for (int k = 0; k < d; ++k) out[1 + k] = bad ? nan : ls * tot[1 + k];
@@ -630,38 +750,72 @@ kmv_status tc_backward(kmv_handle h, const KmvArgs& a, double* grad, cudaStream_
   const Layout& L = h->layout;
   if (a.d > kMaxDT) return tc_fail(h, KMV_EUNSUPPORTED, "tensor-core adjoint supports d <= 32");
   TcState* S = tc_state(h);
-  kmv_status stt = tc_build_plan(h, S, st);
+  const TcTiles tl = tc_tiles_for(h, kTilesAdjoint, a.d, a.m);
+  kmv_status stt = tc_build_plan(h, S, 0, tl.items_per_sm, st);
   if (stt != KMV_OK) return stt;
   const int n_sys = L.n_inst * L.chains;
-  const int KX = x_width(a.d);
-  const int NB = round16(4 * a.d + 1), qcol = 4 * a.d;
+  const int KX = x_width(a.d, kSplitF16);
+  const size_t max_stages = tl.stages > 0 ? (size_t)std::max(2, std::min(tl.stages, 6)) : 6;
   const size_t fixed = 1024 + kTsBarBytes + kTsFoldBytes;
-  // Columns of G, V per launch (mc) and where XA lives: the depth-6 mc GI rows,
-  // the accumulator and (unless XS) the XA rows must fit the TMEM columns left
-  // by S, W and Q, and the stages shared memory.  Fewer launches first, then
-  // XA in TMEM.
-  auto stages_for = [&](bool xs, int mc) -> int {
-    const size_t KG = round16(6 * mc);
-    const size_t stg = (size_t)(KX + KG + NB) * 256;
-    const size_t xa = xs ? (((size_t)KX * 256 + 1023) & ~size_t(1023)) : 0;
-    if (kMaxSmem < fixed + xa + 2 * stg) return 0;
-    return (int)std::min<size_t>(6, (kMaxSmem - fixed - xa) / stg);
+  // Feature-sum layout, columns of G, V per launch (mc) and where XA lives:
+  // the accumulator, the depth-6 mc GI rows and (unless XS) the XA rows must
+  // fit the TMEM columns left by S, W and Qh, Ql, and the stages shared
+  // memory.  Fewest launches first, then the wide layout (fewer MMAs per
+  // half tile), then XA in TMEM.
+  struct Choice {
+    int ksplit, NACC, toff, qcol, NB, mc, n_chunks, stages;
+    bool xs;
   };
-  auto max_mc = [&](bool xs) -> int {
-    for (int mc = a.m; mc >= 1; --mc) {
-      const int cols = (xs ? 0 : KX / 2) + round16(6 * mc) / 2 + NB;
-      if (cols <= kTsCols && stages_for(xs, mc) >= 2) return mc;
+  auto make = [&](int ksplit, bool xs) -> Choice {
+    Choice c{};
+    c.ksplit = ksplit;
+    c.xs = xs;
+    if (!ksplit) {
+      c.toff = 0;
+      c.qcol = 4 * a.d;
+      c.NACC = round16(4 * a.d + 1);
+      c.NB = c.NACC;
+    } else {
+      c.toff = round16(a.d);
+      c.qcol = 2 * c.toff;
+      c.NACC = round16(c.qcol + 1);
+      c.NB = 2 * c.NACC;
     }
-    return 0;
+    // XA in TMEM: the fold reads a row's split values with at most two loads
+    if (!xs && 3 * a.d > 64) {
+      c.mc = 0;
+      c.n_chunks = INT32_MAX;
+      return c;
+    }
+    auto stages_for = [&](int mc) -> int {
+      const size_t KG = round16(6 * mc);
+      const size_t stg = (size_t)(KX + KG + c.NB) * 256;
+      const size_t xa = xs ? (((size_t)KX * 256 + 1023) & ~size_t(1023)) : 0;
+      if (kMaxSmem < fixed + xa + 2 * stg) return 0;
+      return (int)std::min<size_t>(max_stages, (kMaxSmem - fixed - xa) / stg);
+    };
+    for (int mc = a.m; mc >= 1; --mc) {
+      const int cols = (xs ? 0 : KX / 2) + round16(6 * mc) / 2 + c.NACC;
+      if (cols <= kTsCols && stages_for(mc) >= 2) {
+        c.mc = mc;
+        c.n_chunks = (a.m + mc - 1) / mc;
+        c.stages = stages_for(mc);
+        return c;
+      }
+    }
+    c.mc = 0;
+    c.n_chunks = INT32_MAX;
+    return c;
   };
-  const int mc0 = max_mc(false), mc1 = max_mc(true);
-  if (mc0 == 0 && mc1 == 0)
+  Choice best = make(0, false);
+  for (const Choice& c : {make(0, true), make(1, false), make(1, true)})
+    if (c.n_chunks < best.n_chunks) best = c;
+  if (best.mc == 0)
     return tc_fail(h, KMV_EUNSUPPORTED, "tensor-core adjoint operands do not fit in tensor/shared memory");
-  const int nc0 = mc0 ? (a.m + mc0 - 1) / mc0 : INT32_MAX, nc1 = mc1 ? (a.m + mc1 - 1) / mc1 : INT32_MAX;
-  const bool xs = nc1 < nc0;
-  const int mc = xs ? mc1 : mc0, n_chunks = xs ? nc1 : nc0;
+  const bool xs = best.xs;
+  const int mc = best.mc, n_chunks = best.n_chunks, NB = best.NB;
   const int KG = round16(6 * mc);
-  const int stages = stages_for(xs, mc);
+  const int stages = best.stages;
   const size_t XT = (size_t)KX * 256, GT = (size_t)KG * 256, BT = (size_t)NB * 256;
   const size_t STG = XT + GT + BT;
   const size_t smem =
@@ -670,17 +824,22 @@ kmv_status tc_backward(kmv_handle h, const KmvArgs& a, double* grad, cudaStream_
 
   auto al = [](size_t v) { return (v + 255) & ~size_t(255); };
   const size_t tiles = (size_t)L.chains * S->T_total;
+  const size_t gvb = al(sizeof(double) * (size_t)std::max(1, L.n_items) * L.chains);
   const size_t o_xa = 0, o_xb = o_xa + al(tiles * XT), o_gi = o_xb + al(tiles * XT);
   const size_t o_vj = o_gi + al(tiles * GT), o_bg = o_vj + al(tiles * GT), o_mx = o_bg + al(tiles * BT);
   const size_t o_gv = o_mx + al(sizeof(uint32_t) * 2 * n_sys);
-  const size_t o_gp = o_gv + al(sizeof(double) * (size_t)std::max(1, L.n_items) * L.chains);
-  const size_t o_er = o_gp + al(sizeof(double) * (size_t)n_chunks * std::max(1, n_items) * 4 * kGW);
+  const size_t o_gd = o_gv + gvb;
+  const size_t o_ck = o_gd + gvb;
+  const size_t o_gp = o_ck + al(tc_center_bytes(L));
+  const size_t o_er = o_gp + al(sizeof(double) * (size_t)n_chunks * std::max(1, n_items) * kFoldWarps * kGW);
   stt = tc_ensure_buf(h, S, o_er + 256);
   if (stt != KMV_OK) return stt;
   uint8_t* base = static_cast<uint8_t*>(S->buf);
   uint32_t* gmax = reinterpret_cast<uint32_t*>(base + o_mx);
   uint32_t* vmax = gmax + n_sys;
   double* gvpart = reinterpret_cast<double*>(base + o_gv);
+  double* gvdiag = reinterpret_cast<double*>(base + o_gd);
+  uint32_t* ckeys = reinterpret_cast<uint32_t*>(base + o_ck);
   double* gpart = reinterpret_cast<double*>(base + o_gp);
   int* err = reinterpret_cast<int*>(base + o_er);
 
@@ -697,9 +856,13 @@ kmv_status tc_backward(kmv_handle h, const KmvArgs& a, double* grad, cudaStream_
     return tc_fail(h, KMV_ECUDA, "memset failed");
   if (L.n_items > 0)
     tc_bwd_norms_kernel<<<dim3(L.n_items, L.chains), kTile, 0, st>>>(h->dev, L.chains, L.n_total, a.V, a.G, a.m,
-                                                                     gmax, vmax, gvpart, a.sys_active, a.amp);
+                                                                     gmax, vmax, gvpart, gvdiag, a.sys_active,
+                                                                     a.amp);
+  // the adjoint's operand tiles overwrite the forward's
+  S->prep_valid = false;
   if (n_items > 0) {
-    tc_launch_prep_x(h, S, a, KX, 2, base + o_xa, base + o_xb, st);
+    tc_launch_center(h, a, ckeys, st);
+    tc_launch_prep_x(h, S, a, KX, kSplitF16, ckeys, base + o_xa, base + o_xb, err, st);
     TcBwdArgs ba;
     ba.items = S->d_sym_items;
     ba.n_items = n_items;
@@ -708,11 +871,16 @@ kmv_status tc_backward(kmv_handle h, const KmvArgs& a, double* grad, cudaStream_
     ba.KX = KX;
     ba.KG = KG;
     ba.NB = NB;
-    ba.qcol = qcol;
+    ba.ksplit = best.ksplit;
+    ba.NACC = best.NACC;
+    ba.toff = best.toff;
+    ba.qcol = best.qcol;
     ba.S = stages;
+    ba.n_inst = L.n_inst;
     ba.d = a.d;
     ba.n_theta = a.n_theta;
     ba.ard = a.ard;
+    ba.ckeys = ckeys;
     ba.L = h->dev;
     ba.T = S->dev;
     ba.x = a.x;
@@ -733,8 +901,9 @@ kmv_status tc_backward(kmv_handle h, const KmvArgs& a, double* grad, cudaStream_
     for (int ch = 0; ch < n_chunks; ++ch) {
       const int c0 = ch * mc, mcc = std::min(mc, a.m - c0);
       tc_prep_bwd_kernel<<<dim3(S->T_total, L.chains), 128, 0, st>>>(
-          h->dev, S->dev, L.chains, a.d, a.ard, a.n_theta, a.m, c0, mcc, KG, NB, qcol, S->T_total, a.x, a.theta,
-          a.V, a.G, L.n_total, gmax, vmax, a.sys_active, a.amp, base + o_gi, base + o_vj, base + o_bg, err);
+          h->dev, S->dev, L.n_inst, L.chains, a.d, a.ard, a.n_theta, a.m, c0, mcc, KG, NB, best.ksplit, best.NACC,
+          best.toff, best.qcol, S->T_total, a.x, a.theta, ckeys, a.V, a.G, L.n_total, gmax, vmax, a.sys_active,
+          a.amp, base + o_gi, base + o_vj, base + o_bg, err);
       ba.chunk = ch;
       ProfScope prof(h, KMV_KERNEL_ADJOINT, st);
       if (xs)
@@ -744,8 +913,8 @@ kmv_status tc_backward(kmv_handle h, const KmvArgs& a, double* grad, cudaStream_
     }
   }
   tc_bwd_finalize_kernel<<<n_sys, kFinThreads, 0, st>>>(h->dev, S->dev.sym_pref, n_items, n_chunks, L.chains,
-                                                         a.n_theta, a.ard, a.d, a.theta, gpart, gvpart, gmax, vmax,
-                                                         a.sys_active, err, grad);
+                                                         a.n_theta, a.ard, a.d, a.theta, gpart, gvpart, gvdiag, gmax,
+                                                         vmax, a.sys_active, err, grad);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return tc_fail(h, KMV_ECUDA, cudaGetErrorString(e));
   if (a.Y != nullptr) {

@@ -6,6 +6,7 @@
 
 #include <vector>
 
+#include "exp2_poly.cuh"
 #include "kmv_internal.cuh"
 
 namespace kmv {
@@ -19,9 +20,19 @@ constexpr size_t kMinSmem = 120 * 1024;  // keeps one CTA (and one TMEM allocati
 constexpr size_t kMaxSmem = 227 * 1024;
 
 __host__ __device__ constexpr int round16(int v) { return (v + 15) / 16 * 16; }
-// X operand width: 3 d (two-way split) or 6 d (three-way split) product terms
+// How the X operand tiles carry xh (the scaled, centred point):
+//   kSplitBf2: xh = hi + lo in BF16, products hi.hi + hi.lo + lo.hi (|dS| ~ 2^-16 |xh|^2)
+//   kSplitBf3: xh = h + m + l in BF16, six products (|dS| ~ 2^-24 |xh|^2)
+//   kSplitF16: xh = hi + lo in F16, three products (|dS| ~ 2^-24 |xh|^2 at the
+//              depth of kSplitBf2; needs |xh_k| < 240 and |xh|^2 / 2 < 2^15)
+constexpr int kSplitBf2 = 2, kSplitBf3 = 3, kSplitF16 = 4;
+// X operand width: 3 d (two-way splits) or 6 d (three-way split) product terms
 // + 6 bias/one columns, rounded to the MMA K step.
-__host__ __device__ constexpr int x_width(int d, int nsplit = 2) { return round16((nsplit == 3 ? 6 : 3) * d + 6); }
+__host__ __device__ constexpr int x_width(int d, int nsplit = kSplitBf2) {
+  return round16((nsplit == kSplitBf3 ? 6 : 3) * d + 6);
+}
+// Largest |xh|^2 / 2 the F16 operands hold (the bias is split in three F16 terms).
+constexpr float kF16BiasMax = 32768.f;
 
 struct TcTables {
   const int32_t* tile_inst;    // T_total
@@ -34,10 +45,30 @@ struct TcTables {
 
 
 
+// Tile choices of one tensor-core kernel (kmv_tiles of the C ABI).
+struct TcTiles {
+  int stages = 0;        // operand-ring stages, 0 = as many as shared memory holds
+  int items_per_sm = 6;  // work items per SM the plan aims at
+  int exp_split = 0;     // 0: every exp on the MUFU; k: one element in k on the FMA pipe
+};
+// kernel kinds of the tile table (kmv_tile_kernel)
+constexpr int kTilesForward = 0, kTilesForwardFma = 1, kTilesAdjoint = 2, kTilesKinds = 3;
+// A tuned choice for one call shape: kernel kind, d, columns per launch and
+// the largest instance's size class (floor(log2 N_b)).
+struct TcTuned {
+  int kind, d, m, nlog2;
+  TcTiles t;
+  double ms;
+};
+
 struct TcState {
+  // tile choices: per-kernel defaults, and tuned entries matched by shape
+  TcTiles tiles[kTilesKinds];
+  std::vector<TcTuned> tuned;
   // plan key
   std::vector<int64_t> offsets;
   int chains = -1;
+  int plan_ipsm_fwd = -1, plan_ipsm_adj = -1;
   // plan
   int T_total = 0, n_items = 0;
   std::vector<int4> items;
@@ -55,6 +86,12 @@ struct TcState {
   void* buf = nullptr;
   size_t buf_bytes = 0;
   int* err = nullptr;
+  // what the XA / XB tiles at the start of the workspace hold (tc_forward):
+  // valid only until another tensor-core call or a workspace change
+  bool prep_valid = false;
+  const double* prep_theta = nullptr;
+  const float* prep_x = nullptr;
+  int prep_nsplit = 0, prep_d = 0;
   int num_sms = 0;
   bool attr_set = false;
   bool bwd_attr_set = false;
@@ -63,17 +100,60 @@ struct TcState {
 
 
 TcState* tc_state(kmv_handle h);
+// The tiles a call of the given kernel kind and shape runs with: a tuned entry
+// for (kind, d, m, size class of the largest instance), else the default.
+TcTiles tc_tiles_for(kmv_handle h, int kind, int d, int m);
 kmv_status tc_fail(kmv_handle h, kmv_status s, const char* msg);
-kmv_status tc_build_plan(kmv_handle h, TcState* S, cudaStream_t st);
+// Builds (or keeps) the work plans of the forward and the symmetric adjoint for
+// the handle's layout, aiming at ipsm_* work items per SM (<= 0: keep the
+// current value, else the default).
+kmv_status tc_build_plan(kmv_handle h, TcState* S, int ipsm_fwd, int ipsm_adj, cudaStream_t st);
 kmv_status tc_ensure_buf(kmv_handle h, TcState* S, size_t bytes);
-// Writes the XA / XB operand tiles of every (chain, padded tile).
-// nsplit = 2: x = hi + lo, products hi.hi + hi.lo + lo.hi (|dS| ~ 2^-16 |x|^2);
-// nsplit = 3: x = h + m + l, products hh + hm + mh + hl + lh + mm (|dS| ~ 2^-24 |x|^2).
-void tc_launch_prep_x(kmv_handle h, TcState* S, const KmvArgs& a, int KX, int nsplit, uint8_t* XA, uint8_t* XB,
-                      cudaStream_t st);
+// Per-instance centre of the points: c_k = (min_k + max_k) / 2 over the
+// instance's rows.  The kernel depends on differences only, so centring is
+// exact; it shrinks |xh| and with it the rounding of the expanded exponent
+// S = xh_i.xh_j - |xh_i|^2/2 - |xh_j|^2/2.  Min and max are kept as
+// order-preserving integer keys, so the atomics give the same centre in any
+// order.  keys: 2 n_inst d words, [min keys | max keys].
+size_t tc_center_bytes(const Layout& L);
+void tc_launch_center(kmv_handle h, const KmvArgs& a, uint32_t* keys, cudaStream_t st);
+// Writes the XA / XB operand tiles of every (chain, padded tile) in the given
+// split mode (kSplit*), from the centred points.  err (kSplitF16 only): set to
+// 101 when a row leaves the F16 range.
+void tc_launch_prep_x(kmv_handle h, TcState* S, const KmvArgs& a, int KX, int nsplit, const uint32_t* ckeys,
+                      uint8_t* XA, uint8_t* XB, int* err, cudaStream_t st);
 // Y = alpha * sum_k part / colscale + (sigma^2 + shift) V over the product rows of a.
 void tc_launch_epilogue(kmv_handle h, TcState* S, const KmvArgs& a, int c0, int mz, const double* part,
                         const uint32_t* colmax, const int* err, cudaStream_t st);
+
+// Order-preserving map float -> uint32 (larger float, larger key), and back.
+__device__ __forceinline__ uint32_t fkey(float f) {
+  const uint32_t u = __float_as_uint(f);
+  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float fkey_dec(uint32_t k) {
+  return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k);
+}
+// Centre of dimension k of instance b from the keys of tc_launch_center.
+__device__ __forceinline__ float center_of(const uint32_t* keys, int n_inst, int d, int b, int k) {
+  return 0.5f * (fkey_dec(keys[(size_t)b * d + k]) + fkey_dec(keys[((size_t)n_inst + b) * d + k]));
+}
+
+// 2^s for s <= 0 on the FMA pipe, the companion of the MUFU ex2 for a share of
+// the elements.  s = n + f with n = round(s) and |f| <= 1/2 (the reduction of
+// Cody and Waite; for base 2 it is exact), n taken from the low bits of
+// s + 1.5 2^23, 2^f from the degree-DEG minimax polynomial of exp2_poly.cuh
+// (Horner), and 2^n added to the exponent field.  Arguments below -125 give
+// 2^-125 or less (the products treat them as 0).
+template <int DEG>
+__device__ __forceinline__ float exp2_fma(float s) {
+  static_assert(DEG == 3 || DEG == 5, "exp2_poly.cuh holds degrees 3 and 5");
+  const float t = fmaxf(s, -125.f);
+  const float r = __fadd_rn(t, 12582912.f);
+  const float f = __fsub_rn(t, __fsub_rn(r, 12582912.f));
+  const float p = DEG == 3 ? exp2_poly3(f) : exp2_poly5(f);
+  return __uint_as_float(__float_as_uint(p) + (__float_as_uint(r) << 23));
+}
 
 __device__ __forceinline__ uint8_t* align1024(uint8_t* p) {
   return reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(p) + 1023) & ~uintptr_t(1023));

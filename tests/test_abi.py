@@ -108,3 +108,35 @@ def test_argument_errors_need_no_device(so):
     assert so.kmv_accept(4, 3, None, None, None, None, None, None, None, None) == EINVAL
     assert so.kmv_status_merge(-1, None, None, None) == EINVAL
     assert so.kmv_backward_noalloc(None, 1, None, None, None, 1, None, None, None) == EINVAL
+
+
+def test_noalloc_applies_the_common_point_rules(so):
+    """kmv_backward_noalloc checks the point set by the same rules as the
+    handle-based entry points (before any CUDA call): too many systems
+    (n_inst * chains > 2^30), too many rows, decreasing offsets; and the tile
+    calls reject a NULL handle."""
+    from paper_2412_20884_gb300 import binding
+    f = so.kmv_backward_noalloc
+    f.restype, f.argtypes = binding._SIGS["kmv_backward_noalloc"]
+    EINVAL = 1
+    dummy = ctypes.c_void_p(16)   # never dereferenced: the checks fail first
+
+    def pts(offsets, d=2):
+        arr = (ctypes.c_int64 * len(offsets))(*offsets)
+        p = binding._Points(len(offsets) - 1, ctypes.cast(arr, ctypes.POINTER(ctypes.c_int64)), d, 1, dummy, 0)
+        return p, arr
+
+    # 2^15 empty instances x 2^15 + 1 chains: more than 2^30 systems, yet tiny scratch
+    n_inst = 1 << 15
+    p, keep = pts([0] * (n_inst + 1))
+    assert f(ctypes.byref(p), (1 << 15) + 1, dummy, dummy, dummy, 1, dummy, None, None) == EINVAL
+    p, keep = pts([0, 10, 5])
+    assert f(ctypes.byref(p), 1, dummy, dummy, dummy, 1, dummy, None, None) == EINVAL
+    p, keep = pts([0, (1 << 40) + 1])
+    assert f(ctypes.byref(p), 1, dummy, dummy, dummy, 1, dummy, None, None) == EINVAL
+    for name in ("kmv_set_tiles", "kmv_get_tiles"):
+        g = getattr(so, name)
+        g.restype, g.argtypes = binding._SIGS[name]
+        assert g(None, 0, None) == EINVAL
+    so.kmv_autotune.restype, so.kmv_autotune.argtypes = binding._SIGS["kmv_autotune"]
+    assert so.kmv_autotune(None, None, 1, None, 1, None, None) == EINVAL

@@ -123,3 +123,48 @@ def test_preconditioned_graph_replay_equals_eager(kmv_handle):
         assert torch.equal(th_ig, th_ie) and torch.equal(pi_ig, pi_ie)
     finally:
         kmv_handle.set_preconditioner(pts)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16_hilo"])
+def test_captured_solves_stop_at_convergence(kmv_handle, prec):
+    """A captured solve is a conditional WHILE node: the replay stops when every
+    system has converged, so raising cg_maxiter from 200 to 4000 (both far
+    above the ~10^2 iterations these solves need) leaves the replay time
+    unchanged, and the FP32 replay equals the eager run bitwise."""
+    import time
+    pts, theta0, y, phi, pi0 = _inputs(83)
+    dt, steps = 0.02, 2
+    th_e, pi_e = theta0.clone(), pi0.clone()
+    for _ in range(steps):
+        st, _, _ = kmv_handle.leapfrog_step(pts, y, phi, th_e, pi_e, dt, cg_maxiter=4000, prec=prec)
+        assert torch.all(st == 0)
+    times, finals = {}, {}
+    for maxit in (200, 4000):
+        th_g, pi_g = theta0.clone(), pi0.clone()
+        xw = torch.empty_like(phi)
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            kmv_handle.leapfrog_step(pts, y, phi, theta0.clone(), pi0.clone(), dt, cg_maxiter=maxit, x_work=xw,
+                                     prec=prec)
+        torch.cuda.current_stream().wait_stream(side)
+        torch.cuda.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            for _ in range(steps):
+                kmv_handle.leapfrog_step(pts, y, phi, th_g, pi_g, dt, cg_maxiter=maxit, x_work=xw, prec=prec)
+        best = 1e9
+        for _ in range(3):
+            th_g.copy_(theta0)
+            pi_g.copy_(pi0)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            graph.replay()
+            torch.cuda.synchronize()
+            best = min(best, time.perf_counter() - t0)
+        times[maxit] = best
+        finals[maxit] = (th_g.clone(), pi_g.clone())
+    assert times[4000] < 1.5 * times[200] + 2e-3, times
+    assert torch.equal(finals[200][0], finals[4000][0])
+    if prec == "fp32":
+        assert torch.equal(finals[4000][0], th_e) and torch.equal(finals[4000][1], pi_e)

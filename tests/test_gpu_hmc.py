@@ -61,8 +61,9 @@ def _lf_inputs(w, seed):
     return _phi(w, seed), pi0
 
 
+@pytest.mark.parametrize("prec", ["fp32", "bf16_hilo"])
 @pytest.mark.parametrize("ard", [False, True])
-def test_leapfrog_step_matches_oracle(kmv_handle, ard):
+def test_leapfrog_step_matches_oracle(kmv_handle, ard, prec):
     w = wl.ragged([260, 140], d=2, chains=2, m=1, ard=ard, seed=53, sigma2=0.1)
     pts, theta, _, _ = to_dev(w)
     phi, pi0 = _lf_inputs(w, 54)
@@ -72,7 +73,7 @@ def test_leapfrog_step_matches_oracle(kmv_handle, ard):
     pi = torch.tensor(pi0, dtype=torch.float64, device="cuda")
     pr = tuple(torch.tensor(a, dtype=torch.float64, device="cuda") for a in prior)
     st, it, _ = kmv_handle.leapfrog_step(pts, y, torch.tensor(phi, device="cuda"), th, pi, 0.05,
-                                         prior=pr, cg_tol=1e-7, cg_maxiter=2000)
+                                         prior=pr, cg_tol=1e-7, cg_maxiter=2000, prec=prec)
     assert torch.all(st == 0)
     th, pi = th.cpu().numpy(), pi.cpu().numpy()
     X, yh = f32(w.X), f32(w.y)
@@ -83,13 +84,14 @@ def test_leapfrog_step_matches_oracle(kmv_handle, ard):
             t_o, p_o = ohmc.leapfrog(X[r0:r1], yh[r0:r1], f32(phi[c, r0:r1]), w.theta[s], pi0[s], 0.05,
                                      ard, {"mu": prior[0], "prec": prior[1]})
             F_scale = np.abs(ohmc.force(X[r0:r1], yh[r0:r1], f32(phi[c, r0:r1]), w.theta[s], ard)).max()
-            # force error budget: FP32 operator (1e-4 relative gradients) + solve at cg_tol
+            # force error budget: the adjoint (1e-4 relative gradients) + solve at cg_tol
             tol_F = 1e-3 * max(F_scale, 1.0)
             np.testing.assert_allclose(pi[s], p_o, atol=0.05 * tol_F, rtol=0)
             np.testing.assert_allclose(th[s], t_o, atol=0.5 * 0.05 ** 2 * tol_F + 1e-12, rtol=0)
 
 
-def test_leapfrog_free_mask_and_reversibility(kmv_handle):
+@pytest.mark.parametrize("prec", ["fp32", "bf16_hilo"])
+def test_leapfrog_free_mask_and_reversibility(kmv_handle, prec):
     w = wl.ragged([300], d=1, chains=3, m=1, ard=False, seed=55, sigma2=0.1)
     pts, theta, _, _ = to_dev(w)
     phi, pi0 = _lf_inputs(w, 56)
@@ -100,11 +102,13 @@ def test_leapfrog_free_mask_and_reversibility(kmv_handle):
     th = theta.clone()
     pi = torch.tensor(pi0, dtype=torch.float64, device="cuda")
     for _ in range(3):
-        kmv_handle.leapfrog_step(pts, y, ph, th, pi, 0.05, free_mask=mask, cg_tol=1e-7, cg_maxiter=2000)
+        kmv_handle.leapfrog_step(pts, y, ph, th, pi, 0.05, free_mask=mask, cg_tol=1e-7, cg_maxiter=2000,
+                                 prec=prec)
     assert torch.equal(th[:, 2], theta[:, 2])
     pi.neg_()
     for _ in range(3):
-        kmv_handle.leapfrog_step(pts, y, ph, th, pi, 0.05, free_mask=mask, cg_tol=1e-7, cg_maxiter=2000)
+        kmv_handle.leapfrog_step(pts, y, ph, th, pi, 0.05, free_mask=mask, cg_tol=1e-7, cg_maxiter=2000,
+                                 prec=prec)
     pi.neg_()
     np.testing.assert_allclose(th.cpu().numpy(), w.theta, atol=2e-5)
     np.testing.assert_allclose(pi.cpu().numpy(), pi0, atol=2e-4)
@@ -168,7 +172,9 @@ def test_leapfrog_force_with_cancelling_quadratic_forms(kmv_handle, prec):
     """On c1 (N = 2048, sigma^2 = 0.01) x = A^-1 y oscillates and the two
     quadratic forms of the force are sums of N^2 terms that cancel to ~1e-7 of
     their size.  Both forms must still give the oracle's step: the force is the
-    FP32 adjoint in either precision (the solve is refined in the BF16 form)."""
+    adjoint of the call's precision (in the BF16 form the tensor-core adjoint,
+    whose split operands keep each pair's term near FP32 accuracy; the solve is
+    refined against the FP32 operator)."""
     w = wl.c1()
     pts, theta, _, _ = to_dev(w)
     X, yh = f32(w.X), f32(w.y)

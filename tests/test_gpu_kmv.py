@@ -1,12 +1,8 @@
 """GPU parity of kmv_forward / kmv_backward against the FP64 oracle, through the C ABI.
 
-Tolerances:
+Tolerances (the stated targets of the method's GPU form):
   fp32       outputs 1e-5 componentwise, gradients 1e-4
-  bf16_hilo  outputs 2e-3 componentwise, gradients 2e-2.  The BF16 adjoint
-             rounds Q = W K0 to F16 (2^-12) and carries the ~1e-4 relative
-             error of the hi/lo exponent; gradient components that nearly
-             cancel over the N^2 pairs (random G, V) lose up to ~1e-2 of their
-             value to that rounding, typical components ~2e-4.
+  bf16_hilo  outputs 2e-3 componentwise, gradients 1e-4
 Componentwise error of Y is |Y - Y*| / (sum_j |A_ij| |V_j|); gradient error is
 |g - g*| / max(|g*|, 1e-3 ||g*||_inf).  The oracle sees the FP32-rounded inputs.
 """
@@ -22,7 +18,7 @@ from helpers import to_dev, f32, abs_row_products, componentwise_err, grad_err
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"fp32": (1e-5, 1e-4), "bf16_hilo": (2e-3, 2e-2)}
+TOL = {"fp32": (1e-5, 1e-4), "bf16_hilo": (2e-3, 1e-4)}
 PRECS = ["fp32", "bf16_hilo"]
 
 
@@ -232,3 +228,23 @@ def test_many_tiles_per_cta(kmv_handle, prec, m):
     w = wl.ragged([6000, 2192], d=4, chains=1, m=m, ard=True, seed=61)
     _check_forward(kmv_handle, w, prec)
     _check_backward(kmv_handle, w, prec)
+
+
+@pytest.mark.parametrize("case", [c for c in CASES if c[3] <= 2 and c[1] <= 17],
+                         ids=lambda c: f"N{sum(c[0])}d{c[1]}c{c[2]}m{c[3]}")
+def test_bf16_cg_product_has_fp32_accuracy(kmv_handle, case):
+    """The BF16 form's product for one or two columns (the CG iterations and the
+    energy's solves): three-way split exponent and FP32 P.v on the FMA pipe.  It
+    meets the FP32 form's 1e-5, which is why the BF16 form solves with it directly."""
+    sizes, d, chains, m, ard = case
+    w = wl.ragged(sizes, d=d, chains=chains, m=m, ard=ard, seed=sum(sizes) + d)
+    pts, theta, V, _ = to_dev(w)
+    Y = kmv_handle.kmv_forward(pts, theta, V, prec="bf16_hilo").cpu().numpy()
+    X, Vh = f32(w.X), f32(w.V)
+    for b in range(w.n_inst):
+        r0, r1 = w.offsets[b], w.offsets[b + 1]
+        for c in range(w.chains):
+            s = b * w.chains + c
+            ref = sk.kmv(X[r0:r1], w.theta[s], Vh[c, r0:r1], w.ard)
+            scale = abs_row_products(X[r0:r1], w.theta[s], Vh[c, r0:r1], w.ard, None)
+            assert componentwise_err(Y[c, r0:r1], ref, scale) <= 1e-5

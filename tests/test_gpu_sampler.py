@@ -1,7 +1,9 @@
 """Algorithm 1 on the GPU (paper_2412_20884_gb300.sampler.hmc_update: phi draw,
 energies, leapfrog steps and the Metropolis test, all through the C ABI) on the
 Sec. 4.1 verification data, against trapezoid quadrature of Eq. P computed by
-the FP64 oracle; the same settings as the oracle's own sampler test."""
+the FP64 oracle; the same settings as the oracle's own sampler test, in both
+precision forms (the BF16 form draws phi, solves and forms the force with the
+tensor-core products; the energies are FP32 in both)."""
 import json
 import math
 import os
@@ -19,7 +21,8 @@ pytestmark = pytest.mark.gpu
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "verification_sec41.json")
 
 
-def test_algorithm1_matches_quadrature(kmv_handle):
+@pytest.mark.parametrize("prec", ["fp32", "bf16_hilo"])
+def test_algorithm1_matches_quadrature(kmv_handle, prec):
     from paper_2412_20884_gb300 import Points
     from paper_2412_20884_gb300.sampler import hmc_update
     cfg = json.load(open(GOLDEN))
@@ -49,7 +52,7 @@ def test_algorithm1_matches_quadrature(kmv_handle):
         pi = torch.tensor(rng.standard_normal((B, 3)), dtype=torch.float64, device=dev)
         u = torch.tensor(1.0 - rng.uniform(size=B), dtype=torch.float64, device=dev)   # (0, 1]
         ok, fail = hmc_update(kmv_handle, pts, yd, th, cfg["leapfrog_dt"], cfg["leapfrog_n_int"], xi, pi, u,
-                              prior=prior, free_mask=free)
+                              prior=prior, free_mask=free, prec=prec)
         trace.append(th[:, :2].cpu().numpy().copy())
         acc.append(float(ok.float().mean()))
         assert int((fail != 0).sum()) == 0
