@@ -426,6 +426,8 @@ def main():
     # leapfrog steps/s (fp32 vs bf16_hilo) on the N = 2048, d = 1 workload
     if not args.no_leapfrog:
         lf = leapfrog_rates(h, dev, rank, world)
+        if rank == 0:
+            lf["c5"] = c5_full(h, dev)
         if out is not None:
             out["leapfrog"] = lf
 
@@ -545,6 +547,49 @@ def leapfrog_rates(h, dev, rank, world):
             r["hmc"] = c1_hmc(h, dev, w, pts, y)
         res["c1" if w.n_total == 2048 else "c5_n16384"] = r
     return res
+
+
+def c5_full(h, dev):
+    """The large-N workload at full size (N = 2^20, d = 3, ARD, 8 chains): the
+    CG product (m = 1) and the force's adjoint (m = 2) over all 8 chains in both
+    forms (CUDA events around each call, after a warm-up), and the device memory
+    the library and the inputs hold, against N (d + 8 chains) 4 bytes."""
+    import torch
+    import workloads as wl
+    from paper_2412_20884_gb300 import Points
+    w = wl.c5(n=1048576, chains=8)
+    torch.cuda.reset_peak_memory_stats(dev)
+    pts = Points(torch.tensor(w.X, dtype=torch.float32, device=dev), w.offsets, ard=True)
+    th = torch.tensor(w.theta, dtype=torch.float64, device=dev)
+    rng = np.random.default_rng(3)
+    V1 = torch.tensor(rng.standard_normal((8, w.n_total, 1)), dtype=torch.float32, device=dev)
+    V2 = torch.tensor(rng.standard_normal((8, w.n_total, 2)), dtype=torch.float32, device=dev)
+    G2 = torch.tensor(rng.standard_normal((8, w.n_total, 2)), dtype=torch.float32, device=dev)
+    pairs = 8 * w.n_total ** 2
+    out = {"workload": "N=1048576 d=3 x~U[0,1]^3, ARD SE (Sec. 4.2 narrowing rule, sigma2=0.1), 8 chains",
+           "pairs_per_pass": pairs}
+    stream = torch.cuda.current_stream()
+    for prec in ("bf16_hilo", "fp32"):
+        r = {}
+        for name, call in (("cg_product_m1", lambda: h.kmv_forward(pts, th, V1, prec=prec)),
+                           ("force_adjoint_m2", lambda: h.kmv_backward(pts, th, V2, G2, want_grad_V=False,
+                                                                         prec=prec))):
+            call()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            call()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            r[name] = {"ms": ms, "GPair_per_s": pairs / (ms * 1e-3) / 1e9}
+        out[prec] = r
+    out["bf16_over_fp32"] = {k: out["fp32"][k]["ms"] / out["bf16_hilo"][k]["ms"] for k in out["fp32"]}
+    held = torch.cuda.max_memory_allocated(dev) + h.workspace_bytes()
+    lin = w.n_total * (w.d + 8 * 8) * 4
+    out["device_bytes_held"] = {"inputs_and_outputs_peak": int(torch.cuda.max_memory_allocated(dev)),
+                                "library_workspace": int(h.workspace_bytes()), "total": int(held),
+                                "linear_bound_N_d_plus_8chains_x4B": int(lin), "ratio": held / lin}
+    return out
 
 
 def c1_hmc(h, dev, w, pts, y):

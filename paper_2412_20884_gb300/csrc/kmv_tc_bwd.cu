@@ -4,31 +4,41 @@
 // dimension, (xt_ik - xt_jk)^2.  Because K0 and (xt_i - xt_j)^2 are symmetric
 // in (i, j), W may be replaced by W^s = (W + W^T) / 2, and then the sum over
 // tile (J, I) equals the sum over tile (I, J): only the upper triangle of
-// tiles (J >= I) is evaluated, off-diagonal tiles weighted twice.  For a J
-// half tile (64 columns) of an I tile the MMA issuers write into TMEM
+// tiles (J >= I) is evaluated, off-diagonal tiles weighted twice.
+//
+// A work item is one I tile of one system against a range of J tiles; each J
+// tile is split into two 64-column halves, half b for warpgroup b.  The two
+// warpgroups run as independent pipelines, each with its own MMA issuer warp,
+// TMEM buffers and accumulator, sharing only the operand stages.  For its half
+// of a J tile, issuer b writes into TMEM
 //   S = XA_I XB_J^T           the base-2 exponent from F16 hi/lo operands of the
-//                             centred points (|dS| ~ 2^-24 |xh|^2)
+//                             centred points (|dS| ~ 2^-24 |xh|^2); XA from TMEM
 //   W = GI_I VJ_J^T           = G_i . V_j + V_i . G_j with GI rows
-//                             [gh gh gl vh vh vl] and VJ rows [vh vl vh gh gl gh]
-//                             (F16 hi/lo, G and V each scaled by a power of two)
-// an exp warpgroup forms Q = W 2^S in FP32 (halved on the diagonal tile, and
-// zero for i = j, whose (xt_i - xt_i)^2 is 0), splits it exactly into
-// Q = Qh + Ql with Qh holding 11 significant bits (Veltkamp's splitting), and
-// stores both as F16; the feature-sum issuer accumulates, per row i,
-//   ACC += Qh BG + Ql BG      BG: F16 hi/lo of xt_jk and of xt_jk^2 and a ones column
-//                             (the hi and lo parts either in separate accumulator
+//                             [gh gh gl vh vh vl] (shared memory, once per item)
+//                             and VJ rows [vh vl vh gh gl gh] (F16 hi/lo, G and V
+//                             each scaled by a power of two)
+// warpgroup b forms Q = W 2^S in FP32 (halved on the diagonal tile, and zero for
+// i = j, whose (xt_i - xt_i)^2 is 0), splits it exactly into Q = Qh + Ql with Qh
+// holding 11 significant bits (Veltkamp's splitting), stores both as F16, and
+// issuer b accumulates, per row i,
+//   ACC_b += Qh BG + Ql BG    BG: F16 hi/lo of xt_jk and xt_jk^2 and a ones column
+//                             (the hi and lo parts in separate accumulator
 //                             columns, or, for large d, in the same columns by
 //                             splitting the K dimension), giving
 //                             R_ik = sum_j Q_ij xt_jk, T_ik = sum_j Q_ij xt_jk^2, q_i = sum_j Q_ij
-// Every kFoldH half tiles warpgroup 0 folds, per row,
+// Every kFoldOwn own halves warpgroup b folds its accumulator, per row,
 //   sum_j Q_ij (xt_ik - xt_jk)^2 = xt_ik^2 q_i - 2 xt_ik R_ik + T_ik
-// into FP64 sums.  Because q, R and T are formed from the same Q, its rounding
-// cancels in this combination exactly as in the exact sum; leaving out the
-// diagonal keeps its large terms out of that cancellation, and its share of
-// the alpha gradient, sum_i G_i . V_i, is added exactly in FP64.  The scales of
-// G and V are removed at the end; per-warp FP64 partials are reduced per system
-// in a fixed order.  When the depth-6m operands do not fit in TMEM (large m),
-// G and V enter in blocks of columns, one launch per block.
+// into FP64 sums (short accumulations: the tensor core's FP32 accumulator drops
+// low bits at every K step).  The fold reads the accumulator right after
+// waiting for the next Q's buffer, which implies its MMAs are complete, so it
+// adds no wait of its own.  Because q, R and T are formed from the same Q, its
+// rounding cancels in this combination exactly as in the exact sum; leaving
+// out the diagonal keeps its large terms out of that cancellation, and its
+// share of the alpha gradient, sum_i G_i . V_i, is added exactly in FP64.  The
+// scales of G and V are removed at the end; per-warp FP64 partials are reduced
+// per system in a fixed order.  G and V enter in blocks of columns and the
+// feature sums in blocks of dimensions when the operands would not fit, one
+// launch per block pair.
 // dL/dV = A G is the forward product with G in place of V (kmv_tc.cu).
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
@@ -45,17 +55,16 @@
 namespace kmv {
 namespace {
 
-// Half tiles (64 columns) per FP32 accumulation of q, R, T in TMEM before the
-// FP64 fold: the tensor core's FP32 accumulation loses low bits at every K
-// step, so the sums are kept short (4 halves = 256 columns).  The two
-// warpgroups take turns at folding.
+// Own halves (64 columns each) a warpgroup accumulates in TMEM before folding
+// into FP64: the tensor core's FP32 accumulation loses low bits at every K
+// step (8 per half), so the sums are kept short (4 halves = 256 columns).
 #ifndef KMV_BWD_FOLD_HALVES
 #define KMV_BWD_FOLD_HALVES 4
 #endif
-constexpr int kFoldH = KMV_BWD_FOLD_HALVES;
-static_assert(kFoldH >= 2 && kFoldH % 2 == 0, "folds end on a half of warpgroup 1");
-constexpr int kGW = 34;      // doubles per (item, warp) gradient partial: [q, contrib_0..d-1]
-constexpr int kFoldWarps = 8;   // warps holding gradient partials (both warpgroups fold)
+constexpr int kFoldOwn = KMV_BWD_FOLD_HALVES;
+static_assert(kFoldOwn >= 1, "at least one half per fold");
+constexpr int kGW = 34;        // doubles per (item, warp) gradient partial: [q, contrib_0..d-1]
+constexpr int kFoldWarps = 8;  // warps holding gradient partials (both warpgroups fold)
 
 struct TcBwdArgs {
   const int4* items;
@@ -64,30 +73,31 @@ struct TcBwdArgs {
   int T_total;
   int KX, KG, NB, S;
   // Feature-sum layout.  ksplit = 0: BG has NB = NACC features, per dimension
-  // k the columns 4k..4k+3 = [xh, xl, sh, sl], and the ones column qcol = 4d;
-  // the accumulator has the same NACC columns.  ksplit = 1: BG has 2 NACC
-  // features, a hi block [xh_k at k, sh_k at toff + k, 1 at qcol = 2 toff] and a
-  // lo block of the same layout at feature NACC; the accumulator has NACC columns.
-  int ksplit, NACC, toff;
-  int qcol;   // accumulator column of q_i (the ones column of BG)
-  int chunk;  // index of this launch's block of G, V columns (partials are per block)
-  int n_inst;
-  int d, n_theta, ard;
-  const uint32_t* ckeys;   // per-instance centre keys (tc_launch_center)
-  DevLayout L;
-  TcTables T;
-  const float* x;
-  const double* theta;
+  // kk of the block the columns 4kk..4kk+3 = [xh, xl, sh, sl], and the ones
+  // column qcol = 4 dk; the accumulator has the same NACC columns.  ksplit = 1:
+  // BG has 2 NACC features, a hi block [xh_kk at kk, sh_kk at toff + kk, 1 at
+  // qcol = 2 toff] and a lo block of the same layout at feature NACC; the
+  // accumulator has NACC columns.
+  int ksplit, NACC, toff, qcol;
+  int k0, dk;   // dimensions [k0, k0 + dk) of this launch; q enters the alpha sum when k0 == 0
+  int chunk;    // index of this launch's (column block, dimension block) (partials are per chunk)
+  int d;
   const uint8_t* XA;
   const uint8_t* XB;
   const uint8_t* GI;
   const uint8_t* VJ;
   const uint8_t* BG;
-  double* gpart;   // (column blocks, n_items, 4 warps, kGW)
-  int m;
+  double* gpart;   // (chunks, n_items, 8 warps, kGW)
   const int32_t* sys_active;
   int* err;
 };
+
+// K = 64 from TMEM (four K = 16 steps of 8 columns each).
+__device__ __forceinline__ void issue_ts4(uint32_t d_tmem, uint32_t a_tmem, uint64_t db, uint32_t idesc,
+                                          uint32_t acc) {
+#pragma unroll
+  for (int k = 0; k < 4; ++k) ptx::mma_ts(d_tmem, a_tmem + 8 * k, db + 16 * k, idesc, (k > 0) || acc);
+}
 
 // Power-of-two factor putting a largest row norm just below 2^7, so that the
 // F16 operands of G and V hold every element and |W^s| <= 2 2^7 2^7 = 2^15.
@@ -110,36 +120,21 @@ __device__ __forceinline__ void split_q(float q, float& hi, float& lo) {
   lo = __fsub_rn(q, hi);
 }
 
-// K = 64 from TMEM (four K = 16 steps of 8 columns each).
-__device__ __forceinline__ void issue_ts4(uint32_t d_tmem, uint32_t a_tmem, uint64_t db, uint32_t idesc,
-                                          uint32_t acc) {
-#pragma unroll
-  for (int k = 0; k < 4; ++k) ptx::mma_ts(d_tmem, a_tmem + 8 * k, db + 16 * k, idesc, (k > 0) || acc);
-}
-
+// Warps: 0-7 the two warpgroups, 8 the issuer of warpgroup 0 (and TMEM owner),
+// 9 the producer, 10 the issuer of warpgroup 1.  TMEM (512 columns):
+//   S_b [128 b, +64), W_b [128 b + 64, +64), Qh_b [256 + 64 b, +32), Ql_b [+32, +32),
+//   XA [384, 384 + KX/2) unless XS, ACC_b [512 - 2 NACC + b NACC, +NACC).
+// Shared memory: the item's GI tile, the item's XA tile when XS (large d), and
+// the stages [XB | VJ | BG] of the J tiles.
+constexpr int kTsThreads = 352;
 constexpr int kBwdIssue1Warp = 10;
-
-// One I tile at a time over the upper triangle of tiles.  S and W are MMAs on
-// 64-column J halves; warpgroup b takes J columns [64 b, 64 b + 64) of every J
-// tile, in its own S, W buffer, so the MMAs of one warpgroup's next half run
-// while the other warpgroup computes.  The I tile's GI rows are resident in
-// TMEM and its XA rows too when they fit (XS = false): A-from-TMEM MMAs read
-// only the 64-row J half from shared memory.  Otherwise (XS, large d) XA is a
-// shared-memory tile loaded once per item.  Warps: 0-7 the warpgroups, 8 issues
-// S, W for buffer 0 (and owns TMEM), 9 is the producer, 10 issues S, W for
-// buffer 1, 11 issues the feature sums.  TMEM (512 columns):
-//   S_b [128 b, 128 b + 64), W_b [128 b + 64, 128 b + 128), Qh_b [256 + 32 b, +32),
-//   Ql_b [320 + 32 b, +32), XA [384, 384 + KX/2) unless XS, GI after it,
-//   ACC [512 - NACC, 512);
-// the host picks XS and the number of columns of G, V per launch so that these
-// fit.  Warpgroup 0 folds the accumulator into FP64 per-warp sums.
-constexpr int kTsThreads = 384;
-constexpr int kAccWarp = 11;
-constexpr int kTsCols = 128;   // columns for XA, GI and ACC
 constexpr int kMaxDT = 32;     // d <= 32
 constexpr int kXaRegs = 48;    // 32-bit words of an XA row holding the 3 d split values (d <= 32)
 constexpr int kTsBarBytes = 512;                       // mbarriers, TMEM slot, abort flag
 constexpr int kTsFoldBytes = kFoldWarps * kGW * 8;     // per-warp FP64 fold sums of both warpgroups
+constexpr uint32_t kColXA = 384;
+
+__host__ __device__ constexpr size_t al1k(size_t v) { return (v + 1023) & ~size_t(1023); }
 
 template <bool XS>
 __global__ void __launch_bounds__(kTsThreads, 1) tc_bwd_ts_kernel(TcBwdArgs a) {
@@ -149,48 +144,46 @@ __global__ void __launch_bounds__(kTsThreads, 1) tc_bwd_ts_kernel(TcBwdArgs a) {
   const uint32_t XT = a.KX * 256u, GT = a.KG * 256u, BT = a.NB * 256u;
   const uint32_t STG = XT + GT + BT;   // one stage: XB, VJ, BG of a J tile
   const int S = a.S;
-  uint8_t* sXA = smem;                 // XS: the item's XA tile
-  uint8_t* sS = smem + (XS ? ((XT + 1023u) & ~1023u) : 0u);
+  uint8_t* sGI = smem;                                            // the item's GI tile
+  uint8_t* sXA = sGI + al1k(GT);                                  // XS: the item's XA tile
+  uint8_t* sS = sXA + (XS ? al1k(XT) : 0u);                       // stages
   uint64_t* full = reinterpret_cast<uint64_t*>(sS + S * STG);
-  uint64_t* empty = full + S;
-  uint64_t* a_ready = empty + S;     // GI (and XA) of the item stored in TMEM (256 arrivals)
+  uint64_t* empty = full + S;        // both issuers done with the stage (2 commits)
+  uint64_t* a_ready = empty + S;     // XA of the item stored in TMEM (128 arrivals of warpgroup 0)
   uint64_t* seg = a_ready + 1;       // both warpgroups finished the previous item (256)
-  uint64_t* s_full = seg + 1;        // [b] S_b, W_b written
-  uint64_t* s_free = s_full + 2;     // [b] S_b, W_b loaded into registers
+  uint64_t* sw_full = seg + 1;       // [b] S_b, W_b written
+  uint64_t* s_free = sw_full + 2;    // [b] S_b, W_b loaded into registers
   uint64_t* q_ready = s_free + 2;    // [b] Q_b written
-  uint64_t* q_free = q_ready + 2;    // [b] Q_b consumed by the feature sums
-  uint64_t* o_ready = q_free + 2;    // [warpgroup] accumulator of a fold complete, for the folding warpgroup
-  uint64_t* o_free = o_ready + 2;    // [warpgroup] accumulator read
-  uint64_t* done = o_free + 2;       // [issuer], 3
-  uint64_t* xa_full = done + 3;      // XS: XA tile landed
-  uint64_t* xa_empty = xa_full + 1;  // XS: both S issuers done with it (2 arrivals)
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(xa_empty + 1);
+  uint64_t* q_free = q_ready + 2;    // [b] the feature sums of Q_b done
+  uint64_t* done = q_free + 2;       // [issuer b]
+  uint64_t* xa_full = done + 2;      // XS: XA tile landed
+  uint64_t* xa_empty = xa_full + 1;  // XS: both issuers done with it (2 commits)
+  uint64_t* gi_full = xa_empty + 1;  // GI tile landed
+  uint64_t* gi_empty = gi_full + 1;  // both issuers done with it (2 commits)
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(gi_empty + 1);
   volatile int* abort = reinterpret_cast<volatile int*>(tslot + 1);
   // FP64 fold sums, [warpgroup * 4 + warp][q, contrib_0 .. contrib_{d-1}]
   double* wpart = reinterpret_cast<double*>(reinterpret_cast<uint8_t*>(full) + kTsBarBytes);
-  const uint32_t colA = 384, colG = XS ? 384 : 384 + a.KX / 2, colACC = 512 - a.NACC;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
     for (int i = 0; i < S; ++i) {
       mbar_init(&full[i], 1);
-      mbar_init(&empty[i], 1);
+      mbar_init(&empty[i], 2);
     }
-    mbar_init(a_ready, 256);
+    mbar_init(a_ready, 128);
     mbar_init(seg, 256);
     for (int b = 0; b < 2; ++b) {
-      mbar_init(&s_full[b], 1);
+      mbar_init(&sw_full[b], 1);
       mbar_init(&s_free[b], 128);
       mbar_init(&q_ready[b], 128);
       mbar_init(&q_free[b], 1);
+      mbar_init(&done[b], 1);
     }
-    for (int b = 0; b < 2; ++b) {
-      mbar_init(&o_ready[b], 1);
-      mbar_init(&o_free[b], 128);
-    }
-    for (int i = 0; i < 3; ++i) mbar_init(&done[i], 1);
     mbar_init(xa_full, 1);
     mbar_init(xa_empty, 2);
+    mbar_init(gi_full, 1);
+    mbar_init(gi_empty, 2);
     *abort = 0;
     fence_barrier_init();
   }
@@ -203,29 +196,33 @@ __global__ void __launch_bounds__(kTsThreads, 1) tc_bwd_ts_kernel(TcBwdArgs a) {
   tc_fence_after();
   const uint32_t tbase = *tslot;
 
-  // The producer and issuer warps run their loops with all 32 lanes, so that
-  // addresses and descriptors stay warp-uniform, and one elected lane issues
-  // the copies, MMAs and commits: issuing from a lone lane was measured at
-  // 2-3x the cost per tcgen05.mma.
   if (warp == kLoadWarp) {
-    const bool leader = elect_one();
     // ------------------------------------------------------------ producer
-    int n_issued = 0, n_xa = 0;
+    const bool leader = elect_one();
+    int n_issued = 0, n_items_done = 0;
     uint32_t stage = 0, sph = 0;
     bool aborted = false;
     for (int t = blockIdx.x; t < a.n_items && !aborted; t += gridDim.x) {
       const int4 item = a.items[t];
       if (a.sys_active && !a.sys_active[item.x]) continue;
       const int c = item.x % a.chains;
+      const size_t ti = (size_t)c * a.T_total + item.y;
+      const uint32_t ip = (uint32_t)(n_items_done & 1) ^ 1u;
       if (XS) {
-        if (!warp_wait(xa_empty, (uint32_t)(n_xa & 1) ^ 1u, abort, a.err, 33)) { aborted = true; break; }
+        if (!warp_wait(xa_empty, ip, abort, a.err, 33)) { aborted = true; break; }
         if (leader) {
           mbar_arrive_expect_tx(xa_full, XT);
-          bulk_g2s(sXA, a.XA + ((size_t)c * a.T_total + item.y) * XT, XT, xa_full);
+          bulk_g2s(sXA, a.XA + ti * XT, XT, xa_full);
         }
         __syncwarp();
-        ++n_xa;
       }
+      if (!warp_wait(gi_empty, ip, abort, a.err, 35)) { aborted = true; break; }
+      if (leader) {
+        mbar_arrive_expect_tx(gi_full, GT);
+        bulk_g2s(sGI, a.GI + ti * GT, GT, gi_full);
+      }
+      __syncwarp();
+      ++n_items_done;
       for (int j = 0; j < item.w; ++j) {
         if (!warp_wait(&empty[stage], sph ^ 1, abort, a.err, 22)) { aborted = true; break; }
         if (leader) {
@@ -242,34 +239,64 @@ __global__ void __launch_bounds__(kTsThreads, 1) tc_bwd_ts_kernel(TcBwdArgs a) {
       }
     }
     if (aborted) {
+      // the copies already issued must land before the CTA exits
       for (int k = 1; k <= min(n_issued, S); ++k) {
         const int idx = n_issued - k;
         mbar_drain(&full[idx % S], (idx / S) & 1, 500000000ull);
       }
-      if (XS && n_xa > 0) mbar_drain(xa_full, (uint32_t)(n_xa - 1) & 1u, 500000000ull);
+      if (n_items_done > 0) {
+        if (XS) mbar_drain(xa_full, (uint32_t)(n_items_done - 1) & 1u, 500000000ull);
+        mbar_drain(gi_full, (uint32_t)(n_items_done - 1) & 1u, 500000000ull);
+      }
     }
   } else if (warp == kMmaWarp || warp == kBwdIssue1Warp) {
-    // ------------------------------------------------------------ S, W issuer of buffer b
+    // ------------------------------------------------------------ issuer of warpgroup b
+    // Per own half k of the item: S(k), W(k) once the warpgroup has read
+    // S(k-1), W(k-1); then the feature sums of Q(k-1) once it is written.
     const bool leader = elect_one();
     const int b = warp == kMmaWarp ? 0 : 1;
     const uint32_t idSW = idesc_f16(128, 64, 0, 0);
+    const uint32_t idA = idesc_f16(128, a.NACC, 0, 0);
     const int nkx = a.KX / 16, nkg = a.KG / 16;
     const uint64_t dXA = sdesc(smem_u32(sXA), 128, a.KX * 16u);
+    const uint64_t dGI = sdesc(smem_u32(sGI), 128, a.KG * 16u);
     const uint64_t dXB = sdesc(smem_u32(sS + b * a.KX * 128u), 128, a.KX * 16u);
     const uint64_t dVJ = sdesc(smem_u32(sS + XT + b * a.KG * 128u), 128, a.KG * 16u);
-    const uint32_t tS = tbase + 128 * b, tA = tbase + colA, tG = tbase + colG;
-    int u = 0, uses = 0;
+    const uint64_t dBG = sdesc(smem_u32(sS + XT + GT + b * 1024u), 128, 2048);
+    const uint32_t lo_bytes = (uint32_t)a.NACC * 256u;   // ksplit: the lo block of BG
+    const uint32_t tS = tbase + 128 * b, tW = tS + 64, tA = tbase + kColXA;
+    const uint32_t tQh = tbase + 256 + 64 * b, tQl = tQh + 32;
+    const uint32_t tACC = tbase + 512 - 2 * a.NACC + b * a.NACC;
+    int it = 0;
+    long long uses = 0, qr = 0;
     uint32_t stage = 0, sph = 0;
-    for (int t = blockIdx.x; t < a.n_items; t += gridDim.x, ++u) {
-      const int4 item = a.items[t];
-      if (a.sys_active && !a.sys_active[item.x]) {
-        --u;
-        continue;
+    // the feature sums of own half jj (stored in Q_b), from stage st_
+    auto issue_acc = [&](uint32_t st_, int jj) -> bool {
+      if (!warp_wait(&q_ready[b], (uint32_t)(qr & 1), abort, a.err, 26)) return false;
+      ++qr;
+      tc_fence_after();
+      const uint32_t acc = (jj % kFoldOwn) != 0;
+      const uint64_t dbg = sdesc_add(dBG, st_ * STG);
+      if (leader) {
+        issue_ts4(tACC, tQh, dbg, idA, acc);
+        if (a.ksplit) issue_ts4(tACC, tQh, sdesc_add(dbg, lo_bytes), idA, 1);
+        issue_ts4(tACC, tQl, dbg, idA, 1);
+        tc_commit(&q_free[b]);
+        tc_commit(&empty[st_]);
       }
-      if (!warp_wait(a_ready, (uint32_t)u & 1u, abort, a.err, 31)) goto sw_out;
-      if (XS && !warp_wait(xa_full, (uint32_t)u & 1u, abort, a.err, 34)) goto sw_out;
+      __syncwarp();
+      return true;
+    };
+    for (int t = blockIdx.x; t < a.n_items; t += gridDim.x) {
+      const int4 item = a.items[t];
+      if (a.sys_active && !a.sys_active[item.x]) continue;
+      const uint32_t ip = (uint32_t)(it & 1);
+      if (!warp_wait(XS ? xa_full : a_ready, ip, abort, a.err, XS ? 34 : 31)) goto sw_out;
+      if (!warp_wait(gi_full, ip, abort, a.err, 36)) goto sw_out;
+      ++it;
+      uint32_t prev_stage = 0;
       for (int j = 0; j < item.w; ++j) {
-        if (uses > 0 && !warp_wait(&s_free[b], (uint32_t)(uses - 1) & 1u, abort, a.err, 23)) goto sw_out;
+        if (uses > 0 && !warp_wait(&s_free[b], (uint32_t)((uses - 1) & 1), abort, a.err, 23)) goto sw_out;
         if (!warp_wait(&full[stage], sph, abort, a.err, 25)) goto sw_out;
         tc_fence_after();
         // operands computed by the whole warp (warp-uniform), issued by the leader
@@ -285,118 +312,61 @@ __global__ void __launch_bounds__(kTsThreads, 1) tc_bwd_ts_kernel(TcBwdArgs a) {
                 mma_ts(tS, tA + 8 * q, db + 16 * q, idSW, q > 0);
             }
           }
-#pragma unroll
-          for (int q = 0; q < 2 * kTsCols / 16; ++q)
-            if (q < nkg) mma_ts(tS + 64, tG + 8 * q, dv + 16 * q, idSW, q > 0);
-          tc_commit(&s_full[b]);
-          // the XA tile is read only by the S MMAs: released after the item's last one
-          if (XS && j == item.w - 1) tc_commit(xa_empty);
+#pragma unroll 4
+          for (int q = 0; q < nkg; ++q) mma_ss(tW, dGI + 16 * q, dv + 16 * q, idSW, q > 0);
+          tc_commit(&sw_full[b]);
+          // the item's XA and GI tiles are released after its last S, W products
+          if (j == item.w - 1) {
+            tc_commit(gi_empty);
+            if (XS) tc_commit(xa_empty);
+          }
         }
         __syncwarp();
         ++uses;
+        if (j > 0 && !issue_acc(prev_stage, j - 1)) goto sw_out;
+        prev_stage = stage;
         if (++stage == (uint32_t)S) { stage = 0; sph ^= 1; }
       }
+      if (item.w > 0 && !issue_acc(prev_stage, item.w - 1)) goto sw_out;
     }
   sw_out:
     if (leader) tc_commit(&done[b]);
     __syncwarp();
     mbar_drain(&done[b], 0, 500000000ull);
-  } else if (warp == kAccWarp) {
-    // ------------------------------------------------------------ feature-sum issuer
-    const bool leader = elect_one();
-    const uint32_t idA = idesc_f16(128, a.NACC, 0, 0);
-    const uint32_t lo_bytes = (uint32_t)a.NACC * 256u;   // ksplit: the lo block of BG
-    const uint64_t dBG = sdesc(smem_u32(sS + XT + GT), 128, 2048);
-    uint32_t stage = 0;
-    uint32_t of_ph[2] = {0u, 0u};
-    uint32_t qr0 = 0, qr1 = 0;
-    long long fc = 0;   // folds committed: fold f is read by warpgroup f & 1
-    bool open = false;
-    for (int t = blockIdx.x; t < a.n_items; t += gridDim.x) {
-      const int4 item = a.items[t];
-      if (a.sys_active && !a.sys_active[item.x]) continue;
-      const int nH = 2 * item.w;
-      for (int h = 0; h < nH; ++h) {
-        const int b = h & 1;
-        uint32_t& qr = b == 0 ? qr0 : qr1;
-        if (!warp_wait(&q_ready[b], qr & 1u, abort, a.err, 26)) goto acc_out;
-        ++qr;
-        tc_fence_after();
-        const uint32_t acc = (h % kFoldH) != 0;
-        const bool fold_end = (h % kFoldH) == kFoldH - 1 || h == nH - 1;
-        if (!acc && open) {
-          // the previous fold's accumulator must have been read by its warpgroup
-          const int rb = (int)((fc - 1) & 1);
-          if (!warp_wait(&o_free[rb], of_ph[rb], abort, a.err, 27)) goto acc_out;
-          of_ph[rb] ^= 1;
-          open = false;
-          tc_fence_after();
-        }
-        const uint64_t dbg = sdesc_add(dBG, stage * STG + b * 1024u);
-        const uint32_t tqh = tbase + 256 + 32 * b, tql = tbase + 320 + 32 * b, tacc = tbase + colACC;
-        if (leader) {
-          issue_ts4(tacc, tqh, dbg, idA, acc);
-          if (a.ksplit) issue_ts4(tacc, tqh, sdesc_add(dbg, lo_bytes), idA, 1);
-          issue_ts4(tacc, tql, dbg, idA, 1);
-          tc_commit(&q_free[b]);
-          if (fold_end) tc_commit(&o_ready[fc & 1]);
-          // both halves of the stage read (their S, W MMAs completed before Q)
-          if (b == 1) tc_commit(&empty[stage]);
-        }
-        __syncwarp();
-        if (fold_end) {
-          open = true;
-          ++fc;
-        }
-        if (b == 1) {
-          if (++stage == (uint32_t)S) stage = 0;
-        }
-      }
-    }
-  acc_out:
-    if (leader) tc_commit(&done[2]);
-    __syncwarp();
-    mbar_drain(&done[2], 0, 500000000ull);
   } else {
-    // ------------------------------------------------------------ exp warpgroups
+    // ------------------------------------------------------------ warpgroups
     const int b = warp >> 2, w = warp & 3;
     const int row = 32 * w + lane;
     const uint32_t lofs = static_cast<uint32_t>(32 * w) << 16;
-    const uint32_t tS = tbase + lofs + 128 * b, tQh = tbase + lofs + 256 + 32 * b;
-    const uint32_t tQl = tQh + 64;
-    const uint32_t tACC = tbase + lofs + colACC;
-    const int d = a.d;
+    const uint32_t tS = tbase + lofs + 128 * b, tQh = tbase + lofs + 256 + 64 * b;
+    const uint32_t tQl = tQh + 32;
+    const uint32_t tACC = tbase + lofs + 512 - 2 * a.NACC + b * a.NACC;
+    const int d = a.d, dk = a.dk, k0 = a.k0;
     const int qc = a.qcol;
     double* wp = wpart + (b * 4 + w) * kGW;
-    uint32_t sph = 0, oph = 0;
-    long long fcount = 0;   // fold ends passed (both warpgroups see every one)
-    long long uses = 0;
+    long long uses = 0, qf = 0;
     int u = 0;
     for (int t = blockIdx.x; t < a.n_items; t += gridDim.x) {
       const int4 item = a.items[t];
       if (a.sys_active && !a.sys_active[item.x]) continue;
       const int c = item.x % a.chains;
-      const int nH = 2 * item.w;
+      const size_t ti = (size_t)c * a.T_total + item.y;
       if (u > 0) {
-        // both warpgroups have waited for their last S, W of the previous
-        // item and folded its accumulator: nothing reads XA or GI any more
+        // both warpgroups are done with the previous item (its last products
+        // and folds): nothing reads the TMEM XA rows any more
         mbar_arrive(seg);
         const bool ok = mbar_wait(seg, (uint32_t)(u - 1) & 1u, abort, a.err, 32);
         if (!__all_sync(0xffffffffu, ok)) goto exp_out;
       }
       ++u;
-      {
-        // warpgroup 0 stores the item's XA rows (unless XA stays in shared
-        // memory), warpgroup 1 its GI rows
-        const size_t ti = (size_t)c * a.T_total + item.y;
-        const int width = b == 0 ? (XS ? 0 : a.KX) : a.KG;
-        const uint8_t* src = (b == 0 ? a.XA + ti * XT : a.GI + ti * GT) + (row >> 3) * (width * 16) + (row & 7) * 16;
-        const uint32_t col = b == 0 ? colA : colG;
-        for (int q = 0; q < width / 16; ++q) {
+      if (!XS && b == 0) {
+        // warpgroup 0 stores the item's XA rows into TMEM
+        const uint8_t* src = a.XA + ti * XT + (row >> 3) * (a.KX * 16) + (row & 7) * 16;
+        for (int q = 0; q < a.KX / 16; ++q) {
           const uint4 u0 = *reinterpret_cast<const uint4*>(src + 2 * q * 128);
           const uint4 u1 = *reinterpret_cast<const uint4*>(src + (2 * q + 1) * 128);
           const uint32_t v[8] = {u0.x, u0.y, u0.z, u0.w, u1.x, u1.y, u1.z, u1.w};
-          tmem_st8(tbase + lofs + col + 8 * q, v);
+          tmem_st8(tbase + lofs + kColXA + 8 * q, v);
         }
         tmem_st_wait();
         tc_fence_before();
@@ -404,14 +374,94 @@ __global__ void __launch_bounds__(kTsThreads, 1) tc_bwd_ts_kernel(TcBwdArgs a) {
       }
       if (lane == 0)
         for (int v = 0; v <= d; ++v) wp[v] = 0.0;
-      for (int h = b; h < nH; h += 2, ++uses) {
-        bool ok = mbar_wait(&s_full[b], sph, abort, a.err, 28);
+      // Fold of ACC_b (complete): per row xt^2 q - 2 xt R + T per dimension of
+      // the block, summed over the warp's 32 rows in FP32, the warp sums
+      // accumulated in FP64.  xt (the F16 hi + lo of the scaled, centred point,
+      // as in BG) is the row's XA operand: columns 3k, 3k + 1 hold hi and lo of
+      // dimension k (from TMEM, or, when XA is a shared-memory tile, from the
+      // item's tile in global memory, which the next item cannot overwrite).
+      auto fold = [&]() {
+        uint32_t xa[kXaRegs];
+        if (!XS) {
+          uint32_t t0[16], t1[16] = {};
+          tmem_ld16(tbase + lofs + kColXA, t0);
+          if (3 * d > 32) tmem_ld16(tbase + lofs + kColXA + 16, t1);
+          tmem_ld_wait_regs(t0, t1);
+#pragma unroll
+          for (int q = 0; q < kXaRegs; ++q) xa[q] = q < 16 ? t0[q] : (q < 32 ? t1[q - 16] : 0u);
+        }
+        const uint8_t* gxa = a.XA + ti * XT;
+        auto xt_dim = [&](int kk) -> float {
+          uint16_t hb, lb;
+          if (!XS) {
+            // k = kk here (one dimension block): register indices fixed at compile time
+            const uint32_t wh = xa[(3 * kk) >> 1], wl = xa[(3 * kk + 1) >> 1];
+            hb = (uint16_t)(((3 * kk) & 1) ? (wh >> 16) : (wh & 0xffffu));
+            lb = (uint16_t)(((3 * kk + 1) & 1) ? (wl >> 16) : (wl & 0xffffu));
+          } else {
+            const int k = k0 + kk;
+            hb = __ldg(reinterpret_cast<const unsigned short*>(gxa + x_off(row, 3 * k, a.KX)));
+            lb = __ldg(reinterpret_cast<const unsigned short*>(gxa + x_off(row, 3 * k + 1, a.KX)));
+          }
+          return __half2float(__ushort_as_half(hb)) + __half2float(__ushort_as_half(lb));
+        };
+        uint32_t oq[16];
+        tmem_ld16(tACC + 16 * (qc >> 4), oq);
+        tmem_ld_wait_regs(oq);
+        const float qs = __uint_as_float(oq[qc & 15]);
+        if (k0 == 0) {
+          float v = qs;
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+          if (lane == 0) wp[0] += (double)v;
+        }
+        auto fold_dim = [&](int kk, float R, float T) {
+          const float x = xt_dim(kk);
+          float e = fmaf(x, fmaf(x, qs, -2.f * R), T);
+#pragma unroll
+          for (int sft = 16; sft > 0; sft >>= 1) e += __shfl_down_sync(0xffffffffu, e, sft);
+          if (lane == 0) wp[1 + k0 + kk] += (double)e;
+        };
+        if (!a.ksplit) {
+#pragma unroll
+          for (int c4 = 0; c4 < (kMaxDT + 3) / 4; ++c4) {
+            if (4 * c4 < dk) {
+              uint32_t o[16];
+              tmem_ld16(tACC + 16 * c4, o);
+              tmem_ld_wait_regs(o);
+#pragma unroll
+              for (int uu = 0; uu < 4; ++uu) {
+                const int kk = 4 * c4 + uu;
+                if (kk < dk)
+                  fold_dim(kk, __uint_as_float(o[4 * uu]) + __uint_as_float(o[4 * uu + 1]),
+                           __uint_as_float(o[4 * uu + 2]) + __uint_as_float(o[4 * uu + 3]));
+              }
+            }
+          }
+        } else {
+#pragma unroll
+          for (int c16 = 0; c16 < kMaxDT / 16; ++c16) {
+            if (16 * c16 < dk) {
+              uint32_t oR[16], oT[16];
+              tmem_ld16(tACC + 16 * c16, oR);
+              tmem_ld16(tACC + a.toff + 16 * c16, oT);
+              tmem_ld_wait_regs(oR, oT);
+#pragma unroll
+              for (int uu = 0; uu < 16; ++uu) {
+                const int kk = 16 * c16 + uu;
+                if (kk < dk) fold_dim(kk, __uint_as_float(oR[uu]), __uint_as_float(oT[uu]));
+              }
+            }
+          }
+        }
+      };
+      for (int j = 0; j < item.w; ++j, ++uses) {
+        bool ok = mbar_wait(&sw_full[b], (uint32_t)(uses & 1), abort, a.err, 28);
         if (!__all_sync(0xffffffffu, ok)) goto exp_out;
-        sph ^= 1;
         tc_fence_after();
         {
           // the whole half of S and W in registers with one wait, so S_b, W_b
-          // are released at once and the next MMAs into them can start
+          // are released at once and the next products into them can start
           uint32_t s0[32], s1[32], w0[32], w1[32], qq[32];
           tmem_ld32(tS, s0);
           tmem_ld32(tS + 32, s1);
@@ -420,7 +470,7 @@ __global__ void __launch_bounds__(kTsThreads, 1) tc_bwd_ts_kernel(TcBwdArgs a) {
           tmem_ld_wait_regs(s0, s1, w0, w1);
           tc_fence_before();
           mbar_arrive(&s_free[b]);
-          if (item.z + (h >> 1) == item.y) {
+          if (item.z + j == item.y) {
             // diagonal tile of the upper triangle: counted once, off-diagonal
             // tiles twice; the pair i = j is left out (its distance is 0, and its
             // share of the alpha gradient is added exactly at the end)
@@ -449,11 +499,14 @@ __global__ void __launch_bounds__(kTsThreads, 1) tc_bwd_ts_kernel(TcBwdArgs a) {
             qh[16 + q] = pack_f16x2(h0, h1);
             qq[16 + q] = pack_f16x2(l0, l1);
           }
-          if (uses > 0) {
-            // Q_b of this warpgroup's previous half must have been consumed
-            ok = mbar_wait(&q_free[b], (uint32_t)((uses - 1) & 1), abort, a.err, 30);
+          if (j > 0) {
+            // the feature sums of Q(j-1) are done: Q_b may be overwritten, and
+            // ACC_b is complete up to half j-1 (fold it when a fold ends there)
+            ok = mbar_wait(&q_free[b], (uint32_t)(qf & 1), abort, a.err, 30);
             if (!__all_sync(0xffffffffu, ok)) goto exp_out;
+            ++qf;
             tc_fence_after();
+            if (((j - 1) % kFoldOwn) == kFoldOwn - 1) fold();
           }
           tmem_st32(tQh, qh);
           tmem_st32(tQl, qq);
@@ -461,98 +514,14 @@ __global__ void __launch_bounds__(kTsThreads, 1) tc_bwd_ts_kernel(TcBwdArgs a) {
         tmem_st_wait();
         tc_fence_before();
         mbar_arrive(&q_ready[b]);
-        // After the fold's last (odd) half the accumulator holds q, R, T of the
-        // fold; the warpgroups take turns at folding it: per row
-        // xt^2 q - 2 xt R + T, summed over the warp's 32 rows in FP32, the warp
-        // sums accumulated in FP64.  xt (the F16 hi + lo of the scaled, centred
-        // point, as in BG) is read back from the row's XA operand: columns 3k,
-        // 3k + 1 hold hi and lo of dimension k.
-        const int e_half = b == 0 ? h + 1 : h;
-        if ((e_half % kFoldH) == kFoldH - 1 || e_half == nH - 1) {
-          const bool mine = (fcount & 1) == b;
-          ++fcount;
-          if (mine) {
-            ok = mbar_wait(&o_ready[b], oph, abort, a.err, 29);
-            if (!__all_sync(0xffffffffu, ok)) goto exp_out;
-            oph ^= 1;
-            tc_fence_after();
-            // xt of this row, all dimensions (packed F16 pairs)
-            uint32_t xa[kXaRegs];
-            if (XS) {
-              // the shared-memory XA tile may already hold the next item's rows
-              // (it is released after the item's last S product): read the
-              // item's tile in global memory, which stays until the call ends
-              const uint8_t* gxa = a.XA + ((size_t)c * a.T_total + item.y) * XT;
-#pragma unroll
-              for (int q = 0; q < kXaRegs; ++q) {
-                const int kk = 2 * q;
-                xa[q] = kk < 3 * d ? __ldg(reinterpret_cast<const uint32_t*>(gxa + x_off(row, kk, a.KX))) : 0u;
-              }
-            } else {
-              uint32_t t0[16], t1[16] = {};
-              tmem_ld16(tbase + lofs + colA, t0);
-              if (3 * d > 32) tmem_ld16(tbase + lofs + colA + 16, t1);
-              tmem_ld_wait_regs(t0, t1);
-#pragma unroll
-              for (int c = 0; c < kXaRegs; ++c) xa[c] = c < 16 ? t0[c] : (c < 32 ? t1[c - 16] : 0u);
-            }
-            auto xt_dim = [&](int k) -> float {
-              const uint32_t wh = xa[(3 * k) >> 1], wl = xa[(3 * k + 1) >> 1];
-              const uint16_t hb = (uint16_t)(((3 * k) & 1) ? (wh >> 16) : (wh & 0xffffu));
-              const uint16_t lb = (uint16_t)(((3 * k + 1) & 1) ? (wl >> 16) : (wl & 0xffffu));
-              return __half2float(__ushort_as_half(hb)) + __half2float(__ushort_as_half(lb));
-            };
-            uint32_t oq[16];
-            tmem_ld16(tACC + 16 * (qc >> 4), oq);
-            tmem_ld_wait_regs(oq);
-            const float qs = __uint_as_float(oq[qc & 15]);
-            float v = qs;
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-            if (lane == 0) wp[0] += (double)v;
-            auto fold_dim = [&](int kk, float R, float T) {
-              const float x = xt_dim(kk);
-              float e = fmaf(x, fmaf(x, qs, -2.f * R), T);
-#pragma unroll
-              for (int sft = 16; sft > 0; sft >>= 1) e += __shfl_down_sync(0xffffffffu, e, sft);
-              if (lane == 0) wp[1 + kk] += (double)e;
-            };
-            if (!a.ksplit) {
-#pragma unroll
-              for (int c4 = 0; c4 < (kMaxDT + 3) / 4; ++c4) {
-                if (4 * c4 < d) {
-                  uint32_t o[16];
-                  tmem_ld16(tACC + 16 * c4, o);
-                  tmem_ld_wait_regs(o);
-#pragma unroll
-                  for (int uu = 0; uu < 4; ++uu) {
-                    const int kk = 4 * c4 + uu;
-                    if (kk < d)
-                      fold_dim(kk, __uint_as_float(o[4 * uu]) + __uint_as_float(o[4 * uu + 1]),
-                               __uint_as_float(o[4 * uu + 2]) + __uint_as_float(o[4 * uu + 3]));
-                  }
-                }
-              }
-            } else {
-#pragma unroll
-              for (int c16 = 0; c16 < kMaxDT / 16; ++c16) {
-                if (16 * c16 < d) {
-                  uint32_t oR[16], oT[16];
-                  tmem_ld16(tACC + 16 * c16, oR);
-                  tmem_ld16(tACC + a.toff + 16 * c16, oT);
-                  tmem_ld_wait_regs(oR, oT);
-#pragma unroll
-                  for (int uu = 0; uu < 16; ++uu) {
-                    const int kk = 16 * c16 + uu;
-                    if (kk < d) fold_dim(kk, __uint_as_float(oR[uu]), __uint_as_float(oT[uu]));
-                  }
-                }
-              }
-            }
-            tc_fence_before();
-            mbar_arrive(&o_free[b]);
-          }
-        }
+      }
+      if (item.w > 0) {
+        // the item's last feature sums, then its last fold
+        const bool ok = mbar_wait(&q_free[b], (uint32_t)(qf & 1), abort, a.err, 30);
+        if (!__all_sync(0xffffffffu, ok)) goto exp_out;
+        ++qf;
+        tc_fence_after();
+        fold();
       }
       if (lane == 0) {
         // per-warp partial of this item: [q, contrib_0 .. contrib_{d-1}]
@@ -609,10 +578,12 @@ __global__ void tc_bwd_norms_kernel(DevLayout L, int chains, int64_t n_total, co
 // G and V enter by columns [c0, c0 + mc) of their m; GI rows [gh gh gl vh vh vl],
 // VJ rows [vh vl vh gh gl gh] (F16 hi/lo, G and V each scaled by a power of
 // two), so that GI VJ^T = G_i . V_j + V_i . G_j over the block.  BG carries the
-// F16 hi/lo parts of the centred xt and of xt^2 in the layout of TcBwdArgs.
+// F16 hi/lo parts of the centred xt and of xt^2 for the dimensions
+// [k0, k0 + dk), in the layout of TcBwdArgs, and the ones column.
 __global__ void tc_prep_bwd_kernel(DevLayout L, TcTables T, int n_inst, int chains, int d, int ard, int n_theta,
                                    int m, int c0, int mc, int KG, int NB, int ksplit, int NACC, int toff, int qcol,
-                                   int T_total, const float* x, const double* theta, const uint32_t* ckeys,
+                                   int k0, int dk, int T_total, const float* x, const double* theta,
+                                   const uint32_t* ckeys,
                                    const float* V, const float* G, int64_t n_total, const uint32_t* gmax,
                                    const uint32_t* vmax, const int32_t* sys_active, const float* amp,
                                    uint8_t* GI, uint8_t* VJ, uint8_t* BG, int* err) {
@@ -655,7 +626,8 @@ __global__ void tc_prep_bwd_kernel(DevLayout L, TcTables T, int n_inst, int chai
   const double* th = theta + (int64_t)s * n_theta;
   for (int f = 0; f < NB; ++f) bg[t_off(f, r) / 2] = zh;
   if (valid) {
-    for (int k = 0; k < d; ++k) {
+    for (int kk = 0; kk < dk; ++kk) {
+      const int k = k0 + kk;
       const float sc = (float)(sqrt(2.0 * kHalfLog2e) * exp(-th[1 + (ard ? k : 0)]));
       const float xh = (x[i * d + k] - center_of(ckeys, n_inst, d, b, k)) * sc;
       const __half hi = __float2half_rn(xh);
@@ -666,15 +638,15 @@ __global__ void tc_prep_bwd_kernel(DevLayout L, TcTables T, int n_inst, int chai
       const __half sh = __float2half_rn(sq);
       const __half sl = __float2half_rn(sq - __half2float(sh));
       if (!ksplit) {
-        bg[t_off(4 * k, r) / 2] = hi;
-        bg[t_off(4 * k + 1, r) / 2] = lo;
-        bg[t_off(4 * k + 2, r) / 2] = sh;
-        bg[t_off(4 * k + 3, r) / 2] = sl;
+        bg[t_off(4 * kk, r) / 2] = hi;
+        bg[t_off(4 * kk + 1, r) / 2] = lo;
+        bg[t_off(4 * kk + 2, r) / 2] = sh;
+        bg[t_off(4 * kk + 3, r) / 2] = sl;
       } else {
-        bg[t_off(k, r) / 2] = hi;
-        bg[t_off(toff + k, r) / 2] = sh;
-        bg[t_off(NACC + k, r) / 2] = lo;
-        bg[t_off(NACC + toff + k, r) / 2] = sl;
+        bg[t_off(kk, r) / 2] = hi;
+        bg[t_off(toff + kk, r) / 2] = sh;
+        bg[t_off(NACC + kk, r) / 2] = lo;
+        bg[t_off(NACC + toff + kk, r) / 2] = sl;
       }
     }
     bg[t_off(qcol, r) / 2] = __float2half_rn(1.f);
@@ -757,69 +729,70 @@ kmv_status tc_backward(kmv_handle h, const KmvArgs& a, double* grad, cudaStream_
   const int KX = x_width(a.d, kSplitF16);
   const size_t max_stages = tl.stages > 0 ? (size_t)std::max(2, std::min(tl.stages, 6)) : 6;
   const size_t fixed = 1024 + kTsBarBytes + kTsFoldBytes;
-  // Feature-sum layout, columns of G, V per launch (mc) and where XA lives:
-  // the accumulator, the depth-6 mc GI rows and (unless XS) the XA rows must
-  // fit the TMEM columns left by S, W and Qh, Ql, and the stages shared
-  // memory.  Fewest launches first, then the wide layout (fewer MMAs per
-  // half tile), then XA in TMEM.
+  // Feature-sum layout, dimensions per launch (dk), columns of G, V per launch
+  // (mc) and where XA lives: the two accumulators and (unless XS) the XA rows
+  // must fit the TMEM columns left by S, W and Q (128), and the GI tile, the
+  // XA tile (XS) and at least two stages shared memory.  Fewest launches
+  // first, then XA in TMEM, then the wide layout (fewer MMAs per half tile).
   struct Choice {
-    int ksplit, NACC, toff, qcol, NB, mc, n_chunks, stages;
+    int ksplit, NACC, toff, qcol, NB, dk, n_dblk, mc, n_cblk, stages;
     bool xs;
+    long long launches;
   };
-  auto make = [&](int ksplit, bool xs) -> Choice {
+  auto make = [&](int ksplit, bool xs, int n_dblk) -> Choice {
     Choice c{};
     c.ksplit = ksplit;
     c.xs = xs;
+    c.n_dblk = n_dblk;
+    c.dk = (a.d + n_dblk - 1) / n_dblk;
+    c.launches = LLONG_MAX;
+    // XA in TMEM: one dimension block (the fold's register indices are fixed),
+    // and a row's split values in at most two loads
+    if (!xs && (n_dblk != 1 || 3 * a.d > 64)) return c;
     if (!ksplit) {
       c.toff = 0;
-      c.qcol = 4 * a.d;
-      c.NACC = round16(4 * a.d + 1);
+      c.qcol = 4 * c.dk;
+      c.NACC = round16(4 * c.dk + 1);
       c.NB = c.NACC;
     } else {
-      c.toff = round16(a.d);
+      c.toff = round16(c.dk);
       c.qcol = 2 * c.toff;
       c.NACC = round16(c.qcol + 1);
       c.NB = 2 * c.NACC;
     }
-    // XA in TMEM: the fold reads a row's split values with at most two loads
-    if (!xs && 3 * a.d > 64) {
-      c.mc = 0;
-      c.n_chunks = INT32_MAX;
-      return c;
-    }
-    auto stages_for = [&](int mc) -> int {
+    if ((int)kColXA + (xs ? 0 : KX / 2) + 2 * c.NACC > 512) return c;
+    for (int mc = a.m; mc >= 1; --mc) {
       const size_t KG = round16(6 * mc);
       const size_t stg = (size_t)(KX + KG + c.NB) * 256;
-      const size_t xa = xs ? (((size_t)KX * 256 + 1023) & ~size_t(1023)) : 0;
-      if (kMaxSmem < fixed + xa + 2 * stg) return 0;
-      return (int)std::min<size_t>(max_stages, (kMaxSmem - fixed - xa) / stg);
-    };
-    for (int mc = a.m; mc >= 1; --mc) {
-      const int cols = (xs ? 0 : KX / 2) + round16(6 * mc) / 2 + c.NACC;
-      if (cols <= kTsCols && stages_for(mc) >= 2) {
-        c.mc = mc;
-        c.n_chunks = (a.m + mc - 1) / mc;
-        c.stages = stages_for(mc);
-        return c;
-      }
+      const size_t base = fixed + al1k(KG * 256) + (xs ? al1k((size_t)KX * 256) : 0);
+      if (base + 2 * stg > kMaxSmem) continue;
+      c.mc = mc;
+      c.n_cblk = (a.m + mc - 1) / mc;
+      c.stages = (int)std::min<size_t>(max_stages, (kMaxSmem - base) / stg);
+      c.launches = (long long)c.n_cblk * n_dblk;
+      return c;
     }
-    c.mc = 0;
-    c.n_chunks = INT32_MAX;
     return c;
   };
-  Choice best = make(0, false);
-  for (const Choice& c : {make(0, true), make(1, false), make(1, true)})
-    if (c.n_chunks < best.n_chunks) best = c;
-  if (best.mc == 0)
+  Choice best{};
+  best.launches = LLONG_MAX;
+  for (int n_dblk = 1; n_dblk <= a.d; ++n_dblk) {
+    if (n_dblk > 1 && (a.d + n_dblk - 1) / n_dblk == (a.d + n_dblk - 2) / (n_dblk - 1)) continue;
+    for (bool xs : {false, true})
+      for (int ksplit : {0, 1}) {
+        const Choice c = make(ksplit, xs, n_dblk);
+        if (c.launches < best.launches) best = c;
+      }
+    if (best.launches < LLONG_MAX) break;
+  }
+  if (best.launches == LLONG_MAX)
     return tc_fail(h, KMV_EUNSUPPORTED, "tensor-core adjoint operands do not fit in tensor/shared memory");
   const bool xs = best.xs;
-  const int mc = best.mc, n_chunks = best.n_chunks, NB = best.NB;
+  const int mc = best.mc, NB = best.NB, n_chunks = (int)best.launches;
   const int KG = round16(6 * mc);
-  const int stages = best.stages;
   const size_t XT = (size_t)KX * 256, GT = (size_t)KG * 256, BT = (size_t)NB * 256;
   const size_t STG = XT + GT + BT;
-  const size_t smem =
-      std::max(kMinSmem, fixed + (xs ? ((XT + 1023) & ~size_t(1023)) : 0) + stages * STG);
+  const size_t smem = std::max(kMinSmem, fixed + al1k(GT) + (xs ? al1k(XT) : 0) + best.stages * STG);
   const int n_items = S->sym_n_items;
 
   auto al = [](size_t v) { return (v + 255) & ~size_t(255); };
@@ -875,41 +848,40 @@ kmv_status tc_backward(kmv_handle h, const KmvArgs& a, double* grad, cudaStream_
     ba.NACC = best.NACC;
     ba.toff = best.toff;
     ba.qcol = best.qcol;
-    ba.S = stages;
-    ba.n_inst = L.n_inst;
+    ba.S = best.stages;
     ba.d = a.d;
-    ba.n_theta = a.n_theta;
-    ba.ard = a.ard;
-    ba.ckeys = ckeys;
-    ba.L = h->dev;
-    ba.T = S->dev;
-    ba.x = a.x;
-    ba.theta = a.theta;
     ba.XA = base + o_xa;
     ba.XB = base + o_xb;
     ba.GI = base + o_gi;
     ba.VJ = base + o_vj;
     ba.BG = base + o_bg;
     ba.gpart = gpart;
-    ba.m = a.m;
     ba.sys_active = a.sys_active;
     ba.err = err;
     const int grid = std::min(n_items, S->num_sms);
-    // One launch per block of mc columns of G, V: the gradient is a sum over
-    // columns, so the blocks' partials are summed by the finalize.  Stream order
-    // keeps each block's operand tiles until its launch has read them.
-    for (int ch = 0; ch < n_chunks; ++ch) {
-      const int c0 = ch * mc, mcc = std::min(mc, a.m - c0);
-      tc_prep_bwd_kernel<<<dim3(S->T_total, L.chains), 128, 0, st>>>(
-          h->dev, S->dev, L.n_inst, L.chains, a.d, a.ard, a.n_theta, a.m, c0, mcc, KG, NB, best.ksplit, best.NACC,
-          best.toff, best.qcol, S->T_total, a.x, a.theta, ckeys, a.V, a.G, L.n_total, gmax, vmax, a.sys_active,
-          a.amp, base + o_gi, base + o_vj, base + o_bg, err);
-      ba.chunk = ch;
-      ProfScope prof(h, KMV_KERNEL_ADJOINT, st);
-      if (xs)
-        tc_bwd_ts_kernel<true><<<grid, kTsThreads, smem, st>>>(ba);
-      else
-        tc_bwd_ts_kernel<false><<<grid, kTsThreads, smem, st>>>(ba);
+    // One launch per (block of mc columns of G, V, block of dk dimensions): the
+    // gradient is a sum over columns, and the dimensions are separate entries
+    // (q enters once, from the first dimension block), so the finalize sums
+    // every launch's partials.  Stream order keeps each block's operand tiles
+    // until its launch has read them.
+    for (int cb = 0; cb < best.n_cblk; ++cb) {
+      const int c0 = cb * mc, mcc = std::min(mc, a.m - c0);
+      for (int db = 0; db < best.n_dblk; ++db) {
+        const int k0 = db * best.dk, dkk = std::min(best.dk, a.d - k0);
+        if (dkk <= 0) continue;
+        tc_prep_bwd_kernel<<<dim3(S->T_total, L.chains), 128, 0, st>>>(
+            h->dev, S->dev, L.n_inst, L.chains, a.d, a.ard, a.n_theta, a.m, c0, mcc, KG, NB, best.ksplit,
+            best.NACC, best.toff, best.qcol, k0, dkk, S->T_total, a.x, a.theta, ckeys, a.V, a.G, L.n_total, gmax,
+            vmax, a.sys_active, a.amp, base + o_gi, base + o_vj, base + o_bg, err);
+        ba.chunk = cb * best.n_dblk + db;
+        ba.k0 = k0;
+        ba.dk = dkk;
+        ProfScope prof(h, KMV_KERNEL_ADJOINT, st);
+        if (xs)
+          tc_bwd_ts_kernel<true><<<grid, kTsThreads, smem, st>>>(ba);
+        else
+          tc_bwd_ts_kernel<false><<<grid, kTsThreads, smem, st>>>(ba);
+      }
     }
   }
   tc_bwd_finalize_kernel<<<n_sys, kFinThreads, 0, st>>>(h->dev, S->dev.sym_pref, n_items, n_chunks, L.chains,
