@@ -427,6 +427,7 @@ def main():
     if not args.no_leapfrog:
         lf = leapfrog_rates(h, dev, rank, world)
         if rank == 0:
+            lf["c5_n16384"] = c5_copy_hmc(h, dev)
             lf["c5"] = c5_full(h, dev)
         if out is not None:
             out["leapfrog"] = lf
@@ -457,9 +458,7 @@ def leapfrog_rates(h, dev, rank, world):
     import workloads as wl
     from paper_2412_20884_gb300 import Points, KmvError
     cases = [("N=2048 d=1 iso SE (alpha=1, l=0.2, sigma2=0.01), 1 chain, dt=0.01, cg_tol=1e-6", wl.c1(seed=rank), 10,
-              0.01),
-             ("N=16384 d=3 ARD SE (Sec. 4.2 narrowing rule, sigma2=0.1), 8 chains, dt=0.002, cg_tol=1e-6",
-              wl.c5(n=16384, chains=8, seed=rank), 2, 0.002)]
+              0.01)]
     res = {}
     for label, w, steps, DT in cases:
         pts = Points(torch.tensor(w.X, dtype=torch.float32, device=dev), w.offsets, ard=w.ard)
@@ -549,6 +548,68 @@ def leapfrog_rates(h, dev, rank, world):
     return res
 
 
+def c5_copy_hmc(h, dev, n=16384, dt=2.5e-4, updates=10, n_int=20, rank=128):
+    """Algorithm 1 on a 16,384-point copy of the large-N workload (8 chains,
+    d = 3, the Sec. 4.2 narrowing rule for l): a rank-128 randomized Nystrom
+    preconditioner built with FP32 products at the current theta every 5
+    updates (the paper rebuilds it every few updates), phi drawn by the pole
+    expansion, n_int leapfrog steps, FP32 energies, the Metropolis test.  Both
+    forms from the same start and draws: acceptance, |dH|, leapfrog steps per
+    second of the whole loop and of the leapfrog calls alone, CG iterations."""
+    import torch
+    import workloads as wl
+    from paper_2412_20884_gb300 import Points
+    from paper_2412_20884_gb300.binding import accept
+    w = wl.c5(n=n, chains=8)
+    pts = Points(torch.tensor(w.X, dtype=torch.float32, device=dev), w.offsets, ard=True)
+    y = torch.tensor(w.y, dtype=torch.float32, device=dev)
+    out = {"workload": f"N={n} d=3 ARD SE (Sec. 4.2 narrowing rule, sigma2=0.1), 8 chains; Algorithm 1 with "
+                       f"{n_int} leapfrog steps at dt={dt}, rank-{rank} Nystrom preconditioner (FP32 products, "
+                       f"rebuilt every 5 updates), {updates} updates", "dt": dt, "n_int": n_int}
+    stream = torch.cuda.current_stream()
+    for prec in ("fp32", "bf16_hilo"):
+        rng = np.random.default_rng(5)
+        th = torch.tensor(w.theta, dtype=torch.float64, device=dev)
+        acc, dhs, its = [], [], []
+        lf_ms = 0.0
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for it in range(updates):
+            if it % 5 == 0:
+                om = torch.tensor(rng.standard_normal((8, w.n_total, rank)), dtype=torch.float32, device=dev)
+                U, lam, _ = h.nystrom_build(pts, th, om, prec="fp32")
+                h.set_preconditioner(pts, U, lam)
+            xi = torch.tensor(rng.standard_normal((8, w.n_total)), dtype=torch.float32, device=dev)
+            pi = torch.tensor(rng.standard_normal(w.theta.shape), dtype=torch.float64, device=dev)
+            u = torch.tensor(1.0 - rng.uniform(size=8), dtype=torch.float64, device=dev)
+            phi, _, _ = h.phi_refresh(pts, th, xi, n_poles=15, cg_tol=1e-6, cg_maxiter=3000, prec=prec)
+            th_old = th.clone()
+            H0, _, _, _ = h.kmv_energy(pts, y, phi, th, pi, cg_maxiter=3000)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fail = torch.zeros(8, dtype=torch.int32, device=dev)
+            for _ in range(n_int):
+                st, itc, _ = h.leapfrog_step(pts, y, phi, th, pi, dt, cg_maxiter=3000, prec=prec)
+                fail |= st
+                its.append(itc.float().mean())
+            e1.record(stream)
+            H1, _, _, _ = h.kmv_energy(pts, y, phi, th, pi, cg_maxiter=3000)
+            ok = accept(H0, H1, u, th_old, th, status=fail)
+            torch.cuda.synchronize()
+            lf_ms += e0.elapsed_time(e1)
+            acc.append(float(ok.float().mean()))
+            dhs.extend(np.abs((H1 - H0).cpu().numpy()).tolist())
+        torch.cuda.synchronize()
+        sec = time.perf_counter() - t0
+        h.set_preconditioner(pts)
+        out[prec] = {"acceptance": float(np.mean(acc)), "dH_abs_median": float(np.median(dhs)),
+                     "leapfrog_steps_per_s": updates * n_int / (lf_ms * 1e-3),
+                     "leapfrog_steps_per_s_incl_phi_energy_nystrom": updates * n_int / sec,
+                     "mean_cg_iters": float(torch.stack(its).mean())}
+    out["bf16_over_fp32_speed"] = out["bf16_hilo"]["leapfrog_steps_per_s"] / out["fp32"]["leapfrog_steps_per_s"]
+    return out
+
+
 def c5_full(h, dev):
     """The large-N workload at full size (N = 2^20, d = 3, ARD, 8 chains): the
     CG product (m = 1) and the force's adjoint (m = 2) over all 8 chains in both
@@ -630,7 +691,7 @@ def run_suite_adjoint(args):
     (relative error per component, worst over the 32 systems) in both forms,
     and the adjoint kernel's time per launch on the N = 65,536, d = 8, m = 16
     workload (CUDA events).  Rebuilding with -DKMV_BWD_FOLD_HALVES=F sets how
-    many 64-column halves the tensor-core accumulator takes before each FP64 fold."""
+    many 64-column halves the tensor-core accumulator takes before each fold into the running sums."""
     import torch
     import workloads as wl
     from oracle import se_kernel as sk

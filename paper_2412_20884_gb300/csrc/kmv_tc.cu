@@ -65,7 +65,16 @@ __device__ __forceinline__ void issue_pv(uint32_t d_tmem, uint32_t a_tmem, uint6
 // polynomial), the rest on the MUFU; POLY = 0 puts every exp on the MUFU.
 template <int POLY, int DEG>
 __device__ __forceinline__ float exp2_mix(float s, int e) {
-  return (POLY > 0 && (e % POLY) == POLY - 1) ? exp2_fma<DEG>(s) : ptx::ex2(s);
+  if constexpr (POLY > 0) {
+    if ((e % POLY) == POLY - 1) return exp2_fma<DEG>(s);
+  }
+  return ptx::ex2(s);
+}
+
+// FP64 partial of (item t, column q, row rowp in the item's 256 rows): column
+// by column, so that the kernels' writes and the epilogue's reads are coalesced.
+__host__ __device__ __forceinline__ size_t part_idx(int t, int mz, int q, int rowp) {
+  return ((size_t)t * mz + q) * 256 + rowp;
 }
 
 struct TcFwdArgs {
@@ -77,7 +86,7 @@ struct TcFwdArgs {
   const uint8_t* XA;
   const uint8_t* XB;
   const uint8_t* VT;
-  double* part;            // (n_items, 256, mz) FP64
+  double* part;            // (n_items, mz, 256) FP64, part_idx
   int mz;                  // columns of this pass
   const int32_t* sys_active;
   int* err;
@@ -305,7 +314,7 @@ __global__ void __launch_bounds__(kFwdThreads, 1) tc_fwd_kernel(TcFwdArgs a) {
     for (int t = blockIdx.x; t < a.n_items; t += gridDim.x) {
       const int4 item = a.items[t];
       if (a.sys_active && !a.sys_active[item.x]) continue;
-      double* prow = a.part + ((size_t)t * 256 + g * 128 + row) * a.mz;
+      const int rowp = g * 128 + row;
       double racc[RM > 0 ? RM : 1];
 #pragma unroll
       for (int q = 0; q < (RM > 0 ? RM : 1); ++q) racc[q] = 0.0;
@@ -381,7 +390,8 @@ __global__ void __launch_bounds__(kFwdThreads, 1) tc_fwd_kernel(TcFwdArgs a) {
                 const int col = c0 + q;
                 if (col < a.mz) {
                   const double v = (double)__uint_as_float(o[q]);
-                  prow[col] = first ? v : prow[col] + v;
+                  double& pv = a.part[part_idx(t, a.mz, col, rowp)];
+                  pv = first ? v : pv + v;
                 }
               }
             }
@@ -394,7 +404,7 @@ __global__ void __launch_bounds__(kFwdThreads, 1) tc_fwd_kernel(TcFwdArgs a) {
       if (RM > 0) {
 #pragma unroll
         for (int q = 0; q < (RM > 0 ? RM : 1); ++q)
-          if (q < a.mz) prow[q] = racc[q];
+          if (q < a.mz) a.part[part_idx(t, a.mz, q, rowp)] = racc[q];
       }
     }
   exp_out:;
@@ -560,7 +570,7 @@ __global__ void __launch_bounds__(kFwdThreads, 1) tc_fwd_fma_kernel(TcFwdArgs a)
     for (int t = blockIdx.x; t < a.n_items; t += gridDim.x) {
       const int4 item = a.items[t];
       if (a.sys_active && !a.sys_active[item.x]) continue;
-      double* prow = a.part + ((size_t)t * 256 + g * 128 + row) * a.mz;
+      const int rowp = g * 128 + row;
       // four independent FP32 chains per column (short FMA dependency chains)
       double acc64[MZ];
       float acc[MZ][4];
@@ -663,7 +673,7 @@ __global__ void __launch_bounds__(kFwdThreads, 1) tc_fwd_fma_kernel(TcFwdArgs a)
       }
 #pragma unroll
       for (int q = 0; q < MZ; ++q)
-        prow[q] = acc64[q] + (double)((acc[q][0] + acc[q][1]) + (acc[q][2] + acc[q][3]));
+        a.part[part_idx(t, a.mz, q, rowp)] = acc64[q] + (double)((acc[q][0] + acc[q][1]) + (acc[q][2] + acc[q][3]));
     }
   fma_exp_out:;
   }
@@ -693,13 +703,15 @@ __global__ void tc_prep_vf_kernel(DevLayout L, TcTables T, int chains, int64_t n
 // ------------------------------------------------------------------ prep kernels
 
 // Per (instance, dimension) min and max of x as order-preserving keys; one
-// block per 128-row item of the layout, one atomic per warp and dimension.
+// block per 128-row item of the layout: a warp reduction, then a block
+// reduction in shared memory, then one atomic pair per block and dimension.
 __global__ void tc_center_kernel(DevLayout L, int n_inst, int d, const float* x, uint32_t* keys) {
+  __shared__ uint32_t smin[kTile / 32], smax[kTile / 32];
   const int item = blockIdx.x;
   const int b = L.item_inst[item];
   const int64_t i = L.item_row0[item] + threadIdx.x;
   const bool valid = i < L.offsets[b + 1];
-  const int lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   for (int k = 0; k < d; ++k) {
     uint32_t kmin = 0xffffffffu, kmax = 0u;
     if (valid) kmin = kmax = fkey(x[i * d + k]);
@@ -708,10 +720,22 @@ __global__ void tc_center_kernel(DevLayout L, int n_inst, int d, const float* x,
       kmin = min(kmin, __shfl_xor_sync(0xffffffffu, kmin, o));
       kmax = max(kmax, __shfl_xor_sync(0xffffffffu, kmax, o));
     }
-    if (lane == 0 && kmax != 0u) {
-      atomicMin(&keys[(size_t)b * d + k], kmin);
-      atomicMax(&keys[((size_t)n_inst + b) * d + k], kmax);
+    if (lane == 0) {
+      smin[w] = kmin;
+      smax[w] = kmax;
     }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int q = 1; q < kTile / 32; ++q) {
+        kmin = min(kmin, smin[q]);
+        kmax = max(kmax, smax[q]);
+      }
+      if (kmax != 0u) {
+        atomicMin(&keys[(size_t)b * d + k], kmin);
+        atomicMax(&keys[((size_t)n_inst + b) * d + k], kmax);
+      }
+    }
+    __syncthreads();
   }
 }
 
@@ -875,7 +899,7 @@ __global__ void tc_fwd_epilogue_kernel(DevLayout L, TcTables T, KmvArgs a, int c
     const double ai = a.amp ? alpha * (double)a.amp[(int64_t)c * a.n_total + i] : alpha;
     for (int q = 0; q < mz; ++q) {
       double acc = 0.0;
-      for (int k = 0; k < nk; ++k) acc += part[((it0 + k) * 256 + rowp) * mz + q];
+      for (int k = 0; k < nk; ++k) acc += part[part_idx((int)(it0 + k), mz, q, rowp)];
       const int col = c0 + q;
       const int64_t idx = ((int64_t)c * a.n_total + i) * a.m + col;
       const double shift = a.col_shift ? (double)a.col_shift[(int64_t)s * a.col_shift_stride + col] : 0.0;

@@ -28,8 +28,10 @@
 //                             R_ik = sum_j Q_ij xt_jk, T_ik = sum_j Q_ij xt_jk^2, q_i = sum_j Q_ij
 // Every kFoldOwn own halves warpgroup b folds its accumulator, per row,
 //   sum_j Q_ij (xt_ik - xt_jk)^2 = xt_ik^2 q_i - 2 xt_ik R_ik + T_ik
-// into FP64 sums (short accumulations: the tensor core's FP32 accumulator drops
-// low bits at every K step).  The fold reads the accumulator right after
+// summed over the warp's rows into running sums of the item kept as FP32 pairs (TwoSum)
+// (short accumulations: the tensor core's FP32 accumulator drops low bits at
+// every K step), written as the warp's FP64 partial once per item.  The fold
+// reads the accumulator right after
 // waiting for the next Q's buffer, which implies its MMAs are complete, so it
 // adds no wait of its own.  Because q, R and T are formed from the same Q, its
 // rounding cancels in this combination exactly as in the exact sum; leaving
@@ -56,7 +58,7 @@ namespace kmv {
 namespace {
 
 // Own halves (64 columns each) a warpgroup accumulates in TMEM before folding
-// into FP64: the tensor core's FP32 accumulation loses low bits at every K
+// into its running sums: the tensor core's FP32 accumulation loses low bits at every K
 // step (8 per half), so the sums are kept short (4 halves = 256 columns).
 #ifndef KMV_BWD_FOLD_HALVES
 #define KMV_BWD_FOLD_HALVES 4
@@ -129,12 +131,40 @@ __device__ __forceinline__ void split_q(float q, float& hi, float& lo) {
 constexpr int kTsThreads = 352;
 constexpr int kBwdIssue1Warp = 10;
 constexpr int kMaxDT = 32;     // d <= 32
-constexpr int kXaRegs = 48;    // 32-bit words of an XA row holding the 3 d split values (d <= 32)
 constexpr int kTsBarBytes = 512;                       // mbarriers, TMEM slot, abort flag
-constexpr int kTsFoldBytes = kFoldWarps * kGW * 8;     // per-warp FP64 fold sums of both warpgroups
 constexpr uint32_t kColXA = 384;
 
 __host__ __device__ constexpr size_t al1k(size_t v) { return (v + 1023) & ~size_t(1023); }
+
+// Sums v[u] over the warp's 32 lanes for u = 0..7 with 9 shuffles (halving
+// the vector at offsets 16, 8, 4, then a butterfly over 2 and 1); lanes
+// 4u .. 4u + 3 return the sum of v[u].
+__device__ __forceinline__ float warp_reduce_scatter8(const float (&v)[8], int lane) {
+  const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4;
+  float w4[4], w2[2];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+    w4[i] = (b4 ? v[i + 4] : v[i]) + __shfl_xor_sync(0xffffffffu, b4 ? v[i] : v[i + 4], 16);
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+    w2[i] = (b3 ? w4[i + 2] : w4[i]) + __shfl_xor_sync(0xffffffffu, b3 ? w4[i] : w4[i + 2], 8);
+  float z = (b2 ? w2[1] : w2[0]) + __shfl_xor_sync(0xffffffffu, b2 ? w2[0] : w2[1], 4);
+  z += __shfl_xor_sync(0xffffffffu, z, 2);
+  z += __shfl_xor_sync(0xffffffffu, z, 1);
+  return z;
+}
+
+// Running sum as an unevaluated pair s + c: each addition's rounding error,
+// recovered exactly by Knuth's TwoSum, is added to c, so (double)s + (double)c
+// differs from the exact sum of the terms by about u^2 times the sum of their
+// magnitudes (u = 2^-24) instead of u times it.
+__device__ __forceinline__ void two_sum_add(float& s, float& c, float x) {
+  const float t = __fadd_rn(s, x);
+  const float bp = __fsub_rn(t, s);
+  const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(x, bp));
+  c = __fadd_rn(c, err);
+  s = t;
+}
 
 template <bool XS>
 __global__ void __launch_bounds__(kTsThreads, 1) tc_bwd_ts_kernel(TcBwdArgs a) {
@@ -162,8 +192,6 @@ __global__ void __launch_bounds__(kTsThreads, 1) tc_bwd_ts_kernel(TcBwdArgs a) {
   uint64_t* gi_empty = gi_full + 1;  // both issuers done with it (2 commits)
   uint32_t* tslot = reinterpret_cast<uint32_t*>(gi_empty + 1);
   volatile int* abort = reinterpret_cast<volatile int*>(tslot + 1);
-  // FP64 fold sums, [warpgroup * 4 + warp][q, contrib_0 .. contrib_{d-1}]
-  double* wpart = reinterpret_cast<double*>(reinterpret_cast<uint8_t*>(full) + kTsBarBytes);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
@@ -343,7 +371,6 @@ __global__ void __launch_bounds__(kTsThreads, 1) tc_bwd_ts_kernel(TcBwdArgs a) {
     const uint32_t tACC = tbase + lofs + 512 - 2 * a.NACC + b * a.NACC;
     const int d = a.d, dk = a.dk, k0 = a.k0;
     const int qc = a.qcol;
-    double* wp = wpart + (b * 4 + w) * kGW;
     long long uses = 0, qf = 0;
     int u = 0;
     for (int t = blockIdx.x; t < a.n_items; t += gridDim.x) {
@@ -372,86 +399,97 @@ __global__ void __launch_bounds__(kTsThreads, 1) tc_bwd_ts_kernel(TcBwdArgs a) {
         tc_fence_before();
         mbar_arrive(a_ready);
       }
-      if (lane == 0)
-        for (int v = 0; v <= d; ++v) wp[v] = 0.0;
       // Fold of ACC_b (complete): per row xt^2 q - 2 xt R + T per dimension of
-      // the block, summed over the warp's 32 rows in FP32, the warp sums
-      // accumulated in FP64.  xt (the F16 hi + lo of the scaled, centred point,
-      // as in BG) is the row's XA operand: columns 3k, 3k + 1 hold hi and lo of
-      // dimension k (from TMEM, or, when XA is a shared-memory tile, from the
-      // item's tile in global memory, which the next item cannot overwrite).
+      // the block, xt being the F16 hi + lo of the scaled, centred point as in
+      // BG (columns 3k, 3k + 1 of the row's XA operand: from TMEM, or, when XA
+      // is a shared-memory tile, from the item's tile in global memory, which
+      // the next item cannot overwrite).  The warp's 32 rows are summed in FP32
+      // by a reduce-scatter over groups of 8 dimensions, after which lanes
+      // 4u .. 4u + 3 hold dimension 8g + u of group g; lane 4u keeps the item's
+      // running sum of it (an FP32 pair s + c, TwoSum), lane 0 that of q.  Nothing in the
+      // fold touches FP64 or shared memory: the warp's partial is written once
+      // per item.
+      float accg[kMaxDT / 8], cmpg[kMaxDT / 8], accq = 0.f, cmpq = 0.f;
+#pragma unroll
+      for (int g = 0; g < kMaxDT / 8; ++g) accg[g] = cmpg[g] = 0.f;
+      const uint8_t* gxa = a.XA + ti * XT;
       auto fold = [&]() {
-        uint32_t xa[kXaRegs];
-        if (!XS) {
-          uint32_t t0[16], t1[16] = {};
-          tmem_ld16(tbase + lofs + kColXA, t0);
-          if (3 * d > 32) tmem_ld16(tbase + lofs + kColXA + 16, t1);
-          tmem_ld_wait_regs(t0, t1);
-#pragma unroll
-          for (int q = 0; q < kXaRegs; ++q) xa[q] = q < 16 ? t0[q] : (q < 32 ? t1[q - 16] : 0u);
-        }
-        const uint8_t* gxa = a.XA + ti * XT;
-        auto xt_dim = [&](int kk) -> float {
-          uint16_t hb, lb;
-          if (!XS) {
-            // k = kk here (one dimension block): register indices fixed at compile time
-            const uint32_t wh = xa[(3 * kk) >> 1], wl = xa[(3 * kk + 1) >> 1];
-            hb = (uint16_t)(((3 * kk) & 1) ? (wh >> 16) : (wh & 0xffffu));
-            lb = (uint16_t)(((3 * kk + 1) & 1) ? (wl >> 16) : (wl & 0xffffu));
-          } else {
-            const int k = k0 + kk;
-            hb = __ldg(reinterpret_cast<const unsigned short*>(gxa + x_off(row, 3 * k, a.KX)));
-            lb = __ldg(reinterpret_cast<const unsigned short*>(gxa + x_off(row, 3 * k + 1, a.KX)));
-          }
-          return __half2float(__ushort_as_half(hb)) + __half2float(__ushort_as_half(lb));
-        };
-        uint32_t oq[16];
+        uint32_t oq[16], xa0[16], xa1[16] = {};
         tmem_ld16(tACC + 16 * (qc >> 4), oq);
-        tmem_ld_wait_regs(oq);
-        const float qs = __uint_as_float(oq[qc & 15]);
-        if (k0 == 0) {
-          float v = qs;
-#pragma unroll
-          for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-          if (lane == 0) wp[0] += (double)v;
+        if (!XS) {
+          tmem_ld16(tbase + lofs + kColXA, xa0);
+          if (3 * d > 32) tmem_ld16(tbase + lofs + kColXA + 16, xa1);
         }
-        auto fold_dim = [&](int kk, float R, float T) {
-          const float x = xt_dim(kk);
-          float e = fmaf(x, fmaf(x, qs, -2.f * R), T);
 #pragma unroll
-          for (int sft = 16; sft > 0; sft >>= 1) e += __shfl_down_sync(0xffffffffu, e, sft);
-          if (lane == 0) wp[1 + k0 + kk] += (double)e;
-        };
-        if (!a.ksplit) {
+        for (int g = 0; g < kMaxDT / 8; ++g) {
+          if (8 * g >= dk) break;
+          // the group's R and T columns; the first group's wait also covers q
+          // and the XA rows
+          uint32_t o0[16], o1[16] = {};
+          if (!a.ksplit) {
+            // dimension kk: columns 4 kk .. 4 kk + 3 = (R hi, R lo, T hi, T lo);
+            // only columns below NACC = round16(4 dk + 1) are read: the second
+            // load only when the group has a dimension past its fourth
+            tmem_ld16(tACC + 32 * g, o0);
+            if (8 * g + 4 < dk) tmem_ld16(tACC + 32 * g + 16, o1);
+          } else {
+            // R of kk at column kk, T at toff + kk
+            tmem_ld16(tACC + 16 * (g >> 1), o0);
+            tmem_ld16(tACC + a.toff + 16 * (g >> 1), o1);
+          }
+          float xt[8];
 #pragma unroll
-          for (int c4 = 0; c4 < (kMaxDT + 3) / 4; ++c4) {
-            if (4 * c4 < dk) {
-              uint32_t o[16];
-              tmem_ld16(tACC + 16 * c4, o);
-              tmem_ld_wait_regs(o);
-#pragma unroll
-              for (int uu = 0; uu < 4; ++uu) {
-                const int kk = 4 * c4 + uu;
-                if (kk < dk)
-                  fold_dim(kk, __uint_as_float(o[4 * uu]) + __uint_as_float(o[4 * uu + 1]),
-                           __uint_as_float(o[4 * uu + 2]) + __uint_as_float(o[4 * uu + 3]));
-              }
+          for (int u = 0; u < 8; ++u) {
+            const int kk = 8 * g + u;
+            xt[u] = 0.f;
+            if (XS && kk < dk) {
+              const int k = k0 + kk;
+              const uint16_t hb = __ldg(reinterpret_cast<const unsigned short*>(gxa + x_off(row, 3 * k, a.KX)));
+              const uint16_t lb = __ldg(reinterpret_cast<const unsigned short*>(gxa + x_off(row, 3 * k + 1, a.KX)));
+              xt[u] = __half2float(__ushort_as_half(hb)) + __half2float(__ushort_as_half(lb));
             }
           }
-        } else {
+          if (g == 0)
+            tmem_ld_wait_regs(o0, o1, oq, xa0, xa1);
+          else
+            tmem_ld_wait_regs(o0, o1);
+          const float qs = __uint_as_float(oq[qc & 15]);
+          float e[8];
 #pragma unroll
-          for (int c16 = 0; c16 < kMaxDT / 16; ++c16) {
-            if (16 * c16 < dk) {
-              uint32_t oR[16], oT[16];
-              tmem_ld16(tACC + 16 * c16, oR);
-              tmem_ld16(tACC + a.toff + 16 * c16, oT);
-              tmem_ld_wait_regs(oR, oT);
-#pragma unroll
-              for (int uu = 0; uu < 16; ++uu) {
-                const int kk = 16 * c16 + uu;
-                if (kk < dk) fold_dim(kk, __uint_as_float(oR[uu]), __uint_as_float(oT[uu]));
+          for (int u = 0; u < 8; ++u) {
+            const int kk = 8 * g + u;
+            if (!XS && kk < dk) {
+              // one dimension block when XA is in TMEM (k = kk): register
+              // indices fixed at compile time
+              constexpr int kMaxXtReg = 31;
+              const int ih = (3 * kk) >> 1, il = (3 * kk + 1) >> 1;
+              if (il <= kMaxXtReg) {
+                const uint32_t wh = ih < 16 ? xa0[ih & 15] : xa1[ih & 15];
+                const uint32_t wl = il < 16 ? xa0[il & 15] : xa1[il & 15];
+                const uint16_t hb = (uint16_t)(((3 * kk) & 1) ? (wh >> 16) : (wh & 0xffffu));
+                const uint16_t lb = (uint16_t)(((3 * kk + 1) & 1) ? (wl >> 16) : (wl & 0xffffu));
+                xt[u] = __half2float(__ushort_as_half(hb)) + __half2float(__ushort_as_half(lb));
               }
             }
+            float R, T;
+            if (!a.ksplit) {
+              const uint32_t* o = u < 4 ? o0 : o1;
+              const int cc = 4 * (u & 3);
+              R = __uint_as_float(o[cc]) + __uint_as_float(o[cc + 1]);
+              T = __uint_as_float(o[cc + 2]) + __uint_as_float(o[cc + 3]);
+            } else {
+              R = __uint_as_float(o0[8 * (g & 1) + u]);
+              T = __uint_as_float(o1[8 * (g & 1) + u]);
+            }
+            e[u] = kk < dk ? fmaf(xt[u], fmaf(xt[u], qs, -2.f * R), T) : 0.f;
+          }
+          const float sum = warp_reduce_scatter8(e, lane);
+          two_sum_add(accg[g], cmpg[g], sum);
+          if (g == 0 && k0 == 0) {
+            float v = qs;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            two_sum_add(accq, cmpq, v);
           }
         }
       };
@@ -501,17 +539,19 @@ __global__ void __launch_bounds__(kTsThreads, 1) tc_bwd_ts_kernel(TcBwdArgs a) {
           }
           if (j > 0) {
             // the feature sums of Q(j-1) are done: Q_b may be overwritten, and
-            // ACC_b is complete up to half j-1 (fold it when a fold ends there)
+            // ACC_b is complete up to half j-1
             ok = mbar_wait(&q_free[b], (uint32_t)(qf & 1), abort, a.err, 30);
             if (!__all_sync(0xffffffffu, ok)) goto exp_out;
             ++qf;
             tc_fence_after();
-            if (((j - 1) % kFoldOwn) == kFoldOwn - 1) fold();
           }
           tmem_st32(tQh, qh);
           tmem_st32(tQl, qq);
         }
         tmem_st_wait();
+        // a fold ending at half j-1 reads ACC_b before the sums of Q(j) may
+        // restart it (they are issued after q_ready)
+        if (j > 0 && ((j - 1) % kFoldOwn) == kFoldOwn - 1) fold();
         tc_fence_before();
         mbar_arrive(&q_ready[b]);
       }
@@ -523,10 +563,22 @@ __global__ void __launch_bounds__(kTsThreads, 1) tc_bwd_ts_kernel(TcBwdArgs a) {
         tc_fence_after();
         fold();
       }
-      if (lane == 0) {
-        // per-warp partial of this item: [q, contrib_0 .. contrib_{d-1}]
+      {
+        // per-warp partial of this item: [q, contrib_0 .. contrib_{d-1}], the
+        // entries outside the dimension block zero
         double* out = a.gpart + (((size_t)a.chunk * a.n_items + t) * kFoldWarps + b * 4 + w) * kGW;
-        for (int v = 0; v <= d; ++v) out[v] = wp[v];
+        for (int v = lane; v <= d; v += 32) {
+          const int kk = v - 1 - k0;
+          if (v > 0 && kk >= 0 && kk < dk) continue;
+          out[v] = v == 0 && k0 == 0 ? (double)accq + (double)cmpq : 0.0;
+        }
+        if ((lane & 3) == 0) {
+#pragma unroll
+          for (int g = 0; g < kMaxDT / 8; ++g) {
+            const int kk = 8 * g + (lane >> 2);
+            if (kk < dk) out[1 + k0 + kk] = (double)accg[g] + (double)cmpg[g];
+          }
+        }
       }
     }
   exp_out:;
@@ -674,7 +726,10 @@ __global__ void __launch_bounds__(kFinThreads) tc_bwd_finalize_kernel(
     const int64_t r0 = ((int64_t)ch * n_items + pref[s]) * kFoldWarps;
     for (int64_t r = threadIdx.x; r < n_rows; r += kFinThreads) {
       const double* row = gpart + (r0 + r) * kGW;
-      for (int v = 0; v <= d; ++v) acc[v] += row[v];
+      // compile-time indices keep acc in registers
+#pragma unroll
+      for (int v = 0; v < kGW; ++v)
+        if (v <= d) acc[v] += row[v];
     }
   }
   for (int it = L.inst_item0[b] + threadIdx.x; it < L.inst_item0[b + 1]; it += kFinThreads) {
@@ -728,7 +783,7 @@ kmv_status tc_backward(kmv_handle h, const KmvArgs& a, double* grad, cudaStream_
   const int n_sys = L.n_inst * L.chains;
   const int KX = x_width(a.d, kSplitF16);
   const size_t max_stages = tl.stages > 0 ? (size_t)std::max(2, std::min(tl.stages, 6)) : 6;
-  const size_t fixed = 1024 + kTsBarBytes + kTsFoldBytes;
+  const size_t fixed = 1024 + kTsBarBytes;
   // Feature-sum layout, dimensions per launch (dk), columns of G, V per launch
   // (mc) and where XA lives: the two accumulators and (unless XS) the XA rows
   // must fit the TMEM columns left by S, W and Q (128), and the GI tile, the

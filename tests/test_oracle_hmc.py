@@ -176,3 +176,32 @@ def test_sampler_matches_quadrature_tiny_n():
         emp = np.array([(trace[:, :, ax] <= p).mean() for p in pts])
         ref = np.interp(pts, g, cdfs[ax])
         assert np.abs(emp - ref).max() < radius, (ax, np.abs(emp - ref).max(), radius)
+
+
+def test_c1_step_005_is_beyond_the_unit_mass_leapfrog_stability_limit():
+    # The N = 2048 workload (d = 1, alpha = 1, l = 0.2, sigma^2 = 0.01) with the
+    # paper's M = I (Sec. 3.2) and the exact FP64 force: at dt = 0.01 the energy
+    # error stays small along the trajectory, at dt = 0.05 it grows
+    # geometrically step after step (the stiffest mode of U has
+    # dt * omega > 2), so no update can be accepted at that step whatever the
+    # precision of the products.
+    w = wl.c1()
+    X, y = w.X.astype(np.float64), w.y.astype(np.float64)
+    th0 = np.array(w.theta[0], np.float64)
+    rng = np.random.default_rng(11)
+    xi, pi0 = rng.standard_normal(w.n_total), rng.standard_normal(th0.shape)
+    phi = hmc.phi_exact(X, th0, xi, False)
+    H0 = hmc.hamiltonian(X, y, phi, th0, pi0, False)
+
+    def energy_errors(dt, n):
+        th, pi, out = th0.copy(), pi0.copy(), []
+        for _ in range(n):
+            th, pi = hmc.leapfrog(X, y, phi, th, pi, dt, False)
+            out.append(hmc.hamiltonian(X, y, phi, th, pi, False) - H0)
+        return np.array(out)
+
+    small = energy_errors(0.01, 4)
+    assert np.abs(small).max() < 0.05, small
+    big = np.abs(energy_errors(0.05, 4))
+    assert big[-1] > 20.0, big
+    assert np.all(big[2:] / big[1:-1] > 5.0), big
