@@ -21,9 +21,10 @@
 //                  MMAs overlap in the tensor pipe and keep the warpgroups
 //                  independent of each other.
 //   warps 0-7    : two exp warpgroups, one per I tile: TMEM S -> ex2 -> F16 P
-//                  written back over S (the second half tile's TMEM loads
-//                  overlap the first half's exps), and every kFold J tiles
-//                  the FP32 O accumulator is folded into FP64.
+//                  written to its own TMEM columns (the second half tile's
+//                  TMEM loads overlap the first half's exps), and every kFold
+//                  J tiles the FP32 O accumulator is folded into per-column
+//                  FP32 pair sums (TwoSum), written in FP64 once per item.
 // An epilogue kernel sums the per-item partials in a fixed order and applies
 // Y = alpha O + (sigma^2 + shift) V.
 #include <cuda_bf16.h>
@@ -315,9 +316,11 @@ __global__ void __launch_bounds__(kFwdThreads, 1) tc_fwd_kernel(TcFwdArgs a) {
       const int4 item = a.items[t];
       if (a.sys_active && !a.sys_active[item.x]) continue;
       const int rowp = g * 128 + row;
-      double racc[RM > 0 ? RM : 1];
+      // the item's O sums per column as FP32 pairs (TwoSum; the FP64 pipe is a
+      // small fraction of the FP32 rate on this GPU), written in FP64
+      float rs[RM > 0 ? RM : 1], rc[RM > 0 ? RM : 1];
 #pragma unroll
-      for (int q = 0; q < (RM > 0 ? RM : 1); ++q) racc[q] = 0.0;
+      for (int q = 0; q < (RM > 0 ? RM : 1); ++q) rs[q] = rc[q] = 0.f;
       bool first = true;
       for (int j = 0; j < item.w; ++j, ++k) {
         bool ok = mbar_wait(&s_full[g], sph, abort, a.err, 8);
@@ -377,7 +380,7 @@ __global__ void __launch_bounds__(kFwdThreads, 1) tc_fwd_kernel(TcFwdArgs a) {
                 tmem_ld16(tl + o_col + c0, o);
                 tmem_ld_wait_regs(o);
 #pragma unroll
-                for (int q = 0; q < 16; ++q) racc[c0 + q] += (double)__uint_as_float(o[q]);
+                for (int q = 0; q < 16; ++q) two_sum_add(rs[c0 + q], rc[c0 + q], __uint_as_float(o[q]));
               }
             }
           } else {
@@ -404,7 +407,7 @@ __global__ void __launch_bounds__(kFwdThreads, 1) tc_fwd_kernel(TcFwdArgs a) {
       if (RM > 0) {
 #pragma unroll
         for (int q = 0; q < (RM > 0 ? RM : 1); ++q)
-          if (q < a.mz) a.part[part_idx(t, a.mz, q, rowp)] = racc[q];
+          if (q < a.mz) a.part[part_idx(t, a.mz, q, rowp)] = (double)rs[q] + (double)rc[q];
       }
     }
   exp_out:;
@@ -744,9 +747,18 @@ __global__ void tc_center_kernel(DevLayout L, int n_inst, int d, const float* x,
 __global__ void tc_prep_x_kernel(DevLayout L, TcTables T, int n_inst, int chains, int d, int ard, int n_theta,
                                  int KX, int nsplit, int T_total, const float* x, const double* theta,
                                  const uint32_t* ckeys, uint8_t* XA, uint8_t* XB, int* err) {
+  __shared__ float s_sc[kMaxD], s_c[kMaxD];
   const int t = blockIdx.x, c = blockIdx.y, r = threadIdx.x;
   const int b = T.tile_inst[t];
   const int s = b * chains + c;
+  // scale sqrt(log2 e) / l_k and centre c_k of the tile's system, once per
+  // dimension (exp in FP64, once per block, not per point)
+  if (r < d) {
+    const double* th = theta + (int64_t)s * n_theta;
+    s_sc[r] = (float)(sqrt(2.0 * kHalfLog2e) * exp(-th[1 + (ard ? r : 0)]));
+    s_c[r] = center_of(ckeys, n_inst, d, b, r);
+  }
+  __syncthreads();
   const int64_t nb = L.offsets[b + 1] - L.offsets[b];
   const int64_t rl = (int64_t)(t - T.inst_tile0[b]) * 128 + r;
   const bool valid = rl < nb;
@@ -772,13 +784,11 @@ __global__ void tc_prep_x_kernel(DevLayout L, TcTables T, int n_inst, int chains
     return;
   }
   const int64_t i = L.offsets[b] + rl;
-  const double* th = theta + (int64_t)s * n_theta;
   double nrm = 0.0;
   bool range_ok = true;
   for (int k = 0; k < d; ++k) {
     // xh = (x - centre) sqrt(log2 e) / l, so that -|xh_i - xh_j|^2 / 2 = -log2(e) r^2 / 2
-    const float sc = (float)(sqrt(2.0 * kHalfLog2e) * exp(-th[1 + (ard ? k : 0)]));
-    const float xh = (x[i * d + k] - center_of(ckeys, n_inst, d, b, k)) * sc;
+    const float xh = (x[i * d + k] - s_c[k]) * s_sc[k];
     if (f16 && !(fabsf(xh) < 240.f)) range_ok = false;
     const uint16_t hi = enc(xh);
     const float r1 = xh - dec(hi);
@@ -846,12 +856,24 @@ __global__ void tc_vmax_kernel(DevLayout L, int chains, int64_t n_total, const f
   const int b = L.item_inst[item];
   const int s = b * chains + c;
   if (sys_active && !sys_active[s]) return;
+  __shared__ uint32_t smx[kTile / 32];
   const int64_t i = L.item_row0[item] + threadIdx.x;
-  if (i >= L.offsets[b + 1]) return;
-  const float am = amp ? amp[(int64_t)c * n_total + i] : 1.f;
+  const bool valid = i < L.offsets[b + 1];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const float am = (valid && amp) ? amp[(int64_t)c * n_total + i] : 1.f;
+  // per column: the block's maximum (as order-preserving bits of a
+  // non-negative float) by a warp and a block reduction, then one atomic
   for (int q = 0; q < mz; ++q) {
-    const float v = fabsf(V[((int64_t)c * n_total + i) * m + c0 + q] * am);
-    atomicMax(&vmax[(int64_t)s * mz + q], __float_as_uint(v));
+    const float v = valid ? fabsf(V[((int64_t)c * n_total + i) * m + c0 + q] * am) : 0.f;
+    const uint32_t u = __reduce_max_sync(0xffffffffu, __float_as_uint(v));
+    if (lane == 0) smx[w] = u;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      uint32_t mx = smx[0];
+      for (int k = 1; k < kTile / 32; ++k) mx = max(mx, smx[k]);
+      if (mx != 0u) atomicMax(&vmax[(int64_t)s * mz + q], mx);
+    }
+    __syncthreads();
   }
 }
 
@@ -880,10 +902,18 @@ __global__ void tc_prep_v_kernel(DevLayout L, TcTables T, int chains, int64_t n_
 __global__ void tc_fwd_epilogue_kernel(DevLayout L, TcTables T, KmvArgs a, int c0, int mz, const double* part,
                                        const uint32_t* vmax, const int* err) {
   __shared__ double red[kTile / 32];
+  __shared__ double s_alpha, s_s2;
   const int item = blockIdx.x, c = blockIdx.y;
   const int b = L.item_inst[item];
   const int s = b * a.chains + c;
   if (a.sys_active && !a.sys_active[s]) return;
+  if (threadIdx.x == 0) {
+    // alpha and sigma^2 of the system (FP64 exp once per block)
+    const double* th = a.theta + (int64_t)s * a.n_theta;
+    s_alpha = exp(th[0]);
+    s_s2 = exp(th[a.n_theta - 1]);
+  }
+  __syncthreads();
   const int64_t i = L.item_row0[item] + threadIdx.x;
   const bool valid = i < L.offsets[b + 1];
   const int tile_in_inst = (int)((L.item_row0[item] - L.offsets[b]) / 128);
@@ -891,8 +921,7 @@ __global__ void tc_fwd_epilogue_kernel(DevLayout L, TcTables T, KmvArgs a, int c
   const int nk = T.inst_nk[b];
   const int64_t it0 = T.sys_item0[s] + (int64_t)p * nk;
   const int rowp = half * 128 + threadIdx.x;
-  const double* th = a.theta + (int64_t)s * a.n_theta;
-  const double alpha = exp(th[0]), s2 = exp(th[a.n_theta - 1]);
+  const double alpha = s_alpha, s2 = s_s2;
   const bool bad = *err != 0;
   double dot = 0.0;
   if (valid) {
@@ -904,7 +933,10 @@ __global__ void tc_fwd_epilogue_kernel(DevLayout L, TcTables T, KmvArgs a, int c
       const int64_t idx = ((int64_t)c * a.n_total + i) * a.m + col;
       const double shift = a.col_shift ? (double)a.col_shift[(int64_t)s * a.col_shift_stride + col] : 0.0;
       const double vi = (double)a.V[idx];
-      double y = ai * acc / (double)col_scale(vmax[(int64_t)s * mz + q]) + (a.no_diag ? 0.0 : (s2 + shift) * vi);
+      // the column scale is a power of two: multiplying by its reciprocal is
+      // exact, and avoids an FP64 divide per element
+      const double inv_sc = col_scale_inv(vmax[(int64_t)s * mz + q]);
+      double y = ai * acc * inv_sc + (a.no_diag ? 0.0 : (s2 + shift) * vi);
       if (bad) y = __longlong_as_double(0x7ff8000000000000ll);
       a.Y[idx] = (float)y;
       if (a.Y64) a.Y64[idx] = y;

@@ -154,18 +154,6 @@ __device__ __forceinline__ float warp_reduce_scatter8(const float (&v)[8], int l
   return z;
 }
 
-// Running sum as an unevaluated pair s + c: each addition's rounding error,
-// recovered exactly by Knuth's TwoSum, is added to c, so (double)s + (double)c
-// differs from the exact sum of the terms by about u^2 times the sum of their
-// magnitudes (u = 2^-24) instead of u times it.
-__device__ __forceinline__ void two_sum_add(float& s, float& c, float x) {
-  const float t = __fadd_rn(s, x);
-  const float bp = __fsub_rn(t, s);
-  const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(x, bp));
-  c = __fadd_rn(c, err);
-  s = t;
-}
-
 template <bool XS>
 __global__ void __launch_bounds__(kTsThreads, 1) tc_bwd_ts_kernel(TcBwdArgs a) {
   using namespace ptx;
@@ -639,10 +627,20 @@ __global__ void tc_prep_bwd_kernel(DevLayout L, TcTables T, int n_inst, int chai
                                    const float* V, const float* G, int64_t n_total, const uint32_t* gmax,
                                    const uint32_t* vmax, const int32_t* sys_active, const float* amp,
                                    uint8_t* GI, uint8_t* VJ, uint8_t* BG, int* err) {
+  __shared__ float s_sc[kMaxDT], s_c[kMaxDT];
   const int t = blockIdx.x, c = blockIdx.y, r = threadIdx.x;
   const int b = T.tile_inst[t];
   const int s = b * chains + c;
   if (sys_active && !sys_active[s]) return;
+  // scale sqrt(log2 e) / l_k and centre c_k of the block's dimensions, once
+  // per block (exp in FP64)
+  if (r < dk) {
+    const double* th = theta + (int64_t)s * n_theta;
+    const int k = k0 + r;
+    s_sc[r] = (float)(sqrt(2.0 * kHalfLog2e) * exp(-th[1 + (ard ? k : 0)]));
+    s_c[r] = center_of(ckeys, n_inst, d, b, k);
+  }
+  __syncthreads();
   const int64_t nb = L.offsets[b + 1] - L.offsets[b];
   const int64_t rl = (int64_t)(t - T.inst_tile0[b]) * 128 + r;
   const bool valid = rl < nb;
@@ -654,34 +652,45 @@ __global__ void tc_prep_bwd_kernel(DevLayout L, TcTables T, int n_inst, int chai
   const float am = (valid && amp) ? amp[(int64_t)c * n_total + i] : 1.f;
   const float gs = (float)row_scale(gmax[s]) * am, vs = (float)row_scale(vmax[s]) * am;
   const __half zh = __float2half_rn(0.f);
-  for (int q = 0; q < KG; ++q) {
-    __half gval = zh, vval = zh;
-    if (valid && q < 6 * mc) {
-      const int col = q % mc, part = q / mc;
-      const int64_t idx = ((int64_t)c * n_total + i) * m + c0 + col;
-      const float gq = G[idx] * gs, vq = V[idx] * vs;
-      const __half gh = __float2half_rn(gq), vh = __float2half_rn(vq);
-      const __half gl = __float2half_rn(gq - __half2float(gh));
-      const __half vl = __float2half_rn(vq - __half2float(vh));
-      if (part < 3) {
-        gval = part < 2 ? gh : gl;        // [gh, gh, gl]
-        vval = part == 1 ? vl : vh;       // [vh, vl, vh]
-      } else {
-        // symmetrised second half: I rows [vh, vh, vl], J rows [gh, gl, gh]
-        gval = part < 5 ? vh : vl;
-        vval = part == 4 ? gl : gh;
-      }
+  // feature q = part * mc + col: GI rows [gh, gh, gl | vh, vh, vl], VJ rows
+  // [vh, vl, vh | gh, gl, gh] (the second half symmetrises W).  Eight
+  // consecutive features of a row are 16 contiguous bytes of the tile: each
+  // thread assembles them and writes them with one 16-byte store.
+  auto feature = [&](int q, __half& gval, __half& vval) {
+    gval = vval = zh;
+    if (!valid || q >= 6 * mc) return;
+    const int col = q % mc, part = q / mc;
+    const int64_t idx = ((int64_t)c * n_total + i) * m + c0 + col;
+    const float gq = G[idx] * gs, vq = V[idx] * vs;
+    const __half gh = __float2half_rn(gq), vh = __float2half_rn(vq);
+    const __half gl = __float2half_rn(gq - __half2float(gh));
+    const __half vl = __float2half_rn(vq - __half2float(vh));
+    if (part < 3) {
+      gval = part < 2 ? gh : gl;
+      vval = part == 1 ? vl : vh;
+    } else {
+      gval = part < 5 ? vh : vl;
+      vval = part == 4 ? gl : gh;
     }
-    gi[x_off(r, q, KG) / 2] = gval;
-    vj[x_off(r, q, KG) / 2] = vval;
+  };
+  for (int q0 = 0; q0 < KG; q0 += 8) {
+    uint32_t gw[4], vw[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      __half g0, v0, g1, v1;
+      feature(q0 + 2 * e, g0, v0);
+      feature(q0 + 2 * e + 1, g1, v1);
+      gw[e] = (uint32_t)__half_as_ushort(g0) | ((uint32_t)__half_as_ushort(g1) << 16);
+      vw[e] = (uint32_t)__half_as_ushort(v0) | ((uint32_t)__half_as_ushort(v1) << 16);
+    }
+    *reinterpret_cast<uint4*>(reinterpret_cast<uint8_t*>(gi) + x_off(r, q0, KG)) = make_uint4(gw[0], gw[1], gw[2], gw[3]);
+    *reinterpret_cast<uint4*>(reinterpret_cast<uint8_t*>(vj) + x_off(r, q0, KG)) = make_uint4(vw[0], vw[1], vw[2], vw[3]);
   }
-  const double* th = theta + (int64_t)s * n_theta;
   for (int f = 0; f < NB; ++f) bg[t_off(f, r) / 2] = zh;
   if (valid) {
     for (int kk = 0; kk < dk; ++kk) {
       const int k = k0 + kk;
-      const float sc = (float)(sqrt(2.0 * kHalfLog2e) * exp(-th[1 + (ard ? k : 0)]));
-      const float xh = (x[i * d + k] - center_of(ckeys, n_inst, d, b, k)) * sc;
+      const float xh = (x[i * d + k] - s_c[kk]) * s_sc[kk];
       const __half hi = __float2half_rn(xh);
       const __half lo = __float2half_rn(xh - __half2float(hi));
       const float xtv = __half2float(hi) + __half2float(lo);
@@ -710,21 +719,26 @@ __global__ void tc_prep_bwd_kernel(DevLayout L, TcTables T, int n_inst, int chai
 // the threads, so the result is bitwise reproducible.
 constexpr int kFinThreads = 256;
 
-__global__ void __launch_bounds__(kFinThreads) tc_bwd_finalize_kernel(
-    DevLayout L, const int32_t* pref, int n_items, int n_chunks, int chains, int n_theta, int ard, int d,
-    const double* theta, const double* gpart, const double* gvpart, const double* gvdiag, const uint32_t* gmax,
-    const uint32_t* vmax, const int32_t* sys_active, const int* err, double* grad) {
+// Partial sums of one system's gradient partials over a fixed slice of its
+// (item, warp) rows, all chunks, entries 0..d (q and the d dimensions); slice
+// 0 also sums the instance's G.V terms.  Grid (systems, slices): the slices
+// spread a single large system over many SMs, and the fixed split keeps the
+// order of the sums, hence the result, the same on every run.
+__global__ void __launch_bounds__(kFinThreads) tc_bwd_fin_part_kernel(
+    DevLayout L, const int32_t* pref, int n_items, int n_chunks, int chains, int d, int n_slices,
+    const double* gpart, const double* gvpart, const double* gvdiag, const int32_t* sys_active, double* fin) {
   __shared__ double red[kFinThreads / 32][kGW + 2];
-  const int s = blockIdx.x;
+  const int s = blockIdx.x, p = blockIdx.y;
   if (sys_active && !sys_active[s]) return;
   const int b = s / chains, c = s - b * chains;
-  const int64_t n_rows = (int64_t)(pref[s + 1] - pref[s]) * kFoldWarps;   // (item, warp) partial rows per block
+  const int64_t n_rows = (int64_t)(pref[s + 1] - pref[s]) * kFoldWarps;   // (item, warp) partial rows per chunk
+  const int64_t q0 = n_rows * p / n_slices, q1 = n_rows * (p + 1) / n_slices;
   double acc[kGW + 2];
 #pragma unroll
   for (int v = 0; v <= kGW + 1; ++v) acc[v] = 0.0;
   for (int ch = 0; ch < n_chunks; ++ch) {
     const int64_t r0 = ((int64_t)ch * n_items + pref[s]) * kFoldWarps;
-    for (int64_t r = threadIdx.x; r < n_rows; r += kFinThreads) {
+    for (int64_t r = q0 + threadIdx.x; r < q1; r += kFinThreads) {
       const double* row = gpart + (r0 + r) * kGW;
       // compile-time indices keep acc in registers
 #pragma unroll
@@ -732,25 +746,51 @@ __global__ void __launch_bounds__(kFinThreads) tc_bwd_finalize_kernel(
         if (v <= d) acc[v] += row[v];
     }
   }
-  for (int it = L.inst_item0[b] + threadIdx.x; it < L.inst_item0[b + 1]; it += kFinThreads) {
-    acc[kGW] += gvpart[(int64_t)it * chains + c];
-    acc[kGW + 1] += gvdiag[(int64_t)it * chains + c];
+  if (p == 0) {
+    for (int it = L.inst_item0[b] + threadIdx.x; it < L.inst_item0[b + 1]; it += kFinThreads) {
+      acc[kGW] += gvpart[(int64_t)it * chains + c];
+      acc[kGW + 1] += gvdiag[(int64_t)it * chains + c];
+    }
   }
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll
   for (int v = 0; v <= kGW + 1; ++v) {
-    double u = acc[v];
+    if (v <= d || v >= kGW) {
+      double u = acc[v];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) u += __shfl_down_sync(0xffffffffu, u, o);
-    if (lane == 0) red[w][v] = u;
+      for (int o = 16; o > 0; o >>= 1) u += __shfl_down_sync(0xffffffffu, u, o);
+      if (lane == 0) red[w][v] = u;
+    }
   }
   __syncthreads();
-  if (threadIdx.x != 0) return;
-  double tot[kGW + 2];
-  for (int v = 0; v <= kGW + 1; ++v) {
-    tot[v] = 0.0;
-    for (int ww = 0; ww < kFinThreads / 32; ++ww) tot[v] += red[ww][v];
+  double* out = fin + ((int64_t)s * n_slices + p) * (kGW + 2);
+  for (int v = threadIdx.x; v <= kGW + 1; v += kFinThreads) {
+    double tot = 0.0;
+    if (v <= d || v >= kGW)
+      for (int ww = 0; ww < kFinThreads / 32; ++ww) tot += red[ww][v];
+    out[v] = tot;
   }
+}
+
+// The gradient of each system from its slices' sums: one block per system,
+// thread v sums entry v over the slices in slice order, thread 0 applies the
+// scales.
+constexpr int kFinalThreads = 64;   // >= kGW + 2
+static_assert(kFinalThreads >= kGW + 2, "one thread per entry");
+__global__ void __launch_bounds__(kFinalThreads) tc_bwd_finalize_kernel(
+    int n_theta, int ard, int d, int n_slices, const double* theta, const double* fin, const uint32_t* gmax,
+    const uint32_t* vmax, const int32_t* sys_active, const int* err, double* grad) {
+  __shared__ double tot[kGW + 2];
+  const int s = blockIdx.x, v = threadIdx.x;
+  if (sys_active && !sys_active[s]) return;
+  if (v <= kGW + 1) {
+    double acc = 0.0;
+    if (v <= d || v >= kGW)
+      for (int p = 0; p < n_slices; ++p) acc += fin[((int64_t)s * n_slices + p) * (kGW + 2) + v];
+    tot[v] = acc;
+  }
+  __syncthreads();
+  if (v != 0) return;
   const double* th = theta + (int64_t)s * n_theta;
   const double alpha = exp(th[0]), s2 = exp(th[n_theta - 1]);
   // W^s carried the scales of G and V
@@ -859,7 +899,12 @@ kmv_status tc_backward(kmv_handle h, const KmvArgs& a, double* grad, cudaStream_
   const size_t o_gd = o_gv + gvb;
   const size_t o_ck = o_gd + gvb;
   const size_t o_gp = o_ck + al(tc_center_bytes(L));
-  const size_t o_er = o_gp + al(sizeof(double) * (size_t)n_chunks * std::max(1, n_items) * kFoldWarps * kGW);
+  // slices of the finalize: about kFinThreads partial rows per slice on
+  // average, at most 32 per system
+  const int64_t rows_per_sys = (int64_t)std::max(1, n_items) * kFoldWarps / std::max(1, n_sys);
+  const int n_slices = (int)std::max<int64_t>(1, std::min<int64_t>(32, (rows_per_sys + kFinThreads - 1) / kFinThreads));
+  const size_t o_fn = o_gp + al(sizeof(double) * (size_t)n_chunks * std::max(1, n_items) * kFoldWarps * kGW);
+  const size_t o_er = o_fn + al(sizeof(double) * (size_t)n_sys * n_slices * (kGW + 2));
   stt = tc_ensure_buf(h, S, o_er + 256);
   if (stt != KMV_OK) return stt;
   uint8_t* base = static_cast<uint8_t*>(S->buf);
@@ -869,6 +914,7 @@ kmv_status tc_backward(kmv_handle h, const KmvArgs& a, double* grad, cudaStream_
   double* gvdiag = reinterpret_cast<double*>(base + o_gd);
   uint32_t* ckeys = reinterpret_cast<uint32_t*>(base + o_ck);
   double* gpart = reinterpret_cast<double*>(base + o_gp);
+  double* fin = reinterpret_cast<double*>(base + o_fn);
   int* err = reinterpret_cast<int*>(base + o_er);
 
   if (!S->bwd_attr_set) {
@@ -939,9 +985,10 @@ kmv_status tc_backward(kmv_handle h, const KmvArgs& a, double* grad, cudaStream_
       }
     }
   }
-  tc_bwd_finalize_kernel<<<n_sys, kFinThreads, 0, st>>>(h->dev, S->dev.sym_pref, n_items, n_chunks, L.chains,
-                                                         a.n_theta, a.ard, a.d, a.theta, gpart, gvpart, gvdiag, gmax,
-                                                         vmax, a.sys_active, err, grad);
+  tc_bwd_fin_part_kernel<<<dim3(n_sys, n_slices), kFinThreads, 0, st>>>(
+      h->dev, S->dev.sym_pref, n_items, n_chunks, L.chains, a.d, n_slices, gpart, gvpart, gvdiag, a.sys_active, fin);
+  tc_bwd_finalize_kernel<<<n_sys, kFinalThreads, 0, st>>>(a.n_theta, a.ard, a.d, n_slices, a.theta, fin, gmax, vmax,
+                                                           a.sys_active, err, grad);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return tc_fail(h, KMV_ECUDA, cudaGetErrorString(e));
   if (a.Y != nullptr) {

@@ -179,5 +179,26 @@ __device__ __forceinline__ float col_scale(uint32_t bits) {
   return ldexpf(1.f, 14 - e);
 }
 
+// Running sum as an unevaluated pair s + c: each addition's rounding error,
+// recovered exactly by Knuth's TwoSum, is added to c, so (double)s + (double)c
+// differs from the exact sum of the terms by about u^2 times the sum of their
+// magnitudes (u = 2^-24) instead of u times it.
+__device__ __forceinline__ void two_sum_add(float& s, float& c, float x) {
+  const float t = __fadd_rn(s, x);
+  const float bp = __fsub_rn(t, s);
+  const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(x, bp));
+  c = __fadd_rn(c, err);
+  s = t;
+}
+
+// 1 / col_scale(bits), exactly (a power of two, formed from its exponent).
+__device__ __forceinline__ double col_scale_inv(uint32_t bits) {
+  const float mx = __uint_as_float(bits);
+  if (!(mx > 0.f) || !isfinite(mx)) return 1.0;
+  int e;
+  frexpf(mx, &e);
+  return __longlong_as_double((long long)(1023 + e - 14) << 52);
+}
+
 
 }  // namespace kmv
