@@ -38,7 +38,7 @@ FMA_LANES = 128        # FP32 FMA lanes per SM per clock
 MUFU_EX2_LANES = 32    # ex2 per SM per clock on GB300 (measured by an ex2 issue-rate micro-benchmark, profiles/issue_rates_gb300.md)
 # dram__bytes_read.sum + dram__bytes_write.sum per launch of the main loop, from an
 # ncu capture of the same workload; absent once the kernel changes after that capture.
-DRAM_TRAFFIC = {("bf16_hilo", "fwd"): 10542080}
+DRAM_TRAFFIC = {("bf16_hilo", "fwd"): 10552576}   # 10,552,064 read + 512 written (profiles/tc_kernels_c2.md)
 
 
 def peaks():
@@ -346,9 +346,10 @@ def main():
     ms_max = max_over_ranks(ms, world, dev)
     value = aggregate_rate(pairs, world, ms_max)
     # our kernels per step: FP32 form = forward, adjoint, finalize; BF16 form =
-    # forward (prep_x, vmax, prep_v, main, epilogue) + adjoint (norms, prep_x,
-    # prep, main, finalize) + dL/dV = A G through the forward (5 more)
-    launches_per_step = 3 if prec == "fp32" else 15
+    # forward (centre, prep_x, vmax, prep_v, main, epilogue) + adjoint (norms,
+    # centre, prep_x, prep, main, sliced partial sums, finalize) + dL/dV = A G
+    # through the forward (6 more)
+    launches_per_step = 3 if prec == "fp32" else 19
 
     # end to end through the public API: host inputs (pinned) -> device -> host results
     hX = torch.tensor(w.X, dtype=torch.float32).pin_memory()
@@ -447,7 +448,7 @@ def main():
 
 # leapfrog steps: stable for these workloads (0.05 drives log sigma^2 unstable on c1; the
 # curvature grows with N, so the 16,384-point case takes a smaller step)
-GRAPH_CG = 400   # CG iterations recorded per solve in the captured graph
+GRAPH_CG = 400   # cap on CG iterations per solve in the captured graph (its loop stops at convergence)
 
 
 def leapfrog_rates(h, dev, rank, world):
@@ -1024,7 +1025,7 @@ def run_suite_c3c4(args):
                          "ok_fraction": float((st == 0).float().mean())}
     pi0 = torch.tensor(0.1 * np.random.default_rng(6).standard_normal(w.theta.shape), dtype=torch.float64,
                        device=dev)
-    steps, dt, graph_cg = 2, 0.01, 400
+    steps, dt, graph_cg = 2, 0.01, 5000   # the captured solves stop at convergence, as the eager ones
     for prec in ("bf16_hilo", "fp32"):
         th, pi = th0.clone(), pi0.clone()
         xw = torch.empty_like(phi)
@@ -1059,7 +1060,7 @@ def run_suite_c3c4(args):
             torch.cuda.synchronize()
             r["graph_steps_per_s"] = steps / (time.perf_counter() - t0)
             r["graph_theta_maxdiff_vs_eager"] = float((th_g - th).abs().max())
-            r["graph_cg_iterations_per_solve"] = graph_cg
+            r["graph_cg_maxiter"] = graph_cg
         except Exception as e:  # capture needs a CUDA-graph capable torch build
             r["graph_unavailable"] = str(e)[:200]
         c4[prec] = r

@@ -271,8 +271,8 @@ kmv_status run_backward_stationary(kmv_handle h, KmvArgs a, double* grad, double
                                    kmv_precision prec, cudaStream_t st) {
   const Layout& L = h->layout;
   if (prec == KMV_BF16_HILO) {
-    // shapes outside the tensor-core adjoint's range (d > 15, or operand
-    // tiles that do not fit in shared memory) use the FP32 adjoint
+    // shapes outside the tensor-core adjoint's range (d > 32, or operand
+    // tiles that do not fit in tensor or shared memory) use the FP32 adjoint
     const kmv_status s = tc_backward(h, a, grad, st);
     if (s != KMV_EUNSUPPORTED) return s;
   }
