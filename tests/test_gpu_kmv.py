@@ -71,6 +71,18 @@ def _check_backward(h, w, prec):
     return we, wg
 
 
+# Block widths of the tensor-core adjoint's fold: one group of 8 dimensions or
+# several, the wide and the K-split accumulator layouts, XA in tensor or in
+# shared memory, one or two dimension blocks (d = 17..31).
+FOLD_DIMS = [6, 7, 9, 10, 11, 12, 15, 16, 17, 20, 24, 31]
+
+
+@pytest.mark.parametrize("d", FOLD_DIMS)
+def test_backward_parity_across_fold_widths(kmv_handle, d):
+    w = wl.ragged([230, 161], d=d, chains=1, m=5, ard=True, seed=900 + d)
+    _check_backward(kmv_handle, w, "bf16_hilo")
+
+
 CASES = [
     # sizes, d, chains, m, ard
     ([300], 1, 1, 1, False),
