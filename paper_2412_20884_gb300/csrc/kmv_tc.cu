@@ -43,8 +43,8 @@ namespace kmv {
 
 namespace {
 
-// J tiles accumulated in FP32 in TMEM before the FP64 fold (4096 columns):
-// the fold's FP64 adds are slow on this part, so they are kept rare.
+// J tiles accumulated in FP32 in TMEM before each fold (4096 columns) into
+// the per-column TwoSum pairs.
 constexpr int kFold = 32;
 // Forward warp roles: warps 0-7 two exp warpgroups, warp 8 MMA issuer for I
 // tile 0 (and TMEM owner), warp 9 producer, warp 10 MMA issuer for I tile 1.
