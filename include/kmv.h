@@ -76,10 +76,13 @@ typedef enum {
    * with a hi/lo split (hi.hi + hi.lo + lo.hi; a three-way split for m <= 2)
    * and the row biases folded into the same contraction, exp2 in FP32
    * registers, P.V in FP16 (FP32 on the FMA pipe for m <= 2) with FP32
-   * accumulation folded into FP64; relative error against FP64 <= 2e-3.
+   * accumulation over 4096 columns, folded exactly (TwoSum pairs) into FP64
+   * partials; relative error against FP64 <= 2e-3.  For m <= 2 and d <= 17
+   * the probabilities stay FP32 and the product has FP32 accuracy.
    * Adjoint: the exponent and G.V from F16 hi/lo operands, Q = W o K0 kept
-   * exactly as two F16 parts, feature sums folded into FP64 every 1024
-   * columns; gradients to 1e-4 relative like KMV_FP32.  The adjoint needs
+   * exactly as two F16 parts, feature sums accumulated over 256 columns and
+   * folded exactly into FP64 partials; gradients to 1e-4 relative like
+   * KMV_FP32.  The adjoint needs
    * |x_k - c_k| < 200 l_k and sum_k (x_k - c_k)^2 / l_k^2 < 2^16 / log2(e)
    * (c the centre); beyond, its gradients are NaN (use KMV_FP32). */
   KMV_BF16_HILO = 1
@@ -157,20 +160,22 @@ kmv_status kmv_backward(kmv_handle h, const kmv_points* pts, int32_t chains,
  *                otherwise ignored; overwritten with the solution.
  *   chain_status DEVICE int32 (n_inst * chains): KMV_OK or KMV_ENOTCONV.
  *   iters        DEVICE int32 (n_inst * chains) or NULL: iterations used.
- * KMV_BF16_HILO solves by mixed-precision iterative refinement: the residual
+ * KMV_BF16_HILO with d <= 17 runs CG directly on the tensor-core one-column
+ * product, whose probabilities are FP32 (FP32-accurate like KMV_FP32).  For
+ * d > 17 it solves by mixed-precision iterative refinement: the residual
  * rhs - A x is formed with the FP32 operator and each correction is solved by
- * CG with the tensor-core operator (to 1e-5 where the one-column product takes
- * the FMA-pipe form, else 1e-3), so the result meets `tol` against the FP32
- * operator, or stops where the residual no longer falls (its FP32 floor);
- * `iters` then counts the tensor-core CG iterations.  With a Nystrom
- * preconditioner set on the handle (kmv_set_preconditioner) the CG, and the
- * refinement's inner CG, are preconditioned.
+ * CG with the tensor-core operator (to 1e-3), so the result meets `tol`
+ * against the FP32 operator or reports KMV_ENOTCONV; `iters` then counts the
+ * tensor-core CG iterations.  With a Nystrom preconditioner set on the handle
+ * (kmv_set_preconditioner) the CG, and the refinement's inner CG, are
+ * preconditioned.
  * Outside stream capture, the call synchronises `stream` every few iterations
  * to test convergence on the host.  While `stream` is being captured into a
- * CUDA graph it records exactly cg_maxiter iterations instead (KMV_BF16_HILO:
- * three refinement steps of cg_maxiter each), with no host synchronisation;
- * converged systems idle on device-side masks, so a replay gives the eager
- * result whenever the eager solve converges within cg_maxiter.  Under capture
+ * CUDA graph, the iterations after the first are recorded as a conditional
+ * WHILE node whose condition a device kernel sets from the count of systems
+ * still active, so a replay stops at convergence (or at cg_maxiter) exactly
+ * like the eager solve, with no host synchronisation (the refined d > 17
+ * solve records three refinement steps).  Under capture
  * nothing may be allocated: make the same call (same shapes, same stream
  * device) once before capturing, and leapfrog_step / kmv_energy likewise.
  */
@@ -202,11 +207,11 @@ kmv_status kmv_cg_solve(kmv_handle h, const kmv_points* pts, int32_t chains,
  *                the solve failed (theta/pi then hold theta_h / the un-kicked pi;
  *                the caller must reject the trajectory).
  *   cg_iters     DEVICE int32 (n_inst * chains) or NULL.
- * prec selects the operator of the solve (KMV_BF16_HILO: refined to the FP32
- * residual, see kmv_cg_solve).  The force always uses the FP32 adjoint: its two
- * quadratic forms are sums of N^2 terms that cancel to a small fraction of
- * their size (x = A^-1 y oscillates), and the F16 rounding of the tensor-core
- * adjoint leaves errors far above the force there.
+ * prec selects the operator of the solve (see kmv_cg_solve) and the adjoint of
+ * the force.  The force's two quadratic forms are sums of N^2 terms that can
+ * cancel to a small fraction of their size (x = A^-1 y oscillates); the
+ * KMV_BF16_HILO adjoint keeps every pair's term near FP32 accuracy, so its
+ * force agrees with the FP32 one there too.
  */
 kmv_status leapfrog_step(kmv_handle h, const kmv_points* pts, int32_t chains,
                          const float* y, const float* phi, double* theta, double* pi,
@@ -298,10 +303,11 @@ kmv_status kmv_status_merge(int32_t n, const int32_t* src, int32_t* dst, void* s
  * bounds lambda_max because K0 >= 0 entrywise; 1% covers rounding).  The
  * n_poles shifted systems of every system share xi, so one CG sequence on the
  * smallest shift carries them all (multi-shift CG: the shifted iterates follow
- * from its scalars), each shift stopping at cg_tol.  The BF16 form then checks
- * every shifted solution with the FP32 operator and polishes those above
- * cg_tol by refinement (FP32 residuals, corrections by a multi-column CG whose
- * one product per iteration applies all the shifts as column shifts).
+ * from its scalars), each shift stopping at cg_tol.  For d > 17 (where its
+ * one-column product is not FP32-accurate) the BF16 form then checks every
+ * shifted solution with the FP32 operator and polishes those above cg_tol by
+ * refinement (FP32 residuals, corrections by a multi-column CG whose one
+ * product per iteration applies all the shifts as column shifts).
  *
  *   xi          DEVICE FP32 (chains, N_total): the caller's N(0, I) draw.
  *   phi         DEVICE FP32 (chains, N_total), written (must not alias xi).
@@ -312,8 +318,8 @@ kmv_status kmv_status_merge(int32_t n, const int32_t* src, int32_t* dst, void* s
  *   poles_out   DEVICE FP64 (n_inst * chains, 2 + 2 n_poles) or NULL:
  *               [sigma^2, M, w_1..w_Np, lambda_1..lambda_Np] per system.
  * Work: one N^2 pass for A 1, then one single-column N^2 product per CG
- * iteration (a system drops out when all its shifts have stopped); the BF16
- * check costs one n_poles-column FP32 product per refinement step.
+ * iteration (a system drops out when all its shifts have stopped); the d > 17
+ * BF16 check costs one n_poles-column FP32 product per refinement step.
  * cg_iters counts the multi-shift iterations plus the polishing ones.  Allocates workspace; not for use while the
  * stream is being captured (the work plan changes between the two phases).
  */
