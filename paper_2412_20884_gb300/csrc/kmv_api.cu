@@ -358,6 +358,7 @@ struct CgBufs {
   double *partial, *partial2;
   CgSys* sys;
   int32_t *active, *n_active;
+  uint32_t* count;   // 2 n_sys counters of the fused iteration (p.q step, r.r step)
 };
 
 size_t cg_layout(const Layout& L, Arena& ar, size_t off[8]) {
@@ -371,7 +372,7 @@ size_t cg_layout(const Layout& L, Arena& ar, size_t off[8]) {
   off[4] = ar.take(sizeof(double) * items * 2);
   off[5] = ar.take(sizeof(CgSys) * n_sys);
   off[6] = ar.take(sizeof(int32_t) * n_sys);
-  off[7] = ar.take(sizeof(int32_t) * 4);
+  off[7] = ar.take(sizeof(int32_t) * 4 + sizeof(uint32_t) * 2 * n_sys);
   return ar.used;
 }
 
@@ -385,6 +386,7 @@ CgBufs cg_bufs(kmv_handle h, const size_t off[8]) {
   b.sys = at<CgSys>(h, off[5]);
   b.active = at<int32_t>(h, off[6]);
   b.n_active = at<int32_t>(h, off[7]);
+  b.count = reinterpret_cast<uint32_t*>(b.n_active + 4);
   return b;
 }
 
@@ -412,11 +414,30 @@ kmv_status run_cg(kmv_handle h, const kmv_points* pts, const double* theta, cons
   a.Y = B.q;
   a.sys_active = B.active;
   a.dot_partial = B.partial;
+  // With the tensor-core one-column product (KMV_BF16_HILO where it takes the
+  // FMA-pipe form) an iteration needs no separate reduction or direction
+  // launches: the product forms p = r + beta p and its epilogue takes each
+  // system's p.q step, and the x, r update takes the r.r step, with the same
+  // per-system arithmetic in the same order as the separate kernels.
+  const bool fused = prec == KMV_BF16_HILO && x_width_fma_ok(pts->d) && L.n_items > 0;
+  if (fused) {
+    KMV_CUDA(h, cudaMemsetAsync(B.count, 0, sizeof(uint32_t) * 2 * n_sys, st));
+    a.cg_sys = B.sys;
+    a.cg_active = B.active;
+    a.cg_n_active = B.n_active;
+    a.cg_count = B.count;
+    a.cg_r = B.r;
+  }
   // one CG iteration on every active system; theta is fixed within the solve,
   // so the products after the first reuse its operand tiles
   auto iteration = [&](cudaStream_t s, int reuse) -> kmv_status {
     a.reuse_prep = reuse;
     KMV_TRY(run_forward(h, a, prec, s));
+    if (fused) {
+      KMV_CUDA(h, launch_cg_update_xr_rr(h->dev, L.n_items, L.chains, L.n_total, B.sys, B.active, x, B.r, B.p,
+                                         B.q, B.partial, B.count + n_sys, tol, maxiter, B.n_active, s));
+      return KMV_OK;
+    }
     KMV_CUDA(h, launch_cg_reduce_pq(h->dev, L.n_inst, L.chains, B.partial, B.sys, B.active, s));
     KMV_CUDA(h, launch_cg_update_xr(h->dev, L.n_items, L.chains, L.n_total, B.sys, B.active, x, B.r,
                                     B.p, B.q, B.partial, s));

@@ -5,6 +5,7 @@
 // CTAs return at once.
 // Dot products are FP64 per-CTA partials over kTile rows, reduced per system
 // in a fixed order (bitwise reproducible).
+#include "cg_common.cuh"
 #include "simt_common.cuh"
 
 namespace kmv {
@@ -49,14 +50,6 @@ cudaError_t launch_cg_init(const DevLayout& L, int n_items, int chains, int64_t 
 }
 
 // Sum of per-item partials of system s (stride entries apart, component k).
-__device__ __forceinline__ double sys_sum(const DevLayout& L, int b, int c, int chains,
-                                          const double* partial, int stride, int k) {
-  double acc = 0.0;
-  for (int it = L.inst_item0[b]; it < L.inst_item0[b + 1]; ++it)
-    acc += partial[((int64_t)it * chains + c) * stride + k];
-  return acc;
-}
-
 // Number of active systems, counted by one CTA (deterministic).
 __device__ __forceinline__ void count_active(int n_sys, const int32_t* active, int32_t* n_active) {
   __shared__ int cnt[8];
@@ -113,24 +106,9 @@ __global__ void cg_reduce_pq_kernel(DevLayout L, int n_inst, int chains, const d
                                     CgSys* sys, int32_t* active) {
   const int n_sys = n_inst * chains;
   for (int s = threadIdx.x; s < n_sys; s += blockDim.x) {
-    CgSys& S = sys[s];
     if (!active[s]) continue;
     const int b = s / chains, c = s - b * chains;
-    const double pq = sys_sum(L, b, c, chains, partial, 1, 0);
-    S.pq = pq;
-    if (!isfinite(pq)) {
-      S.status = KMV_ENONFINITE;
-      active[s] = 0;
-      S.alpha = 0.0;
-    } else if (!(pq > 0.0)) {
-      // breakdown: the operator is not positive definite along p (a perturbed
-      // operator can be); stop here with the current iterate
-      S.status = KMV_ENOTCONV;
-      active[s] = 0;
-      S.alpha = 0.0;
-    } else {
-      S.alpha = S.rr / pq;
-    }
+    if (!cg_pq_step(sys[s], sys_sum(L, b, c, chains, partial, 1, 0))) active[s] = 0;
   }
 }
 
@@ -170,27 +148,56 @@ cudaError_t launch_cg_update_xr(const DevLayout& L, int n_items, int chains, int
   return cudaGetLastError();
 }
 
+// x += alpha p, r -= alpha q and the r.r partials, as cg_update_xr_kernel;
+// the CTA of each system that finishes last then takes the system's r.r step
+// (as cg_reduce_rr_kernel) and keeps n_active up to date by decrements, so an
+// iteration needs no separate reduction launch.
+__global__ void cg_update_xr_rr_kernel(DevLayout L, int chains, int64_t n_total, CgSys* sys, int32_t* active,
+                                       float* x, float* r, const float* p, const float* q, double* partial,
+                                       uint32_t* count, double tol, int maxiter, int32_t* n_active) {
+  __shared__ double red[kTile / 32];
+  const int item = blockIdx.x, c = blockIdx.y;
+  const int b = L.item_inst[item];
+  const int s = b * chains + c;
+  if (!active[s]) return;
+  const int64_t i = L.item_row0[item] + threadIdx.x;
+  double rr = 0.0;
+  if (i < L.offsets[b + 1]) {
+    const int64_t v = (int64_t)c * n_total + i;
+    const float al = (float)sys[s].alpha;
+    x[v] = fmaf(al, p[v], x[v]);
+    const float ri = fmaf(-al, q[v], r[v]);
+    r[v] = ri;
+    rr = (double)ri * ri;
+  }
+  const double t = block_sum(rr, red);
+  if (threadIdx.x == 0) {
+    partial[(int64_t)item * chains + c] = t;
+    const bool last = last_block_of_system(count, s, (uint32_t)(L.inst_item0[b + 1] - L.inst_item0[b]));
+    if (last && !cg_rr_step(sys[s], sys_sum(L, b, c, chains, partial, 1, 0), tol, maxiter)) {
+      active[s] = 0;
+      atomicSub(n_active, 1);
+    }
+  }
+}
+
+cudaError_t launch_cg_update_xr_rr(const DevLayout& L, int n_items, int chains, int64_t n_total, CgSys* sys,
+                                   int32_t* active, float* x, float* r, const float* p, const float* q,
+                                   double* partial, uint32_t* count, double tol, int maxiter, int32_t* n_active,
+                                   cudaStream_t st) {
+  cg_update_xr_rr_kernel<<<dim3(n_items, chains), kTile, 0, st>>>(L, chains, n_total, sys, active, x, r, p, q,
+                                                                  partial, count, tol, maxiter, n_active);
+  return cudaGetLastError();
+}
+
 __global__ void cg_reduce_rr_kernel(DevLayout L, int n_inst, int chains, const double* partial,
                                     double tol, int maxiter, CgSys* sys, int32_t* active,
                                     int32_t* n_active) {
   const int n_sys = n_inst * chains;
   for (int s = threadIdx.x; s < n_sys; s += blockDim.x) {
-    CgSys& S = sys[s];
     if (!active[s]) continue;
     const int b = s / chains, c = s - b * chains;
-    const double rr = sys_sum(L, b, c, chains, partial, 1, 0);
-    S.iters += 1;
-    if (!isfinite(rr)) {
-      S.status = KMV_ENONFINITE;
-      active[s] = 0;
-    } else if (rr <= tol * tol * S.bb) {
-      active[s] = 0;
-    } else if (S.iters >= maxiter) {
-      S.status = KMV_ENOTCONV;
-      active[s] = 0;
-    }
-    S.beta = rr / S.rr;
-    S.rr = rr;
+    if (!cg_rr_step(sys[s], sys_sum(L, b, c, chains, partial, 1, 0), tol, maxiter)) active[s] = 0;
   }
   __syncthreads();
   count_active(n_sys, active, n_active);

@@ -98,6 +98,16 @@ struct KmvArgs {
   // forward, tensor-core form: the operand tiles of (theta, x) prepared by the
   // previous product of the same solve may be reused (theta and x unchanged)
   int reuse_prep;
+  // forward, tensor-core one-column product inside a CG iteration: when cg_sys
+  // is set, the product first forms p = r + beta p in place (V is p, r is
+  // cg_r), and the CTA of each system that finishes its epilogue last takes
+  // the system's p.q step (alpha, or stopping it: cg_active, cg_n_active).
+  // cg_count holds one zeroed counter per system.
+  CgSys* cg_sys;
+  int32_t* cg_active;
+  int32_t* cg_n_active;
+  uint32_t* cg_count;
+  const float* cg_r;
 };
 
 // The argument rules of a point set and chain count shared by every entry
@@ -124,6 +134,12 @@ cudaError_t launch_cg_reduce_init(const DevLayout& L, int n_inst, int chains, co
                                   cudaStream_t st);
 cudaError_t launch_cg_reduce_pq(const DevLayout& L, int n_inst, int chains, const double* partial,
                                 CgSys* sys, int32_t* active, cudaStream_t st);
+// cg_update_xr followed, per system, by the r.r step of cg_reduce_rr in the CTA
+// that finishes last (count: one zeroed counter per system).
+cudaError_t launch_cg_update_xr_rr(const DevLayout& L, int n_items, int chains, int64_t n_total, CgSys* sys,
+                                   int32_t* active, float* x, float* r, const float* p, const float* q,
+                                   double* partial, uint32_t* count, double tol, int maxiter, int32_t* n_active,
+                                   cudaStream_t st);
 cudaError_t launch_cg_update_xr(const DevLayout& L, int n_items, int chains, int64_t n_total,
                                 const CgSys* sys, const int32_t* active, float* x, float* r,
                                 const float* p, const float* q, double* partial, cudaStream_t st);

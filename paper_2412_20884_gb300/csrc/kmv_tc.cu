@@ -34,6 +34,7 @@
 #include <cmath>
 #include <vector>
 
+#include "cg_common.cuh"
 #include "kmv_tc.cuh"
 #include "simt_common.cuh"
 #include "tc_common.cuh"
@@ -689,7 +690,8 @@ __global__ void __launch_bounds__(kFwdThreads, 1) tc_fwd_fma_kernel(TcFwdArgs a)
 
 // V tiles as FP32 columns for the FMA-pipe product: VF[c][t] = MZ x 128 floats.
 __global__ void tc_prep_vf_kernel(DevLayout L, TcTables T, int chains, int64_t n_total, const float* V, int m,
-                                  int mz, int T_total, const int32_t* sys_active, const float* amp, float* VF) {
+                                  int mz, int T_total, const int32_t* sys_active, const float* amp, float* VF,
+                                  const CgSys* cg_sys, const float* cg_r, float* cg_p) {
   const int t = blockIdx.x, c = blockIdx.y, r = threadIdx.x;
   const int b = T.tile_inst[t];
   const int s = b * chains + c;
@@ -700,6 +702,18 @@ __global__ void tc_prep_vf_kernel(DevLayout L, TcTables T, int chains, int64_t n
   const int64_t i = L.offsets[b] + rl;
   float* dst = VF + ((size_t)c * T_total + t) * (size_t)mz * 128;
   const float am = (valid && amp) ? amp[(int64_t)c * n_total + i] : 1.f;
+  if (cg_sys) {
+    // one column inside a CG iteration (V is p): p = r + beta p first, as the
+    // CG direction update does, then the tile of the new p
+    float pv = 0.f;
+    if (valid) {
+      const int64_t v = (int64_t)c * n_total + i;
+      pv = fmaf((float)cg_sys[s].beta, cg_p[v], cg_r[v]);
+      cg_p[v] = pv;
+    }
+    dst[r] = valid ? pv * am : 0.f;
+    return;
+  }
   for (int q = 0; q < mz; ++q) dst[q * 128 + r] = valid ? V[((int64_t)c * n_total + i) * m + q] * am : 0.f;
 }
 
@@ -945,7 +959,15 @@ __global__ void tc_fwd_epilogue_kernel(DevLayout L, TcTables T, KmvArgs a, int c
   }
   if (a.dot_partial) {
     const double tsum = block_sum(dot, red);
-    if (threadIdx.x == 0) a.dot_partial[(int64_t)item * a.chains + c] = tsum;
+    if (threadIdx.x == 0) {
+      a.dot_partial[(int64_t)item * a.chains + c] = tsum;
+      // inside a CG iteration: the system's last CTA takes its p.q step
+      if (a.cg_sys && last_block_of_system(a.cg_count, s, (uint32_t)(L.inst_item0[b + 1] - L.inst_item0[b])) &&
+          !cg_pq_step(a.cg_sys[s], sys_sum(L, b, c, a.chains, a.dot_partial, 1, 0))) {
+        a.cg_active[s] = 0;
+        atomicSub(a.cg_n_active, 1);
+      }
+    }
   }
 }
 
@@ -1194,6 +1216,9 @@ kmv_status tc_forward(kmv_handle h, const KmvArgs& a, cudaStream_t st) {
   // one or two columns (the CG / energy products) take the FMA-pipe P.v path,
   // where the tensor pipe has room for the three-way split of the exponent
   const bool fma_path = a.m <= 2 && x_width(a.d, kSplitBf3) <= kMaxKX;
+  // the CG-iteration hooks (p update, p.q step) live in the one-column FMA path
+  if (a.cg_sys && !(fma_path && a.m == 1 && a.dot_partial))
+    return tc_fail(h, KMV_EINVAL, "internal: fused CG step needs the one-column FMA-pipe product");
   const int nsplit = fma_path ? kSplitBf3 : kSplitBf2;
   const int KX = x_width(a.d, nsplit);
   if (KX > kMaxKX) return tc_fail(h, KMV_EUNSUPPORTED, "KMV_BF16_HILO supports d <= 35");
@@ -1258,9 +1283,9 @@ kmv_status tc_forward(kmv_handle h, const KmvArgs& a, cudaStream_t st) {
     const size_t smem = std::max(kMinSmem, fixed + stages * (A_TILE + V_TILE) + (2 * stages + 16) * 8);
     if (cudaMemsetAsync(vmax, 0, sizeof(uint32_t) * (size_t)n_sys * mz, st) != cudaSuccess)
       return tc_fail(h, KMV_ECUDA, "memset failed");
-    tc_prep_vf_kernel<<<dim3(S->T_total, L.chains), 128, 0, st>>>(h->dev, S->dev, L.chains, L.n_total, a.V, a.m,
-                                                                  mz, S->T_total, a.sys_active, a.amp,
-                                                                  reinterpret_cast<float*>(VT));
+    tc_prep_vf_kernel<<<dim3(S->T_total, L.chains), 128, 0, st>>>(
+        h->dev, S->dev, L.chains, L.n_total, a.V, a.m, mz, S->T_total, a.sys_active, a.amp,
+        reinterpret_cast<float*>(VT), a.cg_sys, a.cg_r, const_cast<float*>(a.V));
     TcFwdArgs fa;
     fa.items = S->d_items;
     fa.n_items = S->n_items;
