@@ -948,8 +948,9 @@ __global__ void tc_fwd_epilogue_kernel(DevLayout L, TcTables T, KmvArgs a, int c
       const double shift = a.col_shift ? (double)a.col_shift[(int64_t)s * a.col_shift_stride + col] : 0.0;
       const double vi = (double)a.V[idx];
       // the column scale is a power of two: multiplying by its reciprocal is
-      // exact, and avoids an FP64 divide per element
-      const double inv_sc = col_scale_inv(vmax[(int64_t)s * mz + q]);
+      // exact, and avoids an FP64 divide per element (no column maxima: the
+      // FMA-pipe product, whose probabilities and vectors are not scaled)
+      const double inv_sc = vmax ? col_scale_inv(vmax[(int64_t)s * mz + q]) : 1.0;
       double y = ai * acc * inv_sc + (a.no_diag ? 0.0 : (s2 + shift) * vi);
       if (bad) y = __longlong_as_double(0x7ff8000000000000ll);
       a.Y[idx] = (float)y;
@@ -1281,8 +1282,6 @@ kmv_status tc_forward(kmv_handle h, const KmvArgs& a, cudaStream_t st) {
     const size_t V_TILE = (size_t)mz * 512;
     const int stages = (int)std::max<size_t>(2, std::min<size_t>(max_stages, (kMaxSmem - fixed) / (A_TILE + V_TILE + 16)));
     const size_t smem = std::max(kMinSmem, fixed + stages * (A_TILE + V_TILE) + (2 * stages + 16) * 8);
-    if (cudaMemsetAsync(vmax, 0, sizeof(uint32_t) * (size_t)n_sys * mz, st) != cudaSuccess)
-      return tc_fail(h, KMV_ECUDA, "memset failed");
     tc_prep_vf_kernel<<<dim3(S->T_total, L.chains), 128, 0, st>>>(
         h->dev, S->dev, L.chains, L.n_total, a.V, a.m, mz, S->T_total, a.sys_active, a.amp,
         reinterpret_cast<float*>(VT), a.cg_sys, a.cg_r, const_cast<float*>(a.V));
@@ -1306,8 +1305,8 @@ kmv_status tc_forward(kmv_handle h, const KmvArgs& a, cudaStream_t st) {
       ProfScope prof(h, KMV_KERNEL_FORWARD, st);
       fwd_kernel(true, mz, tl.exp_split)<<<grid, kFwdThreads, smem, st>>>(fa);
     }
-    // vmax is zero: the epilogue's column scale is 1
-    tc_launch_epilogue(h, S, a, 0, mz, part, vmax, err, st);
+    // no column maxima: the epilogue's column scale is 1
+    tc_launch_epilogue(h, S, a, 0, mz, part, nullptr, err, st);
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return tc_fail(h, KMV_ECUDA, cudaGetErrorString(e));
     return KMV_OK;
