@@ -250,7 +250,8 @@ def main():
     ap.add_argument("--suite", default=None, choices=["c3c4", "cheb", "precond", "implicit", "adjoint"],
                     help="instead of the headline line: time the C3 products and the C4 leapfrog batch (c3c4), "
                          "the Chebyshev-amplitude kernel family of Sec. 4 (cheb), or the leapfrog step with "
-                         "the randomized Nystrom preconditioner (precond), or the implicit midpoint step (implicit)")
+                         "the randomized Nystrom preconditioner (precond), the implicit midpoint step (implicit), "
+                         "or the adjoint kernel's time and BF16-vs-FP32 gradient agreement (adjoint)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -686,16 +687,17 @@ def c1_hmc(h, dev, w, pts, y):
 
 
 def run_suite_adjoint(args):
-    """Accuracy and time of the adjoint of the build as it stands (one GPU, one
-    JSON line): on the batching workload (256 instances, d = 4, 4 chains, m = 2)
-    the sampled-row gradients of 8 random instances against the FP64 oracle
-    (relative error per component, worst over the 32 systems) in both forms,
-    and the adjoint kernel's time per launch on the N = 65,536, d = 8, m = 16
-    workload (CUDA events).  Rebuilding with -DKMV_BWD_FOLD_HALVES=F sets how
-    many 64-column halves the tensor-core accumulator takes before each fold into the running sums."""
+    """Time and agreement of the adjoint as built (one GPU, one JSON line): the
+    adjoint kernel's time per launch on the N = 65,536, d = 8, m = 16 workload
+    (CUDA events), and, on the batching workload (256 instances, d = 4, 4
+    chains, m = 2) with G on 128 sampled rows of 8 instances, the worst relative
+    difference between the BF16 and the FP32 forms' gradients.  The errors of
+    each form against the FP64 oracle on the same systems are printed by
+    tests/test_gpu_configs.py (pytest -m gpu -s).  Rebuilding with
+    -DKMV_BWD_FOLD_HALVES=F sets how many 64-column halves the tensor-core
+    accumulator takes before each fold into the running sums."""
     import torch
     import workloads as wl
-    from oracle import se_kernel as sk
     from paper_2412_20884_gb300 import Kmv, Points
     from paper_2412_20884_gb300.binding import KMV_KERNEL_ADJOINT
     dev = torch.device("cuda", 0)
@@ -704,28 +706,23 @@ def run_suite_adjoint(args):
     rng = np.random.default_rng(7)
     chosen = np.sort(rng.choice(w.n_inst, 8, replace=False))
     Gs = np.zeros_like(w.G)
-    rows = {}
     for b in chosen:
         r0, r1 = w.offsets[b], w.offsets[b + 1]
-        rows[b] = np.sort(rng.choice(r1 - r0, 128, replace=False))
-        Gs[:, r0 + rows[b]] = w.G[:, r0 + rows[b]]
-    X = w.X.astype(np.float32).astype(np.float64)
+        rows = np.sort(rng.choice(r1 - r0, 128, replace=False))
+        Gs[:, r0 + rows] = w.G[:, r0 + rows]
     pts = Points(torch.tensor(w.X, dtype=torch.float32, device=dev), w.offsets, ard=True)
     th = torch.tensor(w.theta, dtype=torch.float64, device=dev)
     V = torch.tensor(w.V, dtype=torch.float32, device=dev)
     G = torch.tensor(Gs, dtype=torch.float32, device=dev)
     grads = {p: h.kmv_backward(pts, th, V, G, want_grad_V=False, prec=p)[0].cpu().numpy()
              for p in ("fp32", "bf16_hilo")}
-    errs = {p: [] for p in grads}
+    diffs = []
     for b in chosen:
-        r0, r1 = w.offsets[b], w.offsets[b + 1]
         for c in range(w.chains):
             s = b * w.chains + c
-            g_ref, _ = sk.kmv_adjoint(X[r0:r1], w.theta[s], w.V[c, r0:r1].astype(np.float32).astype(np.float64),
-                                      Gs[c, r0:r1].astype(np.float32).astype(np.float64), True, rows=rows[b])
-            floor = 1e-3 * np.abs(g_ref).max()
-            for p, g in grads.items():
-                errs[p].append(float(np.max(np.abs(g[s] - g_ref) / np.maximum(np.abs(g_ref), floor))))
+            g32, g16 = grads["fp32"][s], grads["bf16_hilo"][s]
+            floor = 1e-3 * np.abs(g32).max()
+            diffs.append(float(np.max(np.abs(g16 - g32) / np.maximum(np.abs(g32), floor))))
     w2 = wl.c2()
     pts2 = Points(torch.tensor(w2.X, dtype=torch.float32, device=dev), w2.offsets, ard=True)
     th2 = torch.tensor(w2.theta, dtype=torch.float64, device=dev)
@@ -740,12 +737,11 @@ def run_suite_adjoint(args):
     ms, nl = h.profile_read(KMV_KERNEL_ADJOINT)
     h.profile_enable(False)
     out = {"suite": "adjoint", "data": "synthetic",
-           "batching_sampled_rows": {p: {"worst_gradient_error": max(e), "median": float(np.median(e))}
-                                     for p, e in errs.items()},
+           "batching_sampled_rows_bf16_vs_fp32": {"worst_relative_difference": max(diffs),
+                                                  "median": float(np.median(diffs))},
            "adjoint_kernel_ms_n65536_d8_m16": ms / nl}
     print(json.dumps(out))
     h.close()
-    return 0
 
 
 def run_suite_implicit(args):
