@@ -1,6 +1,7 @@
-// Per-system CG steps shared by the CG kernels (kmv_cg.cu) and the tensor-core
-// product's epilogue when it carries the p.q step of a CG iteration
-// (kmv_tc.cu), so that both paths take the same arithmetic in the same order.
+// Per-system CG steps shared by the CG kernels (kmv_cg.cu) and the products'
+// epilogues when they carry the p.q step of a CG iteration (kmv_tc.cu,
+// kmv_simt_fwd.cu), so that every path takes the same arithmetic in the same
+// order.
 #pragma once
 
 #include "kmv_internal.cuh"

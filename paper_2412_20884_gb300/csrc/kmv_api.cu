@@ -248,6 +248,34 @@ kmv_status cheb_prepare(kmv_handle h, const kmv_points* pts, const double* theta
 
 // --- building blocks used by several entry points -------------------------------------
 
+// The FP32 forward, with its J range split over more CTAs when one CTA per
+// (item, chain, column chunk) would leave most SMs idle (forward_jsplit).
+kmv_status simt_forward(kmv_handle h, const KmvArgs& a, cudaStream_t st) {
+  const Layout& L = h->layout;
+  if (L.n_items == 0) return KMV_OK;
+  if (a.cg_sys && !(a.m == 1 && a.dot_partial))
+    return fail(h, KMV_EINVAL, "internal: fused CG step needs the one-column product");
+  const int js = forward_jsplit(L.n_items, L.chains, a.m, (int64_t)L.max_items_per_inst * kTile, h->num_sms);
+  if (js > 1) {
+    const size_t need = sizeof(double) * (size_t)js * L.chains * (size_t)L.n_total * a.m;
+    if (need > h->simt_part_bytes) {
+      if (h->capturing)
+        return fail(h, KMV_EINVAL, "FP32 forward scratch not prepared: make the same call once before capturing");
+      if (h->simt_part) cudaFree(h->simt_part);
+      h->simt_part = nullptr;
+      h->simt_part_bytes = 0;
+      if (cudaMalloc(&h->simt_part, need) != cudaSuccess) {
+        cudaGetLastError();
+        h->simt_part = nullptr;
+        return fail(h, KMV_ENOMEM, "FP32 forward scratch allocation failed");
+      }
+      h->simt_part_bytes = need;
+    }
+  }
+  KMV_CUDA(h, launch_forward_simt(a, L.n_items, js, h->simt_part, st));
+  return KMV_OK;
+}
+
 kmv_status run_forward(kmv_handle h, const KmvArgs& a, kmv_precision prec, cudaStream_t st) {
   if (h->layout.n_items == 0) return KMV_OK;
   if (prec == KMV_BF16_HILO) {
@@ -256,7 +284,7 @@ kmv_status run_forward(kmv_handle h, const KmvArgs& a, kmv_precision prec, cudaS
   }
   {
     ProfScope prof(h, KMV_KERNEL_FORWARD, st);
-    KMV_CUDA(h, launch_forward_simt(a, h->layout.n_items, st));
+    KMV_TRY(simt_forward(h, a, st));
   }
   return KMV_OK;
 }
@@ -414,12 +442,16 @@ kmv_status run_cg(kmv_handle h, const kmv_points* pts, const double* theta, cons
   a.Y = B.q;
   a.sys_active = B.active;
   a.dot_partial = B.partial;
-  // With the tensor-core one-column product (KMV_BF16_HILO where it takes the
-  // FMA-pipe form) an iteration needs no separate reduction or direction
-  // launches: the product forms p = r + beta p and its epilogue takes each
-  // system's p.q step, and the x, r update takes the r.r step, with the same
-  // per-system arithmetic in the same order as the separate kernels.
-  const bool fused = prec == KMV_BF16_HILO && x_width_fma_ok(pts->d) && L.n_items > 0;
+  // An iteration needs no separate reduction launches: the product's epilogue
+  // takes each system's p.q step in the CTA that finishes the system last, and
+  // the x, r update takes the r.r step likewise, with the same per-system
+  // arithmetic in the same order as the separate kernels.  With the
+  // tensor-core one-column product (KMV_BF16_HILO where it takes the FMA-pipe
+  // form) the product also forms p = r + beta p before its tiles; the FP32
+  // product reads p from every CTA, so there the direction update stays a
+  // kernel at the end of the iteration.
+  const bool tc_fma = prec == KMV_BF16_HILO && x_width_fma_ok(pts->d);
+  const bool fused = L.n_items > 0 && (tc_fma || prec == KMV_FP32);
   if (fused) {
     KMV_CUDA(h, cudaMemsetAsync(B.count, 0, sizeof(uint32_t) * 2 * n_sys, st));
     a.cg_sys = B.sys;
@@ -436,6 +468,8 @@ kmv_status run_cg(kmv_handle h, const kmv_points* pts, const double* theta, cons
     if (fused) {
       KMV_CUDA(h, launch_cg_update_xr_rr(h->dev, L.n_items, L.chains, L.n_total, B.sys, B.active, x, B.r, B.p,
                                          B.q, B.partial, B.count + n_sys, tol, maxiter, B.n_active, s));
+      if (!tc_fma)
+        KMV_CUDA(h, launch_cg_update_p(h->dev, L.n_items, L.chains, L.n_total, B.sys, B.active, B.r, B.p, s));
       return KMV_OK;
     }
     KMV_CUDA(h, launch_cg_reduce_pq(h->dev, L.n_inst, L.chains, B.partial, B.sys, B.active, s));
@@ -643,7 +677,7 @@ kmv_status run_cg_refined(kmv_handle h, const kmv_points* pts, const double* the
     // r = rhs - A x with the FP32 operator; active = ||r|| > tol ||rhs||
     a.V = x;
     a.Y = R.q32;
-    if (L.n_items > 0) KMV_CUDA(h, launch_forward_simt(a, L.n_items, st));
+    KMV_TRY(simt_forward(h, a, st));
     if (L.n_items > 0)
       KMV_CUDA(h, launch_cg_init(h->dev, L.n_items, L.chains, L.n_total, rhs, rhs_stride, R.q32, x, R.r,
                                  R.pdummy, 1, R.partial2, st));
@@ -862,7 +896,7 @@ kmv_status run_mcg_refined(kmv_handle h, const kmv_points* pts, const double* th
     // r = b - (A + shift) x with the FP32 operator; per-column stopping test
     a.V = x;
     a.Y = R.q;
-    if (L.n_items > 0) KMV_CUDA(h, launch_forward_simt(a, L.n_items, st));
+    KMV_TRY(simt_forward(h, a, st));
     KMV_CUDA(h, launch_mcg_init(h->dev, L.n_items, L.chains, L.n_total, m, b, 0, R.q, 1, x, R.r, R.p, R.partial2,
                                 st));
     KMV_CUDA(h, launch_mcg_reduce_init(h->dev, L.n_inst, L.chains, m, R.partial2, tol, R.cols, R.sys_any,
@@ -994,9 +1028,11 @@ kmv_status kmv_create(kmv_handle* out, int device) {
   h->device = device;
   if (cudaSetDevice(device) != cudaSuccess ||
       cudaMallocHost(reinterpret_cast<void**>(&h->host_flag), 64) != cudaSuccess ||
-      cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
     cudaGetLastError();
     if (h->host_flag) cudaFreeHost(h->host_flag);
+    if (h->side) cudaStreamDestroy(h->side);
     delete h;
     return KMV_ECUDA;
   }
@@ -1012,6 +1048,7 @@ kmv_status kmv_destroy(kmv_handle h) {
   if (h->ws) cudaFree(h->ws);
   if (h->tables) cudaFree(h->tables);
   if (h->cheb_buf) cudaFree(h->cheb_buf);
+  if (h->simt_part) cudaFree(h->simt_part);
   if (h->host_flag) cudaFreeHost(h->host_flag);
   if (h->side) cudaStreamDestroy(h->side);
   kmv_profile_enable(h, 0);

@@ -17,6 +17,7 @@ constexpr int kTile = 128;
 constexpr int kMaxD = 64;
 // Columns of V handled by one SIMT pass (forward / backward).
 constexpr int kMaxMPFwd = 64;
+constexpr int kMaxJSplit = 16;   // J-range chunks of the FP32 forward at small sizes
 constexpr int kMaxMPBwd = 32;
 // exp(-r^2/2) = 2^(-h r^2) with h = log2(e)/2; points are pre-scaled by sqrt(h)/l.
 constexpr double kHalfLog2e = 0.72134752044448170368;
@@ -98,11 +99,11 @@ struct KmvArgs {
   // forward, tensor-core form: the operand tiles of (theta, x) prepared by the
   // previous product of the same solve may be reused (theta and x unchanged)
   int reuse_prep;
-  // forward, tensor-core one-column product inside a CG iteration: when cg_sys
-  // is set, the product first forms p = r + beta p in place (V is p, r is
-  // cg_r), and the CTA of each system that finishes its epilogue last takes
-  // the system's p.q step (alpha, or stopping it: cg_active, cg_n_active).
-  // cg_count holds one zeroed counter per system.
+  // forward, one-column product inside a CG iteration (cg_sys set): the CTA of
+  // each system that finishes its epilogue last takes the system's p.q step
+  // (alpha, or stopping it: cg_active, cg_n_active; cg_count holds one zeroed
+  // counter per system), and the tensor-core FMA-pipe product first forms
+  // p = r + beta p in place (V is p, r is cg_r).
   CgSys* cg_sys;
   int32_t* cg_active;
   int32_t* cg_n_active;
@@ -115,7 +116,14 @@ struct KmvArgs {
 const char* points_error(const kmv_points* pts, int32_t chains);
 
 // SIMT kernels (kmv_simt.cu)
-cudaError_t launch_forward_simt(const KmvArgs& a, int n_items, cudaStream_t st);
+// jsplit > 1 splits each system's J range into jsplit chunks of whole J
+// tiles, with per-chunk FP64 row sums in jpart (jsplit * chains * N_total * m
+// doubles) added in chunk order by a combine kernel.
+cudaError_t launch_forward_simt(const KmvArgs& a, int n_items, int jsplit, double* jpart, cudaStream_t st);
+// The J split for a grid of n_items * chains * column chunks CTAs: 1 from two
+// CTAs per SM up, else about two CTAs per SM with at least two J tiles (of
+// the largest instance, max_rows) per chunk, at most kMaxJSplit.
+int forward_jsplit(int n_items, int chains, int m, int64_t max_rows, int num_sms);
 cudaError_t launch_backward_simt(const KmvArgs& a, int n_items, cudaStream_t st);
 int backward_mp(int m);      // columns per backward pass
 int forward_mp(int m);
@@ -365,6 +373,11 @@ struct kmv_handle_s {
   bool capturing = false;
   // stream on which the bodies of conditional (WHILE) graph nodes are captured
   cudaStream_t side = nullptr;
+  // FP32 forward's J-range split (kmv_simt_fwd.cu): per-chunk FP64 row sums,
+  // grown on first use (not under capture); the device's SM count
+  double* simt_part = nullptr;
+  size_t simt_part_bytes = 0;
+  int num_sms = 0;
   // kernel timing (kmv_profile_enable): event pairs around the main product kernels
   bool prof = false;
   std::vector<cudaEvent_t> prof_pool;
