@@ -45,6 +45,10 @@
  *   - A handle is not thread-safe; use one handle per host thread.  Its
  *     workspace is reused by successive calls, so calls on different streams
  *     must be ordered by the caller.
+ *   - While `stream` is being captured into a CUDA graph no call allocates:
+ *     a call whose workspace (or scratch of the FP32 product, which small
+ *     point sets split over more CTAs) is not yet large enough returns
+ *     KMV_EINVAL.  Make the same call once before capturing.
  */
 #ifndef KMV_H
 #define KMV_H
