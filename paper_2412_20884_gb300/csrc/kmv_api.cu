@@ -253,7 +253,7 @@ kmv_status cheb_prepare(kmv_handle h, const kmv_points* pts, const double* theta
 kmv_status simt_forward(kmv_handle h, const KmvArgs& a, cudaStream_t st) {
   const Layout& L = h->layout;
   if (L.n_items == 0) return KMV_OK;
-  if (a.cg_sys && !(a.m == 1 && a.dot_partial))
+  if ((a.cg_sys || a.ms_sys) && !(a.m == 1 && a.dot_partial))
     return fail(h, KMV_EINVAL, "internal: fused CG step needs the one-column product");
   const int js = forward_jsplit(L.n_items, L.chains, a.m, (int64_t)L.max_items_per_inst * kTile, h->num_sms);
   if (js > 1) {
@@ -929,6 +929,7 @@ struct MscgBufs {
   MscgShift* sh;
   float* base;
   int32_t *sys_active, *n_active;
+  uint32_t* count;   // 2 n_sys counters of the fused iteration (alpha step, beta step)
 };
 
 void mscg_layout(const Layout& L, int m, Arena& ar, size_t off[10]) {
@@ -944,7 +945,7 @@ void mscg_layout(const Layout& L, int m, Arena& ar, size_t off[10]) {
   off[6] = ar.take(sizeof(MscgShift) * n_sys * m);
   off[7] = ar.take(sizeof(float) * n_sys);
   off[8] = ar.take(sizeof(int32_t) * n_sys);
-  off[9] = ar.take(sizeof(int32_t) * 4);
+  off[9] = ar.take(sizeof(int32_t) * 4 + sizeof(uint32_t) * 2 * n_sys);
 }
 
 MscgBufs mscg_bufs(kmv_handle h, const size_t off[10]) {
@@ -959,6 +960,7 @@ MscgBufs mscg_bufs(kmv_handle h, const size_t off[10]) {
   b.base = at<float>(h, off[7]);
   b.sys_active = at<int32_t>(h, off[8]);
   b.n_active = at<int32_t>(h, off[9]);
+  b.count = reinterpret_cast<uint32_t*>(b.n_active + 4);
   return b;
 }
 
@@ -983,6 +985,23 @@ kmv_status run_mscg(kmv_handle h, const kmv_points* pts, const double* theta, co
   a.Y = B.q;
   a.sys_active = B.sys_active;
   a.dot_partial = B.partial;
+  // As in run_cg: the alpha step in the product's epilogue and the beta step
+  // in the x, r update (last CTA per system), and with the tensor-core
+  // FMA-pipe product the direction updates in its tile preparation.
+  const int n_sys = L.n_inst * L.chains;
+  const bool tc_fma = prec == KMV_BF16_HILO && x_width_fma_ok(pts->d);
+  const bool fused = L.n_items > 0 && (tc_fma || prec == KMV_FP32);
+  if (fused) {
+    KMV_CUDA(h, cudaMemsetAsync(B.count, 0, sizeof(uint32_t) * 2 * n_sys, st));
+    a.ms_sys = B.sys;
+    a.ms_sh = B.sh;
+    a.ms_m = m;
+    a.ms_ps = B.ps;
+    a.cg_active = B.sys_active;
+    a.cg_n_active = B.n_active;
+    a.cg_count = B.count;
+    a.cg_r = B.r;
+  }
   const int check_every = 4;
   for (int it = 0; it < maxiter; ++it) {
     if (it % check_every == 0) {
@@ -991,6 +1010,15 @@ kmv_status run_mscg(kmv_handle h, const kmv_points* pts, const double* theta, co
       if (*h->host_flag == 0) break;
     }
     KMV_TRY(run_forward(h, a, prec, st));
+    if (fused) {
+      KMV_CUDA(h, launch_mscg_update_xr_beta(h->dev, L.n_items, L.chains, L.n_total, m, B.sys, B.sh, B.sys_active,
+                                             B.r, B.q, x, B.ps, B.partial, B.count + n_sys, tol, maxiter, B.n_active,
+                                             st));
+      if (!tc_fma)
+        KMV_CUDA(h, launch_mscg_update_p(h->dev, L.n_items, L.chains, L.n_total, m, B.sys, B.sh, B.sys_active, B.r,
+                                         B.p, B.ps, st));
+      continue;
+    }
     KMV_CUDA(h, launch_mscg_alpha(h->dev, L.n_inst, L.chains, m, B.partial, B.sys, B.sh, B.sys_active, st));
     KMV_CUDA(h, launch_mscg_update_xr(h->dev, L.n_items, L.chains, L.n_total, m, B.sys, B.sh, B.sys_active, B.r,
                                       B.q, x, B.ps, B.partial, st));

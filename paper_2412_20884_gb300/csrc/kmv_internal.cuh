@@ -109,6 +109,15 @@ struct KmvArgs {
   int32_t* cg_n_active;
   uint32_t* cg_count;
   const float* cg_r;
+  // the same inside a multi-shift CG iteration (ms_sys set; cg_active,
+  // cg_n_active, cg_count and cg_r as above): the last CTA takes the system's
+  // alpha step for its ms_m shifts, and the tensor-core FMA-pipe product first
+  // forms p = r + beta p and p_j = zeta_j r + beta_j p_j (ms_ps, (chains,
+  // N_total, ms_m)).
+  MscgSys* ms_sys;
+  MscgShift* ms_sh;
+  int ms_m;
+  float* ms_ps;
 };
 
 // The argument rules of a point set and chain count shared by every entry
@@ -278,6 +287,12 @@ cudaError_t launch_mscg_update_xr(const DevLayout& L, int n_items, int chains, i
 cudaError_t launch_mscg_beta(const DevLayout& L, int n_inst, int chains, int m, const double* partial, double tol,
                              int maxiter, MscgSys* sys, MscgShift* sh, int32_t* sys_active, int32_t* n_active,
                              cudaStream_t st);
+// mscg_update_xr followed, per system, by the beta step in the CTA that
+// finishes last (count: one zeroed counter per system; n_active decremented).
+cudaError_t launch_mscg_update_xr_beta(const DevLayout& L, int n_items, int chains, int64_t n_total, int m,
+                                       MscgSys* sys, MscgShift* sh, int32_t* sys_active, float* r, const float* q,
+                                       float* xs, const float* ps, double* partial, uint32_t* count, double tol,
+                                       int maxiter, int32_t* n_active, cudaStream_t st);
 cudaError_t launch_mscg_update_p(const DevLayout& L, int n_items, int chains, int64_t n_total, int m,
                                  const MscgSys* sys, const MscgShift* sh, const int32_t* sys_active, const float* r,
                                  float* p, float* ps, cudaStream_t st);

@@ -23,6 +23,7 @@
 // order.
 #include <algorithm>
 
+#include "cg_common.cuh"
 #include "kmv_internal.cuh"
 #include "simt_common.cuh"
 
@@ -75,6 +76,7 @@ __global__ void mscg_setup_kernel(DevLayout L, int n_inst, int chains, int m, co
   y.rr = bb;
   y.bb = bb;
   y.alpha = 0.0;
+  y.beta = 0.0;
   y.alpha_prev = 1.0;
   y.beta_prev = 0.0;
   y.iters = 0;
@@ -97,39 +99,7 @@ __global__ void mscg_alpha_kernel(DevLayout L, int n_inst, int chains, int m, co
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= n_inst * chains || !sys_active[s]) return;
   const int bi = s / chains, c = s - bi * chains;
-  MscgSys& y = sys[s];
-  const double pq = tile_sum(L, bi, c, chains, partial);
-  if (!(pq > 0.0) || !isfinite(pq)) {
-    // breakdown of the base recurrence: every shift still running fails
-    for (int j = 0; j < m; ++j) {
-      MscgShift& k = sh[(int64_t)s * m + j];
-      if (!k.active) continue;
-      k.active = 0;
-      k.status = isfinite(pq) ? KMV_ENOTCONV : KMV_ENONFINITE;
-    }
-    sys_active[s] = 0;
-    return;
-  }
-  const double alpha = y.rr / pq;
-  y.alpha = alpha;
-  for (int j = 0; j < m; ++j) {
-    MscgShift& k = sh[(int64_t)s * m + j];
-    if (!k.active) {
-      k.alpha_s = 0.0;
-      continue;
-    }
-    const double den = alpha * y.beta_prev * (k.zeta_prev - k.zeta) +
-                       k.zeta_prev * y.alpha_prev * (1.0 + k.sigma * alpha);
-    const double zn = k.zeta * k.zeta_prev * y.alpha_prev / den;
-    if (!isfinite(zn) || k.zeta == 0.0) {
-      k.active = 0;
-      k.status = KMV_ENONFINITE;
-      k.alpha_s = 0.0;
-      continue;
-    }
-    k.zeta_next = zn;
-    k.alpha_s = alpha * zn / k.zeta;
-  }
+  if (!mscg_alpha_step(sys[s], sh + (int64_t)s * m, m, tile_sum(L, bi, c, chains, partial))) sys_active[s] = 0;
 }
 
 // x_j += alpha_j p_j (active shifts), r -= alpha Bp; partials of the new r.r
@@ -171,39 +141,50 @@ __global__ void mscg_beta_kernel(DevLayout L, int n_inst, int chains, int m, con
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= n_inst * chains || !sys_active[s]) return;
   const int bi = s / chains, c = s - bi * chains;
-  MscgSys& y = sys[s];
-  const double rr = tile_sum(L, bi, c, chains, partial);
-  const double beta = rr / y.rr;
-  const double lim = tol * tol * y.bb;
-  y.iters += 1;
-  int any = 0;
-  for (int j = 0; j < m; ++j) {
-    MscgShift& k = sh[(int64_t)s * m + j];
-    if (!k.active) continue;
-    k.iters += 1;
-    const double ratio = k.zeta_next / k.zeta;
-    const double res2 = k.zeta_next * k.zeta_next * rr;
-    if (!isfinite(res2) || !isfinite(beta)) {
-      k.active = 0;
-      k.status = KMV_ENONFINITE;
-    } else if (res2 <= lim) {
-      k.active = 0;
-    } else if (k.iters >= maxiter) {
-      k.active = 0;
-      k.status = KMV_ENOTCONV;
-    } else {
-      k.beta_s = beta * ratio * ratio;
-      k.zeta_prev = k.zeta;
-      k.zeta = k.zeta_next;
-    }
-    any |= k.active;
-  }
-  y.rr = rr;
-  y.beta = beta;
-  y.alpha_prev = y.alpha;
-  y.beta_prev = beta;
+  const bool any = mscg_beta_step(sys[s], sh + (int64_t)s * m, m, tile_sum(L, bi, c, chains, partial), tol, maxiter);
   sys_active[s] = any;
   if (any) atomicAdd(n_active, 1);
+}
+
+// mscg_update_xr, then, in the CTA that finishes each system last, the
+// system's beta step (as mscg_beta_kernel); n_active is kept by decrements,
+// so the iteration needs no separate beta launch or counter reset.
+__global__ void mscg_update_xr_beta_kernel(DevLayout L, int chains, int64_t n_total, int m, MscgSys* sys,
+                                           MscgShift* sh, int32_t* sys_active, float* r, const float* q, float* xs,
+                                           const float* ps, double* partial, uint32_t* count, double tol,
+                                           int maxiter, int32_t* n_active) {
+  __shared__ double red[kTile / 32];
+  __shared__ float as[kMaxShifts];
+  __shared__ int on[kMaxShifts];
+  const int item = blockIdx.x, c = blockIdx.y;
+  const int bi = L.item_inst[item];
+  const int s = bi * chains + c;
+  if (!sys_active[s]) return;
+  if (threadIdx.x < m) {
+    const MscgShift& k = sh[(int64_t)s * m + threadIdx.x];
+    as[threadIdx.x] = (float)k.alpha_s;
+    on[threadIdx.x] = k.active;
+  }
+  __syncthreads();
+  const int64_t i = L.item_row0[item] + threadIdx.x;
+  double rr = 0.0;
+  if (i < L.offsets[bi + 1]) {
+    const int64_t v = (int64_t)c * n_total + i;
+    for (int j = 0; j < m; ++j)
+      if (on[j]) xs[v * m + j] = fmaf(as[j], ps[v * m + j], xs[v * m + j]);
+    const float rv = fmaf(-(float)sys[s].alpha, q[v], r[v]);
+    r[v] = rv;
+    rr = (double)rv * rv;
+  }
+  const double t = block_sum(rr, red);
+  if (threadIdx.x == 0) {
+    partial[(int64_t)item * chains + c] = t;
+    if (last_block_of_system(count, s, (uint32_t)(L.inst_item0[bi + 1] - L.inst_item0[bi])) &&
+        !mscg_beta_step(sys[s], sh + (int64_t)s * m, m, tile_sum(L, bi, c, chains, partial), tol, maxiter)) {
+      sys_active[s] = 0;
+      atomicSub(n_active, 1);
+    }
+  }
 }
 
 // p = r + beta p; p_j = zeta_j r + beta_j p_j (active shifts)
@@ -280,6 +261,17 @@ cudaError_t launch_mscg_beta(const DevLayout& L, int n_inst, int chains, int m, 
   const int n = n_inst * chains;
   mscg_beta_kernel<<<(n + 127) / 128, 128, 0, st>>>(L, n_inst, chains, m, partial, tol, maxiter, sys, sh,
                                                     sys_active, n_active);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mscg_update_xr_beta(const DevLayout& L, int n_items, int chains, int64_t n_total, int m,
+                                       MscgSys* sys, MscgShift* sh, int32_t* sys_active, float* r, const float* q,
+                                       float* xs, const float* ps, double* partial, uint32_t* count, double tol,
+                                       int maxiter, int32_t* n_active, cudaStream_t st) {
+  if (n_items == 0) return cudaSuccess;
+  mscg_update_xr_beta_kernel<<<dim3(n_items, chains), kTile, 0, st>>>(L, chains, n_total, m, sys, sh, sys_active, r,
+                                                                      q, xs, ps, partial, count, tol, maxiter,
+                                                                      n_active);
   return cudaGetLastError();
 }
 

@@ -49,13 +49,18 @@ __device__ __forceinline__ void fwd_simt_epilogue(const KmvArgs& a, int s, int i
     const double t = block_sum(dot, red);
     if (threadIdx.x == 0) {
       a.dot_partial[(int64_t)item * a.chains + c] = t;
-      // inside a CG iteration (one column): the system's last CTA takes its
-      // p.q step
+      // inside a (multi-shift) CG iteration (one column): the system's last
+      // CTA takes its p.q (alpha) step
       const int b = a.L.item_inst[item];
-      if (a.cg_sys && last_block_of_system(a.cg_count, s, (uint32_t)(a.L.inst_item0[b + 1] - a.L.inst_item0[b])) &&
-          !cg_pq_step(a.cg_sys[s], sys_sum(a.L, b, c, a.chains, a.dot_partial, 1, 0))) {
-        a.cg_active[s] = 0;
-        atomicSub(a.cg_n_active, 1);
+      if ((a.cg_sys || a.ms_sys) &&
+          last_block_of_system(a.cg_count, s, (uint32_t)(a.L.inst_item0[b + 1] - a.L.inst_item0[b]))) {
+        const double pq = sys_sum(a.L, b, c, a.chains, a.dot_partial, 1, 0);
+        const bool go = a.cg_sys ? cg_pq_step(a.cg_sys[s], pq)
+                                 : mscg_alpha_step(a.ms_sys[s], a.ms_sh + (int64_t)s * a.ms_m, a.ms_m, pq);
+        if (!go) {
+          a.cg_active[s] = 0;
+          atomicSub(a.cg_n_active, 1);
+        }
       }
     }
   }

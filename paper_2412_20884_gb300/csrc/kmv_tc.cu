@@ -691,7 +691,8 @@ __global__ void __launch_bounds__(kFwdThreads, 1) tc_fwd_fma_kernel(TcFwdArgs a)
 // V tiles as FP32 columns for the FMA-pipe product: VF[c][t] = MZ x 128 floats.
 __global__ void tc_prep_vf_kernel(DevLayout L, TcTables T, int chains, int64_t n_total, const float* V, int m,
                                   int mz, int T_total, const int32_t* sys_active, const float* amp, float* VF,
-                                  const CgSys* cg_sys, const float* cg_r, float* cg_p) {
+                                  const CgSys* cg_sys, const MscgSys* ms_sys, const MscgShift* ms_sh, int ms_m,
+                                  float* ms_ps, const float* cg_r, float* cg_p) {
   const int t = blockIdx.x, c = blockIdx.y, r = threadIdx.x;
   const int b = T.tile_inst[t];
   const int s = b * chains + c;
@@ -702,14 +703,21 @@ __global__ void tc_prep_vf_kernel(DevLayout L, TcTables T, int chains, int64_t n
   const int64_t i = L.offsets[b] + rl;
   float* dst = VF + ((size_t)c * T_total + t) * (size_t)mz * 128;
   const float am = (valid && amp) ? amp[(int64_t)c * n_total + i] : 1.f;
-  if (cg_sys) {
-    // one column inside a CG iteration (V is p): p = r + beta p first, as the
-    // CG direction update does, then the tile of the new p
+  if (cg_sys || ms_sys) {
+    // one column inside a (multi-shift) CG iteration (V is p): p = r + beta p
+    // first, as the direction update does, and the shifted directions
+    // p_j = zeta_j r + beta_j p_j of the active shifts; then the tile of p
     float pv = 0.f;
     if (valid) {
       const int64_t v = (int64_t)c * n_total + i;
-      pv = fmaf((float)cg_sys[s].beta, cg_p[v], cg_r[v]);
+      const float rv = cg_r[v];
+      pv = fmaf((float)(cg_sys ? cg_sys[s].beta : ms_sys[s].beta), cg_p[v], rv);
       cg_p[v] = pv;
+      if (ms_sys) {
+        const MscgShift* k = ms_sh + (int64_t)s * ms_m;
+        for (int j = 0; j < ms_m; ++j)
+          if (k[j].active) ms_ps[v * ms_m + j] = fmaf((float)k[j].beta_s, ms_ps[v * ms_m + j], (float)k[j].zeta * rv);
+      }
     }
     dst[r] = valid ? pv * am : 0.f;
     return;
@@ -962,11 +970,17 @@ __global__ void tc_fwd_epilogue_kernel(DevLayout L, TcTables T, KmvArgs a, int c
     const double tsum = block_sum(dot, red);
     if (threadIdx.x == 0) {
       a.dot_partial[(int64_t)item * a.chains + c] = tsum;
-      // inside a CG iteration: the system's last CTA takes its p.q step
-      if (a.cg_sys && last_block_of_system(a.cg_count, s, (uint32_t)(L.inst_item0[b + 1] - L.inst_item0[b])) &&
-          !cg_pq_step(a.cg_sys[s], sys_sum(L, b, c, a.chains, a.dot_partial, 1, 0))) {
-        a.cg_active[s] = 0;
-        atomicSub(a.cg_n_active, 1);
+      // inside a (multi-shift) CG iteration: the system's last CTA takes its
+      // p.q (alpha) step
+      if ((a.cg_sys || a.ms_sys) &&
+          last_block_of_system(a.cg_count, s, (uint32_t)(L.inst_item0[b + 1] - L.inst_item0[b]))) {
+        const double pq = sys_sum(L, b, c, a.chains, a.dot_partial, 1, 0);
+        const bool go = a.cg_sys ? cg_pq_step(a.cg_sys[s], pq)
+                                 : mscg_alpha_step(a.ms_sys[s], a.ms_sh + (int64_t)s * a.ms_m, a.ms_m, pq);
+        if (!go) {
+          a.cg_active[s] = 0;
+          atomicSub(a.cg_n_active, 1);
+        }
       }
     }
   }
@@ -1218,7 +1232,7 @@ kmv_status tc_forward(kmv_handle h, const KmvArgs& a, cudaStream_t st) {
   // where the tensor pipe has room for the three-way split of the exponent
   const bool fma_path = a.m <= 2 && x_width(a.d, kSplitBf3) <= kMaxKX;
   // the CG-iteration hooks (p update, p.q step) live in the one-column FMA path
-  if (a.cg_sys && !(fma_path && a.m == 1 && a.dot_partial))
+  if ((a.cg_sys || a.ms_sys) && !(fma_path && a.m == 1 && a.dot_partial))
     return tc_fail(h, KMV_EINVAL, "internal: fused CG step needs the one-column FMA-pipe product");
   const int nsplit = fma_path ? kSplitBf3 : kSplitBf2;
   const int KX = x_width(a.d, nsplit);
@@ -1284,7 +1298,8 @@ kmv_status tc_forward(kmv_handle h, const KmvArgs& a, cudaStream_t st) {
     const size_t smem = std::max(kMinSmem, fixed + stages * (A_TILE + V_TILE) + (2 * stages + 16) * 8);
     tc_prep_vf_kernel<<<dim3(S->T_total, L.chains), 128, 0, st>>>(
         h->dev, S->dev, L.chains, L.n_total, a.V, a.m, mz, S->T_total, a.sys_active, a.amp,
-        reinterpret_cast<float*>(VT), a.cg_sys, a.cg_r, const_cast<float*>(a.V));
+        reinterpret_cast<float*>(VT), a.cg_sys, a.ms_sys, a.ms_sh, a.ms_m, a.ms_ps, a.cg_r,
+        const_cast<float*>(a.V));
     TcFwdArgs fa;
     fa.items = S->d_items;
     fa.n_items = S->n_items;
