@@ -51,6 +51,11 @@ constexpr int kFold = 32;
 // tile 0 (and TMEM owner), warp 9 producer, warp 10 MMA issuer for I tile 1.
 constexpr int kFwdThreads = 352;
 constexpr int kIssue1Warp = 10;
+// FMA-pipe forward warp roles: warps 0-15 four exp warpgroups (I tile
+// (w >> 2) & 1, S columns 64 (w >> 3) .. + 63), warp 16 MMA issuer for I
+// tile 0 (and TMEM owner), warp 17 producer, warp 18 MMA issuer for I tile 1.
+constexpr int kFmaThreads = 608;
+constexpr int kFmaMmaWarp = 16, kFmaLoadWarp = 17, kFmaIssue1Warp = 18;
 
 // Issues S = A B^T (K = 16 nk) and O (+)= P VT^T (K = 128 from TMEM).
 __device__ __forceinline__ void issue_s(uint32_t d_tmem, uint64_t da, uint64_t db, int nk, uint32_t idesc) {
@@ -423,10 +428,13 @@ __global__ void __launch_bounds__(kFwdThreads, 1) tc_fwd_kernel(TcFwdArgs a) {
 // Forward for one or two columns (the CG product): S = XA XB^T on the tensor
 // core as above, but P.v on the FMA pipe with P kept in FP32 and v in FP32
 // (tile VF: MZ x 128 floats), so the tensor pipe only computes S and the
-// kernel is bound by the exps.  Warp roles as in tc_fwd_kernel; S is double
-// buffered in TMEM (512 columns), so the issuers run one tile ahead.
+// kernel is bound by the exps.  S is double buffered in TMEM (512 columns), so
+// the issuers run one tile ahead.  Each I tile's S is read by two exp
+// warpgroups, one per 64-column half, so that four warps per scheduler hide
+// the exp and FMA latencies; the second half's row sums reach the first
+// through shared memory at the end of each item and are added in that order.
 template <int MZ, int POLY>
-__global__ void __launch_bounds__(kFwdThreads, 1) tc_fwd_fma_kernel(TcFwdArgs a) {
+__global__ void __launch_bounds__(kFmaThreads, 1) tc_fwd_fma_kernel(TcFwdArgs a) {
   using namespace ptx;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = align1024(smem_raw);
@@ -436,20 +444,23 @@ __global__ void __launch_bounds__(kFwdThreads, 1) tc_fwd_fma_kernel(TcFwdArgs a)
   uint8_t* sB = sA + 4 * A_TILE;
   uint8_t* sV = sB + S * A_TILE;
   uint64_t* full = reinterpret_cast<uint64_t*>(sV + S * V_TILE);
-  uint64_t* empty = full + S;        // released by the 2 issuers (S read XB) and 8 exp warps (read VF)
+  uint64_t* empty = full + S;        // released by the 2 issuers (S read XB) and 16 exp warps (read VF)
   uint64_t* a_full = empty + S;
   uint64_t* a_empty = a_full + 2;
   uint64_t* s_full = a_empty + 2;   // [g][buffer]
   uint64_t* s_free = s_full + 4;    // [g][buffer]
   uint64_t* done = s_free + 4;
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(done + 2);
+  uint64_t* comb_full = done + 2;       // [g][item parity] second half's row sums written
+  uint64_t* comb_free = comb_full + 4;  // [g][item parity] ... and read by the first half
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(comb_free + 4);
   volatile int* abort = reinterpret_cast<volatile int*>(tslot + 1);
+  double* s_comb = reinterpret_cast<double*>(tslot + 2);  // [g][item parity][MZ][128 rows]
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
     for (int i = 0; i < S; ++i) {
       mbar_init(&full[i], 1);
-      mbar_init(&empty[i], 2 + 8);
+      mbar_init(&empty[i], 2 + 16);
     }
     for (int g = 0; g < 2; ++g) {
       mbar_init(&a_full[g], 1);
@@ -458,12 +469,14 @@ __global__ void __launch_bounds__(kFwdThreads, 1) tc_fwd_fma_kernel(TcFwdArgs a)
     }
     for (int q = 0; q < 4; ++q) {
       mbar_init(&s_full[q], 1);
-      mbar_init(&s_free[q], 128);
+      mbar_init(&s_free[q], 256);
+      mbar_init(&comb_full[q], 128);
+      mbar_init(&comb_free[q], 128);
     }
     *abort = 0;
     fence_barrier_init();
   }
-  if (warp == kMmaWarp) {
+  if (warp == kFmaMmaWarp) {
     tmem_alloc(tslot, 512);
     tmem_relinquish();
   }
@@ -472,7 +485,7 @@ __global__ void __launch_bounds__(kFwdThreads, 1) tc_fwd_fma_kernel(TcFwdArgs a)
   tc_fence_after();
   const uint32_t tbase = *tslot;
 
-  if (warp == kLoadWarp) {
+  if (warp == kFmaLoadWarp) {
     const bool leader = elect_one();
     {
       int it = 0;
@@ -517,10 +530,10 @@ __global__ void __launch_bounds__(kFwdThreads, 1) tc_fwd_fma_kernel(TcFwdArgs a)
         }
       }
     }
-  } else if (warp == kMmaWarp || warp == kIssue1Warp) {
+  } else if (warp == kFmaMmaWarp || warp == kFmaIssue1Warp) {
     const bool leader = elect_one();
     {
-      const int g = warp == kMmaWarp ? 0 : 1;
+      const int g = warp == kFmaMmaWarp ? 0 : 1;
       const uint32_t idS = idesc_f16(128, 128, 1, 1);
       const uint32_t sboX = a.KX * 16u;
       const int nkx = a.KX / 16;
@@ -566,11 +579,15 @@ __global__ void __launch_bounds__(kFwdThreads, 1) tc_fwd_fma_kernel(TcFwdArgs a)
     }
     __syncwarp();
   } else {
-    const int g = warp >> 2, w = warp & 3;
+    const int g = (warp >> 2) & 1, w = warp & 3, hf = warp >> 3;
     const int row = 32 * w + lane;
     const uint32_t tl = tbase + (static_cast<uint32_t>(32 * w) << 16);
-    uint32_t sph[2] = {0u, 0u}, stage = 0, fph = 0;
+    // barrier phases as bits (bit b: S buffer b; item parity b), kept in registers
+    uint32_t sph = 0, stage = 0, fph = 0;
+    // phases of comb_full (first half) or comb_free (second half)
+    uint32_t cph = 0;
     long long k = 0;
+    int it = 0;
     for (int t = blockIdx.x; t < a.n_items; t += gridDim.x) {
       const int4 item = a.items[t];
       if (a.sys_active && !a.sys_active[item.x]) continue;
@@ -585,21 +602,21 @@ __global__ void __launch_bounds__(kFwdThreads, 1) tc_fwd_fma_kernel(TcFwdArgs a)
       }
       for (int j = 0; j < item.w; ++j, ++k) {
         const int buf = (int)(k & 1);
-        const uint32_t s_col = 256 * buf + g * 128;
-        bool ok = mbar_wait(&s_full[2 * g + buf], sph[buf], abort, a.err, 16);
+        const uint32_t s_col = 256 * buf + g * 128 + 64 * hf;
+        bool ok = mbar_wait(&s_full[2 * g + buf], (sph >> buf) & 1u, abort, a.err, 16);
         // the VF tile of this stage is visible once its copy has completed
         ok = ok && mbar_wait(&full[stage], fph, abort, a.err, 17);
         if (!__all_sync(0xffffffffu, ok)) goto fma_exp_out;
-        sph[buf] ^= 1;
+        sph ^= 1u << buf;
         tc_fence_after();
-        const float4* vs = reinterpret_cast<const float4*>(sV + stage * V_TILE);
+        // this half's 64 columns of v: float4 16 hf .. 16 hf + 15 of each column's 32
+        const float4* vs = reinterpret_cast<const float4*>(sV + stage * V_TILE) + 16 * hf;
         {
-          uint32_t a0[32], a1[32], b0[32], b1[32];
+          // 32 columns at a time (registers are 96 a thread at 608 threads; the
+          // other warps of the scheduler cover the second load)
+          uint32_t a0[32];
           tmem_ld32(tl + s_col, a0);
-          tmem_ld32(tl + s_col + 32, a1);
-          tmem_ld_wait_regs(a0, a1);
-          tmem_ld32(tl + s_col + 64, b0);
-          tmem_ld32(tl + s_col + 96, b1);
+          tmem_ld_wait_regs(a0);
 #pragma unroll
           for (int u = 0; u < 8; ++u) {
             const float p0 = exp2_mix<POLY, 5>(__uint_as_float(a0[4 * u]), 4 * u);
@@ -608,13 +625,19 @@ __global__ void __launch_bounds__(kFwdThreads, 1) tc_fwd_fma_kernel(TcFwdArgs a)
             const float p3 = exp2_mix<POLY, 5>(__uint_as_float(a0[4 * u + 3]), 4 * u + 3);
 #pragma unroll
             for (int q = 0; q < MZ; ++q) {
-              const float4 v = vs[q * 32 + 0 + u];
+              const float4 v = vs[q * 32 + u];
               acc[q][0] = fmaf(p0, v.x, acc[q][0]);
               acc[q][1] = fmaf(p1, v.y, acc[q][1]);
               acc[q][2] = fmaf(p2, v.z, acc[q][2]);
               acc[q][3] = fmaf(p3, v.w, acc[q][3]);
             }
           }
+          uint32_t a1[32];
+          tmem_ld32(tl + s_col + 32, a1);
+          tmem_ld_wait_regs(a1);
+          // this half of S(k) is in registers: once both halves are, the tensor core may overwrite it
+          tc_fence_before();
+          mbar_arrive(&s_free[2 * g + buf]);
 #pragma unroll
           for (int u = 0; u < 8; ++u) {
             const float p0 = exp2_mix<POLY, 5>(__uint_as_float(a1[4 * u]), 4 * u);
@@ -624,39 +647,6 @@ __global__ void __launch_bounds__(kFwdThreads, 1) tc_fwd_fma_kernel(TcFwdArgs a)
 #pragma unroll
             for (int q = 0; q < MZ; ++q) {
               const float4 v = vs[q * 32 + 8 + u];
-              acc[q][0] = fmaf(p0, v.x, acc[q][0]);
-              acc[q][1] = fmaf(p1, v.y, acc[q][1]);
-              acc[q][2] = fmaf(p2, v.z, acc[q][2]);
-              acc[q][3] = fmaf(p3, v.w, acc[q][3]);
-            }
-          }
-          tmem_ld_wait_regs(b0, b1);
-          tc_fence_before();
-          mbar_arrive(&s_free[2 * g + buf]);
-#pragma unroll
-          for (int u = 0; u < 8; ++u) {
-            const float p0 = exp2_mix<POLY, 5>(__uint_as_float(b0[4 * u]), 4 * u);
-            const float p1 = exp2_mix<POLY, 5>(__uint_as_float(b0[4 * u + 1]), 4 * u + 1);
-            const float p2 = exp2_mix<POLY, 5>(__uint_as_float(b0[4 * u + 2]), 4 * u + 2);
-            const float p3 = exp2_mix<POLY, 5>(__uint_as_float(b0[4 * u + 3]), 4 * u + 3);
-#pragma unroll
-            for (int q = 0; q < MZ; ++q) {
-              const float4 v = vs[q * 32 + 16 + u];
-              acc[q][0] = fmaf(p0, v.x, acc[q][0]);
-              acc[q][1] = fmaf(p1, v.y, acc[q][1]);
-              acc[q][2] = fmaf(p2, v.z, acc[q][2]);
-              acc[q][3] = fmaf(p3, v.w, acc[q][3]);
-            }
-          }
-#pragma unroll
-          for (int u = 0; u < 8; ++u) {
-            const float p0 = exp2_mix<POLY, 5>(__uint_as_float(b1[4 * u]), 4 * u);
-            const float p1 = exp2_mix<POLY, 5>(__uint_as_float(b1[4 * u + 1]), 4 * u + 1);
-            const float p2 = exp2_mix<POLY, 5>(__uint_as_float(b1[4 * u + 2]), 4 * u + 2);
-            const float p3 = exp2_mix<POLY, 5>(__uint_as_float(b1[4 * u + 3]), 4 * u + 3);
-#pragma unroll
-            for (int q = 0; q < MZ; ++q) {
-              const float4 v = vs[q * 32 + 24 + u];
               acc[q][0] = fmaf(p0, v.x, acc[q][0]);
               acc[q][1] = fmaf(p1, v.y, acc[q][1]);
               acc[q][2] = fmaf(p2, v.z, acc[q][2]);
@@ -675,9 +665,32 @@ __global__ void __launch_bounds__(kFwdThreads, 1) tc_fwd_fma_kernel(TcFwdArgs a)
           }
         }
       }
+      // the row sums of the two halves, first + second, through shared memory
+      // (a buffer per item parity; each wait bounded like the others)
+      const int par = it & 1;
+      double* cb = s_comb + (size_t)(2 * g + par) * MZ * 128;
+      if (hf == 1) {
+        if (it >= 2) {
+          // the buffer's previous contents (item it - 2) must have been read
+          const bool okf = mbar_wait(&comb_free[2 * g + par], (cph >> par) & 1u, abort, a.err, 18);
+          if (!__all_sync(0xffffffffu, okf)) goto fma_exp_out;
+          cph ^= 1u << par;
+        }
 #pragma unroll
-      for (int q = 0; q < MZ; ++q)
-        a.part[part_idx(t, a.mz, q, rowp)] = acc64[q] + (double)((acc[q][0] + acc[q][1]) + (acc[q][2] + acc[q][3]));
+        for (int q = 0; q < MZ; ++q)
+          cb[q * 128 + row] = acc64[q] + (double)((acc[q][0] + acc[q][1]) + (acc[q][2] + acc[q][3]));
+        mbar_arrive(&comb_full[2 * g + par]);
+      } else {
+        const bool okc = mbar_wait(&comb_full[2 * g + par], (cph >> par) & 1u, abort, a.err, 18);
+        if (!__all_sync(0xffffffffu, okc)) goto fma_exp_out;
+        cph ^= 1u << par;
+#pragma unroll
+        for (int q = 0; q < MZ; ++q)
+          a.part[part_idx(t, a.mz, q, rowp)] =
+              (acc64[q] + (double)((acc[q][0] + acc[q][1]) + (acc[q][2] + acc[q][3]))) + cb[q * 128 + row];
+        mbar_arrive(&comb_free[2 * g + par]);
+      }
+      ++it;
     }
   fma_exp_out:;
   }
@@ -685,7 +698,7 @@ __global__ void __launch_bounds__(kFwdThreads, 1) tc_fwd_fma_kernel(TcFwdArgs a)
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  if (warp == kMmaWarp) tmem_dealloc(tbase, 512);
+  if (warp == kFmaMmaWarp) tmem_dealloc(tbase, 512);
 }
 
 // V tiles as FP32 columns for the FMA-pipe product: VF[c][t] = MZ x 128 floats.
@@ -1294,8 +1307,12 @@ kmv_status tc_forward(kmv_handle h, const KmvArgs& a, cudaStream_t st) {
     // one or two columns: P.v on the FMA pipe (FP32 P and v, no scaling)
     const int mz = a.m;
     const size_t V_TILE = (size_t)mz * 512;
-    const int stages = (int)std::max<size_t>(2, std::min<size_t>(max_stages, (kMaxSmem - fixed) / (A_TILE + V_TILE + 16)));
-    const size_t smem = std::max(kMinSmem, fixed + stages * (A_TILE + V_TILE) + (2 * stages + 16) * 8);
+    // barriers (2 per stage + 22), the TMEM slot and abort flag, and the two
+    // column halves' row-sum buffers (2 I tiles x 2 item parities x mz x 128 FP64)
+    const size_t tail = 24 * 8 + (size_t)4 * mz * 128 * 8;
+    const int stages =
+        (int)std::max<size_t>(2, std::min<size_t>(max_stages, (kMaxSmem - fixed - tail) / (A_TILE + V_TILE + 16)));
+    const size_t smem = std::max(kMinSmem, fixed + stages * (A_TILE + V_TILE + 16) + tail);
     tc_prep_vf_kernel<<<dim3(S->T_total, L.chains), 128, 0, st>>>(
         h->dev, S->dev, L.chains, L.n_total, a.V, a.m, mz, S->T_total, a.sys_active, a.amp,
         reinterpret_cast<float*>(VT), a.cg_sys, a.ms_sys, a.ms_sh, a.ms_m, a.ms_ps, a.cg_r,
@@ -1318,7 +1335,7 @@ kmv_status tc_forward(kmv_handle h, const KmvArgs& a, cudaStream_t st) {
     const int grid = std::min(S->n_items, S->num_sms);
     {
       ProfScope prof(h, KMV_KERNEL_FORWARD, st);
-      fwd_kernel(true, mz, tl.exp_split)<<<grid, kFwdThreads, smem, st>>>(fa);
+      fwd_kernel(true, mz, tl.exp_split)<<<grid, kFmaThreads, smem, st>>>(fa);
     }
     // no column maxima: the epilogue's column scale is 1
     tc_launch_epilogue(h, S, a, 0, mz, part, nullptr, err, st);
