@@ -8,7 +8,7 @@ import pytest
 import torch
 
 import workloads as wl
-from helpers import to_dev
+from helpers import componentwise_err, f32, to_dev
 from test_gpu_kmv import _check_backward, _check_forward
 
 pytestmark = pytest.mark.gpu
@@ -87,3 +87,33 @@ def test_autotune_records_and_cache(kmv_handle, tmp_path):
         h2.close()
     with pytest.raises(Exception):
         h.autotune(pts, theta, 0)
+
+
+@pytest.mark.parametrize("m", [1, 2])
+def test_fma_product_with_many_items_per_cta(kmv_handle, m):
+    """The one- and two-column product (the CG iterations' kernel) with a
+    dense plan, about 30 work items per CTA: each I tile's two column-half
+    warpgroups then hand their row sums over through both parity buffers
+    many times.  Sampled rows against the FP64 oracle at the FP32 form's
+    1e-5 (componentwise, relative to the row sums of |K||V|)."""
+    from oracle import se_kernel as sk
+    h = kmv_handle
+    _, fma, _ = _kinds()
+    before = h.get_tiles(fma)
+    w = wl.ragged([12000, 5000], d=3, chains=2, m=m, ard=True, seed=330 + m)
+    pts, theta, V, _ = to_dev(w)
+    try:
+        h.set_tiles(fma, stages=0, items_per_sm=32, exp_split=0)
+        Y = h.kmv_forward(pts, theta, V, prec="bf16_hilo").cpu().numpy()
+    finally:
+        h.set_tiles(fma, **before)
+    X, Vh = f32(w.X), f32(w.V)
+    rng = np.random.default_rng(331)
+    for b in range(w.n_inst):
+        r0, r1 = w.offsets[b], w.offsets[b + 1]
+        rows = np.sort(rng.choice(r1 - r0, size=64, replace=False))
+        for c in range(w.chains):
+            s = b * w.chains + c
+            ref = sk.kmv(X[r0:r1], w.theta[s], Vh[c, r0:r1], True, rows=rows)
+            scale = sk.kmv(X[r0:r1], w.theta[s], np.abs(Vh[c, r0:r1]), True, rows=rows)
+            assert componentwise_err(Y[c, r0:r1][rows], ref, scale) <= 1e-5, (b, c)
