@@ -360,14 +360,19 @@ __global__ void __launch_bounds__(kFwdThreads, 1) tc_fwd_kernel(TcFwdArgs a) {
             tc_fence_after();
           }
           tmem_st32(tl + p_col, pk);
+          // the second half's exps in place; pk, the source of the store just
+          // issued, is rewritten only after tcgen05.wait::st
 #pragma unroll
-          for (int q = 0; q < 16; ++q)
-            pk[q] = pack_f16x2(exp2_mix<POLY, 3>(__uint_as_float(b0[2 * q]), 2 * q),
-                               exp2_mix<POLY, 3>(__uint_as_float(b0[2 * q + 1]), 2 * q + 1));
+          for (int e = 0; e < 32; ++e) {
+            b0[e] = __float_as_uint(exp2_mix<POLY, 3>(__uint_as_float(b0[e]), e));
+            b1[e] = __float_as_uint(exp2_mix<POLY, 3>(__uint_as_float(b1[e]), e));
+          }
+          tmem_st_wait();
 #pragma unroll
-          for (int q = 0; q < 16; ++q)
-            pk[16 + q] = pack_f16x2(exp2_mix<POLY, 3>(__uint_as_float(b1[2 * q]), 2 * q),
-                               exp2_mix<POLY, 3>(__uint_as_float(b1[2 * q + 1]), 2 * q + 1));
+          for (int q = 0; q < 16; ++q) {
+            pk[q] = pack_f16x2(__uint_as_float(b0[2 * q]), __uint_as_float(b0[2 * q + 1]));
+            pk[16 + q] = pack_f16x2(__uint_as_float(b1[2 * q]), __uint_as_float(b1[2 * q + 1]));
+          }
           tmem_st32(tl + p_col + 32, pk);
         }
         tmem_st_wait();

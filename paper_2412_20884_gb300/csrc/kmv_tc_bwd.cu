@@ -382,8 +382,9 @@ __global__ void __launch_bounds__(kTsThreads, 1) tc_bwd_ts_kernel(TcBwdArgs a) {
           const uint4 u1 = *reinterpret_cast<const uint4*>(src + (2 * q + 1) * 128);
           const uint32_t v[8] = {u0.x, u0.y, u0.z, u0.w, u1.x, u1.y, u1.z, u1.w};
           tmem_st8(tbase + lofs + kColXA + 8 * q, v);
+          // v's registers are the next store's source: reused only after the store completes
+          tmem_st_wait();
         }
-        tmem_st_wait();
         tc_fence_before();
         mbar_arrive(a_ready);
       }
