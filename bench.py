@@ -38,7 +38,7 @@ FMA_LANES = 128        # FP32 FMA lanes per SM per clock
 MUFU_EX2_LANES = 32    # ex2 per SM per clock on GB300 (measured by an ex2 issue-rate micro-benchmark, profiles/issue_rates_gb300.md)
 # dram__bytes_read.sum + dram__bytes_write.sum per launch of the main loop, from an
 # ncu capture of the same workload; absent once the kernel changes after that capture.
-DRAM_TRAFFIC = {("bf16_hilo", "fwd"): 10552576}   # 10,552,064 read + 512 written (profiles/tc_kernels_c2.md)
+DRAM_TRAFFIC = {("bf16_hilo", "fwd"): 10552064}   # 10,551,552 read + 512 written (profiles/tc_kernels_c2.md)
 
 
 def peaks():
